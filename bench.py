@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark of the streaming ST-HOSVD update on one GB300 (or N independent replicas).
+
+Workload: the advected-blob stream, 4-way slices 192 x 192 x 96 x 12 (x, y, z, variable), FP32,
+tau = 1e-4, initial ST-HOSVD on the first 10 slices, then one update (Alg. 5) per step. Every
+step assimilates a new 170 MB slice (larger than the 129 MB L2), all slices resident in HBM before
+the timed region. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision mixed|fp64]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "slices/s and GB/s ingested at ≤1e-5 rel. error vs FP64 oracle; % of roofline"
+GRID = (192, 192, 96)
+NVAR = 12
+NBLOBS = 40
+TAU = 1e-4
+N_INIT = 10
+PHASES = ["k_ttm_proj (mode 1)", "k_ttm_proj (modes 2..d-1)", "growth (gram/eig/append)",
+          "isvd (k_isvd_p/k_isvd_e/secular)", "factor (k_ud_update/k_core_m)", "k_cv_update (C and V)"]
+KERNEL_OF_PHASE = ["k_ttm_proj", "k_ttm_proj", "k_resid_gram", "k_isvd_e", "k_core_m", "k_cv_update"]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6780.7), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic_table():
+    """Per-launch DRAM bytes of the kernels, from the committed ncu summary (profiles/)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(updates: int, warmup: int = 0, slices=None):
+    """Time the FP64 oracle's stream_update on the full-size workload (host cores)."""
+    import numpy as np
+
+    import oracle as O
+    from workloads import BlobField
+
+    bf = BlobField(grid=GRID, nvar=NVAR, nblobs=NBLOBS, noise=1e-5, seed=2)
+    need = N_INIT + warmup + updates
+    if slices is None:
+        slices = [bf.slice_torch(t, "cuda").cpu().numpy().T.astype(np.float64) for t in range(need)]
+    X0 = np.asfortranarray(np.stack(slices[:N_INIT], axis=-1))
+    st = O.init_stream(X0, TAU)
+    del X0
+    for t in range(N_INIT, N_INIT + warmup):
+        O.stream_update(st, slices[t])
+    t0 = time.perf_counter()
+    for t in range(N_INIT + warmup, need):
+        O.stream_update(st, slices[t])
+    dt = time.perf_counter() - t0
+    return updates / dt, dt, st.ranks
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import torch
+
+    K = max(1, min(args.steps, 40))
+    W = min(args.warmup, 5)
+    rate, dt, ranks = cpu_oracle_rate(K, W)
+    cores = os.cpu_count()
+    line = {
+        "metric": METRIC, "value": rate, "unit": "slices/s", "n_gpus": args.gpus, "steps": K,
+        "warmup": W, "ms_per_step": 1e3 * dt / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "advected-blob stream 192x192x96x12 fp32 slices, tau=1e-4, n_init=10",
+                   "parallelism": "host cores (numpy)"},
+        "cpu_baseline": {"value": rate, "unit": "slices/s", "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 oracle: init on 10 slices, {W} warm-up + {K} timed updates"},
+        "e2e": {"value": rate, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "final_ranks": list(ranks),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2308_16395_gb300 as pkg
+    from workloads import BlobField
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    bf = BlobField(grid=GRID, nvar=NVAR, nblobs=NBLOBS, noise=1e-5, seed=2)
+    K, W = args.steps, args.warmup
+    T = N_INIT + W + K
+    dev = torch.device("cuda", local)
+    slices = [bf.slice_torch(t, dev) for t in range(T)]         # (12, 96, 192, 192) FP32 each
+    torch.cuda.synchronize()
+    slice_bytes = slices[0].numel() * slices[0].element_size()
+    caps = [0, 0, 0, 0, 256]
+    kw = dict(precision=args.precision, rank_cap=caps, steps_cap=T + 4, core_cap=4 << 20)
+
+    def fresh_state():
+        X0 = torch.stack(slices[:N_INIT]).contiguous()
+        ts = pkg.TuckerStream(X0, TAU, **kw)
+        del X0
+        for t in range(N_INIT, N_INIT + W):
+            ts.update(slices[t])
+        ts.ranks  # synchronizes, surfaces latched errors
+        return ts
+
+    # ---- device-resident timed region ----
+    ts = fresh_state()
+    stream = torch.cuda.current_stream()
+    pkg.tucker_profile_enable(ts.h, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for t in range(N_INIT + W, T):
+        ts.update(slices[t])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = pkg.tucker_profile_read(ts.h)
+    ranks = ts.ranks
+    eb, dn = ts.error_norm()
+    ts.close()
+    if dist:
+        t_ = torch.tensor([ms], device=dev)
+        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+        ms = float(t_.item())
+
+    # ---- end to end: host slices (pinned), H2D + update + D2H of the error norm per step ----
+    e2e = None
+    if not args.no_e2e:
+        host = [slices[t].cpu().pin_memory() for t in range(N_INIT + W, T)]
+        ts2 = fresh_state()
+        ybuf = torch.empty_like(slices[0])
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for hy in host:
+            ybuf.copy_(hy, non_blocking=True)
+            ts2.update(ybuf)
+            ts2.error_norm()          # device -> host read of the step's result (16 bytes)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = f0.elapsed_time(f1)
+        ts2.close()
+        if dist:
+            t_ = torch.tensor([ms2], device=dev)
+            dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+            ms2 = float(t_.item())
+        e2e = {"value": ws * K / (ms2 / 1e3), "unit": "slices/s", "h2d_bytes_per_step": slice_bytes,
+               "d2h_bytes_per_step": 16}
+        del host
+
+    # ---- roofline of the dominant phase (live CUDA events, library byte accounting) ----
+    peak, peak_src = _peaks()
+    ph = max(range(len(prof["ms"])), key=lambda i: prof["ms"][i])
+    achieved = prof["bytes"][ph] / (prof["ms"][ph] / 1e3) / 1e9 if prof["ms"][ph] > 0 else 0.0
+    traffic = _traffic_table().get(KERNEL_OF_PHASE[ph])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": PHASES[ph],
+                "peak_source": peak_src,
+                "phases_ms_per_step": {PHASES[i]: prof["ms"][i] / max(prof["updates"], 1)
+                                       for i in range(len(PHASES))},
+                "phases_gbs": {PHASES[i]: (prof["bytes"][i] / (prof["ms"][i] / 1e3) / 1e9
+                                           if prof["ms"][i] > 0 else 0.0) for i in range(len(PHASES))}}
+
+    value = ws * K / (ms / 1e3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": "advected-blob stream 192x192x96x12 fp32 slices (40 blobs), tau=1e-4, "
+                               f"n_init=10, timed updates t={N_INIT + W}..{T - 1}",
+                   "precision": args.precision, "parallelism": "replicas" if ws > 1 else "1 gpu",
+                   "l2": "inputs larger than L2: every step reads a new 170 MB slice"},
+        "gbs_ingested": value * slice_bytes / 1e9,
+        "final_ranks": list(ranks), "rel_error_bound": eb / dn,
+        "gpu_launches": int(prof["launches"]),
+        "roofline": roofline,
+        "clocks": ck,
+        "e2e": e2e,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        try:
+            rate, dt, _ = cpu_oracle_rate(args.cpu_updates)
+            out["cpu_baseline"] = {"value": rate, "unit": "slices/s", "cores": os.cpu_count(),
+                                   "kind": "oracle",
+                                   "sample": f"FP64 oracle: init on the first 10 slices (untimed), "
+                                             f"{args.cpu_updates} timed updates of the same workload"}
+        except Exception as e:  # report, do not fail the GPU line
+            out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-updates", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * tucker_stream.h -- C ABI of the GB300 streaming ST-HOSVD library.
+ *
+ * Method: De, Li, Kolla, Phipps, "Efficient Computation of Tucker Decomposition for Streaming
+ * Scientific Data Compression" (arXiv 2308.16395).
+ *
+ * Terms used below (paper notation):
+ *   d        number of tensor modes, the streaming (time) mode last (Sec. 2.4); d-1 spatial modes.
+ *   n_k      size of spatial mode k (fixed for the stream); a slice Y is n_1 x ... x n_{d-1}.
+ *   r_k      Tucker rank of mode k; r_d is the streaming-mode rank.
+ *   n_d      number of slices assimilated so far (rows of the streaming factor U_d).
+ *   tau      relative error tolerance; every call keeps ||X - X^||_F <= tau ||X||_F (Alg. 5).
+ *
+ * Layouts: every tensor crossing this ABI is dense and column-major (mode 1 fastest), the
+ * matricization convention of Sec. 2.1. A row-major array of shape (n_{d-1}, ..., n_1) has the
+ * same bytes. Factor matrices are column-major n_k x r_k.
+ *
+ * Pointers named *_dev are CUDA device pointers on the current device; pointers named *_host are
+ * host pointers. `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *
+ * Ownership: the caller owns every buffer it passes and must keep input buffers unchanged until
+ * the work enqueued on `stream` has completed; the library only reads inputs. The library owns
+ * the tucker_state and all device memory behind it (released by tucker_destroy).
+ *
+ * Errors: argument errors (NULL pointers, d outside 2..8, sizes, tau <= 0, capacities) are
+ * returned synchronously and leave the state unchanged. Conditions detected on the device
+ * (a rank or size capacity exceeded, a non-finite slice norm, an eigensolver that did not
+ * converge) are latched in the state and returned by the next call that synchronizes
+ * (tucker_error_norm, tucker_get_ranks, tucker_get_step_info, tucker_copy_*); after that the
+ * state accepts only tucker_destroy and the query calls. tucker_last_error gives a message.
+ *
+ * Threading: a state may be used from one host thread at a time. Calls on different states are
+ * independent.
+ */
+#ifndef TUCKER_STREAM_H
+#define TUCKER_STREAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TUCKER_MAX_MODES 8
+
+typedef struct tucker_state tucker_state; /* opaque, library-owned */
+
+typedef enum {
+  TUCKER_OK = 0,
+  TUCKER_EINVAL = 1,     /* bad argument */
+  TUCKER_ENOMEM = 2,     /* device allocation failed */
+  TUCKER_ECAPACITY = 3,  /* a rank, the spatial core size or n_d outgrew its capacity */
+  TUCKER_ENUMERIC = 4,   /* non-finite slice norm or eigensolver failure */
+  TUCKER_ETIMEOUT = 5,   /* a bounded device wait gave up */
+  TUCKER_ECUDA = 6,      /* a CUDA runtime call failed */
+  TUCKER_ESTATE = 7      /* state unusable after an earlier latched error */
+} tucker_status;
+
+/* Slice element types. */
+enum { TUCKER_F32 = 0, TUCKER_F64 = 1 };
+
+/* Arithmetic forms.
+ * TUCKER_PREC_FP64 : every step in FP64 (the plain method).
+ * TUCKER_PREC_MIXED: slice-sized contractions (TTM chain, residual Grams, core and V updates) on
+ *   FP32 data with FP32-accurate products; FP64 for norms and the error budget, eigen- and
+ *   secular solves, rank truncation, the factors U_1..U_d, S, and the re-orthogonalisation of
+ *   augmented factors. */
+enum { TUCKER_PREC_FP64 = 0, TUCKER_PREC_MIXED = 1 };
+
+typedef struct {
+  int32_t ndim;                         /* d, 2..8 (spatial modes + the streaming mode) */
+  int32_t dtype;                        /* TUCKER_F32 or TUCKER_F64: element type of slices */
+  int32_t precision;                    /* TUCKER_PREC_FP64 or TUCKER_PREC_MIXED */
+  int32_t reserved0;
+  int64_t n[TUCKER_MAX_MODES];          /* n_1..n_{d-1}; entries >= d-1 ignored */
+  int64_t rank_cap[TUCKER_MAX_MODES];   /* capacity of r_1..r_d (0 = default: n_k for spatial
+                                           modes, 256 for the streaming mode); r_d cap <= 512,
+                                           spatial caps <= n_k, n_k <= 512 */
+  int64_t steps_cap;                    /* capacity of n_d (rows of U_d) */
+  int64_t core_cap;                     /* capacity of r_1*...*r_{d-1} (0 = product of caps) */
+  double tau;                           /* relative tolerance tau > 0 (Sec. 2.3, Alg. 5) */
+  double eps_m;                         /* orthogonality threshold of Alg. 3 (0 = 1e-10) */
+} tucker_config;
+
+/* Per-update decisions of the last tucker_stream_update (Alg. 4, Alg. 3). */
+typedef struct {
+  double eps;                           /* eps = tau ||Y|| / sqrt(d) (Alg. 5) */
+  double y_norm2;                       /* ||Y||_F^2 */
+  double e_norm2[TUCKER_MAX_MODES];     /* ||E_k||_F^2 of each spatial mode (Alg. 4) */
+  int32_t grew[TUCKER_MAX_MODES];       /* 1 if ||E_k|| > eps (the factor was augmented) */
+  int32_t r_add[TUCKER_MAX_MODES];      /* r'_k added to mode k */
+  double q;                             /* ||e|| of the incremental SVD (Alg. 3) */
+  int32_t augmented;                    /* 1 if q > eps (a new streaming basis vector) */
+  int32_t r_stream;                     /* streaming rank after the update */
+  double discarded;                     /* squared error added by this update (Prop. 1, 2) */
+} tucker_step_info;
+
+/* Batch ST-HOSVD (Alg. 2) of the first n_init slices X_dev (n_1 x ... x n_{d-1} x n_init,
+ * column-major, element type cfg->dtype) with eps = tau ||X|| / sqrt(d), followed by the core
+ * factorization C = V x_d S of Assumption 1(c). Creates *out. Synchronizes `stream`.
+ * Errors: EINVAL (arguments, n_init < 1, X all zero), ENOMEM, ECAPACITY (a rank above its cap),
+ * ENUMERIC, ECUDA. */
+tucker_status tucker_init_sthosvd(const tucker_config* cfg, const void* X_dev, int64_t n_init,
+                                  void* stream, tucker_state** out);
+
+/* Streaming ST-HOSVD update (Alg. 5): assimilate one slice Y_dev (n_1 x ... x n_{d-1},
+ * column-major, cfg->dtype). Spatial modes are updated by Alg. 4 (projection, residual,
+ * residual Gram eigendecomposition, augmentation), the streaming mode by the incremental SVD
+ * of Alg. 3, then the core is updated. Enqueued on `stream` without host synchronization; every
+ * data-dependent branch is taken on the device. Errors: EINVAL, ESTATE (synchronous); device-side
+ * conditions are latched (see above). */
+tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* stream);
+
+/* Reconstruction X^(:, ..., t) = C x_1 U_1 ... x_{d-1} U_{d-1} x_d U_d(t, :) for slices
+ * t in [t_begin, t_end) (0-based) into out_dev (n_1 x ... x n_{d-1} x (t_end - t_begin),
+ * column-major, element type cfg->dtype). Enqueued on `stream`. Errors: EINVAL, ESTATE. */
+tucker_status tucker_reconstruct(tucker_state* s, int64_t t_begin, int64_t t_end,
+                                 void* out_dev, void* stream);
+
+/* Running error bound and data norm (Prop. 1, Prop. 2, App. D): *err_bound_host is the square
+ * root of the accumulated squared truncation error (initial ST-HOSVD + every update), an upper
+ * bound of ||X - X^||_F; *data_norm_host = ||X||_F over every slice seen. Synchronizes. */
+tucker_status tucker_error_norm(tucker_state* s, double* err_bound_host, double* data_norm_host);
+
+/* Current ranks r_1..r_d (d entries) and n_d. Synchronizes. */
+tucker_status tucker_get_ranks(tucker_state* s, int64_t* ranks_host, int64_t* n_d_host);
+
+/* Decisions of the most recent update. Synchronizes. */
+tucker_status tucker_get_step_info(tucker_state* s, tucker_step_info* info_host);
+
+/* Copy U_k (mode = 0..d-1, 0-based) as FP64 column-major (rows x r_k) into dst_dev, where rows
+ * is n_k for spatial modes and n_d for the streaming mode. Synchronizes. */
+tucker_status tucker_copy_factor(tucker_state* s, int32_t mode, double* dst_dev);
+
+/* Copy the core C (r_1 x ... x r_d, FP64, column-major) into dst_dev. Synchronizes. */
+tucker_status tucker_copy_core(tucker_state* s, double* dst_dev);
+
+/* Copy S (r_d values, FP64) and V (r_1 x ... x r_d, FP64, column-major; V_(d) row-orthonormal,
+ * C = V x_d S when the last residual was kept, Assumption 1(c)) into device buffers. Either
+ * pointer may be NULL. Synchronizes. */
+tucker_status tucker_copy_sv(tucker_state* s, double* S_dev, double* V_dev);
+
+/* Profiling (tracing) of the update phases. Phase indices: 0 mode-1 projection + residual norm
+ * (the pass over the slice), 1 projections of modes 2..d-1, 2 growth work (residual Gram, eigen-
+ * solve, augmentation, re-projection), 3 incremental-SVD passes and the secular SVD, 4 streaming
+ * factor update and M, 5 core and V updates. */
+#define TUCKER_NPHASES 6
+typedef struct {
+  double ms[TUCKER_NPHASES];     /* CUDA-event time per phase, summed over profiled updates */
+  double bytes[TUCKER_NPHASES];  /* algorithmic bytes per phase (operands read/written once per
+                                    pass, from the ranks in effect), summed */
+  int64_t launches;              /* kernels launched by profiled updates */
+  int64_t updates;               /* profiled updates */
+} tucker_profile;
+
+/* on = 1: the following updates record CUDA events around each phase on their stream (adds
+ * event records, no synchronization); on = 0: stop. Resets the accumulated profile. */
+tucker_status tucker_profile_enable(tucker_state* s, int32_t on);
+
+/* Accumulated profile since tucker_profile_enable. Synchronizes. */
+tucker_status tucker_profile_read(tucker_state* s, tucker_profile* out_host);
+
+/* Message for the last error on this state (static storage owned by the state; never NULL). */
+const char* tucker_last_error(const tucker_state* s);
+
+/* Release the state and its device memory. Synchronizes the device work of the state. */
+void tucker_destroy(tucker_state* s);
+
+/* Library version string. */
+const char* tucker_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUCKER_STREAM_H */

@@ -1,0 +1,301 @@
+"""Python binding of the GB300 streaming ST-HOSVD library (arXiv 2308.16395).
+
+Argument marshalling only: every function forwards to the C ABI declared in
+``include/tucker_stream.h`` (same names). Tensors are passed as device pointers; PyTorch supplies
+device memory and streams. Raises ``RuntimeError`` when the CUDA library is missing -- there is no
+CPU fallback.
+
+Layout: a column-major (mode-1 fastest) tensor n_1 x ... x n_m is a row-major torch tensor of
+shape (n_m, ..., n_1); :func:`paper_order` gives the view with the shape in paper order.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB as _LIB_PATH
+
+MAX_MODES = 8
+TUCKER_F32, TUCKER_F64 = 0, 1
+TUCKER_PREC_FP64, TUCKER_PREC_MIXED = 0, 1
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ENUMERIC", 5: "ETIMEOUT",
+          6: "ECUDA", 7: "ESTATE"}
+EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
+           "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info", "tucker_copy_factor",
+           "tucker_copy_core", "tucker_copy_sv", "tucker_last_error", "tucker_destroy",
+           "tucker_version", "tucker_profile_enable", "tucker_profile_read"]
+NPHASES = 6
+
+
+class TuckerConfig(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("dtype", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("n", ctypes.c_int64 * MAX_MODES),
+                ("rank_cap", ctypes.c_int64 * MAX_MODES), ("steps_cap", ctypes.c_int64),
+                ("core_cap", ctypes.c_int64), ("tau", ctypes.c_double), ("eps_m", ctypes.c_double)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("y_norm2", ctypes.c_double),
+                ("e_norm2", ctypes.c_double * MAX_MODES), ("grew", ctypes.c_int32 * MAX_MODES),
+                ("r_add", ctypes.c_int32 * MAX_MODES), ("q", ctypes.c_double),
+                ("augmented", ctypes.c_int32), ("r_stream", ctypes.c_int32),
+                ("discarded", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * NPHASES), ("bytes", ctypes.c_double * NPHASES),
+                ("launches", ctypes.c_int64), ("updates", ctypes.c_int64)]
+
+
+class TuckerError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libtucker_stream.so (built by ``paper_2308_16395_gb300.build``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library not built: {p} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.tucker_init_sthosvd.argtypes = [ctypes.POINTER(TuckerConfig), vp, i64, vp, ctypes.POINTER(vp)]
+    lib.tucker_stream_update.argtypes = [vp, vp, vp]
+    lib.tucker_reconstruct.argtypes = [vp, i64, i64, vp, vp]
+    lib.tucker_error_norm.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    lib.tucker_get_ranks.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.tucker_get_step_info.argtypes = [vp, ctypes.POINTER(StepInfo)]
+    lib.tucker_copy_factor.argtypes = [vp, i32, vp]
+    lib.tucker_copy_core.argtypes = [vp, vp]
+    lib.tucker_copy_sv.argtypes = [vp, vp, vp]
+    lib.tucker_last_error.argtypes = [vp]
+    lib.tucker_last_error.restype = ctypes.c_char_p
+    lib.tucker_destroy.argtypes = [vp]
+    lib.tucker_destroy.restype = None
+    lib.tucker_version.restype = ctypes.c_char_p
+    lib.tucker_profile_enable.argtypes = [vp, i32]
+    lib.tucker_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
+    for name in ("tucker_profile_enable", "tucker_profile_read", "tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
+                 "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
+                 "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv"):
+        getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(code: int, handle=None):
+    if code != 0:
+        msg = ""
+        if handle:
+            msg = load_library().tucker_last_error(handle).decode()
+        raise TuckerError(code, msg)
+
+
+def make_config(n, tau, *, dtype="f32", precision="mixed", rank_cap=None, steps_cap=0,
+                core_cap=0, eps_m=0.0) -> TuckerConfig:
+    """n: spatial sizes n_1..n_{d-1}; rank_cap: d entries (0 = default)."""
+    c = TuckerConfig()
+    c.ndim = len(n) + 1
+    c.dtype = TUCKER_F32 if dtype in ("f32", "float32") else TUCKER_F64
+    c.precision = TUCKER_PREC_MIXED if precision == "mixed" else TUCKER_PREC_FP64
+    for i, v in enumerate(n):
+        c.n[i] = int(v)
+    if rank_cap is not None:
+        for i, v in enumerate(rank_cap):
+            c.rank_cap[i] = int(v)
+    c.steps_cap = int(steps_cap)
+    c.core_cap = int(core_cap)
+    c.tau = float(tau)
+    c.eps_m = float(eps_m)
+    return c
+
+
+# --- C ABI, same names ------------------------------------------------------------------------
+
+def tucker_init_sthosvd(cfg: TuckerConfig, X_ptr: int, n_init: int, stream: int = 0) -> int:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.tucker_init_sthosvd(ctypes.byref(cfg), ctypes.c_void_p(X_ptr), int(n_init),
+                                   ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h.value
+
+
+def tucker_stream_update(h: int, Y_ptr: int, stream: int = 0) -> None:
+    _check(load_library().tucker_stream_update(h, ctypes.c_void_p(Y_ptr), ctypes.c_void_p(stream)), h)
+
+
+def tucker_reconstruct(h: int, t0: int, t1: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load_library().tucker_reconstruct(h, int(t0), int(t1), ctypes.c_void_p(out_ptr),
+                                             ctypes.c_void_p(stream)), h)
+
+
+def tucker_error_norm(h: int) -> tuple[float, float]:
+    e, n = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().tucker_error_norm(h, ctypes.byref(e), ctypes.byref(n)), h)
+    return e.value, n.value
+
+
+def tucker_get_ranks(h: int, d: int) -> tuple[tuple, int]:
+    arr = (ctypes.c_int64 * MAX_MODES)()
+    nd = ctypes.c_int64()
+    _check(load_library().tucker_get_ranks(h, arr, ctypes.byref(nd)), h)
+    return tuple(int(arr[i]) for i in range(d)), int(nd.value)
+
+
+def tucker_get_step_info(h: int, d: int) -> dict:
+    s = StepInfo()
+    _check(load_library().tucker_get_step_info(h, ctypes.byref(s)), h)
+    m = d - 1
+    return dict(eps=s.eps, y_norm2=s.y_norm2, e_norm2=[s.e_norm2[i] for i in range(m)],
+                grew=[bool(s.grew[i]) for i in range(m)], r_add=[s.r_add[i] for i in range(m)],
+                q=s.q, augmented=bool(s.augmented), r_stream=s.r_stream, discarded=s.discarded)
+
+
+def tucker_copy_factor(h: int, mode: int, dst_ptr: int) -> None:
+    _check(load_library().tucker_copy_factor(h, int(mode), ctypes.c_void_p(dst_ptr)), h)
+
+
+def tucker_copy_core(h: int, dst_ptr: int) -> None:
+    _check(load_library().tucker_copy_core(h, ctypes.c_void_p(dst_ptr)), h)
+
+
+def tucker_copy_sv(h: int, S_ptr: int, V_ptr: int) -> None:
+    _check(load_library().tucker_copy_sv(h, ctypes.c_void_p(S_ptr), ctypes.c_void_p(V_ptr)), h)
+
+
+def tucker_profile_enable(h: int, on: int = 1) -> None:
+    _check(load_library().tucker_profile_enable(h, int(on)), h)
+
+
+def tucker_profile_read(h: int) -> dict:
+    p = Profile()
+    _check(load_library().tucker_profile_read(h, ctypes.byref(p)), h)
+    return dict(ms=[p.ms[i] for i in range(NPHASES)], bytes=[p.bytes[i] for i in range(NPHASES)],
+                launches=int(p.launches), updates=int(p.updates))
+
+
+def tucker_last_error(h: int) -> str:
+    return load_library().tucker_last_error(h).decode()
+
+
+def tucker_destroy(h: int) -> None:
+    if h:
+        load_library().tucker_destroy(h)
+
+
+def tucker_version() -> str:
+    return load_library().tucker_version().decode()
+
+
+def paper_order(t):
+    """View of a row-major torch tensor as the column-major tensor in paper index order."""
+    return t.permute(*reversed(range(t.dim())))
+
+
+class TuckerStream:
+    """Streaming Tucker state on the current CUDA device (torch tensors in, torch tensors out).
+
+    ``X`` holds the first slices as a row-major tensor of shape (n_init, n_{d-1}, ..., n_1)
+    (i.e. column-major n_1 x ... x n_{d-1} x n_init). Every method calls the C ABI.
+    """
+
+    def __init__(self, X, tau, *, precision="mixed", rank_cap=None, steps_cap=0, core_cap=0,
+                 eps_m=0.0, stream=None):
+        import torch
+
+        if not X.is_cuda:
+            raise ValueError("X must be a CUDA tensor")
+        X = X.contiguous()
+        self.n = tuple(reversed(X.shape[1:]))
+        self.d = len(self.n) + 1
+        self.dtype = X.dtype
+        dt = "f32" if X.dtype == torch.float32 else "f64"
+        self.cfg = make_config(self.n, tau, dtype=dt, precision=precision, rank_cap=rank_cap,
+                               steps_cap=steps_cap, core_cap=core_cap, eps_m=eps_m)
+        self._stream = stream
+        self.h = tucker_init_sthosvd(self.cfg, X.data_ptr(), X.shape[0], self._sp())
+
+    def _sp(self) -> int:
+        import torch
+
+        s = self._stream if self._stream is not None else torch.cuda.current_stream()
+        return s.cuda_stream
+
+    def update(self, Y) -> None:
+        if tuple(reversed(Y.shape)) != self.n or Y.dtype != self.dtype or not Y.is_contiguous():
+            raise ValueError("slice shape/dtype/layout mismatch")
+        tucker_stream_update(self.h, Y.data_ptr(), self._sp())
+
+    @property
+    def ranks(self) -> tuple:
+        return tucker_get_ranks(self.h, self.d)[0]
+
+    @property
+    def n_d(self) -> int:
+        return tucker_get_ranks(self.h, self.d)[1]
+
+    def error_norm(self) -> tuple[float, float]:
+        return tucker_error_norm(self.h)
+
+    def step_info(self) -> dict:
+        return tucker_get_step_info(self.h, self.d)
+
+    def reconstruct(self, t0: int, t1: int):
+        import torch
+
+        out = torch.empty((t1 - t0,) + tuple(reversed(self.n)), dtype=self.dtype, device="cuda")
+        tucker_reconstruct(self.h, t0, t1, out.data_ptr(), self._sp())
+        return out
+
+    def factor(self, k: int):
+        """U_k as an FP64 (rows x r_k) tensor."""
+        import torch
+
+        ranks, nd = tucker_get_ranks(self.h, self.d)
+        rows = self.n[k] if k < self.d - 1 else nd
+        buf = torch.empty((ranks[k], rows), dtype=torch.float64, device="cuda")
+        tucker_copy_factor(self.h, k, buf.data_ptr())
+        return buf.t()
+
+    def core(self):
+        """C as an FP64 tensor in paper index order (r_1, ..., r_d)."""
+        import torch
+
+        ranks = self.ranks
+        buf = torch.empty(tuple(reversed(ranks)), dtype=torch.float64, device="cuda")
+        tucker_copy_core(self.h, buf.data_ptr())
+        return paper_order(buf)
+
+    def sv(self):
+        """(S, V) with V in paper index order."""
+        import torch
+
+        ranks = self.ranks
+        S = torch.empty((ranks[-1],), dtype=torch.float64, device="cuda")
+        V = torch.empty(tuple(reversed(ranks)), dtype=torch.float64, device="cuda")
+        tucker_copy_sv(self.h, S.data_ptr(), V.data_ptr())
+        return S, paper_order(V)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            tucker_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,738 @@
+// C ABI of the streaming ST-HOSVD library: state management and the host-side launch sequence
+// of the batch ST-HOSVD (Alg. 2) and of the streaming update (Alg. 5). The update itself is a
+// fixed sequence of kernel launches whose data-dependent branches are taken on the device, so
+// tucker_stream_update never waits for the device.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "../../include/tucker_stream.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace tk;
+
+namespace {
+
+constexpr int kGridP = 152 * 2;    // projection kernel grid (persistent-style, grid-stride)
+constexpr int kGridI = 152 * 4;    // ISVD row-pass grid
+constexpr int kGridCV = 152 * 4;   // core / V update grid
+constexpr int kGramBlocks = 600;   // target blocks of the residual-Gram kernel
+constexpr int kSecMax = TK_STREAM_CAP_MAX + 2;
+
+}  // namespace
+
+struct tucker_state {
+  tucker_config cfg{};
+  int d = 0;
+  int n[TK_MAXD]{};
+  int cap[TK_MAXD]{};
+  long long core_cap = 0;
+  int steps_cap = 0;
+  int ldc = 0;
+  int tw = 8;          // bytes of the work type
+  int tx = 8;          // bytes of the slice type
+  long long N = 0;     // elements per slice
+  int nmax = 0;        // largest eigenproblem
+  int mcap = 0;        // largest number of eigenvectors
+  // device state
+  Ctl* ctl = nullptr;
+  Ctl* hctl = nullptr;  // pinned mirror
+  void* dbuf[3]{};
+  long long dbuf_elems = 0;
+  void** d_dbufs = nullptr;
+  double* U[TK_MAXD]{};
+  void* Uw[TK_MAXD]{};
+  double* Ud[2]{};
+  double** d_udbufs = nullptr;
+  void* Cb[2]{};
+  void* Vb[2]{};
+  void** d_cbufs = nullptr;
+  void** d_vbufs = nullptr;
+  void* evec = nullptr;
+  double* S = nullptr;
+  double* Snew = nullptr;
+  double* part_e2 = nullptr;
+  double* part_y2 = nullptr;
+  double* gpart = nullptr;
+  double* G = nullptr;
+  void* eAw = nullptr;
+  void* eZ = nullptr;
+  void* eLD = nullptr;
+  double* eW = nullptr;
+  double* elam = nullptr;
+  double* part_p = nullptr;
+  double* part_e = nullptr;
+  double* pvec = nullptr;
+  double* esvec = nullptr;
+  SecWork sw{};
+  void* Bc = nullptr;
+  void* Bv = nullptr;
+  void* cu = nullptr;
+  void* wv = nullptr;
+  std::vector<void*> allocs;
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;       // event pool
+  std::vector<int> ev_phase;         // phase of each recorded (start, end) pair
+  size_t ev_used = 0;
+  long long prof_launches = 0, prof_updates = 0;
+  double bytes0[TK_NPH]{};
+  cudaStream_t last_stream = nullptr;
+  int latched = 0;
+  char err[512] = "ok";
+};
+
+namespace {
+
+const char* kVersion = "tucker_stream 0.1 (sm_103a)";
+
+void set_err(tucker_state* s, const char* fmt, const char* a = "", long long b = 0) {
+  if (!s) return;
+  snprintf(s->err, sizeof(s->err), fmt, a, b);
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      set_err(s, "CUDA error: %s (line %lld)", cudaGetErrorString(e_), (long long)__LINE__); \
+      return TUCKER_ECUDA;                                                                 \
+    }                                                                                      \
+  } while (0)
+
+cudaError_t dalloc(tucker_state* s, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) {
+    s->allocs.push_back(*p);
+    e = cudaMemset(*p, 0, bytes);
+  }
+  return e;
+}
+
+void free_all(tucker_state* s) {
+  for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+  s->ev.clear();
+  for (void* p : s->allocs) cudaFree(p);
+  s->allocs.clear();
+  if (s->hctl) cudaFreeHost(s->hctl);
+  s->hctl = nullptr;
+}
+
+tucker_status map_status(int st) {
+  switch (st) {
+    case 0: return TUCKER_OK;
+    case TK_ECAPACITY: return TUCKER_ECAPACITY;
+    case TK_ENUMERIC: return TUCKER_ENUMERIC;
+    case 5: return TUCKER_ETIMEOUT;
+    default: return TUCKER_ENUMERIC;
+  }
+}
+
+const char* status_msg(int st) {
+  switch (st) {
+    case TK_ECAPACITY: return "device: a rank, the spatial core size or n_d exceeded its capacity";
+    case TK_ENUMERIC: return "device: non-finite slice norm or numerical failure";
+    default: return "device: error";
+  }
+}
+
+// Read the control block (synchronizes the last stream used).
+tucker_status sync_ctl(tucker_state* s) {
+  tucker_state* ss = s;
+  {
+    tucker_state* s = ss;
+    CK(cudaMemcpyAsync(s->hctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->last_stream));
+    CK(cudaStreamSynchronize(s->last_stream));
+  }
+  if (s->hctl->status) {
+    s->latched = s->hctl->status;
+    snprintf(s->err, sizeof(s->err), "%s", status_msg(s->hctl->status));
+    return map_status(s->hctl->status);
+  }
+  return TUCKER_OK;
+}
+
+bool validate(const tucker_config* c, int64_t n_init, char* msg, size_t msz) {
+  if (!c) { snprintf(msg, msz, "config is NULL"); return false; }
+  if (c->ndim < 2 || c->ndim > TK_MAXD) { snprintf(msg, msz, "ndim must be in 2..8"); return false; }
+  if (c->dtype != TUCKER_F32 && c->dtype != TUCKER_F64) { snprintf(msg, msz, "bad dtype"); return false; }
+  if (c->precision != TUCKER_PREC_FP64 && c->precision != TUCKER_PREC_MIXED) {
+    snprintf(msg, msz, "bad precision"); return false;
+  }
+  if (!(c->tau > 0.0) || !std::isfinite(c->tau)) { snprintf(msg, msz, "tau must be > 0"); return false; }
+  if (n_init < 1 || n_init > TK_N_MAX) { snprintf(msg, msz, "n_init must be in 1..512"); return false; }
+  const int spatial_cap_max = (c->precision == TUCKER_PREC_FP64) ? 256 : 512;
+  for (int k = 0; k < c->ndim - 1; ++k) {
+    if (c->n[k] < 1 || c->n[k] > TK_N_MAX) { snprintf(msg, msz, "n_%d must be in 1..512", k + 1); return false; }
+    if (c->rank_cap[k] < 0 || c->rank_cap[k] > c->n[k]) {
+      snprintf(msg, msz, "rank_cap[%d] must be in 0..n_%d", k, k + 1); return false;
+    }
+    const long long cap = c->rank_cap[k] ? c->rank_cap[k] : c->n[k];
+    if (cap > spatial_cap_max) {
+      snprintf(msg, msz, "rank_cap[%d] = %lld above %d for this precision (set a smaller cap)", k, cap,
+               spatial_cap_max);
+      return false;
+    }
+  }
+  const long long scap = c->rank_cap[c->ndim - 1];
+  if (scap < 0 || scap > TK_STREAM_CAP_MAX) { snprintf(msg, msz, "streaming rank cap must be <= 512"); return false; }
+  if (c->steps_cap < 0 || (c->steps_cap > 0 && c->steps_cap < n_init)) {
+    snprintf(msg, msz, "steps_cap must be >= n_init"); return false;
+  }
+  if (c->core_cap < 0) { snprintf(msg, msz, "core_cap must be >= 0"); return false; }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// allocation
+// ---------------------------------------------------------------------------------------------
+tucker_status allocate(tucker_state* s, int64_t n_init) {
+  const tucker_config& c = s->cfg;
+  s->d = c.ndim;
+  const int d = s->d;
+  s->tw = (c.precision == TUCKER_PREC_MIXED) ? 4 : 8;
+  s->tx = (c.dtype == TUCKER_F32) ? 4 : 8;
+  s->N = 1;
+  for (int k = 0; k < d - 1; ++k) {
+    s->n[k] = (int)c.n[k];
+    s->cap[k] = (int)(c.rank_cap[k] ? c.rank_cap[k] : c.n[k]);
+    s->N *= s->n[k];
+  }
+  s->cap[d - 1] = (int)(c.rank_cap[d - 1] ? c.rank_cap[d - 1] : 256);
+  s->ldc = s->cap[d - 1];
+  s->steps_cap = (int)(c.steps_cap ? c.steps_cap : n_init + 1024);
+  long long pc = 1;
+  for (int k = 0; k < d - 1; ++k) pc *= s->cap[k];
+  s->core_cap = c.core_cap ? c.core_cap : std::min<long long>(pc, 1LL << 22);
+  s->nmax = (int)n_init;
+  s->mcap = s->cap[d - 1];
+  for (int k = 0; k < d - 1; ++k) {
+    s->nmax = std::max(s->nmax, s->n[k]);
+    s->mcap = std::max(s->mcap, s->cap[k]);
+  }
+  s->mcap = std::min(std::max(s->mcap, (int)n_init), TK_N_MAX);
+  const int tw = s->tw;
+  // D* buffers for one slice: max_k prod_{i<=k} cap_i prod_{i>k} n_i
+  long long maxD = s->N;
+  for (int k = 0; k < d - 1; ++k) {
+    long long sz = 1;
+    for (int i = 0; i < d - 1; ++i) sz *= (i <= k) ? s->cap[i] : s->n[i];
+    maxD = std::max(maxD, sz);
+  }
+  maxD = std::max(maxD, s->core_cap);
+  s->dbuf_elems = maxD;
+  CK(cudaMallocHost((void**)&s->hctl, sizeof(Ctl)));
+  memset(s->hctl, 0, sizeof(Ctl));
+  CK(dalloc(s, (void**)&s->ctl, sizeof(Ctl)));
+  for (int i = 0; i < 3; ++i) CK(dalloc(s, &s->dbuf[i], (size_t)maxD * tw));
+  CK(dalloc(s, (void**)&s->d_dbufs, sizeof(void*) * 3));
+  CK(cudaMemcpy(s->d_dbufs, s->dbuf, sizeof(void*) * 3, cudaMemcpyHostToDevice));
+  for (int k = 0; k < d - 1; ++k) {
+    CK(dalloc(s, (void**)&s->U[k], sizeof(double) * s->n[k] * s->cap[k]));
+    if (tw == 8) s->Uw[k] = s->U[k];
+    else CK(dalloc(s, &s->Uw[k], (size_t)tw * s->n[k] * s->cap[k]));
+  }
+  for (int i = 0; i < 2; ++i) {
+    CK(dalloc(s, (void**)&s->Ud[i], sizeof(double) * (size_t)s->steps_cap * s->ldc));
+    CK(dalloc(s, &s->Cb[i], (size_t)tw * s->core_cap * s->ldc));
+    CK(dalloc(s, &s->Vb[i], (size_t)tw * s->core_cap * s->ldc));
+  }
+  CK(dalloc(s, (void**)&s->d_udbufs, sizeof(void*) * 2));
+  CK(dalloc(s, (void**)&s->d_cbufs, sizeof(void*) * 2));
+  CK(dalloc(s, (void**)&s->d_vbufs, sizeof(void*) * 2));
+  CK(cudaMemcpy(s->d_udbufs, s->Ud, sizeof(void*) * 2, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_cbufs, s->Cb, sizeof(void*) * 2, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_vbufs, s->Vb, sizeof(void*) * 2, cudaMemcpyHostToDevice));
+  CK(dalloc(s, &s->evec, (size_t)tw * s->core_cap));
+  CK(dalloc(s, (void**)&s->S, sizeof(double) * kSecMax));
+  CK(dalloc(s, (void**)&s->Snew, sizeof(double) * kSecMax));
+  CK(dalloc(s, (void**)&s->part_e2, sizeof(double) * 4096));
+  CK(dalloc(s, (void**)&s->part_y2, sizeof(double) * 4096));
+  CK(dalloc(s, (void**)&s->gpart, sizeof(double) * (size_t)(kGramBlocks + 64) * 4096));
+  CK(dalloc(s, (void**)&s->G, sizeof(double) * (size_t)s->nmax * s->nmax));
+  CK(dalloc(s, &s->eAw, sizeof(double) * (size_t)s->nmax * s->nmax));
+  CK(dalloc(s, &s->eZ, sizeof(double) * (size_t)s->nmax * s->mcap));
+  CK(dalloc(s, &s->eLD, sizeof(double) * (size_t)s->mcap * 2 * s->nmax));
+  CK(dalloc(s, (void**)&s->eW, sizeof(double) * (size_t)s->nmax * s->mcap));
+  CK(dalloc(s, (void**)&s->elam, sizeof(double) * (size_t)TK_N_MAX));
+  CK(dalloc(s, (void**)&s->part_p, sizeof(double) * (size_t)kGridI * TK_STREAM_CAP_MAX));
+  CK(dalloc(s, (void**)&s->part_e, sizeof(double) * (size_t)kGridI * (TK_STREAM_CAP_MAX + 2)));
+  CK(dalloc(s, (void**)&s->pvec, sizeof(double) * kSecMax));
+  CK(dalloc(s, (void**)&s->esvec, sizeof(double) * kSecMax));
+  SecWork& w = s->sw;
+  CK(dalloc(s, (void**)&w.delta, sizeof(double) * kSecMax));
+  CK(dalloc(s, (void**)&w.z, sizeof(double) * kSecMax));
+  CK(dalloc(s, (void**)&w.idx, sizeof(int) * kSecMax));
+  CK(dalloc(s, (void**)&w.tau, sizeof(double) * kSecMax));
+  CK(dalloc(s, (void**)&w.org, sizeof(int) * kSecMax));
+  CK(dalloc(s, (void**)&w.lam, sizeof(double) * kSecMax));
+  CK(dalloc(s, (void**)&w.lsrc, sizeof(int) * kSecMax));
+  CK(dalloc(s, (void**)&w.rot, sizeof(double) * 4 * kSecMax));
+  CK(dalloc(s, (void**)&w.nrot, sizeof(int) * 4));
+  CK(dalloc(s, (void**)&w.V2, sizeof(double) * (size_t)kSecMax * kSecMax));
+  CK(dalloc(s, (void**)&w.U2, sizeof(double) * (size_t)kSecMax * kSecMax));
+  CK(dalloc(s, (void**)&w.sv, sizeof(double) * kSecMax));
+  CK(dalloc(s, (void**)&w.pq, sizeof(double) * kSecMax));
+  CK(dalloc(s, (void**)&w.meta, sizeof(int) * 8));
+  CK(dalloc(s, &s->Bc, (size_t)tw * kSecMax * s->ldc));
+  CK(dalloc(s, &s->Bv, (size_t)tw * kSecMax * s->ldc));
+  CK(dalloc(s, &s->cu, (size_t)tw * kSecMax));
+  CK(dalloc(s, &s->wv, (size_t)tw * kSecMax));
+  return TUCKER_OK;
+}
+
+// Phase markers: with profiling on, record an event pair around each phase on the stream.
+struct PhaseMark {
+  tucker_state* s;
+  cudaStream_t st;
+  int phase;
+  size_t idx;
+  PhaseMark(tucker_state* s_, cudaStream_t st_, int ph) : s(s_), st(st_), phase(ph), idx(0) {
+    if (!s->prof) return;
+    while (s->ev.size() < s->ev_used + 2) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      s->ev.push_back(e);
+    }
+    idx = s->ev_used;
+    s->ev_used += 2;
+    s->ev_phase.push_back(phase);
+    cudaEventRecord(s->ev[idx], st);
+  }
+  ~PhaseMark() {
+    if (s->prof) cudaEventRecord(s->ev[idx + 1], st);
+  }
+};
+
+int gram_pairs(int n) {
+  const int T = (n + 63) / 64;
+  return T * (T + 1) / 2;
+}
+int gram_chunks(int n) { return std::max(1, kGramBlocks / gram_pairs(n)); }
+
+// ---------------------------------------------------------------------------------------------
+// batch ST-HOSVD (Alg. 2) on the device
+// ---------------------------------------------------------------------------------------------
+template <typename TX, typename TW, typename TE>
+tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream_t st) {
+  const int d = s->d;
+  Ctl& h = *s->hctl;
+  memset(&h, 0, sizeof(Ctl));
+  h.d = d;
+  for (int k = 0; k < d - 1; ++k) { h.n[k] = s->n[k]; h.r[k] = s->n[k]; }
+  for (int k = 0; k < d; ++k) h.cap[k] = s->cap[k];
+  h.r[d - 1] = (int)n_init;
+  h.core_cap = s->core_cap;
+  h.steps_cap = s->steps_cap;
+  h.ldc = s->ldc;
+  h.tau = s->cfg.tau;
+  h.eps_m = s->cfg.eps_m > 0 ? s->cfg.eps_m : 1e-10;
+  h.xbuf = -1;
+  h.init_nt = (int)n_init;
+  h.tx = s->tx;
+  h.tw = s->tw;
+  h.N = s->N;
+  // ||X||^2 -> eps (Alg. 2, first step)
+  const long long NX = s->N * n_init;
+  CK(launch_norm2<TX>(X, NX, s->part_y2, 1024, st));
+  std::vector<double> parts(1024);
+  CK(cudaMemcpyAsync(parts.data(), s->part_y2, sizeof(double) * 1024, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double x2 = 0.0;
+  for (double v : parts) x2 += v;
+  if (!std::isfinite(x2)) { set_err(s, "initial data is not finite"); return TUCKER_ENUMERIC; }
+  if (x2 == 0.0) { set_err(s, "initial data is all zero (Assumption 1(c) needs S > 0)"); return TUCKER_EINVAL; }
+  h.eps = s->cfg.tau * std::sqrt(x2) / std::sqrt((double)d);
+  h.data2 = x2;
+  h.y2 = x2;
+  CK(cudaMemcpyAsync(s->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  // temporary partial-core buffers (the initial slices are larger than one slice)
+  void* ib[3] = {nullptr, nullptr, nullptr};
+  void** d_ib = nullptr;
+  const size_t ibytes = (size_t)s->tw * (size_t)NX;
+  auto cleanup = [&]() {
+    for (int i = 0; i < 3; ++i) if (ib[i]) cudaFree(ib[i]);
+    if (d_ib) cudaFree(d_ib);
+  };
+  for (int i = 0; i < 3; ++i) {
+    if (cudaMalloc(&ib[i], ibytes) != cudaSuccess) { cleanup(); set_err(s, "out of device memory (initial ST-HOSVD buffers)"); return TUCKER_ENOMEM; }
+  }
+  if (cudaMalloc((void**)&d_ib, sizeof(void*) * 3) != cudaSuccess) { cleanup(); return TUCKER_ENOMEM; }
+  cudaMemcpy(d_ib, ib, sizeof(void*) * 3, cudaMemcpyHostToDevice);
+  double* Utmp = nullptr;
+  void* Uwtmp = nullptr;
+  cudaMalloc((void**)&Utmp, sizeof(double) * n_init * s->cap[d - 1]);
+  cudaMalloc(&Uwtmp, (size_t)s->tw * n_init * s->cap[d - 1]);
+  auto cleanup2 = [&]() { cleanup(); cudaFree(Utmp); cudaFree(Uwtmp); };
+  tucker_status rc = TUCKER_OK;
+  for (int k = 0; k < d && rc == TUCKER_OK; ++k) {
+    const int nv = (k == d - 1) ? (int)n_init : s->n[k];
+    const int pairs = gram_pairs(nv), chunks = gram_chunks(nv);
+    cudaError_t e;
+    if (k == 0) e = launch_resid_gram<TX, double>(s->ctl, k, nv, X, d_ib, nullptr, 0, s->gpart, pairs, chunks, 1, st);
+    else e = launch_resid_gram<TW, double>(s->ctl, k, nv, X, d_ib, nullptr, 0, s->gpart, pairs, chunks, 1, st);
+    if (e == cudaSuccess) e = launch_gram_reduce(s->ctl, k, s->gpart, pairs, chunks, s->G, 1, st);
+    if (e == cudaSuccess) e = launch_eig<double>(s->ctl, k, 1, s->G, s->eAw, s->eZ, s->eLD, s->eW, s->elam, s->mcap, st);
+    double* Uk = (k == d - 1) ? Utmp : s->U[k];
+    void* Uwk = (k == d - 1) ? (s->tw == 8 ? (void*)Utmp : Uwtmp) : s->Uw[k];
+    if (e == cudaSuccess) e = launch_append<TW>(s->ctl, k, 1, s->eW, Uk, (s->tw == 8) ? nullptr : Uwk, nv, nv, st);
+    if (e != cudaSuccess) { set_err(s, "CUDA error: %s", cudaGetErrorString(e)); rc = TUCKER_ECUDA; break; }
+    s->last_stream = st;
+    rc = sync_ctl(s);
+    if (rc != TUCKER_OK) break;
+    const int rk = s->hctl->r[k];
+    if (k == d - 2) {
+      long long R = 1;
+      for (int i = 0; i < d - 1; ++i) R *= s->hctl->r[i];
+      if (R > s->core_cap) { set_err(s, "spatial core size %s%lld exceeds core_cap", "", R); rc = TUCKER_ECAPACITY; break; }
+    }
+    if (k == 0) e = launch_proj<TX, TW>(s->ctl, k, 1, 0, X, d_ib, Uwk, nv, rk, nullptr, nullptr, kGridP, st);
+    else e = launch_proj<TW, TW>(s->ctl, k, 1, 0, X, d_ib, Uwk, nv, rk, nullptr, nullptr, kGridP, st);
+    if (e == cudaSuccess) e = launch_mode_end(s->ctl, k, st);
+    if (e != cudaSuccess) { set_err(s, "CUDA error: %s", cudaGetErrorString(e)); rc = TUCKER_ECUDA; break; }
+  }
+  if (rc == TUCKER_OK) rc = sync_ctl(s);
+  if (rc == TUCKER_OK) {
+    Ctl& c = *s->hctl;
+    long long R = 1;
+    for (int i = 0; i < d - 1; ++i) R *= c.r[i];
+    const int rd = c.r[d - 1];
+    cudaError_t e = launch_init_finish<TW>(s->ctl, ib[c.xbuf], R, rd, s->elam, Utmp, (int)n_init, s->Cb[0], s->Vb[0],
+                                           s->Ud[0], s->S, s->ldc, st);
+    if (e != cudaSuccess) { set_err(s, "CUDA error: %s", cudaGetErrorString(e)); rc = TUCKER_ECUDA; }
+    if (rc == TUCKER_OK) {
+      double err2 = 0.0;
+      for (int k = 0; k < d; ++k) err2 += c.disc[k];
+      c.err2 = err2;
+      c.data2 = x2;
+      c.nd = (int)n_init;
+      c.init_nt = 0;
+      c.xbuf = -1;
+      c.cbuf = 0;
+      for (int k = 0; k < TK_MAXD; ++k) { c.grew[k] = 0; c.radd[k] = 0; c.disc[k] = 0.0; c.rold[k] = c.r[k]; }
+      if (cudaMemcpyAsync(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) { rc = TUCKER_ECUDA; set_err(s, "CUDA error after init"); }
+    }
+  }
+  cleanup2();
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// streaming update (Alg. 5): fixed launch sequence, device-side branches
+// ---------------------------------------------------------------------------------------------
+template <typename TX, typename TW, typename TE>
+tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
+  const int d = s->d;
+  long long launches = 0;
+  CK(launch_begin(s->ctl, st));
+  launches += 1;
+  for (int k = 0; k < d - 1; ++k) {
+    const int n = s->n[k];
+    const int pairs = gram_pairs(n), chunks = gram_chunks(n);
+    {
+      // pass A: P_k = D*_{k-1} x_k U_k^T, ||E_k||^2 (and ||Y||^2 for k = 0); Alg. 4's branch
+      PhaseMark pm(s, st, k == 0 ? TK_PH_PROJ1 : TK_PH_PROJN);
+      if (k == 0)
+        CK((launch_proj<TX, TW>(s->ctl, k, 1, 0, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], s->part_e2,
+                                s->part_y2, kGridP, st)));
+      else
+        CK((launch_proj<TW, TW>(s->ctl, k, 1, 0, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], s->part_e2,
+                                nullptr, kGridP, st)));
+      CK(launch_decide(s->ctl, k, s->part_e2, s->part_y2, kGridP, st));
+    }
+    {
+      // ||E_k|| > eps: residual Gram, eig + rank cut (Alg. 1), augmentation, then
+      // pass C: D*_k = D*_{k-1} x_k U~_k^T (= Concatenate(P_k, L_k), App. C)
+      PhaseMark pm(s, st, TK_PH_GROW);
+      if (k == 0)
+        CK((launch_resid_gram<TX, TW>(s->ctl, k, n, Y, s->d_dbufs, s->Uw[k], n, s->gpart, pairs,
+                                      chunks, 0, st)));
+      else
+        CK((launch_resid_gram<TW, TW>(s->ctl, k, n, Y, s->d_dbufs, s->Uw[k], n, s->gpart, pairs,
+                                      chunks, 0, st)));
+      CK(launch_gram_reduce(s->ctl, k, s->gpart, pairs, chunks, s->G, 0, st));
+      CK(launch_eig<TE>(s->ctl, k, 0, s->G, s->eAw, s->eZ, s->eLD, s->eW, nullptr, s->mcap, st));
+      CK(launch_append<TW>(s->ctl, k, 0, s->eW, s->U[k], (s->tw == 8) ? nullptr : s->Uw[k], n, n, st));
+      if (k == 0)
+        CK((launch_proj<TX, TW>(s->ctl, k, 2, 1, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], nullptr,
+                                nullptr, kGridP, st)));
+      else
+        CK((launch_proj<TW, TW>(s->ctl, k, 2, 1, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], nullptr,
+                                nullptr, kGridP, st)));
+      CK(launch_mode_end(s->ctl, k, st));
+    }
+    launches += 8;
+  }
+  {
+    // streaming mode: incremental SVD (Alg. 3)
+    PhaseMark pm(s, st, TK_PH_ISVD);
+    CK(launch_isvd<TW>(s->ctl, s->d_dbufs, s->d_vbufs, s->part_p, s->part_e, s->pvec, s->esvec,
+                       s->evec, s->S, s->sw, kGridI, st));
+    CK(launch_secular_vectors(s->ctl, s->S, s->sw, s->Snew, st));
+    launches += 7;
+  }
+  {
+    PhaseMark pm(s, st, TK_PH_FACT);
+    CK(launch_factor<TW>(s->ctl, s->d_udbufs, s->sw, s->esvec, s->Bc, s->cu, s->Bv, s->wv, s->ldc,
+                         152 * 2, st));
+    launches += 2;
+  }
+  {
+    // core update (Alg. 5, last step) and V~ = V' V''
+    PhaseMark pm(s, st, TK_PH_CV);
+    CK(launch_cv<TW>(s->ctl, s->d_dbufs, s->d_cbufs, s->d_vbufs, s->sw, s->Bc, s->cu, s->Bv, s->wv,
+                     s->ldc, s->evec, kGridCV, st));
+    launches += 2;
+  }
+  CK(launch_end(s->ctl, s->Snew, s->S, st));
+  launches += 1;
+  if (s->prof) {
+    s->prof_launches += launches;
+    s->prof_updates += 1;
+  }
+  return TUCKER_OK;
+}
+
+template <typename TW>
+tucker_status do_reconstruct(tucker_state* s, int64_t t0, int64_t t1, void* out, cudaStream_t st) {
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  const Ctl& c = *s->hctl;
+  const int d = s->d;
+  const long long T = t1 - t0;
+  long long R = 1;
+  for (int i = 0; i < d - 1; ++i) R *= c.r[i];
+  const int rd = c.r[d - 1];
+  const long long big = s->N * T;
+  void* tmp[2] = {nullptr, nullptr};
+  CK(cudaMallocAsync(&tmp[0], (size_t)s->tw * std::max(big, R * T), st));
+  CK(cudaMallocAsync(&tmp[1], (size_t)s->tw * std::max(big, R * T), st));
+  CK(launch_core_times_ud<TW>(s->Cb[c.cbuf], R, rd, s->ldc, s->Ud[c.cbuf], t0, T, tmp[0], st));
+  int cur = 0;
+  for (int k = 0; k < d - 1; ++k) {
+    long long A = 1, B = T;
+    for (int i = 0; i < k; ++i) A *= s->n[i];
+    for (int i = k + 1; i < d - 1; ++i) B *= c.r[i];
+    const bool last = (k == d - 2);
+    void* dst = last ? out : tmp[cur ^ 1];
+    cudaError_t e;
+    if (s->tw == 4) {
+      if (last && s->tx == 8) e = launch_expand<float, float, double>(tmp[cur], A, c.r[k], B, s->Uw[k], s->n[k], s->n[k], dst, st);
+      else e = launch_expand<float, float, float>(tmp[cur], A, c.r[k], B, s->Uw[k], s->n[k], s->n[k], dst, st);
+    } else {
+      if (last && s->tx == 4) e = launch_expand<double, double, float>(tmp[cur], A, c.r[k], B, s->U[k], s->n[k], s->n[k], dst, st);
+      else e = launch_expand<double, double, double>(tmp[cur], A, c.r[k], B, s->U[k], s->n[k], s->n[k], dst, st);
+    }
+    CK(e);
+    cur ^= 1;
+  }
+  CK(cudaFreeAsync(tmp[0], st));
+  CK(cudaFreeAsync(tmp[1], st));
+  return TUCKER_OK;
+}
+
+bool usable(tucker_state* s) { return s && !s->latched; }
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+const char* tucker_version(void) { return kVersion; }
+
+const char* tucker_last_error(const tucker_state* s) { return s ? s->err : "null state"; }
+
+tucker_status tucker_init_sthosvd(const tucker_config* cfg, const void* X_dev, int64_t n_init,
+                                  void* stream, tucker_state** out) {
+  if (!out) return TUCKER_EINVAL;
+  *out = nullptr;
+  char msg[256];
+  if (!validate(cfg, n_init, msg, sizeof(msg))) {
+    fprintf(stderr, "tucker_init_sthosvd: %s\n", msg);
+    return TUCKER_EINVAL;
+  }
+  if (!X_dev) return TUCKER_EINVAL;
+  tucker_state* s = new tucker_state();
+  s->cfg = *cfg;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  tucker_status rc = allocate(s, n_init);
+  if (rc != TUCKER_OK) {
+    if (rc == TUCKER_ECUDA) rc = TUCKER_ENOMEM;
+    fprintf(stderr, "tucker_init_sthosvd: %s\n", s->err);
+    free_all(s);
+    delete s;
+    return rc;
+  }
+  const bool mixed = cfg->precision == TUCKER_PREC_MIXED;
+  const bool f32 = cfg->dtype == TUCKER_F32;
+  if (mixed) rc = f32 ? do_init<float, float, float>(s, X_dev, n_init, st) : do_init<double, float, float>(s, X_dev, n_init, st);
+  else rc = f32 ? do_init<float, double, double>(s, X_dev, n_init, st) : do_init<double, double, double>(s, X_dev, n_init, st);
+  if (rc != TUCKER_OK) {
+    fprintf(stderr, "tucker_init_sthosvd: %s\n", s->err);
+    cudaDeviceSynchronize();
+    free_all(s);
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* stream) {
+  if (!s || !Y_dev) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  const bool mixed = s->cfg.precision == TUCKER_PREC_MIXED;
+  const bool f32 = s->cfg.dtype == TUCKER_F32;
+  if (mixed) return f32 ? do_update<float, float, float>(s, Y_dev, st) : do_update<double, float, float>(s, Y_dev, st);
+  return f32 ? do_update<float, double, double>(s, Y_dev, st) : do_update<double, double, double>(s, Y_dev, st);
+}
+
+tucker_status tucker_reconstruct(tucker_state* s, int64_t t_begin, int64_t t_end, void* out_dev,
+                                 void* stream) {
+  if (!s || !out_dev) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  s->last_stream = (cudaStream_t)stream;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  if (t_begin < 0 || t_end > s->hctl->nd || t_begin >= t_end) {
+    set_err(s, "slice range out of bounds%s (n_d = %lld)", "", s->hctl->nd);
+    return TUCKER_EINVAL;
+  }
+  if (s->tw == 4) return do_reconstruct<float>(s, t_begin, t_end, out_dev, (cudaStream_t)stream);
+  return do_reconstruct<double>(s, t_begin, t_end, out_dev, (cudaStream_t)stream);
+}
+
+tucker_status tucker_error_norm(tucker_state* s, double* err_bound, double* data_norm) {
+  if (!s || !err_bound || !data_norm) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  *err_bound = std::sqrt(std::max(s->hctl->err2, 0.0));
+  *data_norm = std::sqrt(std::max(s->hctl->data2, 0.0));
+  return TUCKER_OK;
+}
+
+tucker_status tucker_get_ranks(tucker_state* s, int64_t* ranks, int64_t* n_d) {
+  if (!s || !ranks) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  for (int k = 0; k < s->d; ++k) ranks[k] = s->hctl->r[k];
+  if (n_d) *n_d = s->hctl->nd;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_get_step_info(tucker_state* s, tucker_step_info* info) {
+  if (!s || !info) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  const Ctl& c = *s->hctl;
+  memset(info, 0, sizeof(*info));
+  info->eps = c.eps;
+  info->y_norm2 = c.y2;
+  double disc = 0.0;
+  for (int k = 0; k < s->d - 1; ++k) {
+    info->e_norm2[k] = c.e2[k];
+    info->grew[k] = c.grew[k];
+    info->r_add[k] = c.radd[k];
+    disc += c.disc[k];
+  }
+  info->q = c.q;
+  info->augmented = c.aug;
+  info->r_stream = c.r[s->d - 1];
+  info->discarded = disc + (c.aug ? 0.0 : c.q2) + c.dropped;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_copy_factor(tucker_state* s, int32_t mode, double* dst) {
+  if (!s || !dst || mode < 0 || mode >= s->d) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  const Ctl& c = *s->hctl;
+  if (mode < s->d - 1) {
+    CK(cudaMemcpyAsync(dst, s->U[mode], sizeof(double) * s->n[mode] * c.r[mode],
+                       cudaMemcpyDeviceToDevice, s->last_stream));
+  } else {
+    CK(launch_ud_to_colmajor(s->Ud[c.cbuf], c.nd, c.r[s->d - 1], s->ldc, dst, s->last_stream));
+  }
+  CK(cudaStreamSynchronize(s->last_stream));
+  return TUCKER_OK;
+}
+
+tucker_status tucker_copy_core(tucker_state* s, double* dst) {
+  if (!s || !dst) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  const Ctl& c = *s->hctl;
+  long long R = 1;
+  for (int i = 0; i < s->d - 1; ++i) R *= c.r[i];
+  if (s->tw == 4) CK(launch_state_to_colmajor<float>(s->Cb[c.cbuf], R, c.r[s->d - 1], s->ldc, dst, s->last_stream));
+  else CK(launch_state_to_colmajor<double>(s->Cb[c.cbuf], R, c.r[s->d - 1], s->ldc, dst, s->last_stream));
+  CK(cudaStreamSynchronize(s->last_stream));
+  return TUCKER_OK;
+}
+
+tucker_status tucker_copy_sv(tucker_state* s, double* S_dev, double* V_dev) {
+  if (!s) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  const Ctl& c = *s->hctl;
+  const int rd = c.r[s->d - 1];
+  if (S_dev) CK(cudaMemcpyAsync(S_dev, s->S, sizeof(double) * rd, cudaMemcpyDeviceToDevice, s->last_stream));
+  if (V_dev) {
+    long long R = 1;
+    for (int i = 0; i < s->d - 1; ++i) R *= c.r[i];
+    if (s->tw == 4) CK(launch_state_to_colmajor<float>(s->Vb[c.cbuf], R, rd, s->ldc, V_dev, s->last_stream));
+    else CK(launch_state_to_colmajor<double>(s->Vb[c.cbuf], R, rd, s->ldc, V_dev, s->last_stream));
+  }
+  CK(cudaStreamSynchronize(s->last_stream));
+  return TUCKER_OK;
+}
+
+tucker_status tucker_profile_enable(tucker_state* s, int32_t on) {
+  if (!s) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  s->prof = on != 0;
+  s->ev_used = 0;
+  s->ev_phase.clear();
+  s->prof_launches = 0;
+  s->prof_updates = 0;
+  for (int i = 0; i < TK_NPH; ++i) s->bytes0[i] = s->hctl->acc_bytes[i];
+  return TUCKER_OK;
+}
+
+tucker_status tucker_profile_read(tucker_state* s, tucker_profile* out) {
+  if (!s || !out) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  memset(out, 0, sizeof(*out));
+  for (size_t i = 0; i < s->ev_phase.size(); ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, s->ev[2 * i], s->ev[2 * i + 1]));
+    out->ms[s->ev_phase[i]] += ms;
+  }
+  for (int i = 0; i < TK_NPH; ++i) out->bytes[i] = s->hctl->acc_bytes[i] - s->bytes0[i];
+  out->launches = s->prof_launches;
+  out->updates = s->prof_updates;
+  return TUCKER_OK;
+}
+
+void tucker_destroy(tucker_state* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->last_stream);
+  free_all(s);
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Shared definitions of the streaming ST-HOSVD library (device control block, helpers).
+//
+// Design: every data-dependent decision of the streaming update (Alg. 4's ||E_k|| <= eps test,
+// the rank cut of Alg. 1, Alg. 3's q <= eps test and the resulting ranks) is taken on the
+// device and recorded in the control block `Ctl`, which every kernel reads. Kernels are launched
+// with grids sized from capacities and loop over the live extent read from `Ctl`, so one update
+// is a fixed sequence of launches with no host synchronization (and can be captured in a graph).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define TK_MAXD 8
+#define TK_STREAM_CAP_MAX 512   // streaming-rank capacity limit (secular solver sizing)
+#define TK_N_MAX 512            // spatial mode size limit (eigensolver sizing)
+
+// Latched device status codes (same values as tucker_status).
+#define TK_OK 0
+#define TK_ECAPACITY 3
+#define TK_ENUMERIC 4
+
+struct Ctl {
+  // ---- configuration (written at creation) ----
+  int d;                    // number of modes
+  int n[TK_MAXD];           // spatial mode sizes n_1..n_{d-1} (index 0..d-2)
+  int cap[TK_MAXD];         // rank capacities (index d-1 = streaming mode)
+  long long core_cap;       // capacity of prod_{k<d} r_k
+  int steps_cap;            // capacity of n_d
+  int ldc;                  // leading dimension (row stride) of C and V rows (= cap[d-1])
+  double tau;
+  double eps_m;
+  int tx, tw;               // bytes of the slice type and of the work type
+  long long N;              // elements of one slice
+  // ---- state ----
+  int r[TK_MAXD];           // current ranks
+  int nd;                   // n_d: rows of U_d
+  int cbuf;                 // which C/V/U_d ping-pong buffer holds the state
+  int status;               // latched error (0 = ok)
+  int xbuf;                 // D*-buffer holding the input of the current spatial mode (-1: slice)
+  int init_nt;              // > 0 only during the batch ST-HOSVD: number of initial slices
+  // ---- per-update record ----
+  int rold[TK_MAXD];        // ranks when the update started
+  double y2;                // ||Y||^2
+  double eps;               // tau ||Y|| / sqrt(d)
+  double e2[TK_MAXD];       // ||E_k||^2
+  int grew[TK_MAXD];        // ||E_k|| > eps
+  int radd[TK_MAXD];        // r'_k
+  double disc[TK_MAXD];     // discarded energy of mode k
+  double q2;                // ||e||^2 after re-orthogonalisation against V
+  double q;                 // ||e||
+  int aug;                  // q > eps
+  int rnew_d;               // streaming rank after the update
+  double dropped;           // energy removed by the numerical-rank cut of the compact SVD
+  // ---- accumulators (Prop. 1, Prop. 2, App. D) ----
+  double err2;              // running squared error bound
+  double data2;             // ||X||^2 of all data seen
+  long long nupdates;
+  // ---- algorithmic bytes per phase, accumulated by every update (see k_end_update) ----
+  double acc_bytes[8];
+};
+
+// Phases of one update (profiling and byte accounting).
+#define TK_PH_PROJ1 0    // mode-1 projection + residual norm (the pass over the slice)
+#define TK_PH_PROJN 1    // modes 2..d-1 projection + residual norm
+#define TK_PH_GROW 2     // residual Gram, eigensolve, augmentation, re-projection (when grown)
+#define TK_PH_ISVD 3     // p = V^T d, e = d - V p, secular SVD of S'
+#define TK_PH_FACT 4     // U~_d and M
+#define TK_PH_CV 5       // core and V updates
+#define TK_NPH 6
+
+// Mode-k view (A, n, B) of the operand of mode k: A = prod of current ranks of modes < k,
+// n = n_k (or the number of initial slices for the streaming mode during the batch ST-HOSVD),
+// B = prod of the spatial sizes of modes > k (times the initial slices during the batch ST-HOSVD).
+__device__ __forceinline__ int view_n(const Ctl* c, int k) {
+  return (k == c->d - 1) ? c->init_nt : c->n[k];
+}
+__device__ __forceinline__ long long view_A(const Ctl* c, int k) {
+  long long a = 1;
+  for (int i = 0; i < k; ++i) a *= c->r[i];
+  return a;
+}
+__device__ __forceinline__ long long view_B(const Ctl* c, int k) {
+  long long b = 1;
+  for (int i = k + 1; i < c->d - 1; ++i) b *= c->n[i];
+  if (k < c->d - 1 && c->init_nt > 0) b *= c->init_nt;
+  return b;
+}
+
+__host__ __device__ inline long long tk_prod(const int* v, int a, int b) {
+  long long p = 1;
+  for (int i = a; i < b; ++i) p *= v[i];
+  return p;
+}
+
+// ---------------------------------------------------------------------------------------------
+// warp / block reductions
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread receives the result. `sh` needs 32 slots.
+template <typename T>
+__device__ T block_sum(T v, T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T t = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Compensated (Neumaier) accumulation of squares in the element type, flushed into FP64.
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t = s + x;
+    if (fabsf(s) >= fabsf(x)) c += (s - t) + x; else c += (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { typedef KahanF type; };
+struct KahanD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct AccOf<double> { typedef KahanD type; };
+
+// Map a row index of a compact spatial tensor with dims `rn` (new) to the row index in the
+// compact layout with dims `ro` (old); returns -1 if the row is a zero-padded one (some i_k >=
+// ro[k]). Implements PadWithZeros (Eqs. pad_core_with_zeros, pad_singular_vectors_with_zeros).
+__device__ __forceinline__ long long tk_map_new_to_old(long long j, const int* rn, const int* ro,
+                                                       int m) {
+  long long jo = 0, stride = 1;
+  for (int k = 0; k < m; ++k) {
+    const int ik = (int)(j % rn[k]);
+    j /= rn[k];
+    if (ik >= ro[k]) return -1;
+    jo += ik * stride;
+    stride *= ro[k];
+  }
+  return jo;
+}

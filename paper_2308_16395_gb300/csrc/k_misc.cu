@@ -1,0 +1,117 @@
+// Layout conversions between the paper's column-major tensors and the device state layout, and
+// the streaming-mode contraction of the reconstruction.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tk {
+
+// After the batch ST-HOSVD: Ccol is the core as a column-major (R x r_d) array (C_(d)^T).
+// State: C[j*ldc + i] = C(j, i), V[j*ldc + i] = C(j, i) / S_i (V_(d) = S^-1 C_(d), Assumption
+// 1(c)), S_i = sqrt(lambda_i) of the streaming-mode Gram, U_d row-major from Utmp (nt x r_d,
+// column-major).
+template <typename TW>
+__global__ void k_init_finish(const TW* Ccol, long long R, int rd, const double* lam,
+                              const double* Utmp, int nt, TW* C, TW* V, double* Ud, double* S,
+                              int ldc) {
+  const long long total = R * rd;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
+       L += (long long)gridDim.x * blockDim.x) {
+    const long long j = L % R;
+    const int i = (int)(L / R);
+    const TW c = Ccol[L];
+    const double s = sqrt(fmax(lam[i], 0.0));
+    C[j * ldc + i] = c;
+    V[j * ldc + i] = (TW)((double)c / s);
+  }
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < rd; i += blockDim.x) S[i] = sqrt(fmax(lam[i], 0.0));
+    for (int L = threadIdx.x; L < nt * rd; L += blockDim.x) {
+      const int t = L % nt, c = L / nt;
+      Ud[(long long)t * ldc + c] = Utmp[L];
+    }
+  }
+}
+
+template <typename TW>
+cudaError_t launch_init_finish(Ctl* ctl, const void* Ccol, long long R, int rd, const double* lam,
+                               const double* Utmp, int nt, void* C, void* V, double* Ud, double* S,
+                               int ldc, cudaStream_t st) {
+  (void)ctl;
+  const long long total = R * rd;
+  int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+  if (grid < 1) grid = 1;
+  k_init_finish<TW><<<grid, 256, 0, st>>>((const TW*)Ccol, R, rd, lam, Utmp, nt, (TW*)C, (TW*)V,
+                                          Ud, S, ldc);
+  return cudaGetLastError();
+}
+
+// out(j, t) = sum_i C(j, i) U_d(t0 + t, i): the core contracted with rows of U_d, as a
+// column-major (R x T) array (the first step of X^ = C x_d U_d x_{d-1} ... x_1 U_1).
+template <typename TW>
+__global__ void k_core_times_ud(const TW* C, long long R, int rd, int ldc, const double* Ud,
+                                long long t0, long long T, TW* out) {
+  const long long total = R * T;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
+       L += (long long)gridDim.x * blockDim.x) {
+    const long long j = L % R, t = L / R;
+    const TW* row = C + j * ldc;
+    const double* u = Ud + (t0 + t) * ldc;
+    double s = 0.0;
+    for (int i = 0; i < rd; ++i) s += (double)row[i] * u[i];
+    out[L] = (TW)s;
+  }
+}
+
+template <typename TW>
+cudaError_t launch_core_times_ud(const void* C, long long R, int rd, int ldc, const double* Ud,
+                                 long long t0, long long T, void* out, cudaStream_t st) {
+  const long long total = R * T;
+  int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+  if (grid < 1) grid = 1;
+  k_core_times_ud<TW><<<grid, 256, 0, st>>>((const TW*)C, R, rd, ldc, Ud, t0, T, (TW*)out);
+  return cudaGetLastError();
+}
+
+// State rows (R x rd, ld = ldc, type TW) -> FP64 column-major (R x rd).
+template <typename TW>
+__global__ void k_state_to_col(const TW* Src, long long R, int rd, int ldc, double* dst) {
+  const long long total = R * rd;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
+       L += (long long)gridDim.x * blockDim.x) {
+    const long long j = L % R;
+    const int i = (int)(L / R);
+    dst[L] = (double)Src[j * ldc + i];
+  }
+}
+
+template <typename TW>
+cudaError_t launch_state_to_colmajor(const void* Src, long long R, int rd, int ldc, double* dst,
+                                     cudaStream_t st) {
+  const long long total = R * rd;
+  int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+  if (grid < 1) grid = 1;
+  k_state_to_col<TW><<<grid, 256, 0, st>>>((const TW*)Src, R, rd, ldc, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ud_to_colmajor(const double* Ud, int nd, int rd, int ldc, double* dst,
+                                  cudaStream_t st) {
+  return launch_state_to_colmajor<double>(Ud, nd, rd, ldc, dst, st);
+}
+
+template cudaError_t launch_init_finish<float>(Ctl*, const void*, long long, int, const double*,
+                                               const double*, int, void*, void*, double*, double*,
+                                               int, cudaStream_t);
+template cudaError_t launch_init_finish<double>(Ctl*, const void*, long long, int, const double*,
+                                                const double*, int, void*, void*, double*, double*,
+                                                int, cudaStream_t);
+template cudaError_t launch_core_times_ud<float>(const void*, long long, int, int, const double*,
+                                                 long long, long long, void*, cudaStream_t);
+template cudaError_t launch_core_times_ud<double>(const void*, long long, int, int, const double*,
+                                                  long long, long long, void*, cudaStream_t);
+template cudaError_t launch_state_to_colmajor<float>(const void*, long long, int, int, double*,
+                                                     cudaStream_t);
+template cudaError_t launch_state_to_colmajor<double>(const void*, long long, int, int, double*,
+                                                      cudaStream_t);
+
+}  // namespace tk

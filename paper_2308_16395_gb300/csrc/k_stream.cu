@@ -1,0 +1,696 @@
+// Streaming-mode kernels of the update (Alg. 3 inside Alg. 5) and the core update (Alg. 5, last
+// step).
+//
+// State layout (device): C and V are stored "row per spatial index": row j (the column-major
+// linear index of (i_1..i_{d-1}) over the current spatial ranks) holds the r_d streaming-mode
+// coefficients contiguously, row stride ldc = streaming-rank capacity. So C_(d) = C^T and the
+// matrix V of Alg. 3 (V = V_(d)^T) is exactly the stored R x r_d array. U_d is row-major
+// (steps_cap x ldc). Zero padding of C and V in spatial modes (Alg. 4, PadWithZeros) is never
+// materialised: kernels read old rows through the new->old index map (missing rows are zero).
+//
+//   k_isvd_p       p = V^T d                                    (Alg. 3, first step)
+//   k_isvd_e       e = d - V p, ||e||^2, s = V^T e              (Alg. 3, second step + one
+//                  classical Gram-Schmidt re-orthogonalisation of e against V, the QR of Alg. 3
+//                  specialised to orthonormal V)
+//   k_isvd_small   q, the q <= eps branch, the compact SVD of S' through the secular equation
+//                  of S'^T S' = diag(S^2[,0]) + z z^T (O(r^2) instead of O(r^3))
+//   k_ud_update    U~_d = [U_d U''(1:r,:); U''(r+1,:)]          (Alg. 3)
+//   k_core_m       M = U~_d(1:n_d,:)^T U_d                      (Alg. 5, last step)
+//   k_cv_update    C~ = C M^T + d u^T and V~ = V' V''           (Alg. 5 / Alg. 3)
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tk {
+
+// ---------------------------------------------------------------------------------------------
+// p = V_pad^T d over the old rows; partials per block (r doubles each).
+// ---------------------------------------------------------------------------------------------
+template <typename TW>
+__global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW* const* dbufs,
+                                               TW* const* vbufs, double* __restrict__ part) {
+  if (ctl->status) return;
+  const int d = ctl->d, m = d - 1;
+  const int r = ctl->r[d - 1];
+  const int ldc = ctl->ldc;
+  const TW* V = vbufs[ctl->cbuf];
+  const TW* dv = dbufs[ctl->xbuf];
+  long long Ro = 1;
+  for (int i = 0; i < m; ++i) Ro *= ctl->rold[i];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int CPL = TK_STREAM_CAP_MAX / 32;   // columns per lane
+  double acc[CPL];
+  TW accf[CPL];
+#pragma unroll
+  for (int i = 0; i < CPL; ++i) { acc[i] = 0.0; accf[i] = TW(0); }
+  const long long gw = (long long)blockIdx.x * 8 + wid;
+  const long long nw = (long long)gridDim.x * 8;
+  int cnt = 0;
+  for (long long jo = gw; jo < Ro; jo += nw) {
+    // old multi-index -> new linear index
+    long long t = jo, jn = 0, stride = 1;
+    for (int k = 0; k < m; ++k) {
+      const int ik = (int)(t % ctl->rold[k]);
+      t /= ctl->rold[k];
+      jn += ik * stride;
+      stride *= ctl->r[k];
+    }
+    const TW dj = dv[jn];
+    const TW* row = V + jo * ldc;
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) {
+      const int c = lane + 32 * i;
+      if (c < r) accf[i] += row[c] * dj;
+    }
+    if (++cnt == 32) {
+#pragma unroll
+      for (int i = 0; i < CPL; ++i) { acc[i] += (double)accf[i]; accf[i] = TW(0); }
+      cnt = 0;
+    }
+  }
+  __shared__ double sh[8][TK_STREAM_CAP_MAX];
+#pragma unroll
+  for (int i = 0; i < CPL; ++i) {
+    const int c = lane + 32 * i;
+    sh[wid][c] = acc[i] + (double)accf[i];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += sh[w][c];
+    part[(long long)blockIdx.x * TK_STREAM_CAP_MAX + c] = s;
+  }
+}
+
+// fixed-order reduction of per-block vectors of length len (<= TK_STREAM_CAP_MAX + 2)
+__global__ void k_reduce_vec(const Ctl* ctl, const double* part, int nparts, int stride, int len_extra,
+                             double* out) {
+  if (ctl->status) return;
+  const int len = ctl->r[ctl->d - 1] + len_extra;
+  for (int c = threadIdx.x; c < len; c += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[(long long)b * stride + c];
+    out[c] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// e = d - V_pad p over the new rows (stored), ||e||^2 and s = V_pad^T e; partials (r + 1).
+// ---------------------------------------------------------------------------------------------
+template <typename TW>
+__global__ void __launch_bounds__(256) k_isvd_e(const Ctl* __restrict__ ctl, TW* const* dbufs,
+                                               TW* const* vbufs, const double* __restrict__ p,
+                                               TW* __restrict__ evec, double* __restrict__ part) {
+  if (ctl->status) return;
+  const int d = ctl->d, m = d - 1;
+  const int r = ctl->r[d - 1];
+  const int ldc = ctl->ldc;
+  const TW* V = vbufs[ctl->cbuf];
+  const TW* dv = dbufs[ctl->xbuf];
+  long long Rn = 1;
+  for (int i = 0; i < m; ++i) Rn *= ctl->r[i];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int CPL = TK_STREAM_CAP_MAX / 32;
+  TW pl[CPL];
+#pragma unroll
+  for (int i = 0; i < CPL; ++i) {
+    const int c = lane + 32 * i;
+    pl[i] = (c < r) ? (TW)p[c] : TW(0);
+  }
+  double acc[CPL];
+  TW accf[CPL];
+#pragma unroll
+  for (int i = 0; i < CPL; ++i) { acc[i] = 0.0; accf[i] = TW(0); }
+  typename AccOf<TW>::type eacc;
+  const long long gw = (long long)blockIdx.x * 8 + wid;
+  const long long nw = (long long)gridDim.x * 8;
+  int cnt = 0;
+  for (long long jn = gw; jn < Rn; jn += nw) {
+    const long long jo = tk_map_new_to_old(jn, ctl->r, ctl->rold, m);
+    const TW dj = dv[jn];
+    TW vrow[CPL];
+    TW dot = TW(0);
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) {
+      const int c = lane + 32 * i;
+      vrow[i] = (jo >= 0 && c < r) ? V[jo * ldc + c] : TW(0);
+      dot += vrow[i] * pl[i];
+    }
+    dot = warp_sum(dot);
+    const TW ej = dj - dot;
+    if (lane == 0) { evec[jn] = ej; eacc.add(ej * ej); }
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) accf[i] += vrow[i] * ej;
+    if (++cnt == 32) {
+#pragma unroll
+      for (int i = 0; i < CPL; ++i) { acc[i] += (double)accf[i]; accf[i] = TW(0); }
+      cnt = 0;
+    }
+  }
+  __shared__ double sh[8][TK_STREAM_CAP_MAX + 1];
+#pragma unroll
+  for (int i = 0; i < CPL; ++i) sh[wid][lane + 32 * i] = acc[i] + (double)accf[i];
+  if (lane == 0) sh[wid][TK_STREAM_CAP_MAX] = eacc.value();
+  __syncthreads();
+  for (int c = threadIdx.x; c <= r; c += blockDim.x) {
+    const int src = (c == r) ? TK_STREAM_CAP_MAX : c;
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += sh[w][src];
+    part[(long long)blockIdx.x * (TK_STREAM_CAP_MAX + 2) + c] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Secular-equation SVD of S'. Problem: S'^T S' = diag(delta) + z z^T with delta = S^2 (and a
+// trailing 0 when q > eps), z = [p'; q'] (or p'). Eigenvalues lambda = singular values^2 of S',
+// eigenvectors = right singular vectors V''; U'' = S' V'' S~^-1.
+// Roots by bisection refined with safeguarded Newton steps; eigenvectors by the Loewner-formula
+// weights of Gu & Eisenstat (SIAM J. Matrix Anal. Appl. 15, 1994), which keep them orthogonal.
+// ---------------------------------------------------------------------------------------------
+
+
+__global__ void k_isvd_small(Ctl* ctl, const double* p, const double* es, const double* S,
+                             SecWork w) {
+  if (ctl->status) return;
+  if (threadIdx.x != 0) return;   // O(r) bookkeeping on one thread
+  const int d = ctl->d;
+  const int r = ctl->r[d - 1];
+  // CGS-corrected projection: p' = p + s, q'^2 = ||e||^2 - ||s||^2
+  double s2 = 0.0;
+  for (int c = 0; c < r; ++c) s2 += es[c] * es[c];
+  double q2 = es[r] - s2;
+  if (q2 < 0.0) q2 = 0.0;
+  const double q = sqrt(q2);
+  for (int c = 0; c < r; ++c) w.pq[c] = p[c] + es[c];
+  w.pq[r] = q;
+  ctl->q2 = q2;
+  ctl->q = q;
+  const int aug = q > ctl->eps ? 1 : 0;   // Alg. 3: ignore e if q <= eps
+  ctl->aug = aug;
+  if (aug && r + 1 > ctl->cap[d - 1]) { ctl->status = TK_ECAPACITY; return; }
+  long long Rn = 1;
+  for (int i = 0; i < d - 1; ++i) Rn *= ctl->r[i];
+  if (Rn > ctl->core_cap) { ctl->status = TK_ECAPACITY; return; }
+  const int m = r + aug;
+  // poles (descending since S is descending) and weights
+  double zn2 = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double zi = (i < r) ? w.pq[i] : q;
+    zn2 += zi * zi;
+  }
+  const double u = 1.1102230246251565e-16;
+  const double d1 = (r > 0) ? S[0] * S[0] : 0.0;
+  const double scale = fmax(d1, zn2) > 0.0 ? fmax(d1, zn2) : 1.0;
+  const double tol = 8.0 * u * scale;
+  const double zn = sqrt(zn2);
+  int mk = 0, nl = 0, nr = 0;
+  // deflation of tiny weights, merge of (nearly) equal poles by a Givens rotation
+  double pz = 0.0, pd = 0.0;
+  int pidx = -1;
+  for (int i = 0; i < m; ++i) {
+    const double di = (i < r) ? S[i] * S[i] : 0.0;
+    double zi = (i < r) ? w.pq[i] : q;
+    if (fabs(zi) * zn <= tol) {   // deflate: eigenpair (di, e_i)
+      w.lam[nl] = di;
+      w.lsrc[nl] = -(i + 1);
+      ++nl;
+      continue;
+    }
+    if (pidx >= 0 && fabs(pd - di) <= tol) {
+      // rotate (pz at pidx, zi at i) so that the weight of pole i vanishes
+      const double h = hypot(pz, zi);
+      const double c = pz / h, s = zi / h;
+      w.rot[4 * nr + 0] = pidx; w.rot[4 * nr + 1] = i; w.rot[4 * nr + 2] = c; w.rot[4 * nr + 3] = s;
+      ++nr;
+      pz = h;
+      w.z[mk - 1] = h;
+      w.lam[nl] = di;
+      w.lsrc[nl] = -(i + 1);
+      ++nl;
+      continue;
+    }
+    w.delta[mk] = di;
+    w.z[mk] = zi;
+    w.idx[mk] = i;
+    pz = zi; pd = di; pidx = i;
+    ++mk;
+  }
+  w.nrot[0] = nr;
+  w.meta[0] = m;
+  w.meta[1] = mk;
+  w.meta[3] = nl;
+}
+
+__device__ double sec_f(const double* delta, const double* z, int mk, double dorg, double tau,
+                        double* fp, int lane) {
+  double f = 0.0, g = 0.0;
+  for (int i = lane; i < mk; i += 32) {
+    const double den = (delta[i] - dorg) - tau;
+    const double t = z[i] / den;
+    f += z[i] * t;
+    g += t * t;
+  }
+  f = warp_sum(f);
+  g = warp_sum(g);
+  *fp = g;
+  return 1.0 + f;
+}
+
+// One warp per root of 1 + sum z_i^2 / (delta_i - lambda) = 0.
+__global__ void k_secular_roots(const Ctl* ctl, SecWork w) {
+  if (ctl->status) return;
+  const int mk = w.meta[1];
+  const int lane = threadIdx.x & 31;
+  const int root = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (root >= mk) return;
+  double zn2 = 0.0;
+  for (int i = lane; i < mk; i += 32) zn2 += w.z[i] * w.z[i];
+  zn2 = warp_sum(zn2);
+  // interval of lambda_root: (delta_root, delta_{root-1}) or (delta_0, delta_0 + ||z||^2]
+  int o;
+  double lo, hi;   // offsets relative to delta[o]
+  double fp;
+  if (root == 0) {
+    o = 0; lo = 0.0; hi = zn2;
+  } else {
+    const double a = w.delta[root], b = w.delta[root - 1];
+    const double mid = 0.5 * (b - a);
+    const double fm = sec_f(w.delta, w.z, mk, a, mid, &fp, lane);
+    if (fm >= 0.0) { o = root; lo = 0.0; hi = mid; }
+    else { o = root - 1; lo = a - b + mid; hi = 0.0; }   // lo = -(b - a)/2 relative to b
+  }
+  const double dorg = w.delta[o];
+  double tau = 0.5 * (lo + hi);
+  // bisection with Newton acceleration (bracket kept)
+  for (int it = 0; it < 120; ++it) {
+    const double f = sec_f(w.delta, w.z, mk, dorg, tau, &fp, lane);
+    if (f == 0.0) break;
+    if (f > 0.0) hi = tau; else lo = tau;
+    double tn = tau - f / fp;
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    const double width = hi - lo;
+    if (width <= 4.0 * 1.1102230246251565e-16 * fmax(fabs(lo), fabs(hi)) ||
+        fabs(tn - tau) <= 2.0 * 1.1102230246251565e-16 * fabs(tau))
+    { tau = tn; break; }
+    tau = tn;
+  }
+  if (lane == 0) { w.tau[root] = tau; w.org[root] = o; }
+}
+
+// Eigenvalues merged and sorted, Loewner weights, eigenvectors V'' and U'' = S' V'' / sigma.
+__global__ void __launch_bounds__(1024) k_secular_vectors(Ctl* ctl, const double* S, SecWork w,
+                                                         double* Sout) {
+  if (ctl->status) return;
+  const int d = ctl->d;
+  const int r = ctl->r[d - 1];
+  const int aug = ctl->aug;
+  const int m = w.meta[0], mk = w.meta[1], nl = w.meta[3];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ double zhat[TK_STREAM_CAP_MAX + 1];
+  __shared__ double lam_all[TK_STREAM_CAP_MAX + 1];
+  __shared__ int src_all[TK_STREAM_CAP_MAX + 1];
+  __shared__ int order[TK_STREAM_CAP_MAX + 1];
+  __shared__ int s_keep;
+  __shared__ double s_drop;
+  // roots first (index k -> lambda = delta[org] + tau), then deflated
+  for (int k = tid; k < mk; k += nt) {
+    lam_all[k] = w.delta[w.org[k]] + w.tau[k];
+    src_all[k] = k;
+  }
+  for (int k = tid; k < nl; k += nt) {
+    lam_all[mk + k] = w.lam[k];
+    src_all[mk + k] = w.lsrc[k];
+  }
+  __syncthreads();
+  // Loewner weights of the non-deflated problem
+  for (int i = tid; i < mk; i += nt) {
+    // zhat_i^2 = (lambda_i - delta_i) prod_{j != i} (lambda_j - delta_i) / (delta_j - delta_i)
+    double prod = (w.delta[w.org[i]] - w.delta[i]) + w.tau[i];
+    for (int j = 0; j < mk; ++j) {
+      if (j == i) continue;
+      const double num = (w.delta[w.org[j]] - w.delta[i]) + w.tau[j];
+      prod *= num / (w.delta[j] - w.delta[i]);
+    }
+    zhat[i] = copysign(sqrt(fabs(prod)), w.z[i]);
+  }
+  // descending order of all m eigenvalues (rank sort; ties by position)
+  for (int a = tid; a < m; a += nt) {
+    int rank = 0;
+    const double la = lam_all[a];
+    for (int b = 0; b < m; ++b) {
+      const double lb = lam_all[b];
+      if (lb > la || (lb == la && b < a)) ++rank;
+    }
+    order[rank] = a;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // numerical rank of the compact SVD: keep lambda > (r+1) u lambda_max, at most #columns
+    const double lmax = m > 0 ? lam_all[order[0]] : 0.0;
+    const double thr = (double)(r + 1) * 1.1102230246251565e-16 * lmax;
+    int keep = 0;
+    double drop = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double l = lam_all[order[k]];
+      if (keep < m && l > thr && lmax > 0.0) ++keep; else drop += fmax(l, 0.0);
+    }
+    s_keep = keep;
+    s_drop = drop;
+    w.meta[2] = keep;
+    ctl->rnew_d = keep;
+    ctl->dropped = drop;
+  }
+  __syncthreads();
+  const int keep = s_keep;
+  // V'' columns: for kept sorted eigenvalue k
+  for (long long L = tid; L < (long long)m * keep; L += nt) {
+    const int k = (int)(L / m), i = (int)(L % m);   // column k, original row i
+    w.V2[(long long)k * m + i] = 0.0;
+  }
+  __syncthreads();
+  for (int k = tid; k < keep; k += nt) {
+    const int a = order[k];
+    const int src = src_all[a];
+    double* col = w.V2 + (long long)k * m;
+    if (src >= 0) {
+      const int o = w.org[src];
+      const double tau = w.tau[src];
+      double nrm = 0.0;
+      for (int i = 0; i < mk; ++i) {
+        const double den = (w.delta[i] - w.delta[o]) - tau;
+        const double v = zhat[i] / den;
+        col[w.idx[i]] = v;
+        nrm += v * v;
+      }
+      nrm = sqrt(nrm);
+      for (int i = 0; i < mk; ++i) col[w.idx[i]] /= nrm;
+    } else {
+      col[-src - 1] = 1.0;
+    }
+    // undo the Givens merges (applied in reverse order)
+    for (int t = w.nrot[0] - 1; t >= 0; --t) {
+      const int i = (int)w.rot[4 * t + 0], j = (int)w.rot[4 * t + 1];
+      const double c = w.rot[4 * t + 2], s = w.rot[4 * t + 3];
+      const double xi = col[i], xj = col[j];
+      // merged weight lives on i: original (z_i, z_j) = h (c, s); x_orig = G^T x_rot
+      col[i] = c * xi - s * xj;
+      col[j] = s * xi + c * xj;
+    }
+    const double sig = sqrt(fmax(lam_all[a], 0.0));
+    w.sv[k] = sig;
+    Sout[k] = sig;
+  }
+  __syncthreads();
+  // U'' = S' V'' / sigma: rows 0..r-1: S_i V''(i,k); row r: p'^T V''(0:r,k) + q' V''(r,k)
+  for (long long L = tid; L < (long long)(r + 1) * keep; L += nt) {
+    const int k = (int)(L / (r + 1)), i = (int)(L % (r + 1));
+    const double* col = w.V2 + (long long)k * m;
+    double val;
+    if (i < r) {
+      val = S[i] * col[i];
+    } else {
+      val = 0.0;
+      for (int c = 0; c < r; ++c) val += w.pq[c] * col[c];
+      if (aug) val += w.pq[r] * col[r];
+    }
+    const double sig = w.sv[k];
+    w.U2[(long long)k * (r + 1) + i] = sig > 0.0 ? val / sig : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// U~_d = [U_d U''(1:r,:); U''(r+1,:)] into the other buffer (row-major, ld = ldc).
+// ---------------------------------------------------------------------------------------------
+__global__ void k_ud_update(const Ctl* ctl, double* const* udbufs, SecWork w) {
+  if (ctl->status) return;
+  const int d = ctl->d;
+  const int r = ctl->r[d - 1];
+  const int nd = ctl->nd;
+  const int ldc = ctl->ldc;
+  const int keep = w.meta[2];
+  const double* Ud = udbufs[ctl->cbuf];
+  double* Un = udbufs[ctl->cbuf ^ 1];
+  const long long total = (long long)(nd + 1) * keep;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(L / keep), c = (int)(L % keep);
+    const double* u2 = w.U2 + (long long)c * (r + 1);
+    double s;
+    if (t < nd) {
+      s = 0.0;
+      const double* row = Ud + (long long)t * ldc;
+      for (int i = 0; i < r; ++i) s += row[i] * u2[i];
+    } else {
+      s = u2[r];
+    }
+    Un[(long long)t * ldc + c] = s;
+  }
+}
+
+// M = U~_d(1:n_d,:)^T U_d (keep x r), plus the small matrices of the C and V updates:
+//   Bc = M^T (r x keep), cu = U''(r+1,:) (keep)
+//   Bv = V''(1:r,:) - s w^T (r x keep), wv = V''(r+1,:) / q' (keep)   [q > eps]
+//   Bv = V''                                                         [q <= eps]
+template <typename TW>
+__global__ void k_core_m(const Ctl* ctl, double* const* udbufs, SecWork w, const double* es,
+                         TW* Bc, TW* cu, TW* Bv, TW* wv, int ldb) {
+  if (ctl->status) return;
+  const int d = ctl->d;
+  const int r = ctl->r[d - 1];
+  const int nd = ctl->nd;
+  const int ldc = ctl->ldc;
+  const int keep = w.meta[2];
+  const int m = w.meta[0];
+  const int aug = ctl->aug;
+  const double* Ud = udbufs[ctl->cbuf];
+  const double* Un = udbufs[ctl->cbuf ^ 1];
+  const long long total = (long long)keep * r;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(L / r), b = (int)(L % r);   // M(a, b)
+    double s = 0.0;
+    for (int t = 0; t < nd; ++t) s += Un[(long long)t * ldc + a] * Ud[(long long)t * ldc + b];
+    Bc[(long long)b * ldb + a] = (TW)s;              // Bc(b, a) = M(a, b), row-major r x keep
+    const double* col = w.V2 + (long long)a * m;
+    double bv = col[b];
+    if (aug) bv -= es[b] * (col[r] / w.pq[r]);
+    Bv[(long long)b * ldb + a] = (TW)bv;
+  }
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < keep;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)L;
+    cu[a] = (TW)w.U2[(long long)a * (r + 1) + r];
+    const double* col = w.V2 + (long long)a * m;
+    wv[a] = aug ? (TW)(col[r] / w.pq[r]) : TW(0);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Out[j, :] = In_pad[j, 0:r] B + x[j] c  for every new row j (SIMT tiled GEMM).
+// In rows come from the old layout through the new->old row map (zero rows for padding).
+// ---------------------------------------------------------------------------------------------
+constexpr int CV_TM = 64, CV_TN = 64, CV_TK = 32;
+
+template <typename TW>
+__global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, TW* const* ibufs,
+                                                  TW* const* obufs, const TW* __restrict__ Bm,
+                                                  int ldb, const TW* __restrict__ cvec,
+                                                  const TW* __restrict__ xvec, TW* const* xbufs,
+                                                  const SecWork w) {
+  if (ctl->status) return;
+  const int d = ctl->d, mm = d - 1;
+  const int r = ctl->r[d - 1];
+  const int keep = w.meta[2];
+  const int ldc = ctl->ldc;
+  long long Rn = 1;
+  for (int i = 0; i < mm; ++i) Rn *= ctl->r[i];
+  const TW* In = ibufs[ctl->cbuf];
+  TW* Out = obufs[ctl->cbuf ^ 1];
+  const TW* X = xvec ? xvec : xbufs[ctl->xbuf];
+  __shared__ TW As[CV_TK][CV_TM + 1];
+  __shared__ TW Bs[CV_TK][CV_TN];
+  __shared__ long long rowsrc[CV_TM];
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  const long long ntm = (Rn + CV_TM - 1) / CV_TM;
+  const int ntn = (keep + CV_TN - 1) / CV_TN;
+  for (long long tile = blockIdx.x; tile < ntm * ntn; tile += gridDim.x) {
+    const long long tm = tile / ntn;
+    const int tn = (int)(tile % ntn);
+    const long long j0 = tm * CV_TM;
+    const int n0 = tn * CV_TN;
+    __syncthreads();
+    if (tid < CV_TM) {
+      const long long j = j0 + tid;
+      rowsrc[tid] = (j < Rn) ? tk_map_new_to_old(j, ctl->r, ctl->rold, mm) : -1;
+    }
+    TW acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = TW(0);
+    for (int k0 = 0; k0 < r; k0 += CV_TK) {
+      __syncthreads();
+      for (int L = tid; L < CV_TM * CV_TK; L += 256) {
+        const int row = L / CV_TK, kk = L % CV_TK;
+        const long long src = rowsrc[row];
+        As[kk][row] = (src >= 0 && k0 + kk < r) ? In[src * ldc + k0 + kk] : TW(0);
+      }
+      for (int L = tid; L < CV_TK * CV_TN; L += 256) {
+        const int kk = L / CV_TN, cc = L % CV_TN;
+        Bs[kk][cc] = (k0 + kk < r && n0 + cc < keep) ? Bm[(long long)(k0 + kk) * ldb + n0 + cc] : TW(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < CV_TK; ++kk) {
+        TW a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { a[q] = As[kk][ty + 16 * q]; b[q] = Bs[kk][tx + 16 * q]; }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const long long j = j0 + ty + 16 * p;
+      if (j >= Rn) continue;
+      const TW xj = X[j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = n0 + tx + 16 * q;
+        if (c < keep) Out[j * ldc + c] = acc[p][q] + xj * cvec[c];
+      }
+    }
+  }
+}
+
+// End of the update: S <- S~, ranks, n_d, buffers, error bookkeeping (Prop. 1, Prop. 2).
+__global__ void k_end_update(Ctl* ctl, const double* Snew, double* S) {
+  if (ctl->status) return;
+  const int d = ctl->d;
+  const int keep = ctl->rnew_d;
+  for (int i = threadIdx.x; i < keep; i += blockDim.x) S[i] = Snew[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // algorithmic bytes of this update (each operand read or written once per pass)
+    const double tw = ctl->tw, tx = ctl->tx;
+    const int r = ctl->r[d - 1];
+    double Ro = 1.0, Rn = 1.0;
+    for (int k = 0; k < d - 1; ++k) { Ro *= ctl->rold[k]; Rn *= ctl->r[k]; }
+    double A = 1.0;
+    for (int k = 0; k < d - 1; ++k) {
+      double B = 1.0;
+      for (int i = k + 1; i < d - 1; ++i) B *= ctl->n[i];
+      const double in_el = A * ctl->n[k] * B;
+      const double in_b = (k == 0 ? tx : tw) * in_el;
+      const double p_b = tw * A * ctl->rold[k] * B;
+      ctl->acc_bytes[k == 0 ? TK_PH_PROJ1 : TK_PH_PROJN] += in_b + p_b;
+      if (ctl->grew[k]) ctl->acc_bytes[TK_PH_GROW] += 2.0 * in_b + p_b + tw * A * ctl->r[k] * B;
+      A *= ctl->r[k];
+    }
+    ctl->acc_bytes[TK_PH_ISVD] += tw * (2.0 * Ro * r + 3.0 * Rn);
+    ctl->acc_bytes[TK_PH_FACT] += 8.0 * 2.0 * ((double)ctl->nd * r + (double)(ctl->nd + 1) * keep);
+    ctl->acc_bytes[TK_PH_CV] += tw * (2.0 * Ro * r + 2.0 * Rn * keep + 2.0 * Rn);
+    double disc = 0.0;
+    for (int k = 0; k < d - 1; ++k) disc += ctl->disc[k];
+    disc += ctl->aug ? 0.0 : ctl->q2;
+    disc += ctl->dropped;
+    ctl->err2 += disc;
+    ctl->data2 += ctl->y2;
+    ctl->r[d - 1] = keep;
+    ctl->nd += 1;
+    ctl->cbuf ^= 1;
+    ctl->nupdates += 1;
+  }
+}
+
+__global__ void k_begin_update(Ctl* ctl) {
+  if (ctl->status) return;
+  for (int k = 0; k < TK_MAXD; ++k) {
+    ctl->rold[k] = ctl->r[k];
+    ctl->grew[k] = 0;
+    ctl->radd[k] = 0;
+    ctl->e2[k] = 0.0;
+    ctl->disc[k] = 0.0;
+  }
+  ctl->xbuf = -1;
+  ctl->aug = 0;
+  ctl->q = 0.0;
+  ctl->q2 = 0.0;
+  ctl->dropped = 0.0;
+  if (ctl->nd + 1 > ctl->steps_cap) ctl->status = TK_ECAPACITY;
+}
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+template <typename TW>
+cudaError_t launch_isvd(Ctl* ctl, void* const* dbufs, void* const* vbufs, double* part_p,
+                        double* part_e, double* p, double* es, void* evec, const double* S,
+                        SecWork w, int grid, cudaStream_t st) {
+  k_isvd_p<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p);
+  k_reduce_vec<<<1, 512, 0, st>>>(ctl, part_p, grid, TK_STREAM_CAP_MAX, 0, p);
+  k_isvd_e<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p, (TW*)evec,
+                                     part_e);
+  k_reduce_vec<<<1, 512, 0, st>>>(ctl, part_e, grid, TK_STREAM_CAP_MAX + 2, 1, es);
+  k_isvd_small<<<1, 32, 0, st>>>(ctl, p, es, S, w);
+  k_secular_roots<<<(TK_STREAM_CAP_MAX + 1 + 7) / 8, 256, 0, st>>>(ctl, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_secular_vectors(Ctl* ctl, const double* S, SecWork w, double* Snew,
+                                   cudaStream_t st) {
+  k_secular_vectors<<<1, 1024, 0, st>>>(ctl, S, w, Snew);
+  return cudaGetLastError();
+}
+
+template <typename TW>
+cudaError_t launch_factor(Ctl* ctl, double* const* udbufs, SecWork w, const double* es, void* Bc,
+                          void* cu, void* Bv, void* wv, int ldb, int grid_small, cudaStream_t st) {
+  k_ud_update<<<grid_small, 256, 0, st>>>(ctl, udbufs, w);
+  k_core_m<TW><<<grid_small, 256, 0, st>>>(ctl, udbufs, w, es, (TW*)Bc, (TW*)cu, (TW*)Bv, (TW*)wv,
+                                           ldb);
+  return cudaGetLastError();
+}
+
+template <typename TW>
+cudaError_t launch_cv(Ctl* ctl, void* const* dbufs, void* const* cbufs, void* const* vbufs,
+                      SecWork w, const void* Bc, const void* cu, const void* Bv, const void* wv,
+                      int ldb, const void* evec, int grid_cv, cudaStream_t st) {
+  k_cv_update<TW><<<grid_cv, 256, 0, st>>>(ctl, (TW* const*)cbufs, (TW* const*)cbufs,
+                                           (const TW*)Bc, ldb, (const TW*)cu, nullptr,
+                                           (TW* const*)dbufs, w);
+  k_cv_update<TW><<<grid_cv, 256, 0, st>>>(ctl, (TW* const*)vbufs, (TW* const*)vbufs,
+                                           (const TW*)Bv, ldb, (const TW*)wv, (const TW*)evec,
+                                           (TW* const*)dbufs, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_begin(Ctl* ctl, cudaStream_t st) {
+  k_begin_update<<<1, 1, 0, st>>>(ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_end(Ctl* ctl, const double* Snew, double* S, cudaStream_t st) {
+  k_end_update<<<1, 256, 0, st>>>(ctl, Snew, S);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_isvd<float>(Ctl*, void* const*, void* const*, double*, double*, double*,
+                                        double*, void*, const double*, SecWork, int, cudaStream_t);
+template cudaError_t launch_isvd<double>(Ctl*, void* const*, void* const*, double*, double*,
+                                         double*, double*, void*, const double*, SecWork, int,
+                                         cudaStream_t);
+template cudaError_t launch_factor<float>(Ctl*, double* const*, SecWork, const double*, void*,
+                                          void*, void*, void*, int, int, cudaStream_t);
+template cudaError_t launch_factor<double>(Ctl*, double* const*, SecWork, const double*, void*,
+                                           void*, void*, void*, int, int, cudaStream_t);
+template cudaError_t launch_cv<float>(Ctl*, void* const*, void* const*, void* const*, SecWork,
+                                      const void*, const void*, const void*, const void*, int,
+                                      const void*, int, cudaStream_t);
+template cudaError_t launch_cv<double>(Ctl*, void* const*, void* const*, void* const*, SecWork,
+                                       const void*, const void*, const void*, const void*, int,
+                                       const void*, int, cudaStream_t);
+
+}  // namespace tk

@@ -1,0 +1,88 @@
+// Host-side launchers of the device kernels (one declaration per translation unit export).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace tk {
+
+// ---- k_spatial.cu ----
+size_t proj_smem_bytes(int r, int tw_size);
+template <typename TX, typename TW>
+cudaError_t launch_proj(const Ctl* ctl, int k, int out_off, int pred, const void* Xext,
+                        void* const* dbufs, const void* U, int ldu, int rmax, double* part_e2,
+                        double* part_y2, int grid, cudaStream_t st);
+template <typename TX, typename TW>
+cudaError_t launch_resid_gram(const Ctl* ctl, int k, int n, const void* Xext, void* const* dbufs,
+                              const void* U, int ldu, double* gpart, int pairs, int chunks,
+                              int data_only, cudaStream_t st);
+cudaError_t launch_decide(Ctl* ctl, int k, const double* pe, const double* py, int nparts,
+                          cudaStream_t st);
+cudaError_t launch_mode_end(Ctl* ctl, int k, cudaStream_t st);
+cudaError_t launch_gram_reduce(const Ctl* ctl, int k, const double* gpart, int pairs, int chunks,
+                               double* G, int data_only, cudaStream_t st);
+template <typename TI, typename TW, typename TO>
+cudaError_t launch_expand(const void* X, long long A, int r, long long B, const void* U, int ldu,
+                          int n, void* out, cudaStream_t st);
+template <typename TX>
+cudaError_t launch_norm2(const void* X, long long N, double* part, int grid, cudaStream_t st);
+
+// ---- k_eig.cu ----
+template <typename TE>
+cudaError_t launch_eig(Ctl* ctl, int k, int mode, const double* G, void* Aw, void* Z, void* LD,
+                       double* W, double* lam, int mcap, cudaStream_t st);
+template <typename TW>
+cudaError_t launch_append(Ctl* ctl, int k, int mode, const double* W, double* U, void* Uw, int ldu,
+                          int n, cudaStream_t st);
+
+// ---- k_stream.cu ----
+struct SecWork {
+  double* delta;
+  double* z;
+  int* idx;
+  double* tau;
+  int* org;
+  double* lam;
+  int* lsrc;
+  double* rot;
+  int* nrot;
+  double* V2;
+  double* U2;
+  double* sv;
+  double* pq;
+  int* meta;
+};
+template <typename TW>
+cudaError_t launch_isvd(Ctl* ctl, void* const* dbufs, void* const* vbufs, double* part_p,
+                        double* part_e, double* p, double* es, void* evec, const double* S,
+                        SecWork w, int grid, cudaStream_t st);
+cudaError_t launch_secular_vectors(Ctl* ctl, const double* S, SecWork w, double* Snew,
+                                   cudaStream_t st);
+template <typename TW>
+cudaError_t launch_factor(Ctl* ctl, double* const* udbufs, SecWork w, const double* es, void* Bc,
+                          void* cu, void* Bv, void* wv, int ldb, int grid_small, cudaStream_t st);
+template <typename TW>
+cudaError_t launch_cv(Ctl* ctl, void* const* dbufs, void* const* cbufs, void* const* vbufs,
+                      SecWork w, const void* Bc, const void* cu, const void* Bv, const void* wv,
+                      int ldb, const void* evec, int grid_cv, cudaStream_t st);
+cudaError_t launch_begin(Ctl* ctl, cudaStream_t st);
+cudaError_t launch_end(Ctl* ctl, const double* Snew, double* S, cudaStream_t st);
+
+// ---- k_misc.cu ----
+template <typename TW>
+cudaError_t launch_init_finish(Ctl* ctl, const void* Ccol, long long R, int rd, const double* lam,
+                               const double* Utmp, int nt, void* C, void* V, double* Ud, double* S,
+                               int ldc, cudaStream_t st);
+template <typename TW>
+cudaError_t launch_core_times_ud(const void* C, long long R, int rd, int ldc, const double* Ud,
+                                 long long t0, long long T, void* out, cudaStream_t st);
+template <typename TW>
+cudaError_t launch_state_to_colmajor(const void* Src, long long R, int rd, int ldc, double* dst,
+                                     cudaStream_t st);
+cudaError_t launch_ud_to_colmajor(const double* Ud, int nd, int rd, int ldc, double* dst,
+                                  cudaStream_t st);
+
+}  // namespace tk

@@ -1,0 +1,76 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol the header declares
+(no compute call: this runs without a GPU)."""
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", f)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(tucker_[a-z_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2308_16395_gb300 import build as b
+
+    path = b.build()
+    import paper_2308_16395_gb300 as pkg
+
+    return pkg.load_library(), path
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
+                     "tucker_error_norm"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    _, path = lib
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (tucker_[a-z_]+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_names_match_header(lib):
+    import paper_2308_16395_gb300 as pkg
+
+    for n in _declared():
+        assert hasattr(pkg, n), n
+    assert set(pkg.EXPORTS) == set(_declared())
+
+
+def test_library_is_built_for_sm_103a(lib):
+    _, path = lib
+    out = subprocess.run(["/usr/local/cuda/bin/cuobjdump", "--list-elf", path], capture_output=True,
+                         text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_config_struct_size_matches_header(lib):
+    import ctypes
+
+    import paper_2308_16395_gb300 as pkg
+
+    # 4 int32 + 8 int64 + 8 int64 + 2 int64 + 2 double
+    assert ctypes.sizeof(pkg.TuckerConfig) == 16 + 64 + 64 + 16 + 16
+
+
+def test_version_string(lib):
+    import paper_2308_16395_gb300 as pkg
+
+    assert "sm_103a" in pkg.tucker_version()

@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars (written here, derived in the design doc):
+  FP64 form  -- identical ranks every step; reconstruction, subspaces and aligned core within
+                1e-9 relative; error bookkeeping within 1e-8 relative.
+  mixed form -- identical ranks except at decisions within DELTA_DEC (relative) of eps^2;
+                reconstruction within 1e-5 relative of the oracle's.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.parity import aligned_core_diff, decision_margins, subspace_sin, to_device
+from workloads import CONFIG1, BlobField, LowRankStream, config1_tensor
+
+pytestmark = pytest.mark.gpu
+
+DELTA_DEC = 1e-3
+TOL = {"fp64": 1e-9, "mixed": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2308_16395_gb300 as p
+    from paper_2308_16395_gb300 import build as b
+
+    b.build()
+    p.load_library()
+    return p
+
+
+def _run(pkg, X, n_init, tau, precision, dtype, steps=None, check_every=True, caps=None,
+         core_cap=0):
+    """Stream X (n_1 x ... x n_{d-1} x T, FP64) through both; return per-step records."""
+    import torch
+
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    T = X.shape[-1] if steps is None else steps
+    # both sides see exactly the same values: round to the slice type first
+    Xs = X.astype(np.float32).astype(np.float64) if dtype == "f32" else X
+    st = O.init_stream(Xs[..., :n_init].copy(order="F"), tau)
+    Xg = to_device(Xs[..., :T].copy(order="F"), tdt)
+    ts = pkg.TuckerStream(Xg[:n_init].contiguous(), tau, precision=precision,
+                          steps_cap=T + 4, rank_cap=caps, core_cap=core_cap)
+    recs = []
+    assert ts.ranks == st.ranks, ("init", ts.ranks, st.ranks)
+    diverged = False
+    for t in range(n_init, T):
+        O.stream_update(st, Xs[..., t].copy(order="F"))
+        ts.update(Xg[t].contiguous())
+        lg = st.log[-1]
+        margin = decision_margins(lg)
+        rec = dict(t=t, ranks_o=st.ranks, ranks_g=ts.ranks if check_every else None, margin=margin)
+        recs.append(rec)
+        if check_every and rec["ranks_g"] != rec["ranks_o"]:
+            assert margin < DELTA_DEC or precision == "fp64" and margin < 1e-9, \
+                f"rank mismatch at t={t}: gpu {rec['ranks_g']} oracle {rec['ranks_o']} margin {margin}"
+            diverged = True
+            break
+    return st, ts, Xs[..., :T], recs, diverged
+
+
+def _compare_final(pkg, st, ts, Xs, precision):
+    import torch
+
+    tol = TOL[precision]
+    nd = ts.n_d
+    Xh_o = O.reconstruct(st.C, st.Us)
+    Xh_g = pkg.paper_order(ts.reconstruct(0, nd)).cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(Xh_g - Xh_o) / np.linalg.norm(Xh_o)
+    # the reconstruction is returned in the slice type: FP32 output adds ~6e-8 relative rounding
+    rtol = max(tol, 2e-7) if ts.dtype == torch.float32 else tol
+    assert rel < rtol, f"reconstruction rel diff {rel}"
+    # error guarantee on the GPU's own reconstruction
+    true = np.linalg.norm(Xs - Xh_g) / np.linalg.norm(Xs)
+    assert true <= st.tau * (1 + 1e-6), true
+    eb, dn = ts.error_norm()
+    assert abs(dn - math.sqrt(st.data_norm2)) <= 1e-6 * dn
+    assert eb >= np.linalg.norm(Xs - Xh_g) * (1 - 1e-4)
+    # factors and aligned core
+    C_g = ts.core().cpu().numpy()
+    Us_g = [ts.factor(k).cpu().numpy() for k in range(ts.d)]
+    for k in range(ts.d):
+        assert Us_g[k].shape == st.Us[k].shape
+        s = subspace_sin(st.Us[k], Us_g[k])
+        assert s < max(tol, 1e-8) * 100, (k, s)
+        np.testing.assert_allclose(Us_g[k].T @ Us_g[k], np.eye(Us_g[k].shape[1]), atol=1e-6 if precision == "mixed" else 1e-9)
+    cd = aligned_core_diff(st.C, st.Us, C_g, Us_g)
+    assert cd < 100 * tol, cd
+    return rel
+
+
+def test_config1_fp64_exact_parity(pkg):
+    """Plain FP64 form on the exact-rank workload (24x20x16 slices, ranks (4,4,3,6), tau 1e-3)."""
+    s = config1_tensor()
+    X = s.tensor(0, CONFIG1["steps"])
+    st, ts, Xs, recs, div = _run(pkg, X, CONFIG1["n_init"], CONFIG1["tau"], "fp64", "f64")
+    assert not div
+    for r in recs:
+        assert r["ranks_g"] == (4, 4, 3, 6)
+    _compare_final(pkg, st, ts, Xs, "fp64")
+    eb, _ = ts.error_norm()
+    assert abs(eb ** 2 - st.err2) <= 1e-8 * st.err2
+    info = ts.step_info()
+    assert abs(info["eps"] - st.log[-1]["eps"]) <= 1e-12 * info["eps"]
+    ts.close()
+
+
+def test_config1_mixed_parity(pkg):
+    """Mixed form, FP32 slices, same workload: identical ranks, reconstruction within 1e-5."""
+    s = config1_tensor()
+    X = s.tensor(0, CONFIG1["steps"])
+    st, ts, Xs, recs, div = _run(pkg, X, CONFIG1["n_init"], CONFIG1["tau"], "mixed", "f32")
+    assert not div
+    _compare_final(pkg, st, ts, Xs, "mixed")
+    ts.close()
+
+
+def _growth_stream(seed=11, n=(37, 29, 11), T=16):
+    rng = np.random.default_rng(seed)
+    A = [np.linalg.qr(rng.standard_normal((m, 5)))[0] for m in n]
+    X = np.zeros(n + (T,), order="F")
+    for t in range(T):
+        r_use = 2 if t < 6 else (4 if t < 10 else 5)
+        G = rng.standard_normal((r_use,) * 3)
+        X[..., t] = O.reconstruct(G, [a[:, :r_use] for a in A])
+    X += 1e-6 * rng.standard_normal(X.shape)
+    return X
+
+
+@pytest.mark.parametrize("precision,dtype", [("fp64", "f64"), ("fp64", "f32"), ("mixed", "f32")])
+def test_rank_growth_ragged(pkg, precision, dtype):
+    """Spatial ranks grow (2 -> 4 -> 5) on ragged sizes (37 x 29 x 11: not multiples of any tile)."""
+    X = _growth_stream()
+    st, ts, Xs, recs, div = _run(pkg, X, 6, 1e-3, precision, dtype)
+    assert not div
+    assert st.ranks[:3] == (5, 5, 5)
+    _compare_final(pkg, st, ts, Xs, precision)
+    ts.close()
+
+
+def test_blob_field_mixed_small(pkg):
+    """Advected-blob workload (4 spatial modes incl. variables) at a reduced grid, tau = 1e-4."""
+    bf = BlobField(grid=(40, 36, 24), nvar=5, nblobs=12, noise=1e-5, seed=3)
+    T = 26
+    X = np.stack([bf.slice(t).astype(np.float64) for t in range(T)], axis=-1)
+    X = np.asfortranarray(X)
+    st, ts, Xs, recs, div = _run(pkg, X, 8, 1e-4, "mixed", "f32")
+    if not div:
+        _compare_final(pkg, st, ts, Xs, "mixed")
+    ts.close()
+
+
+def test_blob_field_fp64_small(pkg):
+    bf = BlobField(grid=(40, 36, 24), nvar=5, nblobs=12, noise=1e-5, seed=3)
+    T = 20
+    X = np.asfortranarray(np.stack([bf.slice(t).astype(np.float64) for t in range(T)], axis=-1))
+    st, ts, Xs, recs, div = _run(pkg, X, 8, 1e-4, "fp64", "f32")
+    assert not div
+    _compare_final(pkg, st, ts, Xs, "fp64")
+    ts.close()
+
+
+def test_matrix_stream_d2(pkg):
+    """d = 2: column-basis growth + incremental SVD of a matrix stream."""
+    rng = np.random.default_rng(12)
+    n, T, r = 50, 40, 6
+    A = rng.standard_normal((n, r)) @ rng.standard_normal((r, T)) + 1e-7 * rng.standard_normal((n, T))
+    X = np.asfortranarray(A)
+    st, ts, Xs, recs, div = _run(pkg, X, 3, 1e-5, "fp64", "f64")
+    assert not div and ts.ranks == st.ranks
+    _compare_final(pkg, st, ts, Xs, "fp64")
+    ts.close()
+
+
+def test_zero_slice_and_in_span_slice(pkg):
+    import torch
+
+    s = LowRankStream((16, 12, 10), (3, 3, 2, 4), 10, 1e-4, seed=5)
+    X = s.tensor(0, 10)
+    Xz = X.copy(order="F")
+    Xz[..., 7] = 0.0
+    Xz[..., 8] = 0.5 * X[..., 2] - 0.25 * X[..., 4]
+    st, ts, Xs, recs, div = _run(pkg, Xz, 6, 1e-3, "fp64", "f64", steps=10)
+    assert not div
+    _compare_final(pkg, st, ts, Xs, "fp64")
+    ts.close()
+
+
+def test_capacity_and_bad_input_errors(pkg):
+    import torch
+
+    s = LowRankStream((16, 12, 10), (3, 3, 2, 4), 10, 1e-4, seed=5)
+    X = s.tensor(0, 10)
+    Xg = to_device(X, torch.float64)
+    # a spatial rank cap below the initial rank: the initial ST-HOSVD reports ECAPACITY
+    with pytest.raises(pkg.TuckerError) as ei:
+        pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="fp64", rank_cap=[2, 0, 0, 0])
+    assert ei.value.code == 3
+    # steps capacity: the update after the last row is latched and reported
+    ts = pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="fp64", steps_cap=7)
+    ts.update(Xg[6].contiguous())
+    ts.update(Xg[7].contiguous())
+    with pytest.raises(pkg.TuckerError) as ei:
+        ts.ranks
+    assert ei.value.code == 3
+    with pytest.raises(pkg.TuckerError) as ei:
+        ts.update(Xg[8].contiguous())
+    assert ei.value.code == 7
+    ts.close()
+    # non-finite slice -> ENUMERIC latched
+    ts = pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="fp64", steps_cap=16)
+    bad = Xg[6].clone()
+    bad[0, 0, 0] = float("nan")
+    ts.update(bad)
+    with pytest.raises(pkg.TuckerError) as ei:
+        ts.error_norm()
+    assert ei.value.code == 4
+    ts.close()
+    # argument errors are synchronous
+    with pytest.raises(pkg.TuckerError) as ei:
+        pkg.TuckerStream(Xg[:6].contiguous(), -1.0, precision="fp64")
+    assert ei.value.code == 1
+    with pytest.raises(pkg.TuckerError) as ei:
+        pkg.TuckerStream(torch.zeros_like(Xg[:6]).contiguous(), 1e-3, precision="fp64")
+    assert ei.value.code == 1
