@@ -83,7 +83,11 @@ def _compare_final(pkg, st, ts, Xs, precision):
     assert true <= st.tau * (1 + 1e-6), true
     eb, dn = ts.error_norm()
     assert abs(dn - math.sqrt(st.data_norm2)) <= 1e-6 * dn
-    assert eb >= np.linalg.norm(Xs - Xh_g) * (1 - 1e-4)
+    # the bookkeeping bounds the true error up to the Gram route's absolute resolution
+    # (eigenvalues of A A^T carry errors ~ u ||A||^2 per truncation)
+    true_abs = np.linalg.norm(Xs - Xh_g)
+    slack = 64 * 2.2e-16 * dn ** 2 * Xs.shape[-1] * (1e6 if precision == "mixed" else 1.0)
+    assert eb ** 2 >= true_abs ** 2 * (1 - 1e-4) - slack, (eb, true_abs)
     # factors and aligned core
     C_g = ts.core().cpu().numpy()
     Us_g = [ts.factor(k).cpu().numpy() for k in range(ts.d)]
