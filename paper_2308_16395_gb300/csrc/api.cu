@@ -71,6 +71,11 @@ struct tucker_state {
   SecWork sw{};
   void* Bc = nullptr;
   void* Bv = nullptr;
+  float* bsplit[4]{};            // B^T TF32 hi/lo of the core and V updates (mixed form)
+  float** d_bsplit = nullptr;
+  TcMaps maps{};
+  bool tc = false;               // tensor-core path available (mixed form)
+  int nsm = 152;
   void* cu = nullptr;
   void* wv = nullptr;
   std::vector<void*> allocs;
@@ -284,6 +289,24 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
   CK(dalloc(s, &s->Bv, (size_t)tw * kSecMax * s->ldc));
   CK(dalloc(s, &s->cu, (size_t)tw * kSecMax));
   CK(dalloc(s, &s->wv, (size_t)tw * kSecMax));
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (tw == 4 && s->ldc % 4 == 0) {
+    for (int i = 0; i < 4; ++i) CK(dalloc(s, (void**)&s->bsplit[i], sizeof(float) * 512 * 512));
+    CK(dalloc(s, (void**)&s->d_bsplit, sizeof(void*) * 4));
+    CK(cudaMemcpy(s->d_bsplit, s->bsplit, sizeof(void*) * 4, cudaMemcpyHostToDevice));
+    bool ok = true;
+    ok &= make_map_2d_f32(&s->maps.c0, s->Cb[0], s->core_cap, s->ldc, s->ldc, 32, 128);
+    ok &= make_map_2d_f32(&s->maps.c1, s->Cb[1], s->core_cap, s->ldc, s->ldc, 32, 128);
+    ok &= make_map_2d_f32(&s->maps.v0, s->Vb[0], s->core_cap, s->ldc, s->ldc, 32, 128);
+    ok &= make_map_2d_f32(&s->maps.v1, s->Vb[1], s->core_cap, s->ldc, s->ldc, 32, 128);
+    ok &= make_map_2d_f32(&s->maps.bc_hi, s->bsplit[0], 512, 512, 512, 32, 16);
+    ok &= make_map_2d_f32(&s->maps.bc_lo, s->bsplit[1], 512, 512, 512, 32, 16);
+    ok &= make_map_2d_f32(&s->maps.bv_hi, s->bsplit[2], 512, 512, 512, 32, 16);
+    ok &= make_map_2d_f32(&s->maps.bv_lo, s->bsplit[3], 512, 512, 512, 32, 16);
+    s->tc = ok;
+  }
   return TUCKER_OK;
 }
 
@@ -415,6 +438,7 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
       c.init_nt = 0;
       c.xbuf = -1;
       c.cbuf = 0;
+      c.ubuf = 0;
       for (int k = 0; k < TK_MAXD; ++k) { c.grew[k] = 0; c.radd[k] = 0; c.disc[k] = 0.0; c.rold[k] = c.r[k]; }
       if (cudaMemcpyAsync(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess) { rc = TUCKER_ECUDA; set_err(s, "CUDA error after init"); }
@@ -481,12 +505,17 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
   {
     PhaseMark pm(s, st, TK_PH_FACT);
     CK(launch_factor<TW>(s->ctl, s->d_udbufs, s->sw, s->esvec, s->Bc, s->cu, s->Bv, s->wv, s->ldc,
-                         152 * 2, st));
+                         s->tc ? s->d_bsplit : nullptr, 152 * 2, st));
     launches += 2;
   }
   {
     // core update (Alg. 5, last step) and V~ = V' V''
     PhaseMark pm(s, st, TK_PH_CV);
+    if (s->tc) {
+      CK(launch_tc_cv(s->ctl, s->sw, s->maps, s->Cb, s->Vb, s->d_cbufs, s->d_vbufs, s->cu, s->wv,
+                      s->evec, s->d_dbufs, s->ldc, s->nsm, st));
+      launches += 3;
+    }
     CK(launch_cv<TW>(s->ctl, s->d_dbufs, s->d_cbufs, s->d_vbufs, s->sw, s->Bc, s->cu, s->Bv, s->wv,
                      s->ldc, s->evec, kGridCV, st));
     launches += 2;
@@ -514,7 +543,7 @@ tucker_status do_reconstruct(tucker_state* s, int64_t t0, int64_t t1, void* out,
   void* tmp[2] = {nullptr, nullptr};
   CK(cudaMallocAsync(&tmp[0], (size_t)s->tw * std::max(big, R * T), st));
   CK(cudaMallocAsync(&tmp[1], (size_t)s->tw * std::max(big, R * T), st));
-  CK(launch_core_times_ud<TW>(s->Cb[c.cbuf], R, rd, s->ldc, s->Ud[c.cbuf], t0, T, tmp[0], st));
+  CK(launch_core_times_ud<TW>(s->Cb[c.cbuf], R, rd, s->ldc, s->Ud[c.ubuf], t0, T, tmp[0], st));
   int cur = 0;
   for (int k = 0; k < d - 1; ++k) {
     long long A = 1, B = T;
@@ -663,7 +692,7 @@ tucker_status tucker_copy_factor(tucker_state* s, int32_t mode, double* dst) {
     CK(cudaMemcpyAsync(dst, s->U[mode], sizeof(double) * s->n[mode] * c.r[mode],
                        cudaMemcpyDeviceToDevice, s->last_stream));
   } else {
-    CK(launch_ud_to_colmajor(s->Ud[c.cbuf], c.nd, c.r[s->d - 1], s->ldc, dst, s->last_stream));
+    CK(launch_ud_to_colmajor(s->Ud[c.ubuf], c.nd, c.r[s->d - 1], s->ldc, dst, s->last_stream));
   }
   CK(cudaStreamSynchronize(s->last_stream));
   return TUCKER_OK;

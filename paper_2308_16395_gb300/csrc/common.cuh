@@ -34,7 +34,8 @@ struct Ctl {
   // ---- state ----
   int r[TK_MAXD];           // current ranks
   int nd;                   // n_d: rows of U_d
-  int cbuf;                 // which C/V/U_d ping-pong buffer holds the state
+  int cbuf;                 // which C/V ping-pong buffer holds the state
+  int ubuf;                 // which U_d ping-pong buffer holds the state
   int status;               // latched error (0 = ok)
   int xbuf;                 // D*-buffer holding the input of the current spatial mode (-1: slice)
   int init_nt;              // > 0 only during the batch ST-HOSVD: number of initial slices
@@ -154,4 +155,27 @@ __device__ __forceinline__ long long tk_map_new_to_old(long long j, const int* r
     stride *= ro[k];
   }
   return jo;
+}
+
+// ---- tensor-core path of the core / V update (mixed form) ----
+#define TC_KC 32                        // FP32 elements of K per stage (128 bytes)
+#define TC_BRES_BYTES (160 * 1024)      // resident B^T (TF32 hi + lo) in shared memory
+
+// Whether the core/V update of this step runs on the tensor cores: mixed form, B^T (N x K split
+// into TF32 hi/lo) fits in shared memory, N <= 256. A pure function of the control block and the
+// kept streaming rank, evaluated identically by every kernel of the update.
+__device__ __forceinline__ bool tc_cv_ok(const Ctl* ctl, int keep) {
+  if (ctl->tw != 4) return false;
+  const int r = ctl->r[ctl->d - 1];
+  if (r < 1 || keep < 1) return false;
+  const int kc = (r + TC_KC - 1) / TC_KC;
+  const int np = (keep + 15) / 16 * 16;
+  if (np > 256) return false;
+  return (long long)kc * np * TC_KC * 4 * 2 <= TC_BRES_BYTES;
+}
+
+__device__ __forceinline__ bool spatial_grew(const Ctl* ctl) {
+  for (int k = 0; k < ctl->d - 1; ++k)
+    if (ctl->r[k] != ctl->rold[k]) return true;
+  return false;
 }

@@ -23,8 +23,13 @@
 namespace tk {
 
 // ---------------------------------------------------------------------------------------------
-// p = V_pad^T d over the old rows; partials per block (r doubles each).
+// Row passes over V (Alg. 3's projections). A warp streams batches of RB rows; lanes cover 32
+// columns per column group, so every row read is coalesced and each lane keeps RB independent
+// loads in flight. FP32 products are accumulated in FP32 over 32 rows, then flushed to FP64.
 // ---------------------------------------------------------------------------------------------
+constexpr int RB = 8;   // rows per warp batch
+
+// p = V_pad^T d over the old rows; partials per block (TK_STREAM_CAP_MAX doubles each).
 template <typename TW>
 __global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW* const* dbufs,
                                                TW* const* vbufs, double* __restrict__ part) {
@@ -37,42 +42,54 @@ __global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW*
   long long Ro = 1;
   for (int i = 0; i < m; ++i) Ro *= ctl->rold[i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int CPL = TK_STREAM_CAP_MAX / 32;   // columns per lane
+  constexpr int CPL = TK_STREAM_CAP_MAX / 32;   // column groups
+  const int CG = (r + 31) / 32;
   double acc[CPL];
   TW accf[CPL];
 #pragma unroll
   for (int i = 0; i < CPL; ++i) { acc[i] = 0.0; accf[i] = TW(0); }
   const long long gw = (long long)blockIdx.x * 8 + wid;
   const long long nw = (long long)gridDim.x * 8;
-  int cnt = 0;
-  for (long long jo = gw; jo < Ro; jo += nw) {
-    // old multi-index -> new linear index
-    long long t = jo, jn = 0, stride = 1;
-    for (int k = 0; k < m; ++k) {
-      const int ik = (int)(t % ctl->rold[k]);
-      t /= ctl->rold[k];
-      jn += ik * stride;
-      stride *= ctl->r[k];
-    }
-    const TW dj = dv[jn];
-    const TW* row = V + jo * ldc;
+  int batches = 0;
+  for (long long j0 = gw * RB; j0 < Ro; j0 += nw * RB) {
+    TW dj[RB];
+    long long jo[RB];
 #pragma unroll
-    for (int i = 0; i < CPL; ++i) {
-      const int c = lane + 32 * i;
-      if (c < r) accf[i] += row[c] * dj;
+    for (int i = 0; i < RB; ++i) {
+      jo[i] = j0 + i;
+      if (jo[i] < Ro) {
+        long long t = jo[i], jn = 0, stride = 1;
+        for (int k = 0; k < m; ++k) {
+          const int ik = (int)(t % ctl->rold[k]);
+          t /= ctl->rold[k];
+          jn += ik * stride;
+          stride *= ctl->r[k];
+        }
+        dj[i] = dv[jn];
+      } else {
+        dj[i] = TW(0);
+        jo[i] = -1;
+      }
     }
-    if (++cnt == 32) {
 #pragma unroll
-      for (int i = 0; i < CPL; ++i) { acc[i] += (double)accf[i]; accf[i] = TW(0); }
-      cnt = 0;
+    for (int g = 0; g < CPL; ++g) {
+      if (g >= CG) break;
+      const int c = g * 32 + lane;
+      TW v[RB];
+#pragma unroll
+      for (int i = 0; i < RB; ++i) v[i] = (jo[i] >= 0 && c < r) ? V[jo[i] * ldc + c] : TW(0);
+#pragma unroll
+      for (int i = 0; i < RB; ++i) accf[g] += v[i] * dj[i];
+    }
+    if (++batches == 4) {
+#pragma unroll
+      for (int g = 0; g < CPL; ++g) { acc[g] += (double)accf[g]; accf[g] = TW(0); }
+      batches = 0;
     }
   }
   __shared__ double sh[8][TK_STREAM_CAP_MAX];
 #pragma unroll
-  for (int i = 0; i < CPL; ++i) {
-    const int c = lane + 32 * i;
-    sh[wid][c] = acc[i] + (double)accf[i];
-  }
+  for (int g = 0; g < CPL; ++g) sh[wid][g * 32 + lane] = acc[g] + (double)accf[g];
   __syncthreads();
   for (int c = threadIdx.x; c < r; c += blockDim.x) {
     double s = 0.0;
@@ -81,15 +98,25 @@ __global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW*
   }
 }
 
-// fixed-order reduction of per-block vectors of length len (<= TK_STREAM_CAP_MAX + 2)
-__global__ void k_reduce_vec(const Ctl* ctl, const double* part, int nparts, int stride, int len_extra,
-                             double* out) {
+// Fixed-order reduction of per-block vectors: out[c] = sum_b part[b * stride + c] for
+// c < r_d + len_extra. One block per 32 columns, warps split the partials.
+__global__ void __launch_bounds__(256) k_reduce_vec(const Ctl* ctl, const double* part, int nparts,
+                                                   int stride, int len_extra, double* out) {
   if (ctl->status) return;
   const int len = ctl->r[ctl->d - 1] + len_extra;
-  for (int c = threadIdx.x; c < len; c += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += part[(long long)b * stride + c];
-    out[c] = s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  if (blockIdx.x * 32 >= len) return;
+  double s = 0.0;
+  if (c < len)
+    for (int b = wid; b < nparts; b += 8) s += part[(long long)b * stride + c];
+  __shared__ double sh[8][32];
+  sh[wid][lane] = s;
+  __syncthreads();
+  if (wid == 0 && c < len) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w][lane];
+    out[c] = t;
   }
 }
 
@@ -110,45 +137,80 @@ __global__ void __launch_bounds__(256) k_isvd_e(const Ctl* __restrict__ ctl, TW*
   for (int i = 0; i < m; ++i) Rn *= ctl->r[i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int CPL = TK_STREAM_CAP_MAX / 32;
+  const int CG = (r + 31) / 32;
   TW pl[CPL];
 #pragma unroll
-  for (int i = 0; i < CPL; ++i) {
-    const int c = lane + 32 * i;
-    pl[i] = (c < r) ? (TW)p[c] : TW(0);
+  for (int g = 0; g < CPL; ++g) {
+    const int c = lane + 32 * g;
+    pl[g] = (c < r) ? (TW)p[c] : TW(0);
   }
   double acc[CPL];
   TW accf[CPL];
 #pragma unroll
-  for (int i = 0; i < CPL; ++i) { acc[i] = 0.0; accf[i] = TW(0); }
+  for (int g = 0; g < CPL; ++g) { acc[g] = 0.0; accf[g] = TW(0); }
   typename AccOf<TW>::type eacc;
   const long long gw = (long long)blockIdx.x * 8 + wid;
   const long long nw = (long long)gridDim.x * 8;
-  int cnt = 0;
-  for (long long jn = gw; jn < Rn; jn += nw) {
-    const long long jo = tk_map_new_to_old(jn, ctl->r, ctl->rold, m);
-    const TW dj = dv[jn];
-    TW vrow[CPL];
-    TW dot = TW(0);
+  int batches = 0;
+  for (long long j0 = gw * RB; j0 < Rn; j0 += nw * RB) {
+    long long jo[RB];
+    TW dj[RB], dot[RB];
 #pragma unroll
-    for (int i = 0; i < CPL; ++i) {
-      const int c = lane + 32 * i;
-      vrow[i] = (jo >= 0 && c < r) ? V[jo * ldc + c] : TW(0);
-      dot += vrow[i] * pl[i];
+    for (int i = 0; i < RB; ++i) {
+      const long long jn = j0 + i;
+      jo[i] = (jn < Rn) ? tk_map_new_to_old(jn, ctl->r, ctl->rold, m) : -1;
+      dj[i] = (jn < Rn) ? dv[jn] : TW(0);
+      dot[i] = TW(0);
     }
-    dot = warp_sum(dot);
-    const TW ej = dj - dot;
-    if (lane == 0) { evec[jn] = ej; eacc.add(ej * ej); }
 #pragma unroll
-    for (int i = 0; i < CPL; ++i) accf[i] += vrow[i] * ej;
-    if (++cnt == 32) {
+    for (int g = 0; g < CPL; ++g) {
+      if (g >= CG) break;
+      const int c = g * 32 + lane;
+      TW v[RB];
 #pragma unroll
-      for (int i = 0; i < CPL; ++i) { acc[i] += (double)accf[i]; accf[i] = TW(0); }
-      cnt = 0;
+      for (int i = 0; i < RB; ++i) v[i] = (jo[i] >= 0 && c < r) ? V[jo[i] * ldc + c] : TW(0);
+#pragma unroll
+      for (int i = 0; i < RB; ++i) dot[i] += v[i] * pl[g];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int i = 0; i < RB; ++i) dot[i] += __shfl_xor_sync(0xffffffffu, dot[i], o);
+    TW e[RB];
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      e[i] = dj[i] - dot[i];
+      if (j0 + i >= Rn) e[i] = TW(0);
+    }
+    if (lane < RB) {
+      TW mine = e[0];
+#pragma unroll
+      for (int i = 1; i < RB; ++i) if (lane == i) mine = e[i];
+      if (j0 + lane < Rn) evec[j0 + lane] = mine;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i) eacc.add(e[i] * e[i]);
+    }
+#pragma unroll
+    for (int g = 0; g < CPL; ++g) {
+      if (g >= CG) break;
+      const int c = g * 32 + lane;
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const TW v = (jo[i] >= 0 && c < r) ? V[jo[i] * ldc + c] : TW(0);
+        accf[g] += v * e[i];
+      }
+    }
+    if (++batches == 4) {
+#pragma unroll
+      for (int g = 0; g < CPL; ++g) { acc[g] += (double)accf[g]; accf[g] = TW(0); }
+      batches = 0;
     }
   }
   __shared__ double sh[8][TK_STREAM_CAP_MAX + 1];
 #pragma unroll
-  for (int i = 0; i < CPL; ++i) sh[wid][lane + 32 * i] = acc[i] + (double)accf[i];
+  for (int g = 0; g < CPL; ++g) sh[wid][lane + 32 * g] = acc[g] + (double)accf[g];
   if (lane == 0) sh[wid][TK_STREAM_CAP_MAX] = eacc.value();
   __syncthreads();
   for (int c = threadIdx.x; c <= r; c += blockDim.x) {
@@ -310,7 +372,6 @@ __global__ void __launch_bounds__(1024) k_secular_vectors(Ctl* ctl, const double
   __shared__ int src_all[TK_STREAM_CAP_MAX + 1];
   __shared__ int order[TK_STREAM_CAP_MAX + 1];
   __shared__ int s_keep;
-  __shared__ double s_drop;
   // roots first (index k -> lambda = delta[org] + tau), then deflated
   for (int k = tid; k < mk; k += nt) {
     lam_all[k] = w.delta[w.org[k]] + w.tau[k];
@@ -354,7 +415,6 @@ __global__ void __launch_bounds__(1024) k_secular_vectors(Ctl* ctl, const double
       if (keep < m && l > thr && lmax > 0.0) ++keep; else drop += fmax(l, 0.0);
     }
     s_keep = keep;
-    s_drop = drop;
     w.meta[2] = keep;
     ctl->rnew_d = keep;
     ctl->dropped = drop;
@@ -427,8 +487,8 @@ __global__ void k_ud_update(const Ctl* ctl, double* const* udbufs, SecWork w) {
   const int nd = ctl->nd;
   const int ldc = ctl->ldc;
   const int keep = w.meta[2];
-  const double* Ud = udbufs[ctl->cbuf];
-  double* Un = udbufs[ctl->cbuf ^ 1];
+  const double* Ud = udbufs[ctl->ubuf];
+  double* Un = udbufs[ctl->ubuf ^ 1];
   const long long total = (long long)(nd + 1) * keep;
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
        L += (long long)gridDim.x * blockDim.x) {
@@ -450,9 +510,11 @@ __global__ void k_ud_update(const Ctl* ctl, double* const* udbufs, SecWork w) {
 //   Bc = M^T (r x keep), cu = U''(r+1,:) (keep)
 //   Bv = V''(1:r,:) - s w^T (r x keep), wv = V''(r+1,:) / q' (keep)   [q > eps]
 //   Bv = V''                                                         [q <= eps]
+// bsplit (mixed form only): B^T of both updates split into TF32 hi/lo, row stride 512, zero padded
+// to K = ceil32(r), N = ceil16(keep): [0] Mhi, [1] Mlo (= (M^T)^T), [2] Bv^T hi, [3] Bv^T lo.
 template <typename TW>
 __global__ void k_core_m(const Ctl* ctl, double* const* udbufs, SecWork w, const double* es,
-                         TW* Bc, TW* cu, TW* Bv, TW* wv, int ldb) {
+                         TW* Bc, TW* cu, TW* Bv, TW* wv, int ldb, float* const* bsplit) {
   if (ctl->status) return;
   const int d = ctl->d;
   const int r = ctl->r[d - 1];
@@ -461,8 +523,8 @@ __global__ void k_core_m(const Ctl* ctl, double* const* udbufs, SecWork w, const
   const int keep = w.meta[2];
   const int m = w.meta[0];
   const int aug = ctl->aug;
-  const double* Ud = udbufs[ctl->cbuf];
-  const double* Un = udbufs[ctl->cbuf ^ 1];
+  const double* Ud = udbufs[ctl->ubuf];
+  const double* Un = udbufs[ctl->ubuf ^ 1];
   const long long total = (long long)keep * r;
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
        L += (long long)gridDim.x * blockDim.x) {
@@ -474,6 +536,33 @@ __global__ void k_core_m(const Ctl* ctl, double* const* udbufs, SecWork w, const
     double bv = col[b];
     if (aug) bv -= es[b] * (col[r] / w.pq[r]);
     Bv[(long long)b * ldb + a] = (TW)bv;
+    if (bsplit) {
+      // B^T(n = a, k = b) split for the tensor-core update
+      const float fs = (float)s, fb = (float)bv;
+      const float hs = __uint_as_float((__float_as_uint(fs) + 0x1000u) & 0xFFFFE000u);
+      const float hb = __uint_as_float((__float_as_uint(fb) + 0x1000u) & 0xFFFFE000u);
+      const long long o = (long long)a * 512 + b;
+      bsplit[0][o] = hs;
+      bsplit[1][o] = fs - hs;
+      bsplit[2][o] = hb;
+      bsplit[3][o] = fb - hb;
+    }
+  }
+  if (bsplit) {
+    // zero the padding read by the tensor cores: k in [r, ceil32(r)) for n < ceil16(keep), and
+    // rows n in [keep, ceil16(keep))
+    const int kp = (r + 31) / 32 * 32, np = (keep + 15) / 16 * 16;
+    const long long tot = (long long)np * kp;
+    for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < tot;
+         L += (long long)gridDim.x * blockDim.x) {
+      const int n = (int)(L / kp), k = (int)(L % kp);
+      if (n < keep && k < r) continue;
+      const long long o = (long long)n * 512 + k;
+      bsplit[0][o] = 0.f;
+      bsplit[1][o] = 0.f;
+      bsplit[2][o] = 0.f;
+      bsplit[3][o] = 0.f;
+    }
   }
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < keep;
        L += (long long)gridDim.x * blockDim.x) {
@@ -497,6 +586,7 @@ __global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, 
                                                   const TW* __restrict__ xvec, TW* const* xbufs,
                                                   const SecWork w) {
   if (ctl->status) return;
+  if (tc_cv_ok(ctl, w.meta[2])) return;   // the tensor-core kernel does this update
   const int d = ctl->d, mm = d - 1;
   const int r = ctl->r[d - 1];
   const int keep = w.meta[2];
@@ -598,9 +688,13 @@ __global__ void k_end_update(Ctl* ctl, const double* Snew, double* S) {
     disc += ctl->dropped;
     ctl->err2 += disc;
     ctl->data2 += ctl->y2;
+    // the tensor-core path after spatial growth expands into the other buffer and writes back
+    // into this one; every other path writes the other buffer
+    const bool stay = tc_cv_ok(ctl, keep) && spatial_grew(ctl);
     ctl->r[d - 1] = keep;
     ctl->nd += 1;
-    ctl->cbuf ^= 1;
+    if (!stay) ctl->cbuf ^= 1;
+    ctl->ubuf ^= 1;
     ctl->nupdates += 1;
   }
 }
@@ -630,10 +724,10 @@ cudaError_t launch_isvd(Ctl* ctl, void* const* dbufs, void* const* vbufs, double
                         double* part_e, double* p, double* es, void* evec, const double* S,
                         SecWork w, int grid, cudaStream_t st) {
   k_isvd_p<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p);
-  k_reduce_vec<<<1, 512, 0, st>>>(ctl, part_p, grid, TK_STREAM_CAP_MAX, 0, p);
+  k_reduce_vec<<<(TK_STREAM_CAP_MAX + 2 + 31) / 32, 256, 0, st>>>(ctl, part_p, grid, TK_STREAM_CAP_MAX, 0, p);
   k_isvd_e<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p, (TW*)evec,
                                      part_e);
-  k_reduce_vec<<<1, 512, 0, st>>>(ctl, part_e, grid, TK_STREAM_CAP_MAX + 2, 1, es);
+  k_reduce_vec<<<(TK_STREAM_CAP_MAX + 2 + 31) / 32, 256, 0, st>>>(ctl, part_e, grid, TK_STREAM_CAP_MAX + 2, 1, es);
   k_isvd_small<<<1, 32, 0, st>>>(ctl, p, es, S, w);
   k_secular_roots<<<(TK_STREAM_CAP_MAX + 1 + 7) / 8, 256, 0, st>>>(ctl, w);
   return cudaGetLastError();
@@ -647,10 +741,11 @@ cudaError_t launch_secular_vectors(Ctl* ctl, const double* S, SecWork w, double*
 
 template <typename TW>
 cudaError_t launch_factor(Ctl* ctl, double* const* udbufs, SecWork w, const double* es, void* Bc,
-                          void* cu, void* Bv, void* wv, int ldb, int grid_small, cudaStream_t st) {
+                          void* cu, void* Bv, void* wv, int ldb, float* const* bsplit,
+                          int grid_small, cudaStream_t st) {
   k_ud_update<<<grid_small, 256, 0, st>>>(ctl, udbufs, w);
   k_core_m<TW><<<grid_small, 256, 0, st>>>(ctl, udbufs, w, es, (TW*)Bc, (TW*)cu, (TW*)Bv, (TW*)wv,
-                                           ldb);
+                                           ldb, bsplit);
   return cudaGetLastError();
 }
 
@@ -683,9 +778,11 @@ template cudaError_t launch_isvd<double>(Ctl*, void* const*, void* const*, doubl
                                          double*, double*, void*, const double*, SecWork, int,
                                          cudaStream_t);
 template cudaError_t launch_factor<float>(Ctl*, double* const*, SecWork, const double*, void*,
-                                          void*, void*, void*, int, int, cudaStream_t);
+                                          void*, void*, void*, int, float* const*, int,
+                                          cudaStream_t);
 template cudaError_t launch_factor<double>(Ctl*, double* const*, SecWork, const double*, void*,
-                                           void*, void*, void*, int, int, cudaStream_t);
+                                           void*, void*, void*, int, float* const*, int,
+                                           cudaStream_t);
 template cudaError_t launch_cv<float>(Ctl*, void* const*, void* const*, void* const*, SecWork,
                                       const void*, const void*, const void*, const void*, int,
                                       const void*, int, cudaStream_t);

@@ -1,0 +1,341 @@
+// Tensor-core (tcgen05 + TMA) kernels of the mixed form.
+//
+// k_tc_rowgemm: Out[j, 0:N] = In[j, 0:K] B + x[j] c for every row j of the state (the core
+// update C~ = C M^T + d u^T of Alg. 5 and V~ = V' V'' of Alg. 3, Sec. 3.4). In rows stream through
+// shared memory by TMA (128 rows x 32 FP32 per stage, 128-byte swizzle); B^T (N x K) is split
+// once per update into TF32 high/low parts and kept resident in shared memory; each 32-wide K chunk
+// issues 3 MMAs per K step of 8 (hi*hi + hi*lo + lo*hi, "3xTF32"), accumulating in FP32 in tensor
+// memory. The A low part is produced on chip by converter warps. The kernel is persistent: one CTA
+// per SM loops over 128-row tiles with two TMEM accumulators, so the epilogue of one tile overlaps
+// the loads and MMAs of the next.
+//
+// Warp roles (256 threads): warp 0 TMA producer, warp 1 TMEM owner + MMA issuer, warps 2-3 A
+// splitters, warps 4-7 epilogue (TMEM lanes 0-127 = the tile's rows).
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_common.cuh"
+
+namespace tk {
+
+using namespace tc;
+
+constexpr int TC_M = 128;        // rows per tile
+constexpr int TC_S = 2;          // pipeline stages
+constexpr int TC_BROWS = 16;     // rows of B^T per TMA box
+constexpr int TC_STAGE_BYTES = 2 * TC_M * TC_KC * 4;  // hi + lo of one A stage
+constexpr size_t TC_SMEM = (size_t)TC_S * TC_STAGE_BYTES + TC_BRES_BYTES + 1024 + 256;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait (1 s of wall time), sets *abort on timeout.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (long long i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63) {
+      if (*abort) return false;
+      if (gtimer() - t0 > 1000000000ull) { *abort = 1; return false; }
+    }
+  }
+}
+
+// Zero-padded expansion of the old C and V rows into the new spatial layout (PadWithZeros of
+// Alg. 4), written into the other buffer, only when a spatial rank grew and the tensor-core path
+// runs (the tensor-core kernel reads contiguous rows through TMA).
+__global__ void __launch_bounds__(256) k_cv_expand(const Ctl* __restrict__ ctl, const SecWork w,
+                                                  float* const* cbufs, float* const* vbufs) {
+  if (ctl->status) return;
+  if (!tc_cv_ok(ctl, w.meta[2]) || !spatial_grew(ctl)) return;
+  const int d = ctl->d, m = d - 1;
+  const int r = ctl->r[d - 1];
+  const int ldc = ctl->ldc;
+  long long Rn = 1;
+  for (int i = 0; i < m; ++i) Rn *= ctl->r[i];
+  const float* Ci = cbufs[ctl->cbuf];
+  const float* Vi = vbufs[ctl->cbuf];
+  float* Co = cbufs[ctl->cbuf ^ 1];
+  float* Vo = vbufs[ctl->cbuf ^ 1];
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long j = gw; j < Rn; j += nw) {
+    const long long jo = tk_map_new_to_old(j, ctl->r, ctl->rold, m);
+    for (int c = lane; c < r; c += 32) {
+      Co[j * ldc + c] = jo >= 0 ? Ci[jo * ldc + c] : 0.f;
+      Vo[j * ldc + c] = jo >= 0 ? Vi[jo * ldc + c] : 0.f;
+    }
+  }
+}
+
+struct TcRowGemmArgs {
+  float* buf0;          // the two state buffers (also the A tensor maps' bases)
+  float* buf1;
+  const float* cvec;    // rank-1 column vector (N)
+  const float* xvec;    // rank-1 row vector (rows); nullptr: D*_{d-1} in dbufs[xbuf]
+  float* const* dbufs;
+  int ldc;
+};
+
+__global__ void __launch_bounds__(256, 1) k_tc_rowgemm(Ctl* ctl, const SecWork w,
+                                                      const __grid_constant__ CUtensorMap mA0,
+                                                      const __grid_constant__ CUtensorMap mA1,
+                                                      const __grid_constant__ CUtensorMap mBhi,
+                                                      const __grid_constant__ CUtensorMap mBlo,
+                                                      TcRowGemmArgs a) {
+  if (ctl->status) return;
+  const int keep = w.meta[2];
+  if (!tc_cv_ok(ctl, keep)) return;
+  const int d = ctl->d;
+  const int K = ctl->r[d - 1];
+  const int Kc = (K + TC_KC - 1) / TC_KC;
+  const int Np = (keep + 15) / 16 * 16;
+  long long Rn = 1;
+  for (int i = 0; i < d - 1; ++i) Rn *= ctl->r[i];
+  const bool grown = spatial_grew(ctl);
+  const int inb = grown ? (ctl->cbuf ^ 1) : ctl->cbuf;
+  const CUtensorMap* mA = inb ? &mA1 : &mA0;
+  float* out = (inb ? a.buf0 : a.buf1);
+  const float* X = a.xvec ? a.xvec : a.dbufs[ctl->xbuf];
+  const long long ntiles = (Rn + TC_M - 1) / TC_M;
+
+  extern __shared__ __align__(1024) unsigned char tsm_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~uintptr_t(1023));
+  float* Ast = reinterpret_cast<float*>(base);                              // [S][2][M*KC]
+  float* Bhi = reinterpret_cast<float*>(base + TC_S * TC_STAGE_BYTES);      // [Kc][Np*KC]
+  float* Blo = Bhi + (size_t)Kc * Np * TC_KC;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_S * TC_STAGE_BYTES + TC_BRES_BYTES);
+  uint64_t* full = bars;
+  uint64_t* conv = bars + TC_S;
+  uint64_t* empty = bars + 2 * TC_S;
+  uint64_t* accfull = bars + 3 * TC_S;
+  uint64_t* accempty = accfull + 2;
+  uint64_t* bload = accempty + 2;
+  uint64_t* done = bload + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 64);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 128);
+    }
+    mbar_init(bload, 1);
+    mbar_init(done, 1);
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+    // ---------------- TMA producer (one thread; lanes 1-31 idle) ----------------
+    tma_prefetch(mA);
+    tma_prefetch(&mBhi);
+    tma_prefetch(&mBlo);
+    const uint32_t bbytes = (uint32_t)Kc * Np * TC_KC * 4 * 2;
+    mbar_arrive_expect_tx(bload, bbytes);
+    for (int kc = 0; kc < Kc; ++kc)
+      for (int n0 = 0; n0 < Np; n0 += TC_BROWS) {
+        tma_load_2d(&mBhi, bload, Bhi + ((size_t)kc * Np + n0) * TC_KC, kc * TC_KC, n0);
+        tma_load_2d(&mBlo, bload, Blo + ((size_t)kc * Np + n0) * TC_KC, kc * TC_KC, n0);
+      }
+    long long q = 0;
+    for (long long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+      for (int kc = 0; kc < Kc; ++kc, ++q) {
+        const int s = (int)(q % TC_S);
+        const uint32_t ph = (uint32_t)((q / TC_S) & 1);
+        if (!wait_bar(&empty[s], ph ^ 1, abort)) break;
+        mbar_arrive_expect_tx(&full[s], TC_M * TC_KC * 4);
+        tma_load_2d(mA, &full[s], Ast + (size_t)s * 2 * TC_M * TC_KC, kc * TC_KC, (int)(t * TC_M));
+      }
+    }
+    // drain: wait until the last issued stages were consumed before leaving
+    for (long long j = (q > TC_S ? q - TC_S : 0); j < q; ++j) {
+      const int s = (int)(j % TC_S);
+      wait_bar(&empty[s], (uint32_t)((j / TC_S) & 1), abort);
+    }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(TC_M, Np);
+      bool ok = wait_bar(bload, 0, abort);
+      long long q = 0;
+      int it = 0;
+      for (long long t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++it) {
+        const int b = it & 1;
+        if (!wait_bar(&accempty[b], (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(b * 256);
+        for (int kc = 0; kc < Kc; ++kc, ++q) {
+          const int s = (int)(q % TC_S);
+          if (!wait_bar(&conv[s], (uint32_t)((q / TC_S) & 1), abort)) { ok = false; break; }
+          tc_fence_after();
+          const uint64_t ahi = desc_sw128(Ast + (size_t)s * 2 * TC_M * TC_KC);
+          const uint64_t alo = desc_sw128(Ast + (size_t)s * 2 * TC_M * TC_KC + TC_M * TC_KC);
+          const uint64_t bhi = desc_sw128(Bhi + (size_t)kc * Np * TC_KC);
+          const uint64_t blo = desc_sw128(Blo + (size_t)kc * Np * TC_KC);
+#pragma unroll
+          for (int k4 = 0; k4 < TC_KC / 8; ++k4) {
+            const uint64_t o = (uint64_t)(k4 * 32) >> 4;   // 8 TF32 = 32 bytes per K step
+            mma_tf32(dt, ahi + o, bhi + o, idesc, (kc | k4) ? 1u : 0u);
+            mma_tf32(dt, ahi + o, blo + o, idesc, 1u);
+            mma_tf32(dt, alo + o, bhi + o, idesc, 1u);
+          }
+          tc_commit(&empty[s]);
+        }
+        if (!ok) break;
+        tc_commit(&accfull[b]);
+      }
+      tc_commit(done);
+      wait_bar(done, 0, abort);
+    }
+    __syncwarp();
+  } else if (warp == 2 || warp == 3) {
+    // ---------------- A splitters: hi = tf32(a) in place, lo = a - hi ----------------
+    const int ct = threadIdx.x - 64;   // 0..63
+    long long q = 0;
+    for (long long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+      for (int kc = 0; kc < Kc; ++kc, ++q) {
+        const int s = (int)(q % TC_S);
+        if (!wait_bar(&full[s], (uint32_t)((q / TC_S) & 1), abort)) break;
+        float4* hi = reinterpret_cast<float4*>(Ast + (size_t)s * 2 * TC_M * TC_KC);
+        float4* lo = hi + TC_M * TC_KC / 4;
+#pragma unroll 4
+        for (int i = ct; i < TC_M * TC_KC / 4; i += 64) {
+          float4 v = hi[i], h, l;
+          tf32_split(v.x, h.x, l.x);
+          tf32_split(v.y, h.y, l.y);
+          tf32_split(v.z, h.z, l.z);
+          tf32_split(v.w, h.w, l.w);
+          hi[i] = h;
+          lo[i] = l;
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(&conv[s]);
+      }
+      if (*abort) break;
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- epilogue: TMEM -> registers -> + x_j c -> global (full warps only) ----
+    const int wq = warp - 4;   // TMEM lane quarter
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int b = it & 1;
+      bool okw = wait_bar(&accfull[b], (uint32_t)((it >> 1) & 1), abort);
+      okw = __all_sync(0xffffffffu, okw);
+      if (!okw) break;
+      tc_fence_after();
+      const long long row = t * TC_M + wq * 32 + lane;
+      const bool live = row < Rn;
+      const float xj = live ? X[row] : 0.f;
+      float* orow = out + row * a.ldc;
+      for (int c0 = 0; c0 < Np; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * 256 + c0), v);
+        if (live) {
+          if (c0 + 32 <= keep) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+              float4 o;
+              o.x = v[i] + xj * a.cvec[c0 + i];
+              o.y = v[i + 1] + xj * a.cvec[c0 + i + 1];
+              o.z = v[i + 2] + xj * a.cvec[c0 + i + 2];
+              o.w = v[i + 3] + xj * a.cvec[c0 + i + 3];
+              *reinterpret_cast<float4*>(orow + c0 + i) = o;
+            }
+          } else {
+            for (int i = 0; i < 32 && c0 + i < keep; ++i) orow[c0 + i] = v[i] + xj * a.cvec[c0 + i];
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&accempty[b]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+  if (threadIdx.x == 0 && *abort) ctl->status = 5;   // TUCKER_ETIMEOUT
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D FP32 row-major matrix (rows x cols, row stride ld elements), box (box_cols x box_rows),
+// 128-byte swizzle, out-of-range elements read as zero.
+bool make_map_2d_f32(CUtensorMap* map, const void* base, long long rows, long long cols,
+                     long long ld, int box_cols, int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+size_t tc_rowgemm_smem() { return TC_SMEM; }
+
+cudaError_t launch_tc_cv(Ctl* ctl, SecWork w, const TcMaps& maps, void* const* cbufs_host,
+                         void* const* vbufs_host, void* const* d_cbufs, void* const* d_vbufs,
+                         const void* cu, const void* wv, const void* evec, void* const* dbufs,
+                         int ldc, int grid, cudaStream_t st) {
+  k_cv_expand<<<152 * 4, 256, 0, st>>>(ctl, w, (float* const*)d_cbufs, (float* const*)d_vbufs);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_rowgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    attr = true;
+  }
+  TcRowGemmArgs ac{(float*)cbufs_host[0], (float*)cbufs_host[1], (const float*)cu, nullptr,
+                   (float* const*)dbufs, ldc};
+  k_tc_rowgemm<<<grid, 256, TC_SMEM, st>>>(ctl, w, maps.c0, maps.c1, maps.bc_hi, maps.bc_lo, ac);
+  TcRowGemmArgs av{(float*)vbufs_host[0], (float*)vbufs_host[1], (const float*)wv,
+                   (const float*)evec, (float* const*)dbufs, ldc};
+  k_tc_rowgemm<<<grid, 256, TC_SMEM, st>>>(ctl, w, maps.v0, maps.v1, maps.bv_hi, maps.bv_lo, av);
+  return cudaGetLastError();
+}
+
+}  // namespace tk

@@ -1,6 +1,7 @@
 // Host-side launchers of the device kernels (one declaration per translation unit export).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,13 +64,27 @@ cudaError_t launch_secular_vectors(Ctl* ctl, const double* S, SecWork w, double*
                                    cudaStream_t st);
 template <typename TW>
 cudaError_t launch_factor(Ctl* ctl, double* const* udbufs, SecWork w, const double* es, void* Bc,
-                          void* cu, void* Bv, void* wv, int ldb, int grid_small, cudaStream_t st);
+                          void* cu, void* Bv, void* wv, int ldb, float* const* bsplit,
+                          int grid_small, cudaStream_t st);
 template <typename TW>
 cudaError_t launch_cv(Ctl* ctl, void* const* dbufs, void* const* cbufs, void* const* vbufs,
                       SecWork w, const void* Bc, const void* cu, const void* Bv, const void* wv,
                       int ldb, const void* evec, int grid_cv, cudaStream_t st);
 cudaError_t launch_begin(Ctl* ctl, cudaStream_t st);
 cudaError_t launch_end(Ctl* ctl, const double* Snew, double* S, cudaStream_t st);
+
+// ---- k_tc.cu ----
+struct TcMaps {
+  CUtensorMap c0, c1, v0, v1;           // state buffers: rows x ldc FP32, box 32 x 128
+  CUtensorMap bc_hi, bc_lo, bv_hi, bv_lo;  // B^T (N x K) TF32 splits, row stride 512, box 32 x 16
+};
+bool make_map_2d_f32(CUtensorMap* map, const void* base, long long rows, long long cols,
+                     long long ld, int box_cols, int box_rows);
+size_t tc_rowgemm_smem();
+cudaError_t launch_tc_cv(Ctl* ctl, SecWork w, const TcMaps& maps, void* const* cbufs_host,
+                         void* const* vbufs_host, void* const* d_cbufs, void* const* d_vbufs,
+                         const void* cu, const void* wv, const void* evec, void* const* dbufs,
+                         int ldc, int grid, cudaStream_t st);
 
 // ---- k_misc.cu ----
 template <typename TW>
