@@ -75,6 +75,10 @@ struct tucker_state {
   float** d_bsplit = nullptr;
   TcMaps maps{};
   bool tc = false;               // tensor-core path available (mixed form)
+  float* usplit[4]{};            // U_1 TF32 hi/lo copies for the tensor-core mode-1 pass
+  float** d_usplit = nullptr;
+  TcProjMaps pmaps{};
+  bool tcp = false;              // tensor-core mode-1 pass available (mixed form, FP32 slices)
   int nsm = 152;
   void* cu = nullptr;
   void* wv = nullptr;
@@ -307,6 +311,21 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
     ok &= make_map_2d_f32(&s->maps.bv_lo, s->bsplit[3], 512, 512, 512, 32, 16);
     s->tc = ok;
   }
+  if (tw == 4 && s->tx == 4 && d >= 2 && s->n[0] % 4 == 0 && s->n[0] <= 256) {
+    const int n1 = s->n[0];
+    CK(dalloc(s, (void**)&s->usplit[0], sizeof(float) * n1 * s->cap[0]));
+    CK(dalloc(s, (void**)&s->usplit[1], sizeof(float) * n1 * s->cap[0]));
+    CK(dalloc(s, (void**)&s->usplit[2], sizeof(float) * n1 * 64));
+    CK(dalloc(s, (void**)&s->usplit[3], sizeof(float) * n1 * 64));
+    CK(dalloc(s, (void**)&s->d_usplit, sizeof(void*) * 4));
+    CK(cudaMemcpy(s->d_usplit, s->usplit, sizeof(void*) * 4, cudaMemcpyHostToDevice));
+    bool ok = true;
+    ok &= make_map_2d_f32(&s->pmaps.uhi, s->usplit[0], s->cap[0], n1, n1, 32, 16);
+    ok &= make_map_2d_f32(&s->pmaps.ulo, s->usplit[1], s->cap[0], n1, n1, 32, 16);
+    ok &= make_map_2d_f32(&s->pmaps.urhi, s->usplit[2], n1, 64, 64, 32, 16);
+    ok &= make_map_2d_f32(&s->pmaps.urlo, s->usplit[3], n1, 64, 64, 32, 16);
+    s->tcp = ok;
+  }
   return TUCKER_OK;
 }
 
@@ -401,10 +420,11 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
     if (k == 0) e = launch_resid_gram<TX, double>(s->ctl, k, nv, X, d_ib, nullptr, 0, s->gpart, pairs, chunks, 1, st);
     else e = launch_resid_gram<TW, double>(s->ctl, k, nv, X, d_ib, nullptr, 0, s->gpart, pairs, chunks, 1, st);
     if (e == cudaSuccess) e = launch_gram_reduce(s->ctl, k, s->gpart, pairs, chunks, s->G, 1, st);
-    if (e == cudaSuccess) e = launch_eig<double>(s->ctl, k, 1, s->G, s->eAw, s->eZ, s->eLD, s->eW, s->elam, s->mcap, st);
+    if (e == cudaSuccess) e = launch_eig<double>(s->ctl, k, 1, s->G, s->eAw, s->eZ, s->eLD, s->eW, s->elam, s->mcap, nv, st);
     double* Uk = (k == d - 1) ? Utmp : s->U[k];
     void* Uwk = (k == d - 1) ? (s->tw == 8 ? (void*)Utmp : Uwtmp) : s->Uw[k];
     if (e == cudaSuccess) e = launch_append<TW>(s->ctl, k, 1, s->eW, Uk, (s->tw == 8) ? nullptr : Uwk, nv, nv, st);
+    if (e == cudaSuccess && k == 0 && s->tcp) e = launch_split_u1(s->ctl, 0, s->U[0], s->n[0], s->usplit, st);
     if (e != cudaSuccess) { set_err(s, "CUDA error: %s", cudaGetErrorString(e)); rc = TUCKER_ECUDA; break; }
     s->last_stream = st;
     rc = sync_ctl(s);
@@ -463,6 +483,11 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
     {
       // pass A: P_k = D*_{k-1} x_k U_k^T, ||E_k||^2 (and ||Y||^2 for k = 0); Alg. 4's branch
       PhaseMark pm(s, st, k == 0 ? TK_PH_PROJ1 : TK_PH_PROJN);
+      if (k == 0 && s->tcp) {
+        CK(launch_tc_proj1(s->ctl, 1, 0, (const float*)Y, s->N / n, n, s->pmaps, s->d_dbufs, 1,
+                           s->part_e2, s->part_y2, kGridP, s->nsm, st));
+        launches += 1;
+      }
       if (k == 0)
         CK((launch_proj<TX, TW>(s->ctl, k, 1, 0, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], s->part_e2,
                                 s->part_y2, kGridP, st)));
@@ -482,8 +507,14 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
         CK((launch_resid_gram<TW, TW>(s->ctl, k, n, Y, s->d_dbufs, s->Uw[k], n, s->gpart, pairs,
                                       chunks, 0, st)));
       CK(launch_gram_reduce(s->ctl, k, s->gpart, pairs, chunks, s->G, 0, st));
-      CK(launch_eig<TE>(s->ctl, k, 0, s->G, s->eAw, s->eZ, s->eLD, s->eW, nullptr, s->mcap, st));
+      CK(launch_eig<TE>(s->ctl, k, 0, s->G, s->eAw, s->eZ, s->eLD, s->eW, nullptr, s->mcap, n, st));
       CK(launch_append<TW>(s->ctl, k, 0, s->eW, s->U[k], (s->tw == 8) ? nullptr : s->Uw[k], n, n, st));
+      if (k == 0 && s->tcp) {
+        CK(launch_split_u1(s->ctl, 1, s->U[0], n, s->usplit, st));
+        CK(launch_tc_proj1(s->ctl, 0, 1, (const float*)Y, s->N / n, n, s->pmaps, s->d_dbufs, 2,
+                           nullptr, nullptr, kGridP, s->nsm, st));
+        launches += 2;
+      }
       if (k == 0)
         CK((launch_proj<TX, TW>(s->ctl, k, 2, 1, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], nullptr,
                                 nullptr, kGridP, st)));

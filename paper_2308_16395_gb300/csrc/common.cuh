@@ -179,3 +179,18 @@ __device__ __forceinline__ bool spatial_grew(const Ctl* ctl) {
     if (ctl->r[k] != ctl->rold[k]) return true;
   return false;
 }
+
+// ---- tensor-core path of the mode-1 projection (mixed form, FP32 slices) ----
+#define TP_RMAX 64                      // largest padded r_1 handled on the tensor cores
+#define TP_SMEM_BUDGET (224 * 1024)
+
+// Mode-1 pass on the tensor cores: mixed form with FP32 slices, n_1 a multiple of 4 (TMA row
+// stride) and <= 256, padded rank <= 64, resident U_1 (n_1 x ceil32(r)) fits the budget.
+__device__ __forceinline__ bool tc_proj1_ok(const Ctl* c, int r) {
+  if (c->tw != 4 || c->tx != 4 || c->init_nt != 0) return false;
+  const int n1 = c->n[0];
+  if (n1 % 4 != 0 || n1 > 256 || r < 1) return false;
+  const int rp = (r + 15) / 16 * 16;
+  if (rp > TP_RMAX) return false;
+  return true;
+}

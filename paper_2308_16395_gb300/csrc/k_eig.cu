@@ -49,15 +49,18 @@ struct EigArgs {
 
 // mode 0: residual Gram of spatial mode k (Alg. 4), predicated on ctl->grew[k].
 // mode 1: data Gram of mode k in the batch ST-HOSVD (Alg. 2): r >= 1.
+// use_smem: the n x n working matrix lives in (dynamic) shared memory instead of global memory.
 template <typename TE>
-__global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, EigArgs ea) {
+__global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, EigArgs ea,
+                                                    int use_smem) {
+  extern __shared__ __align__(16) unsigned char eig_dyn[];
   if (ctl->status) return;
   if (mode == 0 && !ctl->grew[k]) return;
   const int d = ctl->d;
   const int n = (k == d - 1) ? ctl->init_nt : ctl->n[k];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
-  TE* A = reinterpret_cast<TE*>(ea.Aw);
+  TE* A = use_smem ? reinterpret_cast<TE*>(eig_dyn) : reinterpret_cast<TE*>(ea.Aw);
   __shared__ TE sa[TK_N_MAX], sb[TK_N_MAX], sb2[TK_N_MAX], stau[TK_N_MAX], slam[TK_N_MAX];
   __shared__ TE sv[TK_N_MAX], sp[TK_N_MAX];
   __shared__ TE tred[32];
@@ -319,11 +322,17 @@ __global__ void __launch_bounds__(1024) k_append_factor(Ctl* ctl, int k, int mod
   if (tid == 0 && mode == 0) ctl->r[k] = r0 + m;
 }
 
+constexpr size_t EIG_SMEM_MAX = 180 * 1024;
+
 template <typename TE>
 cudaError_t launch_eig(Ctl* ctl, int k, int mode, const double* G, void* Aw, void* Z, void* LD,
-                       double* W, double* lam, int mcap, cudaStream_t st) {
+                       double* W, double* lam, int mcap, int n, cudaStream_t st) {
   EigArgs ea{G, Aw, Z, LD, W, lam, mcap};
-  k_eig_topk<TE><<<1, EIG_NT, 0, st>>>(ctl, k, mode, ea);
+  const size_t need = (size_t)n * n * sizeof(TE);
+  const int use = need <= EIG_SMEM_MAX ? 1 : 0;
+  const size_t sm = use ? need : 0;
+  if (use) cudaFuncSetAttribute(k_eig_topk<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_eig_topk<TE><<<1, EIG_NT, sm, st>>>(ctl, k, mode, ea, use);
   return cudaGetLastError();
 }
 
@@ -335,9 +344,9 @@ cudaError_t launch_append(Ctl* ctl, int k, int mode, const double* W, double* U,
 }
 
 template cudaError_t launch_eig<double>(Ctl*, int, int, const double*, void*, void*, void*, double*,
-                                        double*, int, cudaStream_t);
+                                        double*, int, int, cudaStream_t);
 template cudaError_t launch_eig<float>(Ctl*, int, int, const double*, void*, void*, void*, double*,
-                                       double*, int, cudaStream_t);
+                                       double*, int, int, cudaStream_t);
 template cudaError_t launch_append<double>(Ctl*, int, int, const double*, double*, void*, int, int,
                                            cudaStream_t);
 template cudaError_t launch_append<float>(Ctl*, int, int, const double*, double*, void*, int, int,

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
   const long long A = view_A(ctl, k);
   const long long B = view_B(ctl, k);
   const int r = ctl->r[k];
+  if (k == 0 && tc_proj1_ok(ctl, r)) return;   // the tensor-core kernel does this pass
   const long long F = A * B;
   const int xb = ctl->xbuf;
   const TX* X = (xb < 0) ? Xext : reinterpret_cast<const TX*>(dbufs[xb]);

@@ -339,3 +339,345 @@ cudaError_t launch_tc_cv(Ctl* ctl, SecWork w, const TcMaps& maps, void* const* c
 }
 
 }  // namespace tk
+
+namespace tk {
+
+// =============================================================================================
+// k_tc_proj1: the mode-1 pass of Alg. 4 on the tensor cores, fused.
+//   MMA1  P = Y_(1)^T U_1  as rows: P[f, :] = Y[f, :] U_1 (f = mode-1 fiber, K = n_1), 3xTF32,
+//         Y tiles by TMA, U_1 chunks (TF32 hi/lo) streamed with them; P accumulates in TMEM.
+//   epi-1 P -> global (the output D*), P split in place into TF32 hi (TMEM cols 0..63) and lo
+//         (cols 64..127).
+//   MMA2  (RESID) Rec = P U_1^T with A = P read from tensor memory, B = U_1 rows resident in
+//         shared memory, 3xTF32; Rec in TMEM cols 128..128+n_1.
+//   epi-2 (RESID) E = Y - Rec with Y re-read (L2-resident), ||E||^2 and ||Y||^2 (compensated,
+//         per-block partials).
+// =============================================================================================
+constexpr int TP_STAGE = 48 * 1024;                // Y hi | Y lo | U chunk hi | U chunk lo
+constexpr int TP_S = 2;
+constexpr size_t TP_SMEM = (size_t)TP_S * TP_STAGE + 128 * 1024 + 1024 + 256;
+
+struct TcProjArgs {
+  float* const* dbufs;
+  int out_off;
+  double* part_e2;
+  double* part_y2;
+  int nparts;
+  const float* Y;
+};
+
+template <bool RESID>
+__global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl, int pred,
+                                                    const __grid_constant__ CUtensorMap mY,
+                                                    const __grid_constant__ CUtensorMap mUhi,
+                                                    const __grid_constant__ CUtensorMap mUlo,
+                                                    const __grid_constant__ CUtensorMap mUrhi,
+                                                    const __grid_constant__ CUtensorMap mUrlo,
+                                                    TcProjArgs a) {
+  if (ctl->status) return;
+  if (pred && !ctl->grew[0]) return;
+  const int r = ctl->r[0];
+  if (!tc_proj1_ok(ctl, r)) return;
+  const int d = ctl->d;
+  const int n1 = ctl->n[0];
+  long long F = 1;
+  for (int i = 1; i < d - 1; ++i) F *= ctl->n[i];
+  const int Rp = (r + 15) / 16 * 16;
+  const int n1p = (n1 + 15) / 16 * 16;
+  const int Kc1 = (n1 + TC_KC - 1) / TC_KC;
+  const int Kc2 = (Rp + TC_KC - 1) / TC_KC;
+  const long long ntiles = (F + TC_M - 1) / TC_M;
+  float* P = a.dbufs[(ctl->xbuf + a.out_off + 3) % 3];
+
+  extern __shared__ __align__(1024) unsigned char psm_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(psm_raw) + 1023) & ~uintptr_t(1023));
+  float* B2hi = reinterpret_cast<float*>(base + TP_S * TP_STAGE);   // [Kc2][n1p][32]
+  float* B2lo = B2hi + (size_t)Kc2 * n1p * TC_KC;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TP_S * TP_STAGE + 128 * 1024);
+  uint64_t* full = bars;
+  uint64_t* conv = bars + TP_S;
+  uint64_t* empty = bars + 2 * TP_S;
+  uint64_t* d1full = bars + 3 * TP_S;
+  uint64_t* pready = d1full + 1;
+  uint64_t* d2full = pready + 1;
+  uint64_t* d2free = d2full + 1;
+  uint64_t* mma2done = d2free + 1;
+  uint64_t* bload = mma2done + 1;
+  uint64_t* done = bload + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* red = reinterpret_cast<double*>(tmem_slot + 4);   // [8] doubles
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TP_S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 64);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(d1full, 1);
+    mbar_init(pready, 128);
+    mbar_init(d2full, 1);
+    mbar_init(d2free, 128);
+    mbar_init(mma2done, 1);
+    mbar_init(bload, 1);
+    mbar_init(done, 1);
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tD1 = tmem, tDlo = tmem + 64, tD2 = tmem + 128;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      tma_prefetch(&mY);
+      tma_prefetch(&mUhi);
+      tma_prefetch(&mUlo);
+      if (RESID) {
+        tma_prefetch(&mUrhi);
+        tma_prefetch(&mUrlo);
+        mbar_arrive_expect_tx(bload, (uint32_t)Kc2 * n1p * TC_KC * 4 * 2);
+        for (int kc = 0; kc < Kc2; ++kc)
+          for (int n0 = 0; n0 < n1p; n0 += 16) {
+            tma_load_2d(&mUrhi, bload, B2hi + ((size_t)kc * n1p + n0) * TC_KC, kc * TC_KC, n0);
+            tma_load_2d(&mUrlo, bload, B2lo + ((size_t)kc * n1p + n0) * TC_KC, kc * TC_KC, n0);
+          }
+      }
+      long long q = 0;
+      for (long long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+        for (int kc = 0; kc < Kc1; ++kc, ++q) {
+          const int s = (int)(q % TP_S);
+          if (!wait_bar(&empty[s], (uint32_t)(((q / TP_S) & 1) ^ 1), abort)) break;
+          unsigned char* st = base + (size_t)s * TP_STAGE;
+          mbar_arrive_expect_tx(&full[s], (uint32_t)(TC_M * TC_KC * 4 + Rp * TC_KC * 4 * 2));
+          tma_load_2d(&mY, &full[s], st, kc * TC_KC, (int)(t * TC_M));
+          for (int n0 = 0; n0 < Rp; n0 += 16) {
+            tma_load_2d(&mUhi, &full[s], st + 32 * 1024 + n0 * 128, kc * TC_KC, n0);
+            tma_load_2d(&mUlo, &full[s], st + 40 * 1024 + n0 * 128, kc * TC_KC, n0);
+          }
+        }
+      }
+      for (long long j = (q > TP_S ? q - TP_S : 0); j < q; ++j)
+        wait_bar(&empty[j % TP_S], (uint32_t)((j / TP_S) & 1), abort);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t id1 = idesc_tf32(TC_M, Rp);
+      const uint32_t id2 = idesc_tf32(TC_M, n1p);
+      bool ok = RESID ? wait_bar(bload, 0, abort) : true;
+      long long q = 0;
+      int it = 0;
+      for (long long t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++it) {
+        // D1 may be overwritten once the previous tile's P was consumed
+        if (it > 0) {
+          if (RESID) ok = wait_bar(mma2done, (uint32_t)((it - 1) & 1), abort);
+          else ok = wait_bar(pready, (uint32_t)((it - 1) & 1), abort);
+          if (!ok) break;
+        }
+        for (int kc = 0; kc < Kc1; ++kc, ++q) {
+          const int s = (int)(q % TP_S);
+          if (!wait_bar(&conv[s], (uint32_t)((q / TP_S) & 1), abort)) { ok = false; break; }
+          tc_fence_after();
+          unsigned char* st = base + (size_t)s * TP_STAGE;
+          const uint64_t ahi = desc_sw128(st), alo = desc_sw128(st + 16 * 1024);
+          const uint64_t bhi = desc_sw128(st + 32 * 1024), blo = desc_sw128(st + 40 * 1024);
+#pragma unroll
+          for (int k4 = 0; k4 < TC_KC / 8; ++k4) {
+            const uint64_t o = (uint64_t)(k4 * 32) >> 4;
+            mma_tf32(tD1, ahi + o, bhi + o, id1, (kc | k4) ? 1u : 0u);
+            mma_tf32(tD1, ahi + o, blo + o, id1, 1u);
+            mma_tf32(tD1, alo + o, bhi + o, id1, 1u);
+          }
+          tc_commit(&empty[s]);
+        }
+        if (!ok) break;
+        tc_commit(d1full);
+        if (RESID) {
+          if (!wait_bar(pready, (uint32_t)(it & 1), abort)) break;
+          if (!wait_bar(d2free, (uint32_t)((it & 1) ^ 1), abort)) break;
+          tc_fence_after();
+          for (int k8 = 0; k8 < Rp / 8; ++k8) {
+            const int kc = k8 >> 2;
+            const uint64_t o = (uint64_t)((k8 & 3) * 32) >> 4;
+            const uint64_t bhi = desc_sw128(B2hi + (size_t)kc * n1p * TC_KC) + o;
+            const uint64_t blo = desc_sw128(B2lo + (size_t)kc * n1p * TC_KC) + o;
+            mma_tf32_ts(tD2, tD1 + 8 * k8, bhi, id2, k8 ? 1u : 0u);
+            mma_tf32_ts(tD2, tD1 + 8 * k8, blo, id2, 1u);
+            mma_tf32_ts(tD2, tDlo + 8 * k8, bhi, id2, 1u);
+          }
+          tc_commit(d2full);
+          tc_commit(mma2done);
+        }
+      }
+      tc_commit(done);
+      wait_bar(done, 0, abort);
+      (void)Kc2;
+    }
+    __syncwarp();
+  } else if (warp == 2 || warp == 3) {
+    // ---------------- Y splitters ----------------
+    const int ct = threadIdx.x - 64;
+    long long q = 0;
+    for (long long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+      for (int kc = 0; kc < Kc1; ++kc, ++q) {
+        const int s = (int)(q % TP_S);
+        if (!wait_bar(&full[s], (uint32_t)((q / TP_S) & 1), abort)) break;
+        float4* hi = reinterpret_cast<float4*>(base + (size_t)s * TP_STAGE);
+        float4* lo = hi + TC_M * TC_KC / 4;
+#pragma unroll 4
+        for (int i = ct; i < TC_M * TC_KC / 4; i += 64) {
+          float4 v = hi[i], h, l;
+          tf32_split(v.x, h.x, l.x);
+          tf32_split(v.y, h.y, l.y);
+          tf32_split(v.z, h.z, l.z);
+          tf32_split(v.w, h.w, l.w);
+          hi[i] = h;
+          lo[i] = l;
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(&conv[s]);
+      }
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- epilogue ----------------
+    const int wq = warp - 4;
+    const uint32_t lq = (uint32_t)(wq * 32) << 16;
+    KahanF eacc, yacc;
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      bool okw = wait_bar(d1full, (uint32_t)(it & 1), abort);
+      okw = __all_sync(0xffffffffu, okw);
+      if (!okw) break;
+      tc_fence_after();
+      const long long f = t * TC_M + wq * 32 + lane;
+      const bool live = f < F;
+      for (int c0 = 0; c0 < Rp; c0 += 32) {
+        float v[32];
+        tmem_ld32(tD1 + lq + c0, v);
+        if (live) {
+          float* prow = P + f * r;
+          for (int i = 0; i < 32 && c0 + i < r; ++i) prow[c0 + i] = v[i];
+        }
+        if (RESID) {
+          float h[32], l[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) tf32_split(v[i], h[i], l[i]);
+          tmem_st32(tD1 + lq + c0, h);
+          tmem_st32(tDlo + lq + c0, l);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(pready);
+      if (RESID) {
+        okw = wait_bar(d2full, (uint32_t)(it & 1), abort);
+        okw = __all_sync(0xffffffffu, okw);
+        if (!okw) break;
+        tc_fence_after();
+        const float* yrow = a.Y + f * n1;
+        for (int c0 = 0; c0 < n1p; c0 += 32) {
+          float v[32];
+          tmem_ld32(tD2 + lq + c0, v);
+          if (live) {
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+              if (c0 + i < n1) {
+                const float y = yrow[c0 + i];
+                const float e = y - v[i];
+                eacc.add(e * e);
+                yacc.add(y * y);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(d2free);
+      }
+    }
+    if (RESID) {
+      double se = warp_sum(eacc.value()), sy = warp_sum(yacc.value());
+      if (lane == 0) { red[wq] = se; red[4 + wq] = sy; }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (wq == 0 && lane == 0) {
+        const double te = red[0] + red[1] + red[2] + red[3];
+        const double ty = red[4] + red[5] + red[6] + red[7];
+        for (int j = blockIdx.x; j < a.nparts; j += gridDim.x) {
+          a.part_e2[j] = (j == (int)blockIdx.x) ? te : 0.0;
+          if (a.part_y2) a.part_y2[j] = (j == (int)blockIdx.x) ? ty : 0.0;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+  if (threadIdx.x == 0 && *abort) const_cast<Ctl*>(ctl)->status = 5;
+}
+
+// Split copies of U_1 for the tensor-core pass (after the initial ST-HOSVD and after growth):
+// column-major (n_1 x cap, as the FP32 work copy) and row-major (n_1 x 64) TF32 hi/lo parts.
+__global__ void k_split_u1(const Ctl* ctl, int pred, const double* U, int ldu, float* uhi,
+                           float* ulo, float* urhi, float* urlo) {
+  if (ctl->status) return;
+  if (pred && !ctl->grew[0]) return;
+  const int n1 = ctl->n[0];
+  const int r = ctl->r[0];
+  const int cap = ctl->cap[0];
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < (long long)n1 * cap;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(L % n1), i = (int)(L / n1);
+    const float v = (i < r) ? (float)U[(long long)i * ldu + j] : 0.f;
+    float h, l;
+    tf32_split(v, h, l);
+    uhi[L] = h;
+    ulo[L] = l;
+    if (i < TP_RMAX) {
+      urhi[(long long)j * TP_RMAX + i] = h;
+      urlo[(long long)j * TP_RMAX + i] = l;
+    }
+  }
+}
+
+cudaError_t launch_split_u1(const Ctl* ctl, int pred, const double* U, int ldu, float* const* sp,
+                            cudaStream_t st) {
+  k_split_u1<<<64, 256, 0, st>>>(ctl, pred, U, ldu, sp[0], sp[1], sp[2], sp[3]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_proj1(const Ctl* ctl, int resid, int pred, const float* Y, long long F,
+                            int n1, const TcProjMaps& m, void* const* dbufs, int out_off,
+                            double* part_e2, double* part_y2, int nparts, int grid,
+                            cudaStream_t st) {
+  CUtensorMap mY;
+  if (!make_map_2d_f32(&mY, Y, F, n1, n1, 32, 128)) return cudaErrorInvalidValue;
+  TcProjArgs a{(float* const*)dbufs, out_off, part_e2, part_y2, nparts, Y};
+  if (resid) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_tc_proj1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM);
+      attr = true;
+    }
+    k_tc_proj1<true><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_tc_proj1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM);
+      attr = true;
+    }
+    k_tc_proj1<false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tk

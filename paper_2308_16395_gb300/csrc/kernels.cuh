@@ -34,7 +34,7 @@ cudaError_t launch_norm2(const void* X, long long N, double* part, int grid, cud
 // ---- k_eig.cu ----
 template <typename TE>
 cudaError_t launch_eig(Ctl* ctl, int k, int mode, const double* G, void* Aw, void* Z, void* LD,
-                       double* W, double* lam, int mcap, cudaStream_t st);
+                       double* W, double* lam, int mcap, int n, cudaStream_t st);
 template <typename TW>
 cudaError_t launch_append(Ctl* ctl, int k, int mode, const double* W, double* U, void* Uw, int ldu,
                           int n, cudaStream_t st);
@@ -81,6 +81,16 @@ struct TcMaps {
 bool make_map_2d_f32(CUtensorMap* map, const void* base, long long rows, long long cols,
                      long long ld, int box_cols, int box_rows);
 size_t tc_rowgemm_smem();
+struct TcProjMaps {
+  CUtensorMap uhi, ulo;     // U_1 TF32 splits, column-major n_1 x cap (rows of B1 = columns of U)
+  CUtensorMap urhi, urlo;   // U_1 TF32 splits, row-major n_1 x 64
+};
+cudaError_t launch_split_u1(const Ctl* ctl, int pred, const double* U, int ldu, float* const* sp,
+                            cudaStream_t st);
+cudaError_t launch_tc_proj1(const Ctl* ctl, int resid, int pred, const float* Y, long long F,
+                            int n1, const TcProjMaps& m, void* const* dbufs, int out_off,
+                            double* part_e2, double* part_y2, int nparts, int grid,
+                            cudaStream_t st);
 cudaError_t launch_tc_cv(Ctl* ctl, SecWork w, const TcMaps& maps, void* const* cbufs_host,
                          void* const* vbufs_host, void* const* d_cbufs, void* const* d_vbufs,
                          const void* cu, const void* wv, const void* evec, void* const* dbufs,
