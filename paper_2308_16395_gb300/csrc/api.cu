@@ -79,6 +79,7 @@ struct tucker_state {
   float** d_usplit = nullptr;
   TcProjMaps pmaps{};
   bool tcp = false;              // tensor-core mode-1 pass available (mixed form, FP32 slices)
+  float* et = nullptr;           // E^T of mode 1 (n_1 x F) for the tensor-core Gram
   int nsm = 152;
   void* cu = nullptr;
   void* wv = nullptr;
@@ -263,7 +264,14 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
   CK(dalloc(s, (void**)&s->Snew, sizeof(double) * kSecMax));
   CK(dalloc(s, (void**)&s->part_e2, sizeof(double) * 4096));
   CK(dalloc(s, (void**)&s->part_y2, sizeof(double) * 4096));
-  CK(dalloc(s, (void**)&s->gpart, sizeof(double) * (size_t)(kGramBlocks + 64) * 4096));
+  {
+    int dev0 = 0, nsm0 = 152;
+    CK(cudaGetDevice(&dev0));
+    CK(cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0));
+    // SIMT residual Gram tiles, or the tensor-core split-K blocks (<= nsm x 128 x 256)
+    const size_t g1 = (size_t)(kGramBlocks + 64) * 4096, g2 = (size_t)nsm0 * 128 * 256;
+    CK(dalloc(s, (void**)&s->gpart, sizeof(double) * std::max(g1, g2)));
+  }
   CK(dalloc(s, (void**)&s->G, sizeof(double) * (size_t)s->nmax * s->nmax));
   CK(dalloc(s, &s->eAw, sizeof(double) * (size_t)s->nmax * s->nmax));
   CK(dalloc(s, &s->eZ, sizeof(double) * (size_t)s->nmax * s->mcap));
@@ -311,7 +319,8 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
     ok &= make_map_2d_f32(&s->maps.bv_lo, s->bsplit[3], 512, 512, 512, 32, 16);
     s->tc = ok;
   }
-  if (tw == 4 && s->tx == 4 && d >= 2 && s->n[0] % 4 == 0 && s->n[0] <= 256) {
+  if (tw == 4 && s->tx == 4 && d >= 2 && s->n[0] % 4 == 0 && s->n[0] <= 256 &&
+      (s->N / s->n[0]) % 4 == 0) {
     const int n1 = s->n[0];
     CK(dalloc(s, (void**)&s->usplit[0], sizeof(float) * n1 * s->cap[0]));
     CK(dalloc(s, (void**)&s->usplit[1], sizeof(float) * n1 * s->cap[0]));
@@ -324,6 +333,7 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
     ok &= make_map_2d_f32(&s->pmaps.ulo, s->usplit[1], s->cap[0], n1, n1, 32, 16);
     ok &= make_map_2d_f32(&s->pmaps.urhi, s->usplit[2], n1, 64, 64, 32, 16);
     ok &= make_map_2d_f32(&s->pmaps.urlo, s->usplit[3], n1, 64, 64, 32, 16);
+    CK(dalloc(s, (void**)&s->et, sizeof(float) * (size_t)s->N));
     s->tcp = ok;
   }
   return TUCKER_OK;
@@ -485,7 +495,7 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       PhaseMark pm(s, st, k == 0 ? TK_PH_PROJ1 : TK_PH_PROJN);
       if (k == 0 && s->tcp) {
         CK(launch_tc_proj1(s->ctl, 1, 0, (const float*)Y, s->N / n, n, s->pmaps, s->d_dbufs, 1,
-                           s->part_e2, s->part_y2, kGridP, s->nsm, st));
+                           s->part_e2, s->part_y2, kGridP, nullptr, s->nsm, st));
         launches += 1;
       }
       if (k == 0)
@@ -500,6 +510,13 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       // ||E_k|| > eps: residual Gram, eig + rank cut (Alg. 1), augmentation, then
       // pass C: D*_k = D*_{k-1} x_k U~_k^T (= Concatenate(P_k, L_k), App. C)
       PhaseMark pm(s, st, TK_PH_GROW);
+      if (k == 0 && s->tcp) {
+        // residual E^T of mode 1, then its Gram on the tensor cores (only if mode 1 grew)
+        CK(launch_tc_proj1(s->ctl, 2, 1, (const float*)Y, s->N / n, n, s->pmaps, s->d_dbufs, 1,
+                           nullptr, nullptr, kGridP, s->et, s->nsm, st));
+        CK(launch_tc_gram1(s->ctl, s->et, s->N / n, n, s->gpart, s->G, s->nsm, st));
+        launches += 3;
+      }
       if (k == 0)
         CK((launch_resid_gram<TX, TW>(s->ctl, k, n, Y, s->d_dbufs, s->Uw[k], n, s->gpart, pairs,
                                       chunks, 0, st)));
@@ -512,7 +529,7 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       if (k == 0 && s->tcp) {
         CK(launch_split_u1(s->ctl, 1, s->U[0], n, s->usplit, st));
         CK(launch_tc_proj1(s->ctl, 0, 1, (const float*)Y, s->N / n, n, s->pmaps, s->d_dbufs, 2,
-                           nullptr, nullptr, kGridP, s->nsm, st));
+                           nullptr, nullptr, kGridP, nullptr, s->nsm, st));
         launches += 2;
       }
       if (k == 0)

@@ -141,6 +141,19 @@ struct KahanD {
 };
 template <> struct AccOf<double> { typedef KahanD type; };
 
+// 32-bit version of tk_map_new_to_old (core sizes stay below 2^31).
+__device__ __forceinline__ int map_new_to_old32(int j, const int* rn, const int* ro, int m) {
+  int jo = 0, stride = 1;
+  for (int k = 0; k < m; ++k) {
+    const int ik = j % rn[k];
+    j /= rn[k];
+    if (ik >= ro[k]) return -1;
+    jo += ik * stride;
+    stride *= ro[k];
+  }
+  return jo;
+}
+
 // Map a row index of a compact spatial tensor with dims `rn` (new) to the row index in the
 // compact layout with dims `ro` (old); returns -1 if the row is a zero-padded one (some i_k >=
 // ro[k]). Implements PadWithZeros (Eqs. pad_core_with_zeros, pad_singular_vectors_with_zeros).

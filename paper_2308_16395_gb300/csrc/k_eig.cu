@@ -24,14 +24,19 @@ template <> struct Eps<float> { static __device__ float u() { return 5.9604645e-
 
 // Sturm count: number of eigenvalues of the tridiagonal (a, b) strictly below x.
 template <typename TE>
+__device__ __forceinline__ TE sturm_div(TE a, TE b) { return a / b; }
+template <>
+__device__ __forceinline__ float sturm_div<float>(float a, float b) { return __fdividef(a, b); }
+
+template <typename TE>
 __device__ int sturm_count(const TE* a, const TE* b2, int n, TE x, TE pivmin) {
   int cnt = 0;
   TE q = a[0] - x;
-  if (fabs((double)q) < (double)pivmin) q = -pivmin;
+  if (fabs(q) < pivmin) q = -pivmin;
   if (q < TE(0)) ++cnt;
   for (int i = 1; i < n; ++i) {
-    q = (a[i] - x) - b2[i - 1] / q;
-    if (fabs((double)q) < (double)pivmin) q = -pivmin;
+    q = (a[i] - x) - sturm_div(b2[i - 1], q);
+    if (fabs(q) < pivmin) q = -pivmin;
     if (q < TE(0)) ++cnt;
   }
   return cnt;

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
   TW* Us = Xs + JC * FT;                                    // JC * max(RC, r)
   const int ucols = r > RC ? r : RC;
   TW* Ps = Us + JC * ucols;                                 // r * FT (RESID only)
-  __shared__ long long fbase[FT];
+  __shared__ long long fbase[FT], pbase[FT];
   __shared__ double red[32];
 
   const int tid = threadIdx.x;
@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
       if (f >= F) f = F - 1;
       const long long a = f % A, b = f / A;
       fbase[tid] = a + A * (long long)n * b;
+      pbase[tid] = a + A * (long long)r * b;
     }
     __syncthreads();
     for (int rc0 = 0; rc0 < r; rc0 += RC) {
@@ -111,9 +112,11 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
           for (int f = 0; f < FT / 16; ++f) xv[f] = Xs[jj * FT + tx + 16 * f];
 #pragma unroll
           for (int i = 0; i < RC / 16; ++i) {
-            const TW u = Us[jj * RC + ty + 16 * i];
+            if (16 * i < rcn) {
+              const TW u = Us[jj * RC + ty + 16 * i];
 #pragma unroll
-            for (int f = 0; f < FT / 16; ++f) acc[i][f] += u * xv[f];
+              for (int f = 0; f < FT / 16; ++f) acc[i][f] += u * xv[f];
+            }
           }
         }
       }
@@ -126,10 +129,7 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
         for (int f = 0; f < FT / 16; ++f) {
           const int ff = tx + 16 * f;
           const long long fg = f0 + ff;
-          if (fg < F) {
-            const long long a = fg % A, b = fg / A;
-            P[a + A * ((long long)row + (long long)r * b)] = acc[i][f];
-          }
+          if (fg < F) P[pbase[ff] + A * (long long)row] = acc[i][f];
           if (RESID) Ps[(long long)row * FT + ff] = acc[i][f];
         }
       }
@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(NT) k_resid_gram(const Ctl* __restrict__ ctl, 
                                                   double* __restrict__ gpart, int data_only) {
   if (ctl->status) return;
   if (!data_only && !ctl->grew[k]) return;
+  if (!data_only && k == 0 && tc_proj1_ok(ctl, ctl->r[0])) return;   // tensor-core Gram
   const int n = view_n(ctl, k);
   const long long A = view_A(ctl, k);
   const long long B = view_B(ctl, k);
@@ -337,6 +338,7 @@ __global__ void k_gram_reduce(const Ctl* ctl, int k, const double* gpart, int pa
                               double* G, int data_only) {
   if (ctl->status) return;
   if (!data_only && !ctl->grew[k]) return;
+  if (!data_only && k == 0 && tc_proj1_ok(ctl, ctl->r[0])) return;   // tensor-core Gram
   const int n = view_n(ctl, k);
   const int T = (n + GT - 1) / GT;
   const long long total = (long long)pairs * GT * GT;

@@ -41,6 +41,9 @@ __global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW*
   const TW* dv = dbufs[ctl->xbuf];
   long long Ro = 1;
   for (int i = 0; i < m; ++i) Ro *= ctl->rold[i];
+  const bool same = !spatial_grew(ctl);
+  int ro[TK_MAXD], rn[TK_MAXD];
+  for (int i = 0; i < TK_MAXD; ++i) { ro[i] = ctl->rold[i]; rn[i] = ctl->r[i]; }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int CPL = TK_STREAM_CAP_MAX / 32;   // column groups
   const int CG = (r + 31) / 32;
@@ -58,12 +61,16 @@ __global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW*
     for (int i = 0; i < RB; ++i) {
       jo[i] = j0 + i;
       if (jo[i] < Ro) {
-        long long t = jo[i], jn = 0, stride = 1;
-        for (int k = 0; k < m; ++k) {
-          const int ik = (int)(t % ctl->rold[k]);
-          t /= ctl->rold[k];
-          jn += ik * stride;
-          stride *= ctl->r[k];
+        int jn = (int)jo[i];
+        if (!same) {
+          int t = (int)jo[i], stride = 1;
+          jn = 0;
+          for (int k = 0; k < m; ++k) {
+            const int ik = t % ro[k];
+            t /= ro[k];
+            jn += ik * stride;
+            stride *= rn[k];
+          }
         }
         dj[i] = dv[jn];
       } else {
@@ -135,6 +142,9 @@ __global__ void __launch_bounds__(256) k_isvd_e(const Ctl* __restrict__ ctl, TW*
   const TW* dv = dbufs[ctl->xbuf];
   long long Rn = 1;
   for (int i = 0; i < m; ++i) Rn *= ctl->r[i];
+  const bool same = !spatial_grew(ctl);
+  int ro[TK_MAXD], rn[TK_MAXD];
+  for (int i = 0; i < TK_MAXD; ++i) { ro[i] = ctl->rold[i]; rn[i] = ctl->r[i]; }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int CPL = TK_STREAM_CAP_MAX / 32;
   const int CG = (r + 31) / 32;
@@ -158,7 +168,7 @@ __global__ void __launch_bounds__(256) k_isvd_e(const Ctl* __restrict__ ctl, TW*
 #pragma unroll
     for (int i = 0; i < RB; ++i) {
       const long long jn = j0 + i;
-      jo[i] = (jn < Rn) ? tk_map_new_to_old(jn, ctl->r, ctl->rold, m) : -1;
+      jo[i] = (jn < Rn) ? (same ? jn : (long long)map_new_to_old32((int)jn, rn, ro, m)) : -1;
       dj[i] = (jn < Rn) ? dv[jn] : TW(0);
       dot[i] = TW(0);
     }

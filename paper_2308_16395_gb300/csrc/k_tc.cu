@@ -364,9 +364,12 @@ struct TcProjArgs {
   double* part_y2;
   int nparts;
   const float* Y;
+  float* Et;
 };
 
-template <bool RESID>
+// WRITE_ET (growth pre-pass of the residual Gram): E^T (n_1 x F, row-major) is written instead
+// of P and of the norm partials.
+template <bool RESID, bool WRITE_ET>
 __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl, int pred,
                                                     const __grid_constant__ CUtensorMap mY,
                                                     const __grid_constant__ CUtensorMap mUhi,
@@ -553,7 +556,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
     // ---------------- epilogue ----------------
     const int wq = warp - 4;
     const uint32_t lq = (uint32_t)(wq * 32) << 16;
-    KahanF eacc, yacc;
+    double eacc = 0.0, yacc = 0.0;
     int it = 0;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       bool okw = wait_bar(d1full, (uint32_t)(it & 1), abort);
@@ -565,9 +568,16 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
       for (int c0 = 0; c0 < Rp; c0 += 32) {
         float v[32];
         tmem_ld32(tD1 + lq + c0, v);
-        if (live) {
+        if (live && !WRITE_ET) {
           float* prow = P + f * r;
-          for (int i = 0; i < 32 && c0 + i < r; ++i) prow[c0 + i] = v[i];
+          if ((r & 3) == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              if (c0 + i < r)
+                *reinterpret_cast<float4*>(prow + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          } else {
+            for (int i = 0; i < 32 && c0 + i < r; ++i) prow[c0 + i] = v[i];
+          }
         }
         if (RESID) {
           float h[32], l[32];
@@ -589,14 +599,23 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
           float v[32];
           tmem_ld32(tD2 + lq + c0, v);
           if (live) {
-#pragma unroll 8
-            for (int i = 0; i < 32; ++i) {
+            // FP32 partial sums over 32 elements, flushed to FP64 per chunk
+            float es = 0.f, ys = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
               if (c0 + i < n1) {
-                const float y = yrow[c0 + i];
-                const float e = y - v[i];
-                eacc.add(e * e);
-                yacc.add(y * y);
+                const float4 y = *reinterpret_cast<const float4*>(yrow + c0 + i);
+                const float e0 = y.x - v[i], e1 = y.y - v[i + 1], e2 = y.z - v[i + 2], e3 = y.w - v[i + 3];
+                es = fmaf(e0, e0, es); es = fmaf(e1, e1, es); es = fmaf(e2, e2, es); es = fmaf(e3, e3, es);
+                ys = fmaf(y.x, y.x, ys); ys = fmaf(y.y, y.y, ys); ys = fmaf(y.z, y.z, ys); ys = fmaf(y.w, y.w, ys);
               }
+            }
+            eacc += (double)es;
+            yacc += (double)ys;
+            if (WRITE_ET) {
+#pragma unroll 8
+              for (int i = 0; i < 32; ++i)
+                if (c0 + i < n1) a.Et[(long long)(c0 + i) * F + f] = yrow[c0 + i] - v[i];
             }
           }
         }
@@ -604,8 +623,8 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
         mbar_arrive(d2free);
       }
     }
-    if (RESID) {
-      double se = warp_sum(eacc.value()), sy = warp_sum(yacc.value());
+    if (RESID && !WRITE_ET) {
+      double se = warp_sum(eacc), sy = warp_sum(yacc);
       if (lane == 0) { red[wq] = se; red[4 + wq] = sy; }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (wq == 0 && lane == 0) {
@@ -655,28 +674,206 @@ cudaError_t launch_split_u1(const Ctl* ctl, int pred, const double* U, int ldu, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_proj1(const Ctl* ctl, int resid, int pred, const float* Y, long long F,
+cudaError_t launch_tc_proj1(const Ctl* ctl, int mode, int pred, const float* Y, long long F,
                             int n1, const TcProjMaps& m, void* const* dbufs, int out_off,
-                            double* part_e2, double* part_y2, int nparts, int grid,
+                            double* part_e2, double* part_y2, int nparts, float* Et, int grid,
                             cudaStream_t st) {
   CUtensorMap mY;
   if (!make_map_2d_f32(&mY, Y, F, n1, n1, 32, 128)) return cudaErrorInvalidValue;
-  TcProjArgs a{(float* const*)dbufs, out_off, part_e2, part_y2, nparts, Y};
-  if (resid) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_tc_proj1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM);
-      attr = true;
-    }
-    k_tc_proj1<true><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
+  TcProjArgs a{(float* const*)dbufs, out_off, part_e2, part_y2, nparts, Y, Et};
+  static bool attr[3] = {false, false, false};
+  if (mode == 0) {
+    if (!attr[0]) { cudaFuncSetAttribute(k_tc_proj1<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[0] = true; }
+    k_tc_proj1<false, false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
+  } else if (mode == 1) {
+    if (!attr[1]) { cudaFuncSetAttribute(k_tc_proj1<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[1] = true; }
+    k_tc_proj1<true, false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_tc_proj1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM);
-      attr = true;
-    }
-    k_tc_proj1<false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
+    if (!attr[2]) { cudaFuncSetAttribute(k_tc_proj1<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[2] = true; }
+    k_tc_proj1<true, true><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
   }
+  return cudaGetLastError();
+}
+
+// =============================================================================================
+// k_tc_syrk: partial Gram G = E^T E of the mode-1 residual unfolding (Alg. 1's Gram of E_(1)),
+// split over the fibers (K). E^T (n_1 x F) streams by TMA in 32-fiber chunks; both operands are
+// split on chip into TF32 hi/lo (3xTF32); one CTA per (128-row block of G, K split); partial
+// blocks are summed in FP64 by k_syrk_reduce.
+// =============================================================================================
+constexpr int TS_STAGE = 96 * 1024;    // A hi | A lo | B hi | B lo (B up to 256 rows)
+constexpr int TS_S = 2;
+constexpr size_t TS_SMEM = (size_t)TS_S * TS_STAGE + 1024 + 256;
+
+__global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl,
+                                                   const __grid_constant__ CUtensorMap mEa,
+                                                   const __grid_constant__ CUtensorMap mEb,
+                                                   double* __restrict__ gpart, long long F) {
+  if (ctl->status) return;
+  if (!ctl->grew[0] || !tc_proj1_ok(ctl, ctl->r[0])) return;
+  const int n1 = ctl->n[0];
+  const int n1p = (n1 + 15) / 16 * 16;
+  const int MT = gridDim.y, mt = blockIdx.y;
+  const int S = gridDim.x, sp = blockIdx.x;
+  const long long KC = (F + TC_KC - 1) / TC_KC;
+  const long long per = (KC + S - 1) / S;
+  const long long c_beg = sp * per;
+  const long long c_end = c_beg + per < KC ? c_beg + per : KC;
+  const int nchunks = c_end > c_beg ? (int)(c_end - c_beg) : 0;
+
+  extern __shared__ __align__(1024) unsigned char ssm_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(ssm_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TS_S * TS_STAGE);
+  uint64_t* full = bars;
+  uint64_t* conv = bars + TS_S;
+  uint64_t* empty = bars + 2 * TS_S;
+  uint64_t* accfull = bars + 3 * TS_S;
+  uint64_t* done = accfull + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TS_S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 64);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accfull, 1);
+    mbar_init(done, 1);
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // stage layout: A hi [0,16K) A lo [16K,32K) B hi [32K,64K) B lo [64K,96K)
+  if (warp == 0) {
+    if (lane == 0) {
+      tma_prefetch(&mEa);
+      tma_prefetch(&mEb);
+      for (int c = 0; c < nchunks && !*abort; ++c) {
+        const int s = c % TS_S;
+        if (!wait_bar(&empty[s], (uint32_t)(((c / TS_S) & 1) ^ 1), abort)) break;
+        unsigned char* st = base + (size_t)s * TS_STAGE;
+        const int x = (int)((c_beg + c) * TC_KC);
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(TC_M * TC_KC * 4 + n1p * TC_KC * 4));
+        tma_load_2d(&mEa, &full[s], st, x, mt * TC_M);
+        for (int n0 = 0; n0 < n1p; n0 += 16)
+          tma_load_2d(&mEb, &full[s], st + 32 * 1024 + n0 * 128, x, n0);
+      }
+      for (int j = (nchunks > TS_S ? nchunks - TS_S : 0); j < nchunks; ++j)
+        wait_bar(&empty[j % TS_S], (uint32_t)((j / TS_S) & 1), abort);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc_tf32(TC_M, n1p);
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c % TS_S;
+        if (!wait_bar(&conv[s], (uint32_t)((c / TS_S) & 1), abort)) { ok = false; break; }
+        tc_fence_after();
+        unsigned char* st = base + (size_t)s * TS_STAGE;
+        const uint64_t ahi = desc_sw128(st), alo = desc_sw128(st + 16 * 1024);
+        const uint64_t bhi = desc_sw128(st + 32 * 1024), blo = desc_sw128(st + 64 * 1024);
+#pragma unroll
+        for (int k4 = 0; k4 < TC_KC / 8; ++k4) {
+          const uint64_t o = (uint64_t)(k4 * 32) >> 4;
+          mma_tf32(tmem, ahi + o, bhi + o, id, (c | k4) ? 1u : 0u);
+          mma_tf32(tmem, ahi + o, blo + o, id, 1u);
+          mma_tf32(tmem, alo + o, bhi + o, id, 1u);
+        }
+        tc_commit(&empty[s]);
+      }
+      if (ok) tc_commit(accfull);
+      tc_commit(done);
+      wait_bar(done, 0, abort);
+    }
+    __syncwarp();
+  } else if (warp == 2 || warp == 3) {
+    const int ct = threadIdx.x - 64;
+    for (int c = 0; c < nchunks && !*abort; ++c) {
+      const int s = c % TS_S;
+      if (!wait_bar(&full[s], (uint32_t)((c / TS_S) & 1), abort)) break;
+      unsigned char* st = base + (size_t)s * TS_STAGE;
+      float4* ahi = reinterpret_cast<float4*>(st);
+      float4* alo = reinterpret_cast<float4*>(st + 16 * 1024);
+      float4* bhi = reinterpret_cast<float4*>(st + 32 * 1024);
+      float4* blo = reinterpret_cast<float4*>(st + 64 * 1024);
+      for (int i = ct; i < TC_M * TC_KC / 4; i += 64) {
+        float4 v = ahi[i], h, l;
+        tf32_split(v.x, h.x, l.x); tf32_split(v.y, h.y, l.y);
+        tf32_split(v.z, h.z, l.z); tf32_split(v.w, h.w, l.w);
+        ahi[i] = h; alo[i] = l;
+      }
+      for (int i = ct; i < n1p * TC_KC / 4; i += 64) {
+        float4 v = bhi[i], h, l;
+        tf32_split(v.x, h.x, l.x); tf32_split(v.y, h.y, l.y);
+        tf32_split(v.z, h.z, l.z); tf32_split(v.w, h.w, l.w);
+        bhi[i] = h; blo[i] = l;
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&conv[s]);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    const int wq = warp - 4;
+    bool okw = nchunks > 0 ? wait_bar(accfull, 0, abort) : false;
+    okw = __all_sync(0xffffffffu, okw);
+    const int row = wq * 32 + lane;   // row of the 128-row block
+    double* out = gpart + (((long long)sp * MT + mt) * TC_M + row) * n1p;
+    if (okw) {
+      tc_fence_after();
+      for (int c0 = 0; c0 < n1p; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (c0 + i < n1p) out[c0 + i] = (double)v[i];
+      }
+    } else {
+      for (int c0 = 0; c0 < n1p; ++c0) out[c0] = 0.0;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 256);
+  if (threadIdx.x == 0 && *abort) const_cast<Ctl*>(ctl)->status = 5;
+}
+
+// G (n_1 x n_1, FP64, column-major) = sum over K splits of the partial 128-row blocks.
+__global__ void k_syrk_reduce(const Ctl* ctl, const double* gpart, int S, int MT, double* G) {
+  if (ctl->status) return;
+  if (!ctl->grew[0] || !tc_proj1_ok(ctl, ctl->r[0])) return;
+  const int n1 = ctl->n[0];
+  const int n1p = (n1 + 15) / 16 * 16;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < (long long)n1 * n1;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(L % n1), j = (int)(L / n1);
+    const int mt = i / TC_M, row = i % TC_M;
+    double acc = 0.0;
+    for (int sp = 0; sp < S; ++sp) acc += gpart[(((long long)sp * MT + mt) * TC_M + row) * n1p + j];
+    G[(long long)j * n1 + i] = acc;
+  }
+}
+
+cudaError_t launch_tc_gram1(const Ctl* ctl, const float* Et, long long F, int n1, double* gpart,
+                            double* G, int nsm, cudaStream_t st) {
+  CUtensorMap ma, mb;
+  if (!make_map_2d_f32(&ma, Et, n1, F, F, 32, 128)) return cudaErrorInvalidValue;
+  if (!make_map_2d_f32(&mb, Et, n1, F, F, 32, 16)) return cudaErrorInvalidValue;
+  const int MT = (n1 + TC_M - 1) / TC_M;
+  const int S = nsm / MT;
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_tc_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM); attr = true; }
+  k_tc_syrk<<<dim3(S, MT), 256, TS_SMEM, st>>>(ctl, ma, mb, gpart, F);
+  k_syrk_reduce<<<64, 256, 0, st>>>(ctl, gpart, S, MT, G);
   return cudaGetLastError();
 }
 

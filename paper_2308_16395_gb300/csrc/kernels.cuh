@@ -87,10 +87,14 @@ struct TcProjMaps {
 };
 cudaError_t launch_split_u1(const Ctl* ctl, int pred, const double* U, int ldu, float* const* sp,
                             cudaStream_t st);
-cudaError_t launch_tc_proj1(const Ctl* ctl, int resid, int pred, const float* Y, long long F,
+// mode 0: projection only (pass C), 1: projection + residual norms (pass A),
+// 2: residual E^T written to Et (pre-pass of the Gram, only when mode 1 grew).
+cudaError_t launch_tc_proj1(const Ctl* ctl, int mode, int pred, const float* Y, long long F,
                             int n1, const TcProjMaps& m, void* const* dbufs, int out_off,
-                            double* part_e2, double* part_y2, int nparts, int grid,
+                            double* part_e2, double* part_y2, int nparts, float* Et, int grid,
                             cudaStream_t st);
+cudaError_t launch_tc_gram1(const Ctl* ctl, const float* Et, long long F, int n1, double* gpart,
+                            double* G, int nsm, cudaStream_t st);
 cudaError_t launch_tc_cv(Ctl* ctl, SecWork w, const TcMaps& maps, void* const* cbufs_host,
                          void* const* vbufs_host, void* const* d_cbufs, void* const* d_vbufs,
                          const void* cu, const void* wv, const void* evec, void* const* dbufs,

@@ -139,10 +139,14 @@ def _growth_stream(seed=11, n=(37, 29, 11), T=16):
     return X
 
 
-@pytest.mark.parametrize("precision,dtype", [("fp64", "f64"), ("fp64", "f32"), ("mixed", "f32")])
-def test_rank_growth_ragged(pkg, precision, dtype):
-    """Spatial ranks grow (2 -> 4 -> 5) on ragged sizes (37 x 29 x 11: not multiples of any tile)."""
-    X = _growth_stream()
+@pytest.mark.parametrize("precision,dtype,n", [("fp64", "f64", (37, 29, 11)),
+                                                ("fp64", "f32", (37, 29, 11)),
+                                                ("mixed", "f32", (37, 29, 11)),
+                                                ("mixed", "f32", (40, 28, 12))])
+def test_rank_growth_ragged(pkg, precision, dtype, n):
+    """Spatial ranks grow (2 -> 4 -> 5): ragged sizes (37 x 29 x 11: not multiples of any tile,
+    SIMT mode-1 path) and 40 x 28 x 12 (tensor-core mode-1 pass, residual Gram on tcgen05)."""
+    X = _growth_stream(n=n)
     st, ts, Xs, recs, div = _run(pkg, X, 6, 1e-3, precision, dtype)
     assert not div
     assert st.ranks[:3] == (5, 5, 5)
