@@ -75,11 +75,12 @@ struct tucker_state {
   float** d_bsplit = nullptr;
   TcMaps maps{};
   bool tc = false;               // tensor-core path available (mixed form)
-  float* usplit[4]{};            // U_1 TF32 hi/lo copies for the tensor-core mode-1 pass
-  float** d_usplit = nullptr;
-  TcProjMaps pmaps{};
-  bool tcp = false;              // tensor-core mode-1 pass available (mixed form, FP32 slices)
-  float* et = nullptr;           // E^T of mode 1 (n_1 x F) for the tensor-core Gram
+  float* usplit[TK_MAXD][4]{};   // U_k TF32 hi/lo copies for the tensor-core spatial passes
+  TcProjMaps pmaps[TK_MAXD]{};
+  int tcmask = 0;                 // bit k: tensor-core projection of spatial mode k available
+  int etmask = 0;                 // bit k: tensor-core residual Gram of spatial mode k available
+  float* et = nullptr;            // E^T of the growing mode (n_k x Fs_k) for the Gram
+  long long et_stride[TK_MAXD]{};
   int nsm = 152;
   void* cu = nullptr;
   void* wv = nullptr;
@@ -319,22 +320,36 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
     ok &= make_map_2d_f32(&s->maps.bv_lo, s->bsplit[3], 512, 512, 512, 32, 16);
     s->tc = ok;
   }
-  if (tw == 4 && s->tx == 4 && d >= 2 && s->n[0] % 4 == 0 && s->n[0] <= 256 &&
-      (s->N / s->n[0]) % 4 == 0) {
-    const int n1 = s->n[0];
-    CK(dalloc(s, (void**)&s->usplit[0], sizeof(float) * n1 * s->cap[0]));
-    CK(dalloc(s, (void**)&s->usplit[1], sizeof(float) * n1 * s->cap[0]));
-    CK(dalloc(s, (void**)&s->usplit[2], sizeof(float) * n1 * 64));
-    CK(dalloc(s, (void**)&s->usplit[3], sizeof(float) * n1 * 64));
-    CK(dalloc(s, (void**)&s->d_usplit, sizeof(void*) * 4));
-    CK(cudaMemcpy(s->d_usplit, s->usplit, sizeof(void*) * 4, cudaMemcpyHostToDevice));
-    bool ok = true;
-    ok &= make_map_2d_f32(&s->pmaps.uhi, s->usplit[0], s->cap[0], n1, n1, 32, 16);
-    ok &= make_map_2d_f32(&s->pmaps.ulo, s->usplit[1], s->cap[0], n1, n1, 32, 16);
-    ok &= make_map_2d_f32(&s->pmaps.urhi, s->usplit[2], n1, 64, 64, 32, 16);
-    ok &= make_map_2d_f32(&s->pmaps.urlo, s->usplit[3], n1, 64, 64, 32, 16);
-    CK(dalloc(s, (void**)&s->et, sizeof(float) * (size_t)s->N));
-    s->tcp = ok;
+  if (tw == 4) {
+    // tensor-core spatial passes: per mode, TF32 splits of U_k and the tensor maps.
+    // E^T rows have stride Fs_k >= max fibers + 32, so a Gram K chunk never leaves its row.
+    size_t et_elems = 16;
+    for (int k = 0; k < d - 1; ++k) {
+      const long long fs = (s->dbuf_elems / s->n[k] + 32 + 3) / 4 * 4;
+      et_elems = std::max(et_elems, (size_t)fs * s->n[k]);
+    }
+    CK(dalloc(s, (void**)&s->et, sizeof(float) * et_elems));
+    for (int k = 0; k < d - 1; ++k) {
+      const int nk = s->n[k];
+      if (nk % 4 != 0 || nk > 256 || (k == 0 && s->tx != 4)) continue;
+      for (int i = 0; i < 2; ++i) CK(dalloc(s, (void**)&s->usplit[k][i], sizeof(float) * nk * s->cap[k]));
+      for (int i = 2; i < 4; ++i) CK(dalloc(s, (void**)&s->usplit[k][i], sizeof(float) * nk * 64));
+      TcProjMaps& m = s->pmaps[k];
+      bool ok = true;
+      ok &= make_map_2d_f32(&m.uhi, s->usplit[k][0], s->cap[k], nk, nk, 32, 16);
+      ok &= make_map_2d_f32(&m.ulo, s->usplit[k][1], s->cap[k], nk, nk, 32, 16);
+      ok &= make_map_2d_f32(&m.urhi, s->usplit[k][2], nk, 64, 64, 32, 16);
+      ok &= make_map_2d_f32(&m.urlo, s->usplit[k][3], nk, 64, 64, 32, 16);
+      const long long rows = s->dbuf_elems / nk;
+      for (int i = 0; i < 3; ++i) ok &= make_map_2d_f32(&m.d[i], s->dbuf[i], rows, nk, nk, 32, 128);
+      if (!ok) continue;
+      s->tcmask |= 1 << k;
+      const long long fs = (s->dbuf_elems / nk + 32 + 3) / 4 * 4;
+      s->et_stride[k] = fs;
+      bool oke = make_map_2d_f32(&m.eta, s->et, nk, fs, fs, 32, 128);
+      oke &= make_map_2d_f32(&m.etb, s->et, nk, fs, fs, 32, 16);
+      if (oke) s->etmask |= 1 << k;
+    }
   }
   return TUCKER_OK;
 }
@@ -390,6 +405,8 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
   h.tx = s->tx;
   h.tw = s->tw;
   h.N = s->N;
+  h.tcmask = s->tcmask;
+  h.etmask = s->etmask;
   // ||X||^2 -> eps (Alg. 2, first step)
   const long long NX = s->N * n_init;
   CK(launch_norm2<TX>(X, NX, s->part_y2, 1024, st));
@@ -434,7 +451,8 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
     double* Uk = (k == d - 1) ? Utmp : s->U[k];
     void* Uwk = (k == d - 1) ? (s->tw == 8 ? (void*)Utmp : Uwtmp) : s->Uw[k];
     if (e == cudaSuccess) e = launch_append<TW>(s->ctl, k, 1, s->eW, Uk, (s->tw == 8) ? nullptr : Uwk, nv, nv, st);
-    if (e == cudaSuccess && k == 0 && s->tcp) e = launch_split_u1(s->ctl, 0, s->U[0], s->n[0], s->usplit, st);
+    if (e == cudaSuccess && k < d - 1 && ((s->tcmask >> k) & 1))
+      e = launch_split_u(s->ctl, k, 0, s->U[k], s->n[k], s->usplit[k], st);
     if (e != cudaSuccess) { set_err(s, "CUDA error: %s", cudaGetErrorString(e)); rc = TUCKER_ECUDA; break; }
     s->last_stream = st;
     rc = sync_ctl(s);
@@ -490,12 +508,14 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
   for (int k = 0; k < d - 1; ++k) {
     const int n = s->n[k];
     const int pairs = gram_pairs(n), chunks = gram_chunks(n);
+    const bool tck = (s->tcmask >> k) & 1;
     {
       // pass A: P_k = D*_{k-1} x_k U_k^T, ||E_k||^2 (and ||Y||^2 for k = 0); Alg. 4's branch
       PhaseMark pm(s, st, k == 0 ? TK_PH_PROJ1 : TK_PH_PROJN);
-      if (k == 0 && s->tcp) {
-        CK(launch_tc_proj1(s->ctl, 1, 0, (const float*)Y, s->N / n, n, s->pmaps, s->d_dbufs, 1,
-                           s->part_e2, s->part_y2, kGridP, nullptr, s->nsm, st));
+      if (tck) {
+        CK(launch_tc_proj(s->ctl, k, 1, 0, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
+                          s->d_dbufs, 1, s->part_e2, k == 0 ? s->part_y2 : nullptr, kGridP,
+                          nullptr, 0, s->nsm, st));
         launches += 1;
       }
       if (k == 0)
@@ -510,11 +530,12 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       // ||E_k|| > eps: residual Gram, eig + rank cut (Alg. 1), augmentation, then
       // pass C: D*_k = D*_{k-1} x_k U~_k^T (= Concatenate(P_k, L_k), App. C)
       PhaseMark pm(s, st, TK_PH_GROW);
-      if (k == 0 && s->tcp) {
-        // residual E^T of mode 1, then its Gram on the tensor cores (only if mode 1 grew)
-        CK(launch_tc_proj1(s->ctl, 2, 1, (const float*)Y, s->N / n, n, s->pmaps, s->d_dbufs, 1,
-                           nullptr, nullptr, kGridP, s->et, s->nsm, st));
-        CK(launch_tc_gram1(s->ctl, s->et, s->N / n, n, s->gpart, s->G, s->nsm, st));
+      if ((s->etmask >> k) & 1) {
+        // residual E^T of mode k, then its Gram on the tensor cores (only if mode k grew)
+        CK(launch_tc_proj(s->ctl, k, 2, 1, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
+                          s->d_dbufs, 1, nullptr, nullptr, kGridP, s->et, s->et_stride[k],
+                          s->nsm, st));
+        CK(launch_tc_gram(s->ctl, k, s->pmaps[k], n, s->gpart, s->G, s->nsm, st));
         launches += 3;
       }
       if (k == 0)
@@ -526,10 +547,10 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       CK(launch_gram_reduce(s->ctl, k, s->gpart, pairs, chunks, s->G, 0, st));
       CK(launch_eig<TE>(s->ctl, k, 0, s->G, s->eAw, s->eZ, s->eLD, s->eW, nullptr, s->mcap, n, st));
       CK(launch_append<TW>(s->ctl, k, 0, s->eW, s->U[k], (s->tw == 8) ? nullptr : s->Uw[k], n, n, st));
-      if (k == 0 && s->tcp) {
-        CK(launch_split_u1(s->ctl, 1, s->U[0], n, s->usplit, st));
-        CK(launch_tc_proj1(s->ctl, 0, 1, (const float*)Y, s->N / n, n, s->pmaps, s->d_dbufs, 2,
-                           nullptr, nullptr, kGridP, nullptr, s->nsm, st));
+      if (tck) {
+        CK(launch_split_u(s->ctl, k, 1, s->U[k], n, s->usplit[k], st));
+        CK(launch_tc_proj(s->ctl, k, 0, 1, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
+                          s->d_dbufs, 2, nullptr, nullptr, kGridP, nullptr, 0, s->nsm, st));
         launches += 2;
       }
       if (k == 0)

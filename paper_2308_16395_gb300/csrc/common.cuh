@@ -39,6 +39,8 @@ struct Ctl {
   int status;               // latched error (0 = ok)
   int xbuf;                 // D*-buffer holding the input of the current spatial mode (-1: slice)
   int init_nt;              // > 0 only during the batch ST-HOSVD: number of initial slices
+  int tcmask;               // bit k: tensor-core projection maps exist for spatial mode k
+  int etmask;               // bit k: tensor-core residual-Gram maps exist for spatial mode k
   // ---- per-update record ----
   int rold[TK_MAXD];        // ranks when the update started
   double y2;                // ||Y||^2
@@ -69,13 +71,24 @@ struct Ctl {
 #define TK_PH_CV 5       // core and V updates
 #define TK_NPH 6
 
-// Mode-k view (A, n, B) of the operand of mode k: A = prod of current ranks of modes < k,
-// n = n_k (or the number of initial slices for the streaming mode during the batch ST-HOSVD),
-// B = prod of the spatial sizes of modes > k (times the initial slices during the batch ST-HOSVD).
+// Mode-k view (A, n, B) of the operand of mode k, column-major: element (a, j, b) at
+// a + A (j + n b).
+//
+// Batch ST-HOSVD (init_nt > 0): the standard view, A = product of the truncated ranks of modes
+// < k, n = n_k (or the number of initial slices for the streaming mode), B = product of the
+// sizes of the later modes (times the initial slices).
+//
+// Streaming update (init_nt == 0), rotating layout: the input of spatial mode k is a row-major
+// (F_k x n_k) matrix (A = 1, B = F_k) whose rows are the mode-k fibers, with
+// F_k = prod_{i>k} n_i * prod_{i<k} r~_i; mode k writes its output column-major (F_k x r_k).
+// That output, read as row-major (F_{k+1} x n_{k+1}), is the next mode's input (its fibers are
+// again contiguous), and after the last spatial mode the order is the natural column-major order
+// of the core (i_1 fastest).
 __device__ __forceinline__ int view_n(const Ctl* c, int k) {
   return (k == c->d - 1) ? c->init_nt : c->n[k];
 }
 __device__ __forceinline__ long long view_A(const Ctl* c, int k) {
+  if (c->init_nt == 0) return 1;
   long long a = 1;
   for (int i = 0; i < k; ++i) a *= c->r[i];
   return a;
@@ -83,8 +96,22 @@ __device__ __forceinline__ long long view_A(const Ctl* c, int k) {
 __device__ __forceinline__ long long view_B(const Ctl* c, int k) {
   long long b = 1;
   for (int i = k + 1; i < c->d - 1; ++i) b *= c->n[i];
-  if (k < c->d - 1 && c->init_nt > 0) b *= c->init_nt;
+  if (c->init_nt == 0) {
+    for (int i = 0; i < k; ++i) b *= c->r[i];
+  } else if (k < c->d - 1) {
+    b *= c->init_nt;
+  }
   return b;
+}
+// Address of output element (fiber f = a + A b, row i): standard (a + A (i + r b)) or rotating
+// (f + F i) layout.
+__device__ __forceinline__ long long out_base(const Ctl* c, long long f, long long A, int r) {
+  if (c->init_nt == 0) return f;
+  const long long a = f % A, b = f / A;
+  return a + A * (long long)r * b;
+}
+__device__ __forceinline__ long long out_stride(const Ctl* c, long long A, long long F) {
+  return (c->init_nt == 0) ? F : A;
 }
 
 __host__ __device__ inline long long tk_prod(const int* v, int a, int b) {
@@ -193,17 +220,21 @@ __device__ __forceinline__ bool spatial_grew(const Ctl* ctl) {
   return false;
 }
 
-// ---- tensor-core path of the mode-1 projection (mixed form, FP32 slices) ----
-#define TP_RMAX 64                      // largest padded r_1 handled on the tensor cores
-#define TP_SMEM_BUDGET (224 * 1024)
+// ---- tensor-core path of the spatial-mode projections (mixed form) ----
+#define TP_RMAX 64                      // largest padded r_k handled on the tensor cores
 
-// Mode-1 pass on the tensor cores: mixed form with FP32 slices, n_1 a multiple of 4 (TMA row
-// stride) and <= 256, padded rank <= 64, resident U_1 (n_1 x ceil32(r)) fits the budget.
-__device__ __forceinline__ bool tc_proj1_ok(const Ctl* c, int r) {
-  if (c->tw != 4 || c->tx != 4 || c->init_nt != 0) return false;
-  const int n1 = c->n[0];
-  if (n1 % 4 != 0 || n1 > 256 || r < 1) return false;
-  const int rp = (r + 15) / 16 * 16;
-  if (rp > TP_RMAX) return false;
-  return true;
+// Spatial mode k on the tensor cores: mixed form, streaming update (rotating layout), the host
+// built the tensor maps for this mode (bit k of tcmask), FP32 input (the slice for k = 0),
+// n_k a multiple of 4 (TMA row stride) and <= 256, padded rank <= 64.
+__device__ __forceinline__ bool tc_proj_ok(const Ctl* c, int k, int r) {
+  if (c->tw != 4 || c->init_nt != 0) return false;
+  if (!((c->tcmask >> k) & 1)) return false;
+  if (k == 0 && c->tx != 4) return false;
+  const int nk = c->n[k];
+  if (nk % 4 != 0 || nk > 256 || r < 1) return false;
+  return (r + 15) / 16 * 16 <= TP_RMAX;
+}
+// Residual Gram of mode k on the tensor cores (needs the E^T maps, bit k of etmask).
+__device__ __forceinline__ bool tc_gram_ok(const Ctl* c, int k) {
+  return c->grew[k] && ((c->etmask >> k) & 1) && tc_proj_ok(c, k, c->rold[k]);
 }

@@ -108,9 +108,10 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     const TE K = -TE(0.5) * tau * pv;
     for (int i = tid; i < m; i += nt) sp[i] += K * sv[i];   // w
     __syncthreads();
-    for (long long L = tid; L < (long long)m * m; L += nt) {
-      const int i = (int)(L % m), j = (int)(L / m);
-      A[(long long)(c + 1 + j) * n + (c + 1 + i)] -= sv[i] * sp[j] + sp[i] * sv[j];
+    for (int j = wid; j < m; j += nwarp) {
+      TE* colj = A + (long long)(c + 1 + j) * n + (c + 1);
+      const TE svj = sv[j], spj = sp[j];
+      for (int i = lane; i < m; i += 32) colj[i] -= sv[i] * spj + sp[i] * svj;
     }
     for (int i = tid; i < m; i += nt) x[i] = sv[i];
     if (tid == 0) { stau[c] = tau; sb[c] = beta; }

@@ -58,8 +58,9 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
   const long long A = view_A(ctl, k);
   const long long B = view_B(ctl, k);
   const int r = ctl->r[k];
-  if (k == 0 && tc_proj1_ok(ctl, r)) return;   // the tensor-core kernel does this pass
+  if (tc_proj_ok(ctl, k, r)) return;   // the tensor-core kernel does this pass
   const long long F = A * B;
+  const long long pstr = out_stride(ctl, A, F);
   const int xb = ctl->xbuf;
   const TX* X = (xb < 0) ? Xext : reinterpret_cast<const TX*>(dbufs[xb]);
   TW* P = dbufs[(xb + out_off + 3) % 3];
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
       if (f >= F) f = F - 1;
       const long long a = f % A, b = f / A;
       fbase[tid] = a + A * (long long)n * b;
-      pbase[tid] = a + A * (long long)r * b;
+      pbase[tid] = out_base(ctl, f, A, r);
     }
     __syncthreads();
     for (int rc0 = 0; rc0 < r; rc0 += RC) {
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
         for (int f = 0; f < FT / 16; ++f) {
           const int ff = tx + 16 * f;
           const long long fg = f0 + ff;
-          if (fg < F) P[pbase[ff] + A * (long long)row] = acc[i][f];
+          if (fg < F) P[pbase[ff] + pstr * (long long)row] = acc[i][f];
           if (RESID) Ps[(long long)row * FT + ff] = acc[i][f];
         }
       }
@@ -229,12 +230,13 @@ __global__ void __launch_bounds__(NT) k_resid_gram(const Ctl* __restrict__ ctl, 
                                                   double* __restrict__ gpart, int data_only) {
   if (ctl->status) return;
   if (!data_only && !ctl->grew[k]) return;
-  if (!data_only && k == 0 && tc_proj1_ok(ctl, ctl->r[0])) return;   // tensor-core Gram
+  if (!data_only && tc_gram_ok(ctl, k)) return;   // tensor-core Gram
   const int n = view_n(ctl, k);
   const long long A = view_A(ctl, k);
   const long long B = view_B(ctl, k);
   const int r = data_only ? 0 : ctl->rold[k];
   const long long F = A * B;
+  const long long pstr = out_stride(ctl, A, F);
   const int xb = ctl->xbuf;
   const TX* X = (xb < 0) ? Xext : reinterpret_cast<const TX*>(dbufs[xb]);
   const TW* P = data_only ? nullptr : dbufs[(xb + 1 + 3) % 3];
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(NT) k_resid_gram(const Ctl* __restrict__ ctl, 
       if (f >= fe) f = fe - 1;
       const long long a = f % A, b = f / A;
       fbase[tid] = a + A * (long long)n * b;
-      pbase[tid] = a + A * (long long)r * b;
+      pbase[tid] = out_base(ctl, f, A, r);
     }
     __syncthreads();
     // x rows of both tiles
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(NT) k_resid_gram(const Ctl* __restrict__ ctl, 
       for (int L = tid; L < GC * GF; L += NT) {
         const int c = L / GF, ff = L % GF;
         const bool ok = (f0 + ff < fe) && (c0 + c < r);
-        Pc[c][ff] = ok ? P[pbase[ff] + A * (long long)(c0 + c)] : TW(0);
+        Pc[c][ff] = ok ? P[pbase[ff] + pstr * (long long)(c0 + c)] : TW(0);
       }
       for (int L = tid; L < 2 * GT * GC; L += NT) {
         const int which = L / (GT * GC);
@@ -338,7 +340,7 @@ __global__ void k_gram_reduce(const Ctl* ctl, int k, const double* gpart, int pa
                               double* G, int data_only) {
   if (ctl->status) return;
   if (!data_only && !ctl->grew[k]) return;
-  if (!data_only && k == 0 && tc_proj1_ok(ctl, ctl->r[0])) return;   // tensor-core Gram
+  if (!data_only && tc_gram_ok(ctl, k)) return;   // tensor-core Gram
   const int n = view_n(ctl, k);
   const int T = (n + GT - 1) / GT;
   const long long total = (long long)pairs * GT * GT;

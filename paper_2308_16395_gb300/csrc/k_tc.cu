@@ -343,17 +343,19 @@ cudaError_t launch_tc_cv(Ctl* ctl, SecWork w, const TcMaps& maps, void* const* c
 namespace tk {
 
 // =============================================================================================
-// k_tc_proj1: the mode-1 pass of Alg. 4 on the tensor cores, fused.
-//   MMA1  P = Y_(1)^T U_1  as rows: P[f, :] = Y[f, :] U_1 (f = mode-1 fiber, K = n_1), 3xTF32,
-//         Y tiles by TMA, U_1 chunks (TF32 hi/lo) streamed with them; P accumulates in TMEM.
-//   epi-1 P -> global (the output D*), P split in place into TF32 hi (TMEM cols 0..63) and lo
-//         (cols 64..127).
-//   MMA2  (RESID) Rec = P U_1^T with A = P read from tensor memory, B = U_1 rows resident in
-//         shared memory, 3xTF32; Rec in TMEM cols 128..128+n_1.
-//   epi-2 (RESID) E = Y - Rec with Y re-read (L2-resident), ||E||^2 and ||Y||^2 (compensated,
-//         per-block partials).
+// k_tc_proj: the pass of Alg. 4 for spatial mode k on the tensor cores, fused. The input X is
+// the row-major (F x n_k) matrix of mode-k fibers (the slice for k = 0, else the previous mode's
+// output in the rotating layout).
+//   MMA1  P[f, :] = X[f, :] U_k (K = n_k), 3xTF32, X tiles by TMA, U_k chunks (TF32 hi/lo)
+//         streamed with them; P accumulates in TMEM.
+//   epi-1 P -> global, column-major (F x r_k) (the next mode's input); P split in place into
+//         TF32 hi (TMEM cols 0..63) and lo (cols 64..127).
+//   MMA2  (RESID) Rec = P U_k^T with A = P read from tensor memory, B = U_k rows resident in
+//         shared memory, 3xTF32; Rec in TMEM cols 128..128+n_k.
+//   epi-2 (RESID) E = X - Rec with X re-read (L2-resident), ||E||^2 (and ||Y||^2 for k = 0) as
+//         per-block partials; WRITE_ET: E^T (n_k x Fs, row stride Fs) for the residual Gram.
 // =============================================================================================
-constexpr int TP_STAGE = 48 * 1024;                // Y hi | Y lo | U chunk hi | U chunk lo
+constexpr int TP_STAGE = 48 * 1024;                // X hi | X lo | U chunk hi | U chunk lo
 constexpr int TP_S = 2;
 constexpr size_t TP_SMEM = (size_t)TP_S * TP_STAGE + 128 * 1024 + 1024 + 256;
 
@@ -365,32 +367,37 @@ struct TcProjArgs {
   int nparts;
   const float* Y;
   float* Et;
+  long long et_stride;
+  int k;
 };
 
-// WRITE_ET (growth pre-pass of the residual Gram): E^T (n_1 x F, row-major) is written instead
-// of P and of the norm partials.
 template <bool RESID, bool WRITE_ET>
-__global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl, int pred,
-                                                    const __grid_constant__ CUtensorMap mY,
-                                                    const __grid_constant__ CUtensorMap mUhi,
-                                                    const __grid_constant__ CUtensorMap mUlo,
-                                                    const __grid_constant__ CUtensorMap mUrhi,
-                                                    const __grid_constant__ CUtensorMap mUrlo,
-                                                    TcProjArgs a) {
+__global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl, int pred,
+                                                   const __grid_constant__ CUtensorMap mY,
+                                                   const __grid_constant__ CUtensorMap mD0,
+                                                   const __grid_constant__ CUtensorMap mD1,
+                                                   const __grid_constant__ CUtensorMap mD2,
+                                                   const __grid_constant__ CUtensorMap mUhi,
+                                                   const __grid_constant__ CUtensorMap mUlo,
+                                                   const __grid_constant__ CUtensorMap mUrhi,
+                                                   const __grid_constant__ CUtensorMap mUrlo,
+                                                   TcProjArgs a) {
   if (ctl->status) return;
-  if (pred && !ctl->grew[0]) return;
-  const int r = ctl->r[0];
-  if (!tc_proj1_ok(ctl, r)) return;
-  const int d = ctl->d;
-  const int n1 = ctl->n[0];
-  long long F = 1;
-  for (int i = 1; i < d - 1; ++i) F *= ctl->n[i];
+  const int k = a.k;
+  if (pred && !ctl->grew[k]) return;
+  const int r = ctl->r[k];
+  if (!tc_proj_ok(ctl, k, r)) return;
+  const int n1 = ctl->n[k];
+  const long long F = view_B(ctl, k);
   const int Rp = (r + 15) / 16 * 16;
   const int n1p = (n1 + 15) / 16 * 16;
   const int Kc1 = (n1 + TC_KC - 1) / TC_KC;
   const int Kc2 = (Rp + TC_KC - 1) / TC_KC;
   const long long ntiles = (F + TC_M - 1) / TC_M;
-  float* P = a.dbufs[(ctl->xbuf + a.out_off + 3) % 3];
+  const int xb = ctl->xbuf;
+  const CUtensorMap* mX = xb < 0 ? &mY : (xb == 0 ? &mD0 : (xb == 1 ? &mD1 : &mD2));
+  const float* Xg = xb < 0 ? a.Y : a.dbufs[xb];
+  float* P = a.dbufs[(xb + a.out_off + 3) % 3];
 
   extern __shared__ __align__(1024) unsigned char psm_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -442,7 +449,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      tma_prefetch(&mY);
+      tma_prefetch(mX);
       tma_prefetch(&mUhi);
       tma_prefetch(&mUlo);
       if (RESID) {
@@ -462,7 +469,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
           if (!wait_bar(&empty[s], (uint32_t)(((q / TP_S) & 1) ^ 1), abort)) break;
           unsigned char* st = base + (size_t)s * TP_STAGE;
           mbar_arrive_expect_tx(&full[s], (uint32_t)(TC_M * TC_KC * 4 + Rp * TC_KC * 4 * 2));
-          tma_load_2d(&mY, &full[s], st, kc * TC_KC, (int)(t * TC_M));
+          tma_load_2d(mX, &full[s], st, kc * TC_KC, (int)(t * TC_M));
           for (int n0 = 0; n0 < Rp; n0 += 16) {
             tma_load_2d(&mUhi, &full[s], st + 32 * 1024 + n0 * 128, kc * TC_KC, n0);
             tma_load_2d(&mUlo, &full[s], st + 40 * 1024 + n0 * 128, kc * TC_KC, n0);
@@ -525,11 +532,10 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
       }
       tc_commit(done);
       wait_bar(done, 0, abort);
-      (void)Kc2;
     }
     __syncwarp();
   } else if (warp == 2 || warp == 3) {
-    // ---------------- Y splitters ----------------
+    // ---------------- X splitters ----------------
     const int ct = threadIdx.x - 64;
     long long q = 0;
     for (long long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
@@ -569,15 +575,10 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
         float v[32];
         tmem_ld32(tD1 + lq + c0, v);
         if (live && !WRITE_ET) {
-          float* prow = P + f * r;
-          if ((r & 3) == 0) {
+          // column-major (F x r): consecutive threads write consecutive addresses
 #pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              if (c0 + i < r)
-                *reinterpret_cast<float4*>(prow + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-          } else {
-            for (int i = 0; i < 32 && c0 + i < r; ++i) prow[c0 + i] = v[i];
-          }
+          for (int i = 0; i < 32; ++i)
+            if (c0 + i < r) P[f + F * (c0 + i)] = v[i];
         }
         if (RESID) {
           float h[32], l[32];
@@ -594,7 +595,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
         okw = __all_sync(0xffffffffu, okw);
         if (!okw) break;
         tc_fence_after();
-        const float* yrow = a.Y + f * n1;
+        const float* xrow = Xg + f * n1;
         for (int c0 = 0; c0 < n1p; c0 += 32) {
           float v[32];
           tmem_ld32(tD2 + lq + c0, v);
@@ -604,19 +605,25 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
 #pragma unroll
             for (int i = 0; i < 32; i += 4) {
               if (c0 + i < n1) {
-                const float4 y = *reinterpret_cast<const float4*>(yrow + c0 + i);
+                const float4 y = *reinterpret_cast<const float4*>(xrow + c0 + i);
                 const float e0 = y.x - v[i], e1 = y.y - v[i + 1], e2 = y.z - v[i + 2], e3 = y.w - v[i + 3];
                 es = fmaf(e0, e0, es); es = fmaf(e1, e1, es); es = fmaf(e2, e2, es); es = fmaf(e3, e3, es);
                 ys = fmaf(y.x, y.x, ys); ys = fmaf(y.y, y.y, ys); ys = fmaf(y.z, y.z, ys); ys = fmaf(y.w, y.w, ys);
+                if (WRITE_ET) {
+                  float* et = a.Et + f;
+                  et[(long long)(c0 + i) * a.et_stride] = e0;
+                  et[(long long)(c0 + i + 1) * a.et_stride] = e1;
+                  et[(long long)(c0 + i + 2) * a.et_stride] = e2;
+                  et[(long long)(c0 + i + 3) * a.et_stride] = e3;
+                }
               }
             }
             eacc += (double)es;
             yacc += (double)ys;
-            if (WRITE_ET) {
-#pragma unroll 8
-              for (int i = 0; i < 32; ++i)
-                if (c0 + i < n1) a.Et[(long long)(c0 + i) * F + f] = yrow[c0 + i] - v[i];
-            }
+          } else if (WRITE_ET && f < a.et_stride) {
+            // zero the padding fibers the Gram's last K chunk reads
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < n1) a.Et[(long long)(c0 + i) * a.et_stride + f] = 0.f;
           }
         }
         tc_fence_before();
@@ -644,15 +651,15 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj1(const Ctl* __restrict__ ctl
   if (threadIdx.x == 0 && *abort) const_cast<Ctl*>(ctl)->status = 5;
 }
 
-// Split copies of U_1 for the tensor-core pass (after the initial ST-HOSVD and after growth):
-// column-major (n_1 x cap, as the FP32 work copy) and row-major (n_1 x 64) TF32 hi/lo parts.
-__global__ void k_split_u1(const Ctl* ctl, int pred, const double* U, int ldu, float* uhi,
-                           float* ulo, float* urhi, float* urlo) {
+// Split copies of U_k for the tensor-core passes (after the initial ST-HOSVD and after growth):
+// column-major (n_k x cap, as the FP32 work copy) and row-major (n_k x 64) TF32 hi/lo parts.
+__global__ void k_split_u(const Ctl* ctl, int k, int pred, const double* U, int ldu, float* uhi,
+                          float* ulo, float* urhi, float* urlo) {
   if (ctl->status) return;
-  if (pred && !ctl->grew[0]) return;
-  const int n1 = ctl->n[0];
-  const int r = ctl->r[0];
-  const int cap = ctl->cap[0];
+  if (pred && !ctl->grew[k]) return;
+  const int n1 = ctl->n[k];
+  const int r = ctl->r[k];
+  const int cap = ctl->cap[k];
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < (long long)n1 * cap;
        L += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(L % n1), i = (int)(L / n1);
@@ -668,50 +675,55 @@ __global__ void k_split_u1(const Ctl* ctl, int pred, const double* U, int ldu, f
   }
 }
 
-cudaError_t launch_split_u1(const Ctl* ctl, int pred, const double* U, int ldu, float* const* sp,
-                            cudaStream_t st) {
-  k_split_u1<<<64, 256, 0, st>>>(ctl, pred, U, ldu, sp[0], sp[1], sp[2], sp[3]);
+cudaError_t launch_split_u(const Ctl* ctl, int k, int pred, const double* U, int ldu,
+                           float* const* sp, cudaStream_t st) {
+  k_split_u<<<64, 256, 0, st>>>(ctl, k, pred, U, ldu, sp[0], sp[1], sp[2], sp[3]);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_proj1(const Ctl* ctl, int mode, int pred, const float* Y, long long F,
-                            int n1, const TcProjMaps& m, void* const* dbufs, int out_off,
-                            double* part_e2, double* part_y2, int nparts, float* Et, int grid,
-                            cudaStream_t st) {
+cudaError_t launch_tc_proj(const Ctl* ctl, int k, int mode, int pred, const float* Y,
+                           long long F0, int n0, const TcProjMaps& m, void* const* dbufs,
+                           int out_off, double* part_e2, double* part_y2, int nparts, float* Et,
+                           long long et_stride, int grid, cudaStream_t st) {
   CUtensorMap mY;
-  if (!make_map_2d_f32(&mY, Y, F, n1, n1, 32, 128)) return cudaErrorInvalidValue;
-  TcProjArgs a{(float* const*)dbufs, out_off, part_e2, part_y2, nparts, Y, Et};
+  if (k == 0) {
+    if (!make_map_2d_f32(&mY, Y, F0, n0, n0, 32, 128)) return cudaErrorInvalidValue;
+  } else {
+    mY = m.d[0];   // unused for k >= 1 (the input is a D buffer)
+  }
+  TcProjArgs a{(float* const*)dbufs, out_off, part_e2, part_y2, nparts, Y, Et, et_stride, k};
   static bool attr[3] = {false, false, false};
   if (mode == 0) {
-    if (!attr[0]) { cudaFuncSetAttribute(k_tc_proj1<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[0] = true; }
-    k_tc_proj1<false, false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
+    if (!attr[0]) { cudaFuncSetAttribute(k_tc_proj<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[0] = true; }
+    k_tc_proj<false, false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
   } else if (mode == 1) {
-    if (!attr[1]) { cudaFuncSetAttribute(k_tc_proj1<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[1] = true; }
-    k_tc_proj1<true, false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
+    if (!attr[1]) { cudaFuncSetAttribute(k_tc_proj<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[1] = true; }
+    k_tc_proj<true, false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
   } else {
-    if (!attr[2]) { cudaFuncSetAttribute(k_tc_proj1<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[2] = true; }
-    k_tc_proj1<true, true><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.uhi, m.ulo, m.urhi, m.urlo, a);
+    if (!attr[2]) { cudaFuncSetAttribute(k_tc_proj<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[2] = true; }
+    k_tc_proj<true, true><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
   }
   return cudaGetLastError();
 }
 
 // =============================================================================================
-// k_tc_syrk: partial Gram G = E^T E of the mode-1 residual unfolding (Alg. 1's Gram of E_(1)),
-// split over the fibers (K). E^T (n_1 x F) streams by TMA in 32-fiber chunks; both operands are
-// split on chip into TF32 hi/lo (3xTF32); one CTA per (128-row block of G, K split); partial
-// blocks are summed in FP64 by k_syrk_reduce.
+// k_tc_syrk: partial Gram G = E^T E of the mode-k residual unfolding (Alg. 1's Gram of E_(k)),
+// split over the fibers (K). E^T (n_k x Fs, row stride Fs) streams by TMA in 32-fiber chunks;
+// both operands are split on chip into TF32 hi/lo (3xTF32); one CTA per (128-row block of G, K
+// split); partial blocks are summed in FP64 by k_syrk_reduce.
 // =============================================================================================
 constexpr int TS_STAGE = 96 * 1024;    // A hi | A lo | B hi | B lo (B up to 256 rows)
 constexpr int TS_S = 2;
 constexpr size_t TS_SMEM = (size_t)TS_S * TS_STAGE + 1024 + 256;
 
-__global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl,
+__global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl, int k,
                                                    const __grid_constant__ CUtensorMap mEa,
                                                    const __grid_constant__ CUtensorMap mEb,
-                                                   double* __restrict__ gpart, long long F) {
+                                                   double* __restrict__ gpart) {
   if (ctl->status) return;
-  if (!ctl->grew[0] || !tc_proj1_ok(ctl, ctl->r[0])) return;
-  const int n1 = ctl->n[0];
+  if (!tc_gram_ok(ctl, k)) return;
+  const int n1 = ctl->n[k];
+  const long long F = view_B(ctl, k);
   const int n1p = (n1 + 15) / 16 * 16;
   const int MT = gridDim.y, mt = blockIdx.y;
   const int S = gridDim.x, sp = blockIdx.x;
@@ -720,7 +732,6 @@ __global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl,
   const long long c_beg = sp * per;
   const long long c_end = c_beg + per < KC ? c_beg + per : KC;
   const int nchunks = c_end > c_beg ? (int)(c_end - c_beg) : 0;
-
   extern __shared__ __align__(1024) unsigned char ssm_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(ssm_raw) + 1023) & ~uintptr_t(1023));
@@ -847,11 +858,11 @@ __global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl,
   if (threadIdx.x == 0 && *abort) const_cast<Ctl*>(ctl)->status = 5;
 }
 
-// G (n_1 x n_1, FP64, column-major) = sum over K splits of the partial 128-row blocks.
-__global__ void k_syrk_reduce(const Ctl* ctl, const double* gpart, int S, int MT, double* G) {
+// G (n_k x n_k, FP64, column-major) = sum over K splits of the partial 128-row blocks.
+__global__ void k_syrk_reduce(const Ctl* ctl, int k, const double* gpart, int S, int MT, double* G) {
   if (ctl->status) return;
-  if (!ctl->grew[0] || !tc_proj1_ok(ctl, ctl->r[0])) return;
-  const int n1 = ctl->n[0];
+  if (!tc_gram_ok(ctl, k)) return;
+  const int n1 = ctl->n[k];
   const int n1p = (n1 + 15) / 16 * 16;
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < (long long)n1 * n1;
        L += (long long)gridDim.x * blockDim.x) {
@@ -863,17 +874,14 @@ __global__ void k_syrk_reduce(const Ctl* ctl, const double* gpart, int S, int MT
   }
 }
 
-cudaError_t launch_tc_gram1(const Ctl* ctl, const float* Et, long long F, int n1, double* gpart,
-                            double* G, int nsm, cudaStream_t st) {
-  CUtensorMap ma, mb;
-  if (!make_map_2d_f32(&ma, Et, n1, F, F, 32, 128)) return cudaErrorInvalidValue;
-  if (!make_map_2d_f32(&mb, Et, n1, F, F, 32, 16)) return cudaErrorInvalidValue;
+cudaError_t launch_tc_gram(const Ctl* ctl, int k, const TcProjMaps& m, int n1, double* gpart,
+                           double* G, int nsm, cudaStream_t st) {
   const int MT = (n1 + TC_M - 1) / TC_M;
   const int S = nsm / MT;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_tc_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM); attr = true; }
-  k_tc_syrk<<<dim3(S, MT), 256, TS_SMEM, st>>>(ctl, ma, mb, gpart, F);
-  k_syrk_reduce<<<64, 256, 0, st>>>(ctl, gpart, S, MT, G);
+  k_tc_syrk<<<dim3(S, MT), 256, TS_SMEM, st>>>(ctl, k, m.eta, m.etb, gpart);
+  k_syrk_reduce<<<64, 256, 0, st>>>(ctl, k, gpart, S, MT, G);
   return cudaGetLastError();
 }
 

@@ -81,24 +81,26 @@ struct TcMaps {
 bool make_map_2d_f32(CUtensorMap* map, const void* base, long long rows, long long cols,
                      long long ld, int box_cols, int box_rows);
 size_t tc_rowgemm_smem();
-struct TcProjMaps {
-  CUtensorMap uhi, ulo;     // U_1 TF32 splits, column-major n_1 x cap (rows of B1 = columns of U)
-  CUtensorMap urhi, urlo;   // U_1 TF32 splits, row-major n_1 x 64
-};
-cudaError_t launch_split_u1(const Ctl* ctl, int pred, const double* U, int ldu, float* const* sp,
-                            cudaStream_t st);
-// mode 0: projection only (pass C), 1: projection + residual norms (pass A),
-// 2: residual E^T written to Et (pre-pass of the Gram, only when mode 1 grew).
-cudaError_t launch_tc_proj1(const Ctl* ctl, int mode, int pred, const float* Y, long long F,
-                            int n1, const TcProjMaps& m, void* const* dbufs, int out_off,
-                            double* part_e2, double* part_y2, int nparts, float* Et, int grid,
-                            cudaStream_t st);
-cudaError_t launch_tc_gram1(const Ctl* ctl, const float* Et, long long F, int n1, double* gpart,
-                            double* G, int nsm, cudaStream_t st);
 cudaError_t launch_tc_cv(Ctl* ctl, SecWork w, const TcMaps& maps, void* const* cbufs_host,
                          void* const* vbufs_host, void* const* d_cbufs, void* const* d_vbufs,
                          const void* cu, const void* wv, const void* evec, void* const* dbufs,
                          int ldc, int grid, cudaStream_t st);
+struct TcProjMaps {
+  CUtensorMap uhi, ulo;     // U_k TF32 splits, column-major n_k x cap (rows of B1 = columns of U)
+  CUtensorMap urhi, urlo;   // U_k TF32 splits, row-major n_k x 64
+  CUtensorMap d[3];         // the D* buffers viewed as row-major (rows x n_k), box 32 x 128
+  CUtensorMap eta, etb;     // E^T (n_k x Fs), boxes 32 x 128 and 32 x 16
+};
+cudaError_t launch_split_u(const Ctl* ctl, int k, int pred, const double* U, int ldu,
+                           float* const* sp, cudaStream_t st);
+// mode 0: projection only (pass C), 1: projection + residual norms (pass A),
+// 2: residual E^T written to Et (pre-pass of the Gram, only when mode k grew).
+cudaError_t launch_tc_proj(const Ctl* ctl, int k, int mode, int pred, const float* Y,
+                           long long F0, int n0, const TcProjMaps& m, void* const* dbufs,
+                           int out_off, double* part_e2, double* part_y2, int nparts, float* Et,
+                           long long et_stride, int grid, cudaStream_t st);
+cudaError_t launch_tc_gram(const Ctl* ctl, int k, const TcProjMaps& m, int n1, double* gpart,
+                           double* G, int nsm, cudaStream_t st);
 
 // ---- k_misc.cu ----
 template <typename TW>
