@@ -42,6 +42,28 @@ __device__ int sturm_count(const TE* a, const TE* b2, int n, TE x, TE pivmin) {
   return cnt;
 }
 
+// Sturm counts at three shifts in one sweep (three independent recurrences per step).
+template <typename TE>
+__device__ void sturm_count3(const TE* a, const TE* b2, int n, TE x0, TE x1, TE x2, TE pivmin,
+                             int& c0, int& c1, int& c2) {
+  c0 = c1 = c2 = 0;
+  TE q0 = a[0] - x0, q1 = a[0] - x1, q2 = a[0] - x2;
+  if (fabs(q0) < pivmin) q0 = -pivmin;
+  if (fabs(q1) < pivmin) q1 = -pivmin;
+  if (fabs(q2) < pivmin) q2 = -pivmin;
+  c0 += q0 < TE(0); c1 += q1 < TE(0); c2 += q2 < TE(0);
+  for (int i = 1; i < n; ++i) {
+    const TE ai = a[i], bi = b2[i - 1];
+    q0 = (ai - x0) - sturm_div(bi, q0);
+    q1 = (ai - x1) - sturm_div(bi, q1);
+    q2 = (ai - x2) - sturm_div(bi, q2);
+    if (fabs(q0) < pivmin) q0 = -pivmin;
+    if (fabs(q1) < pivmin) q1 = -pivmin;
+    if (fabs(q2) < pivmin) q2 = -pivmin;
+    c0 += q0 < TE(0); c1 += q1 < TE(0); c2 += q2 < TE(0);
+  }
+}
+
 struct EigArgs {
   const double* G;   // n x n FP64 input (column-major)
   void* Aw;          // n x n TE scratch
@@ -55,9 +77,13 @@ struct EigArgs {
 // mode 0: residual Gram of spatial mode k (Alg. 4), predicated on ctl->grew[k].
 // mode 1: data Gram of mode k in the batch ST-HOSVD (Alg. 2): r >= 1.
 // use_smem: the n x n working matrix lives in (dynamic) shared memory instead of global memory.
+constexpr int EIG_SMEM_VECS = 16;
+
+// use_smem: dynamic shared memory holds the eigenvector workspaces (up to EIG_SMEM_VECS vectors)
+// after the n x n working matrix when use_amat, else at its start.
 template <typename TE>
 __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, EigArgs ea,
-                                                    int use_smem) {
+                                                    int use_smem, int use_amat) {
   extern __shared__ __align__(16) unsigned char eig_dyn[];
   if (ctl->status) return;
   if (mode == 0 && !ctl->grew[k]) return;
@@ -65,7 +91,7 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   const int n = (k == d - 1) ? ctl->init_nt : ctl->n[k];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
-  TE* A = use_smem ? reinterpret_cast<TE*>(eig_dyn) : reinterpret_cast<TE*>(ea.Aw);
+  TE* A = use_amat ? reinterpret_cast<TE*>(eig_dyn) : reinterpret_cast<TE*>(ea.Aw);
   __shared__ TE sa[TK_N_MAX], sb[TK_N_MAX], sb2[TK_N_MAX], stau[TK_N_MAX], slam[TK_N_MAX];
   __shared__ TE sv[TK_N_MAX], sp[TK_N_MAX];
   __shared__ TE tred[32];
@@ -76,23 +102,43 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   __syncthreads();
 
   // ---- Householder tridiagonalization: A = Q T Q^T, reflectors stored below the diagonal ----
-  for (int c = 0; c < n - 2; ++c) {
+  // Reflector c (LAPACK convention H = I - tau v v^T, v_0 = 1) from column c below the
+  // diagonal; warp 0 forms it (warp reduction) as soon as that column is final, into one of two
+  // buffers, while the other warps finish the rank-2 update of the previous step.
+  __shared__ TE svb[2][TK_N_MAX];
+  __shared__ int s_skip[2];
+  auto make_reflector = [&](int c, int buf) {
+    // warp 0 only
     const int m = n - c - 1;
     TE* x = A + (long long)c * n + c + 1;
     TE part = TE(0);
-    for (int i = 1 + tid; i < m; i += nt) part += x[i] * x[i];
-    const TE xn2 = block_sum(part, tred);
+    for (int i = 1 + lane; i < m; i += 32) part += x[i] * x[i];
+    const TE xn2 = warp_sum(part);
     const TE alpha = x[0];
     if (xn2 == TE(0)) {
-      if (tid == 0) { stau[c] = TE(0); sb[c] = alpha; }
-      __syncthreads();
-      continue;
+      if (lane == 0) { stau[c] = TE(0); sb[c] = alpha; s_skip[buf] = 1; }
+      return;
     }
     const TE beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
     const TE tau = (beta - alpha) / beta;
     const TE scal = TE(1) / (alpha - beta);
-    for (int i = tid; i < m; i += nt) sv[i] = (i == 0) ? TE(1) : x[i] * scal;
-    __syncthreads();
+    for (int i = lane; i < m; i += 32) svb[buf][i] = (i == 0) ? TE(1) : x[i] * scal;
+    if (lane == 0) { stau[c] = tau; sb[c] = beta; s_skip[buf] = 0; }
+  };
+  if (n > 2 && wid == 0) make_reflector(0, 0);
+  __syncthreads();
+  for (int c = 0; c < n - 2; ++c) {
+    const int m = n - c - 1;
+    const int cur = c & 1;
+    const TE* sv = svb[cur];
+    TE* x = A + (long long)c * n + c + 1;
+    if (s_skip[cur]) {
+      __syncthreads();
+      if (wid == 0 && c + 1 < n - 2) make_reflector(c + 1, cur ^ 1);
+      __syncthreads();
+      continue;
+    }
+    const TE tau = stau[c];
     // p = tau * A22 v  (A22 symmetric: p_i = sum_j A22(j, i) v_j, column i contiguous)
     for (int i = wid; i < m; i += nwarp) {
       const TE* col = A + (long long)(c + 1 + i) * n + (c + 1);
@@ -102,19 +148,27 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
       if (lane == 0) sp[i] = tau * s;
     }
     __syncthreads();
-    TE pv = TE(0);
-    for (int i = tid; i < m; i += nt) pv += sp[i] * sv[i];
-    pv = block_sum(pv, tred);
-    const TE K = -TE(0.5) * tau * pv;
-    for (int i = tid; i < m; i += nt) sp[i] += K * sv[i];   // w
+    if (wid == 0) {
+      // w = p - (tau/2)(p^T v) v
+      TE pv = TE(0);
+      for (int i = lane; i < m; i += 32) pv += sp[i] * sv[i];
+      pv = warp_sum(pv);
+      const TE K = -TE(0.5) * tau * pv;
+      for (int i = lane; i < m; i += 32) sp[i] += K * sv[i];
+    }
     __syncthreads();
+    // A22 -= v w^T + w v^T; warp 0 owns column 0 of A22 (the next reflector's column) and forms
+    // the next reflector right after updating it.
     for (int j = wid; j < m; j += nwarp) {
       TE* colj = A + (long long)(c + 1 + j) * n + (c + 1);
       const TE svj = sv[j], spj = sp[j];
       for (int i = lane; i < m; i += 32) colj[i] -= sv[i] * spj + sp[i] * svj;
+      if (j == 0 && c + 1 < n - 2) {
+        __syncwarp();
+        make_reflector(c + 1, cur ^ 1);
+      }
     }
     for (int i = tid; i < m; i += nt) x[i] = sv[i];
-    if (tid == 0) { stau[c] = tau; sb[c] = beta; }
     __syncthreads();
   }
   for (int i = tid; i < n; i += nt) sa[i] = A[(long long)i * n + i];
@@ -142,10 +196,17 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     const TE pivmin = max(Eps<TE>::tiny(), u * u * bmax2);
     for (int i = tid; i < n; i += nt) {
       TE lo = gl, hi = gu;
-      for (int it = 0; it < 200; ++it) {
-        const TE mid = TE(0.5) * (lo + hi);
-        if (hi - lo <= TE(2) * u * max(fabs(lo), fabs(hi)) + pivmin || mid == lo || mid == hi) break;
-        if (sturm_count(sa, sb2, n, mid, pivmin) > i) hi = mid; else lo = mid;
+      for (int it = 0; it < 100; ++it) {
+        const TE w = hi - lo;
+        if (w <= TE(2) * u * max(fabs(lo), fabs(hi)) + pivmin) break;
+        const TE x0 = lo + TE(0.25) * w, x1 = lo + TE(0.5) * w, x2 = lo + TE(0.75) * w;
+        if (!(x0 > lo && x2 < hi)) break;
+        int c0, c1, c2;
+        sturm_count3(sa, sb2, n, x0, x1, x2, pivmin, c0, c1, c2);
+        if (c0 > i) hi = x0;
+        else if (c1 > i) { lo = x0; hi = x1; }
+        else if (c2 > i) { lo = x1; hi = x2; }
+        else lo = x2;
       }
       slam[n - 1 - i] = TE(0.5) * (lo + hi);   // store descending
     }
@@ -196,8 +257,11 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   }
 
   // ---- inverse iteration for the top m eigenvalues ----
-  TE* Z = reinterpret_cast<TE*>(ea.Z);        // n x m
-  TE* LD = reinterpret_cast<TE*>(ea.LD);      // per vector: L (n), D (n)
+  // eigenvector workspaces in shared memory when up to EIG_SMEM_VECS vectors are needed
+  const bool zsm = use_smem && m <= EIG_SMEM_VECS;
+  TE* zbase = reinterpret_cast<TE*>(eig_dyn) + (size_t)n * n * use_amat;
+  TE* Z = zsm ? zbase : reinterpret_cast<TE*>(ea.Z);                       // n x m
+  TE* LD = zsm ? zbase + (size_t)EIG_SMEM_VECS * n : reinterpret_cast<TE*>(ea.LD);  // L, D
   TE tnorm = TE(0);
   for (int i = 0; i < n; ++i) tnorm = max(tnorm, fabs(sa[i]) + (i < n - 1 ? fabs(sb[i]) : TE(0)) + (i > 0 ? fabs(sb[i - 1]) : TE(0)));
   const TE u = Eps<TE>::u();
@@ -328,17 +392,19 @@ __global__ void __launch_bounds__(1024) k_append_factor(Ctl* ctl, int k, int mod
   if (tid == 0 && mode == 0) ctl->r[k] = r0 + m;
 }
 
-constexpr size_t EIG_SMEM_MAX = 180 * 1024;
+constexpr size_t EIG_SMEM_MAX = 200 * 1024;
 
 template <typename TE>
 cudaError_t launch_eig(Ctl* ctl, int k, int mode, const double* G, void* Aw, void* Z, void* LD,
                        double* W, double* lam, int mcap, int n, cudaStream_t st) {
   EigArgs ea{G, Aw, Z, LD, W, lam, mcap};
-  const size_t need = (size_t)n * n * sizeof(TE);
-  const int use = need <= EIG_SMEM_MAX ? 1 : 0;
-  const size_t sm = use ? need : 0;
-  if (use) cudaFuncSetAttribute(k_eig_topk<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_eig_topk<TE><<<1, EIG_NT, sm, st>>>(ctl, k, mode, ea, use);
+  const size_t mat = (size_t)n * n * sizeof(TE);
+  const size_t vec = (size_t)EIG_SMEM_VECS * 3 * n * sizeof(TE);
+  const int use_vec = (vec <= 150 * 1024) ? 1 : 0;
+  const int use_amat = (use_vec && mat + vec <= EIG_SMEM_MAX) ? 1 : 0;
+  const size_t sm = (use_amat ? mat : 0) + (use_vec ? vec : 0);
+  if (sm) cudaFuncSetAttribute(k_eig_topk<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_eig_topk<TE><<<1, EIG_NT, sm, st>>>(ctl, k, mode, ea, use_vec, use_amat);
   return cudaGetLastError();
 }
 
