@@ -64,6 +64,214 @@ __device__ void sturm_count3(const TE* a, const TE* b2, int n, TE x0, TE x1, TE 
   }
 }
 
+// Householder tridiagonalization of an FP32 Gram matrix held in registers (n <= 192), one CTA of
+// 12 warps run before the eigensolver. Thread (warp w, lane l) owns A(w + 12a, l + 32b) for
+// a < RA, b < CB. Step c: every warp forms reflector c (LAPACK convention H = I - tau v v^T,
+// v_0 = 1) from column c in shared memory; p = tau A22 v is reduced across a warp's lanes by a
+// butterfly that halves the rows a lane carries at each level (RA rows cost RA shuffles rather
+// than 5 RA); after one barrier every warp forms w = p - (tau/2)(p^T v) v itself, applies
+// A22 -= v w^T + w v^T to its registers and the owners of column c+1 publish it; second barrier.
+// The step body is instantiated per first live column block CB0 = (c+1)/32, so blocks of rows
+// and columns left of the trailing matrix drop out at compile time and the loops carry no
+// branches; entries outside the trailing matrix are masked by selects.
+// Output: reflector c in V[c n + c + 1 ...]; tri = [diagonal (n), off-diagonal (n), tau (n)].
+constexpr int TRI_NW = 12;
+
+// p ? x : y through PTX selp. Picking register areg[a][b] for a run-time b with a plain
+// comparison lets the compiler turn the unrolled choice into an indexed access, which moves the
+// whole register array to local memory; the opaque select keeps it in registers.
+__device__ __forceinline__ float sel_f32(bool p, float x, float y) {
+  float r;
+  asm("{.reg .pred q; setp.ne.u32 q, %1, 0; selp.f32 %0, %2, %3, q;}"
+      : "=f"(r) : "r"((unsigned)p), "f"(x), "f"(y));
+  return r;
+}
+
+struct TriSmem {
+  float* sx0;
+  float* sx1;
+  float* sw;
+  float* sa;
+  float* sb;
+  float* stau;
+};
+
+template <int RA, int CB, int CB0>
+__device__ __forceinline__ void tri_step(float (&areg)[RA][CB], int c, int n, int lane, int wid,
+                                         float* V, const TriSmem& sm) {
+  constexpr int LOGRA = RA == 16 ? 4 : RA == 8 ? 3 : RA == 4 ? 2 : RA == 2 ? 1 : 0;
+  // row blocks a whose rows w + 12a all lie left of column 32 CB0 - 1 <= c are dead
+  constexpr int A0 = CB0 == 0 ? 0 : (32 * CB0 - TRI_NW) / TRI_NW + 1;
+  const float* x = (c & 1) ? sm.sx1 : sm.sx0;
+  float* xn = (c & 1) ? sm.sx0 : sm.sx1;
+  // reflector from x = A(c+1:n, c); the same in every warp (same inputs and reduction order)
+  float xc[CB];
+  float part = 0.f;
+#pragma unroll
+  for (int b = CB0; b < CB; ++b) {
+    const int j = lane + 32 * b;
+    xc[b] = x[j];
+    part += sel_f32(j >= c + 2 && j < n, xc[b] * xc[b], 0.f);
+  }
+  const float xn2 = warp_sum(part);
+  const float alpha = x[c + 1];
+  float tau = 0.f, scal = 0.f, beta = alpha;
+  if (xn2 != 0.f) {
+    beta = -copysignf(sqrtf(alpha * alpha + xn2), alpha);
+    tau = __fdividef(beta - alpha, beta);
+    scal = __fdividef(1.f, alpha - beta);
+  }
+  // tau = 0 leaves v = e_1 and p = w = 0: the step is an exact no-op
+  float vc[CB];
+#pragma unroll
+  for (int b = CB0; b < CB; ++b) {
+    const int j = lane + 32 * b;
+    vc[b] = sel_f32(j == c + 1, 1.f, sel_f32(j > c + 1 && j < n, xc[b] * scal, 0.f));
+  }
+  if (wid == 0) {
+    if (lane == 0) { sm.stau[c] = tau; sm.sb[c] = beta; }
+#pragma unroll
+    for (int b = CB0; b < CB; ++b) {
+      const int j = lane + 32 * b;
+      if (j > c && j < n) V[(long long)c * n + j] = vc[b];
+    }
+  }
+  float acc[RA];
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    acc[a] = 0.f;
+    if (a < A0) continue;
+#pragma unroll
+    for (int b = CB0; b < CB; ++b) acc[a] = fmaf(areg[a][b], vc[b], acc[a]);
+  }
+  // butterfly reduce-scatter: at level M the lanes with bit M set keep the upper half
+#pragma unroll
+  for (int lev = 0; lev < LOGRA; ++lev) {
+    const int M = 16 >> lev;
+    const int H = RA >> (lev + 1);
+    const bool up = (lane & M) != 0;
+#pragma unroll
+    for (int t = 0; t < H; ++t) {
+      const float keep = up ? acc[H + t] : acc[t];
+      const float send = up ? acc[t] : acc[H + t];
+      acc[t] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+    }
+  }
+#pragma unroll
+  for (int M = 16 >> LOGRA; M > 0; M >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], M);
+  {
+    const int my_a = lane >> (5 - LOGRA);
+    const bool writer = (lane & ((1 << (5 - LOGRA)) - 1)) == 0;
+    const int i = wid + TRI_NW * my_a;
+    if (writer && i > c && i < n) sm.sw[i] = tau * acc[0];
+  }
+  __syncthreads();
+  // w = p - (tau/2)(p^T v) v, again the same in every warp
+  float swc[CB];
+  float pv = 0.f;
+#pragma unroll
+  for (int b = CB0; b < CB; ++b) {
+    const int j = lane + 32 * b;
+    swc[b] = sm.sw[j];
+    pv += sel_f32(j > c && j < n, swc[b] * vc[b], 0.f);
+  }
+  pv = warp_sum(pv);
+  const float K = -0.5f * tau * pv;
+  float wc[CB];
+#pragma unroll
+  for (int b = CB0; b < CB; ++b) {
+    const int j = lane + 32 * b;
+    wc[b] = sel_f32(j > c && j < n, swc[b] + K * vc[b], 0.f);
+  }
+#pragma unroll
+  for (int a = A0; a < RA; ++a) {
+    const int i = wid + TRI_NW * a;
+    const bool live = i > c && i < n;
+    const float vi = sel_f32(i == c + 1, 1.f, sel_f32(live, x[i] * scal, 0.f));
+    const float wi = sel_f32(live, sm.sw[i] + K * vi, 0.f);
+#pragma unroll
+    for (int b = CB0; b < CB; ++b) areg[a][b] = fmaf(-vi, wc[b], fmaf(-wi, vc[b], areg[a][b]));
+  }
+  // column c+1 (block CB0) from its owners
+  if (lane == ((c + 1) & 31)) {
+#pragma unroll
+    for (int a = A0; a < RA; ++a) {
+      const int i = wid + TRI_NW * a;
+      if (i == c + 1) sm.sa[c + 1] = areg[a][CB0];
+      else if (i > c + 1 && i < n) xn[i] = areg[a][CB0];
+    }
+  }
+  __syncthreads();
+}
+
+template <int RA, int CB, int CB0>
+__device__ __forceinline__ void tri_steps(float (&areg)[RA][CB], int n, int lane, int wid, float* V,
+                                          const TriSmem& sm) {
+  // steps whose next column c+1 lies in block CB0
+  const int c_lo = CB0 == 0 ? 0 : 32 * CB0 - 1;
+  const int c_hi = min(32 * CB0 + 30, n - 3);
+  for (int c = c_lo; c <= c_hi; ++c) tri_step<RA, CB, CB0>(areg, c, n, lane, wid, V, sm);
+  if constexpr (CB0 + 1 < CB) tri_steps<RA, CB, CB0 + 1>(areg, n, lane, wid, V, sm);
+}
+
+template <int RA, int CB>
+__global__ void __launch_bounds__(TRI_NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int mode,
+                                                              const double* __restrict__ G, float* V,
+                                                              float* tri) {
+  if (ctl->status) return;
+  if (mode == 0 && !ctl->grew[k]) return;
+  const int d = ctl->d;
+  const int n = (k == d - 1) ? ctl->init_nt : ctl->n[k];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int SZ = TRI_NW * RA + 32;
+  static_assert(SZ > 32 * CB, "shared vectors must cover every column index");
+  __shared__ float sx[2][SZ];
+  __shared__ float sw[SZ];
+  __shared__ float sa[SZ], sb[SZ], stau[SZ];
+  for (int i = tid; i < SZ; i += blockDim.x) { sx[0][i] = 0.f; sx[1][i] = 0.f; sw[i] = 0.f; }
+  float areg[RA][CB];
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int i = wid + TRI_NW * a, j = lane + 32 * b;
+      areg[a][b] = (i < n && j < n) ? (float)G[(long long)i * n + j] : 0.f;
+    }
+  __syncthreads();
+  // column 0
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      const int i = wid + TRI_NW * a;
+      if (i == 0) sa[0] = areg[a][0];
+      else if (i < n) sx[0][i] = areg[a][0];
+    }
+  }
+  __syncthreads();
+  const TriSmem sm{sx[0], sx[1], sw, sa, sb, stau};
+  tri_steps<RA, CB, 0>(areg, n, lane, wid, V, sm);
+  // trailing entries: column n-2 is in buffer (n-2)&1; A(n-1, n-1) with its owner
+  if (lane == ((n - 1) & 31) && wid == (n - 1) % TRI_NW) {
+    const int a0 = (n - 1) / TRI_NW, b0 = (n - 1) >> 5;
+    float v = 0.f;
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int b = 0; b < CB; ++b) v = sel_f32(a == a0 && b == b0, areg[a][b], v);
+    sa[n - 1] = v;
+  }
+  if (tid == 0) {
+    if (n >= 2) { sb[n - 2] = sx[(n - 2) & 1][n - 1]; stau[n - 2] = 0.f; }
+    stau[n - 1] = 0.f;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) {
+    tri[i] = sa[i];
+    tri[n + i] = sb[i];
+    tri[2 * n + i] = stau[i];
+  }
+}
+
 struct EigArgs {
   const double* G;   // n x n FP64 input (column-major)
   void* Aw;          // n x n TE scratch
@@ -83,7 +291,7 @@ constexpr int EIG_SMEM_VECS = 16;
 // after the n x n working matrix when use_amat, else at its start.
 template <typename TE>
 __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, EigArgs ea,
-                                                    int use_smem, int use_amat) {
+                                                    int use_smem, int use_amat, int pre) {
   extern __shared__ __align__(16) unsigned char eig_dyn[];
   if (ctl->status) return;
   if (mode == 0 && !ctl->grew[k]) return;
@@ -98,6 +306,17 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   __shared__ int s_m;
   __shared__ double s_disc;
 
+  __shared__ TE svb[2][TK_N_MAX];
+  __shared__ int s_skip[2];
+  if (pre) {
+    // tridiagonal form and reflectors from k_tridiag_reg: tri follows the n x n reflector block
+    const TE* V = reinterpret_cast<const TE*>(ea.Aw);
+    const TE* tri = V + (long long)n * n;
+    for (int i = tid; i < n; i += nt) { sa[i] = tri[i]; sb[i] = tri[n + i]; stau[i] = tri[2 * n + i]; }
+    if (use_amat)
+      for (long long L = tid; L < (long long)n * n; L += nt) A[L] = V[L];
+    __syncthreads();
+  } else {
   for (long long L = tid; L < (long long)n * n; L += nt) A[L] = (TE)ea.G[L];
   __syncthreads();
 
@@ -105,8 +324,6 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   // Reflector c (LAPACK convention H = I - tau v v^T, v_0 = 1) from column c below the
   // diagonal; warp 0 forms it (warp reduction) as soon as that column is final, into one of two
   // buffers, while the other warps finish the rank-2 update of the previous step.
-  __shared__ TE svb[2][TK_N_MAX];
-  __shared__ int s_skip[2];
   auto make_reflector = [&](int c, int buf) {
     // warp 0 only
     const int m = n - c - 1;
@@ -177,6 +394,7 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     if (n >= 1) stau[n - 1] = TE(0);
   }
   __syncthreads();
+  }  // !pre
   for (int i = tid; i < n - 1; i += nt) sb2[i] = sb[i] * sb[i];
   __syncthreads();
 
@@ -404,7 +622,20 @@ cudaError_t launch_eig(Ctl* ctl, int k, int mode, const double* G, void* Aw, voi
   const int use_amat = (use_vec && mat + vec <= EIG_SMEM_MAX) ? 1 : 0;
   const size_t sm = (use_amat ? mat : 0) + (use_vec ? vec : 0);
   if (sm) cudaFuncSetAttribute(k_eig_topk<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_eig_topk<TE><<<1, EIG_NT, sm, st>>>(ctl, k, mode, ea, use_vec, use_amat);
+  // FP32 Grams up to 192 x 192 are tridiagonalized by the register kernel first; the reflectors
+  // (n x n floats) and the tridiagonal (3n floats) fit in Aw, which holds n x n doubles
+  int pre = 0;
+  if (sizeof(TE) == 4 && n >= 3 && n <= TRI_NW * 16) {
+    float* V = reinterpret_cast<float*>(Aw);
+    float* tri = V + (size_t)n * n;
+    constexpr int T = TRI_NW * 32;
+    if (n <= 24) k_tridiag_reg<2, 1><<<1, T, 0, st>>>(ctl, k, mode, G, V, tri);
+    else if (n <= 48) k_tridiag_reg<4, 2><<<1, T, 0, st>>>(ctl, k, mode, G, V, tri);
+    else if (n <= 96) k_tridiag_reg<8, 3><<<1, T, 0, st>>>(ctl, k, mode, G, V, tri);
+    else k_tridiag_reg<16, 6><<<1, T, 0, st>>>(ctl, k, mode, G, V, tri);
+    pre = 1;
+  }
+  k_eig_topk<TE><<<1, EIG_NT, sm, st>>>(ctl, k, mode, ea, use_vec, use_amat, pre);
   return cudaGetLastError();
 }
 
