@@ -180,7 +180,9 @@ def run_ours(args):
     slices = [bf.slice_torch(t, dev) for t in range(T)]         # (12, 96, 192, 192) FP32 each
     torch.cuda.synchronize()
     slice_bytes = slices[0].numel() * slices[0].element_size()
-    caps = [0, 0, 0, 0, 256]
+    # the streaming rank never exceeds the number of slices seen, so that bounds its capacity
+    # (and the row stride of the core and V)
+    caps = [0, 0, 0, 0, min(256, (T + 4 + 7) // 8 * 8)]
     kw = dict(precision=args.precision, rank_cap=caps, steps_cap=T + 4, core_cap=4 << 20)
 
     def fresh_state():

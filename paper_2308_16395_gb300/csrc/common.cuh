@@ -181,6 +181,24 @@ __device__ __forceinline__ int map_new_to_old32(int j, const int* rn, const int*
   return jo;
 }
 
+// Register-resident form for per-lane row passes: the loops are unrolled over TK_MAXD so that
+// the rank arrays stay in registers.
+__device__ __forceinline__ int map_new_to_old_reg(int j, const int (&rn)[TK_MAXD],
+                                                  const int (&ro)[TK_MAXD], int m) {
+  int jo = 0, stride = 1;
+#pragma unroll
+  for (int k = 0; k < TK_MAXD; ++k) {
+    if (k < m) {
+      const int ik = j % rn[k];
+      j /= rn[k];
+      if (ik >= ro[k]) return -1;
+      jo += ik * stride;
+      stride *= ro[k];
+    }
+  }
+  return jo;
+}
+
 // Map a row index of a compact spatial tensor with dims `rn` (new) to the row index in the
 // compact layout with dims `ro` (old); returns -1 if the row is a zero-padded one (some i_k >=
 // ro[k]). Implements PadWithZeros (Eqs. pad_core_with_zeros, pad_singular_vectors_with_zeros).
@@ -204,7 +222,19 @@ __device__ __forceinline__ long long tk_map_new_to_old(long long j, const int* r
 // Whether the core/V update of this step runs on the tensor cores: mixed form, B^T (N x K split
 // into TF32 hi/lo) fits in shared memory, N <= 256. A pure function of the control block and the
 // kept streaming rank, evaluated identically by every kernel of the update.
+// Row passes with one row of C / V per lane (streaming rank up to 32 before and after the
+// update): the state is read once, in row-contiguous pieces, by every lane independently.
+#define ROWS_RMAX 32
+__device__ __forceinline__ bool rows_isvd_ok(const Ctl* ctl) {
+  const int r = ctl->r[ctl->d - 1];
+  return r >= 1 && r <= ROWS_RMAX;
+}
+__device__ __forceinline__ bool rows_cv_ok(const Ctl* ctl, int keep) {
+  return rows_isvd_ok(ctl) && keep >= 1 && keep <= ROWS_RMAX;
+}
+
 __device__ __forceinline__ bool tc_cv_ok(const Ctl* ctl, int keep) {
+  if (rows_cv_ok(ctl, keep)) return false;
   if (ctl->tw != 4) return false;
   const int r = ctl->r[ctl->d - 1];
   if (r < 1 || keep < 1) return false;

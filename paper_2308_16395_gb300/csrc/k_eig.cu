@@ -22,45 +22,32 @@ template <typename TE> struct Eps;
 template <> struct Eps<double> { static __device__ double u() { return 1.1102230246251565e-16; } static __device__ double tiny() { return 1e-290; } };
 template <> struct Eps<float> { static __device__ float u() { return 5.9604645e-08f; } static __device__ float tiny() { return 1e-35f; } };
 
-// Sturm count: number of eigenvalues of the tridiagonal (a, b) strictly below x.
-template <typename TE>
-__device__ __forceinline__ TE sturm_div(TE a, TE b) { return a / b; }
-template <>
-__device__ __forceinline__ float sturm_div<float>(float a, float b) { return __fdividef(a, b); }
+// Sturm counts at NS shifts in one sweep (NS independent recurrences per step). The quotient
+// b_i^2 / q uses the fast hardware reciprocal in FP32: the count only needs the sign of q, and a
+// relative error of a few ulp in one term moves it no more than the rounding of the subtraction.
+// The reciprocal unit (a quarter of the FMA rate) bounds the sweep, so three shifts per sweep
+// (two bits) balance its throughput against the latency of the recurrence.
+template <typename TE> __device__ __forceinline__ TE sturm_recip(TE q) { return TE(1) / q; }
+template <> __device__ __forceinline__ float sturm_recip<float>(float q) { return __fdividef(1.f, q); }
 
-template <typename TE>
-__device__ int sturm_count(const TE* a, const TE* b2, int n, TE x, TE pivmin) {
-  int cnt = 0;
-  TE q = a[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  if (q < TE(0)) ++cnt;
-  for (int i = 1; i < n; ++i) {
-    q = (a[i] - x) - sturm_div(b2[i - 1], q);
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < TE(0)) ++cnt;
+template <typename TE, int NS>
+__device__ void sturm_countN(const TE* a, const TE* b2, int n, const TE (&x)[NS], TE pivmin,
+                             int (&cnt)[NS]) {
+  TE q[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    q[s] = a[0] - x[s];
+    if (fabs(q[s]) < pivmin) q[s] = -pivmin;
+    cnt[s] = q[s] < TE(0);
   }
-  return cnt;
-}
-
-// Sturm counts at three shifts in one sweep (three independent recurrences per step).
-template <typename TE>
-__device__ void sturm_count3(const TE* a, const TE* b2, int n, TE x0, TE x1, TE x2, TE pivmin,
-                             int& c0, int& c1, int& c2) {
-  c0 = c1 = c2 = 0;
-  TE q0 = a[0] - x0, q1 = a[0] - x1, q2 = a[0] - x2;
-  if (fabs(q0) < pivmin) q0 = -pivmin;
-  if (fabs(q1) < pivmin) q1 = -pivmin;
-  if (fabs(q2) < pivmin) q2 = -pivmin;
-  c0 += q0 < TE(0); c1 += q1 < TE(0); c2 += q2 < TE(0);
   for (int i = 1; i < n; ++i) {
     const TE ai = a[i], bi = b2[i - 1];
-    q0 = (ai - x0) - sturm_div(bi, q0);
-    q1 = (ai - x1) - sturm_div(bi, q1);
-    q2 = (ai - x2) - sturm_div(bi, q2);
-    if (fabs(q0) < pivmin) q0 = -pivmin;
-    if (fabs(q1) < pivmin) q1 = -pivmin;
-    if (fabs(q2) < pivmin) q2 = -pivmin;
-    c0 += q0 < TE(0); c1 += q1 < TE(0); c2 += q2 < TE(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      q[s] = fma(-bi, sturm_recip(q[s]), ai - x[s]);
+      if (fabs(q[s]) < pivmin) q[s] = -pivmin;
+      cnt[s] += q[s] < TE(0);
+    }
   }
 }
 
@@ -412,19 +399,30 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     gl -= TE(2) * u * scale * n + Eps<TE>::tiny();
     gu += TE(2) * u * scale * n + Eps<TE>::tiny();
     const TE pivmin = max(Eps<TE>::tiny(), u * u * bmax2);
+    // absolute floor u |T|: the reduction to tridiagonal form already moves every eigenvalue by
+    // that much, so refining eigenvalues near zero (the residual Gram has r_k of them) further
+    // buys nothing and costs most of the sweeps
+    const TE atol = max(pivmin, u * scale);
     for (int i = tid; i < n; i += nt) {
       TE lo = gl, hi = gu;
-      for (int it = 0; it < 100; ++it) {
+      constexpr int NS = 3;   // 4-way multisection: two bits per sweep
+      for (int it = 0; it < 60; ++it) {
         const TE w = hi - lo;
-        if (w <= TE(2) * u * max(fabs(lo), fabs(hi)) + pivmin) break;
-        const TE x0 = lo + TE(0.25) * w, x1 = lo + TE(0.5) * w, x2 = lo + TE(0.75) * w;
-        if (!(x0 > lo && x2 < hi)) break;
-        int c0, c1, c2;
-        sturm_count3(sa, sb2, n, x0, x1, x2, pivmin, c0, c1, c2);
-        if (c0 > i) hi = x0;
-        else if (c1 > i) { lo = x0; hi = x1; }
-        else if (c2 > i) { lo = x1; hi = x2; }
-        else lo = x2;
+        if (w <= TE(2) * u * max(fabs(lo), fabs(hi)) + atol) break;
+        TE x[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) x[s] = lo + TE(s + 1) * TE(0.25) * w;
+        if (!(x[0] > lo && x[NS - 1] < hi)) break;
+        int cnt[NS];
+        sturm_countN<TE, NS>(sa, sb2, n, x, pivmin, cnt);
+        // the eigenvalue of ascending index i lies in the first sub-interval whose right end
+        // counts more than i eigenvalues below it
+        TE nlo = x[NS - 1], nhi = hi;
+#pragma unroll
+        for (int s = NS - 1; s >= 0; --s)
+          if (cnt[s] > i) { nhi = x[s]; nlo = (s > 0) ? x[s - 1] : lo; }
+        lo = nlo;
+        hi = nhi;
       }
       slam[n - 1 - i] = TE(0.5) * (lo + hi);   // store descending
     }
@@ -485,25 +483,29 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   const TE u = Eps<TE>::u();
   const TE pivt = max(u * tnorm, Eps<TE>::tiny());
   for (int v = tid; v < m; v += nt) {
-    // shift slightly away from the computed eigenvalue so the factorization is nonsingular
+    // shift slightly away from the computed eigenvalue so the factorization is nonsingular;
+    // LD holds L (n) and the reciprocal pivots 1/D (n) of T - sig I = L D L^T
     const TE sig = slam[v] + TE(4) * u * tnorm;
     TE* Lv = LD + (long long)v * 2 * n;
     TE* Dv = Lv + n;
     TE dcur = sa[0] - sig;
     if (fabs(dcur) < pivt) dcur = copysign(pivt, dcur == TE(0) ? TE(1) : dcur);
-    Dv[0] = dcur;
+    TE dinv = TE(1) / dcur;
+    Dv[0] = dinv;
     for (int i = 0; i < n - 1; ++i) {
-      const TE l = sb[i] / dcur;
+      const TE l = sb[i] * dinv;
       Lv[i] = l;
       dcur = (sa[i + 1] - sig) - l * sb[i];
       if (fabs(dcur) < pivt) dcur = copysign(pivt, dcur == TE(0) ? TE(1) : dcur);
-      Dv[i + 1] = dcur;
+      dinv = TE(1) / dcur;
+      Dv[i + 1] = dinv;
     }
-    // deterministic start vector
+    // deterministic start vector with entries in [1, 1.5]
+#pragma unroll 4
     for (int i = 0; i < n; ++i) {
       unsigned h = (unsigned)(i * 2654435761u) ^ (unsigned)((v + 1) * 40503u);
       h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
-      Z[(long long)v * n + i] = TE(1) + TE(0.5) * (TE)((h & 0xffff) / 65535.0);
+      Z[(long long)v * n + i] = TE(1) + TE(0.5 / 65535.0) * (TE)(h & 0xffffu);
     }
   }
   __syncthreads();
@@ -512,30 +514,51 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
       const TE* Lv = LD + (long long)v * 2 * n;
       const TE* Dv = Lv + n;
       TE* z = Z + (long long)v * n;
-      for (int i = 1; i < n; ++i) z[i] -= Lv[i - 1] * z[i - 1];
-      for (int i = 0; i < n; ++i) z[i] /= Dv[i];
-      for (int i = n - 2; i >= 0; --i) z[i] -= Lv[i] * z[i + 1];
+      // L y = z, then D L^T x = y with the pivot scaling folded into the backward sweep
+      TE prev = z[0];
+#pragma unroll 8
+      for (int i = 1; i < n; ++i) { prev = z[i] - Lv[i - 1] * prev; z[i] = prev; }
+      prev = prev * Dv[n - 1];
+      z[n - 1] = prev;
+      TE amax = fabs(prev);
+#pragma unroll 8
+      for (int i = n - 2; i >= 0; --i) {
+        prev = z[i] * Dv[i] - Lv[i] * prev;
+        z[i] = prev;
+        amax = max(amax, fabs(prev));
+      }
+      // the solve amplifies by up to 1/(4 u |T|): rescale to unit max-norm so the sums of
+      // squares below cannot overflow whatever the scale of the Gram matrix
+      const TE sc = amax > TE(0) ? TE(1) / amax : TE(0);
+#pragma unroll 8
+      for (int i = 0; i < n; ++i) z[i] *= sc;
     }
     __syncthreads();
-    // modified Gram-Schmidt across the m vectors (separates clusters), block-wide
-    for (int v = 0; v < m; ++v) {
-      TE* z = Z + (long long)v * n;
-      TE part = TE(0);
-      for (int i = tid; i < n; i += nt) part += z[i] * z[i];
-      const TE nrm = sqrt(block_sum(part, tred));
-      const TE inv = nrm > TE(0) ? TE(1) / nrm : TE(0);
-      for (int i = tid; i < n; i += nt) z[i] *= inv;
-      __syncthreads();
-      // project out of later vectors: one warp per later vector
+    // modified Gram-Schmidt across the m vectors (separates clusters): at step v, every later
+    // vector loses its component along z_v (one warp per later vector, z_v's norm recomputed
+    // by each warp), one barrier per step; all vectors are normalised together at the end
+    for (int v = 0; v + 1 < m; ++v) {
+      const TE* z = Z + (long long)v * n;
       for (int w = v + 1 + wid; w < m; w += nwarp) {
         TE* y = Z + (long long)w * n;
-        TE s = TE(0);
-        for (int i = lane; i < n; i += 32) s += z[i] * y[i];
+        TE s = TE(0), zz = TE(0);
+        for (int i = lane; i < n; i += 32) { s += z[i] * y[i]; zz += z[i] * z[i]; }
         s = warp_sum(s);
-        for (int i = lane; i < n; i += 32) y[i] -= s * z[i];
+        zz = warp_sum(zz);
+        const TE coef = zz > TE(0) ? s / zz : TE(0);
+        for (int i = lane; i < n; i += 32) y[i] -= coef * z[i];
       }
       __syncthreads();
     }
+    for (int v = wid; v < m; v += nwarp) {
+      TE* z = Z + (long long)v * n;
+      TE part = TE(0);
+      for (int i = lane; i < n; i += 32) part += z[i] * z[i];
+      const TE nrm = sqrt(warp_sum(part));
+      const TE inv = nrm > TE(0) ? TE(1) / nrm : TE(0);
+      for (int i = lane; i < n; i += 32) z[i] *= inv;
+    }
+    __syncthreads();
   }
   // ---- back-transform: x = H_0 H_1 ... H_{n-3} z (one warp per vector) ----
   for (int v = wid; v < m; v += nwarp) {

@@ -34,6 +34,7 @@ template <typename TW>
 __global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW* const* dbufs,
                                                TW* const* vbufs, double* __restrict__ part) {
   if (ctl->status) return;
+  if (rows_isvd_ok(ctl)) return;   // k_isvd_p_rows does this pass
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
   const int ldc = ctl->ldc;
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(256) k_isvd_e(const Ctl* __restrict__ ctl, TW*
                                                TW* const* vbufs, const double* __restrict__ p,
                                                TW* __restrict__ evec, double* __restrict__ part) {
   if (ctl->status) return;
+  if (rows_isvd_ok(ctl)) return;   // k_isvd_e_rows does this pass
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
   const int ldc = ctl->ldc;
@@ -597,6 +599,7 @@ __global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, 
                                                   const SecWork w) {
   if (ctl->status) return;
   if (tc_cv_ok(ctl, w.meta[2])) return;   // the tensor-core kernel does this update
+  if (rows_cv_ok(ctl, w.meta[2])) return;  // k_cv_rows does this update
   const int d = ctl->d, mm = d - 1;
   const int r = ctl->r[d - 1];
   const int keep = w.meta[2];
@@ -660,6 +663,266 @@ __global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, 
       for (int q = 0; q < 4; ++q) {
         const int c = n0 + tx + 16 * q;
         if (c < keep) Out[j * ldc + c] = acc[p][q] + xj * cvec[c];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Row passes with one row per lane (r_d <= 32). Each lane owns rows jn = g, g + G, ... of the new
+// spatial layout, maps each to its old row (zero padding has none), reads that row's r_d
+// coefficients as 16-byte pieces (the row start is aligned when ldc is a multiple of 4 floats /
+// 2 doubles) and keeps them in registers. Nothing is recomputed across lanes, so the index map
+// costs one mixed-radix decomposition per row. FP32 partial sums cover at most ROWS_FLUSH rows
+// before they are added into FP64 shared-memory slots.
+// ---------------------------------------------------------------------------------------------
+constexpr int ROWS_NT = 256;
+constexpr int ROWS_FLUSH = 32;
+
+template <typename TW>
+__device__ __forceinline__ void load_row(const TW* __restrict__ row, int r, bool vec, TW (&v)[ROWS_RMAX]) {
+  if (sizeof(TW) == 4 && vec) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int q = 0; q < ROWS_RMAX / 4; ++q) {
+      if (4 * q < r) {
+        const float4 t = __ldg(r4 + q);
+        v[4 * q] = (TW)t.x; v[4 * q + 1] = (TW)t.y; v[4 * q + 2] = (TW)t.z; v[4 * q + 3] = (TW)t.w;
+      } else {
+        v[4 * q] = v[4 * q + 1] = v[4 * q + 2] = v[4 * q + 3] = TW(0);
+      }
+    }
+  } else if (sizeof(TW) == 8 && vec) {
+    const double2* r2 = reinterpret_cast<const double2*>(row);
+#pragma unroll
+    for (int q = 0; q < ROWS_RMAX / 2; ++q) {
+      if (2 * q < r) {
+        const double2 t = __ldg(r2 + q);
+        v[2 * q] = (TW)t.x; v[2 * q + 1] = (TW)t.y;
+      } else {
+        v[2 * q] = v[2 * q + 1] = TW(0);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < ROWS_RMAX; ++c) v[c] = (c < r) ? row[c] : TW(0);
+  }
+  // columns r.. of the last piece are not part of the state (possibly never written)
+#pragma unroll
+  for (int c = 0; c < ROWS_RMAX; ++c) v[c] = (c < r) ? v[c] : TW(0);
+}
+
+// Adds the warp's FP32 partial sums acc[c] (c < ROWS_RMAX) into the FP64 slots sw[c] (lane 0).
+template <typename TW>
+__device__ __forceinline__ void rows_flush(TW (&acc)[ROWS_RMAX], double* sw, int lane) {
+#pragma unroll
+  for (int c = 0; c < ROWS_RMAX; ++c) {
+    const double t = warp_sum((double)acc[c]);
+    if (lane == 0) sw[c] += t;
+    acc[c] = TW(0);
+  }
+}
+
+// part[blockIdx.x * stride + c] = sum over the block's warps of sw[w][c], c < ncol.
+__device__ __forceinline__ void rows_block_sum(double (*sw)[ROWS_RMAX + 1], int ncol,
+                                               double* __restrict__ part, long long stride) {
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncol; c += ROWS_NT) {
+    double s = 0.0;
+    for (int w = 0; w < ROWS_NT / 32; ++w) s += sw[w][c];
+    part[(long long)blockIdx.x * stride + c] = s;
+  }
+}
+
+// p = V_pad^T d: partials per block in the layout of k_isvd_p. Warps walk 32 consecutive new
+// rows at a time (a warp-uniform loop, so the periodic FP64 flush is a warp reduction).
+template <typename TW>
+__global__ void __launch_bounds__(ROWS_NT) k_isvd_p_rows(const Ctl* __restrict__ ctl,
+                                                        TW* const* dbufs, TW* const* vbufs,
+                                                        double* __restrict__ part) {
+  if (ctl->status) return;
+  if (!rows_isvd_ok(ctl)) return;
+  const int d = ctl->d, m = d - 1;
+  const int r = ctl->r[d - 1];
+  const int ldc = ctl->ldc;
+  const bool vec = (ldc % (16 / (int)sizeof(TW))) == 0;
+  const TW* V = vbufs[ctl->cbuf];
+  const TW* dv = dbufs[ctl->xbuf];
+  int ro[TK_MAXD], rn[TK_MAXD];
+  long long Rn = 1;
+#pragma unroll
+  for (int i = 0; i < TK_MAXD; ++i) {
+    ro[i] = (i < m) ? ctl->rold[i] : 1;
+    rn[i] = (i < m) ? ctl->r[i] : 1;
+    Rn *= rn[i];
+  }
+  const bool same = !spatial_grew(ctl);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ double sw[ROWS_NT / 32][ROWS_RMAX + 1];
+  for (int c = lane; c <= ROWS_RMAX; c += 32) sw[wid][c] = 0.0;
+  TW acc[ROWS_RMAX];
+#pragma unroll
+  for (int c = 0; c < ROWS_RMAX; ++c) acc[c] = TW(0);
+  int it = 0;
+  const long long G = (long long)gridDim.x * ROWS_NT;
+  for (long long jb = (long long)blockIdx.x * ROWS_NT + wid * 32; jb < Rn; jb += G) {
+    const long long jn = jb + lane;
+    const int jo = (jn >= Rn) ? -1 : (same ? (int)jn : map_new_to_old_reg((int)jn, rn, ro, m));
+    if (jo >= 0) {
+      const TW dj = dv[jn];
+      TW v[ROWS_RMAX];
+      load_row<TW>(V + (long long)jo * ldc, r, vec, v);
+#pragma unroll
+      for (int c = 0; c < ROWS_RMAX; ++c) acc[c] += v[c] * dj;
+    }
+    if (++it == ROWS_FLUSH) { rows_flush<TW>(acc, sw[wid], lane); it = 0; }
+  }
+  rows_flush<TW>(acc, sw[wid], lane);
+  rows_block_sum(sw, r, part, TK_STREAM_CAP_MAX);
+}
+
+// e = d - V_pad p (stored), ||e||^2 and s = V_pad^T e: partials in the layout of k_isvd_e
+// (s in columns 0..r-1, ||e||^2 in column r).
+template <typename TW>
+__global__ void __launch_bounds__(ROWS_NT) k_isvd_e_rows(const Ctl* __restrict__ ctl,
+                                                        TW* const* dbufs, TW* const* vbufs,
+                                                        const double* __restrict__ p,
+                                                        TW* __restrict__ evec,
+                                                        double* __restrict__ part) {
+  if (ctl->status) return;
+  if (!rows_isvd_ok(ctl)) return;
+  const int d = ctl->d, m = d - 1;
+  const int r = ctl->r[d - 1];
+  const int ldc = ctl->ldc;
+  const bool vec = (ldc % (16 / (int)sizeof(TW))) == 0;
+  const TW* V = vbufs[ctl->cbuf];
+  const TW* dv = dbufs[ctl->xbuf];
+  int ro[TK_MAXD], rn[TK_MAXD];
+  long long Rn = 1;
+#pragma unroll
+  for (int i = 0; i < TK_MAXD; ++i) {
+    ro[i] = (i < m) ? ctl->rold[i] : 1;
+    rn[i] = (i < m) ? ctl->r[i] : 1;
+    Rn *= rn[i];
+  }
+  const bool same = !spatial_grew(ctl);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ double sw[ROWS_NT / 32][ROWS_RMAX + 1];
+  __shared__ TW pl[ROWS_RMAX];
+  for (int c = lane; c <= ROWS_RMAX; c += 32) sw[wid][c] = 0.0;
+  if (threadIdx.x < ROWS_RMAX) pl[threadIdx.x] = (threadIdx.x < r) ? (TW)p[threadIdx.x] : TW(0);
+  __syncthreads();
+  TW acc[ROWS_RMAX];
+#pragma unroll
+  for (int c = 0; c < ROWS_RMAX; ++c) acc[c] = TW(0);
+  typename AccOf<TW>::type eacc;
+  int it = 0;
+  const long long G = (long long)gridDim.x * ROWS_NT;
+  for (long long jb = (long long)blockIdx.x * ROWS_NT + wid * 32; jb < Rn; jb += G) {
+    const long long jn = jb + lane;
+    if (jn < Rn) {
+      const int jo = same ? (int)jn : map_new_to_old_reg((int)jn, rn, ro, m);
+      const TW dj = dv[jn];
+      TW e = dj;
+      if (jo >= 0) {
+        TW v[ROWS_RMAX];
+        load_row<TW>(V + (long long)jo * ldc, r, vec, v);
+        TW dot = TW(0);
+#pragma unroll
+        for (int c = 0; c < ROWS_RMAX; ++c) dot += v[c] * pl[c];
+        e = dj - dot;
+#pragma unroll
+        for (int c = 0; c < ROWS_RMAX; ++c) acc[c] += v[c] * e;
+      }
+      evec[jn] = e;
+      eacc.add(e * e);
+    }
+    if (++it == ROWS_FLUSH) { rows_flush<TW>(acc, sw[wid], lane); it = 0; }
+  }
+  rows_flush<TW>(acc, sw[wid], lane);
+  const double e2 = warp_sum(eacc.value());
+  if (lane == 0) sw[wid][ROWS_RMAX] = e2;
+  __syncthreads();
+  // ||e||^2 moves to column r (columns r.. of the slots hold zeros)
+  if (threadIdx.x < ROWS_NT / 32 && r < ROWS_RMAX) {
+    sw[threadIdx.x][r] = sw[threadIdx.x][ROWS_RMAX];
+  }
+  rows_block_sum(sw, r + 1, part, TK_STREAM_CAP_MAX + 2);
+}
+
+// C~ = C_pad B_c + d c_c^T (blockIdx.y = 0) and V~ = V_pad B_v + e w_v^T (blockIdx.y = 1), one
+// new row per lane, into the other buffer. B is r x keep row-major (ld ldb), staged in shared
+// memory and read as 4-wide broadcasts.
+template <typename TW>
+__global__ void __launch_bounds__(ROWS_NT) k_cv_rows(const Ctl* __restrict__ ctl,
+                                                    TW* const* cbufs, TW* const* vbufs,
+                                                    const TW* __restrict__ Bc,
+                                                    const TW* __restrict__ Bv, int ldb,
+                                                    const TW* __restrict__ cu,
+                                                    const TW* __restrict__ wv,
+                                                    const TW* __restrict__ evec,
+                                                    TW* const* dbufs, const SecWork w) {
+  if (ctl->status) return;
+  const int keep = w.meta[2];
+  if (!rows_cv_ok(ctl, keep)) return;
+  const int d = ctl->d, m = d - 1;
+  const int r = ctl->r[d - 1];
+  const int ldc = ctl->ldc;
+  const bool vec = (ldc % (16 / (int)sizeof(TW))) == 0;
+  const bool isV = blockIdx.y == 1;
+  const TW* In = (isV ? vbufs : cbufs)[ctl->cbuf];
+  TW* Out = (isV ? vbufs : cbufs)[ctl->cbuf ^ 1];
+  const TW* B = isV ? Bv : Bc;
+  const TW* cvec = isV ? wv : cu;
+  const TW* X = isV ? evec : dbufs[ctl->xbuf];
+  __shared__ __align__(16) TW Bs[ROWS_RMAX][ROWS_RMAX];
+  __shared__ __align__(16) TW cs[ROWS_RMAX];
+  for (int L = threadIdx.x; L < ROWS_RMAX * ROWS_RMAX; L += ROWS_NT) {
+    const int k = L / ROWS_RMAX, c = L % ROWS_RMAX;
+    Bs[k][c] = (k < r && c < keep) ? B[(long long)k * ldb + c] : TW(0);
+  }
+  if (threadIdx.x < ROWS_RMAX) cs[threadIdx.x] = (threadIdx.x < keep) ? cvec[threadIdx.x] : TW(0);
+  int ro[TK_MAXD], rn[TK_MAXD];
+  long long Rn = 1;
+#pragma unroll
+  for (int i = 0; i < TK_MAXD; ++i) {
+    ro[i] = (i < m) ? ctl->rold[i] : 1;
+    rn[i] = (i < m) ? ctl->r[i] : 1;
+    Rn *= rn[i];
+  }
+  const bool same = !spatial_grew(ctl);
+  __syncthreads();
+  const long long G = (long long)gridDim.x * ROWS_NT;
+  for (long long jn = (long long)blockIdx.x * ROWS_NT + threadIdx.x; jn < Rn; jn += G) {
+    const int jo = same ? (int)jn : map_new_to_old_reg((int)jn, rn, ro, m);
+    TW v[ROWS_RMAX];
+    if (jo >= 0) load_row<TW>(In + (long long)jo * ldc, r, vec, v);
+    else {
+#pragma unroll
+      for (int c = 0; c < ROWS_RMAX; ++c) v[c] = TW(0);
+    }
+    const TW xj = X[jn];
+    TW* orow = Out + jn * ldc;
+#pragma unroll
+    for (int c4 = 0; c4 < ROWS_RMAX / 4; ++c4) {
+      if (4 * c4 >= keep) break;
+      TW o[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) o[t] = xj * cs[4 * c4 + t];
+#pragma unroll
+      for (int k = 0; k < ROWS_RMAX; ++k) {
+        if (k >= r) break;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) o[t] += v[k] * Bs[k][4 * c4 + t];
+      }
+      if (vec && sizeof(TW) == 4) {
+        // columns keep.. of the last piece are zero (B and c are zero-padded); ldc % 4 == 0
+        // keeps the piece inside the row
+        *reinterpret_cast<float4*>(orow + 4 * c4) = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (4 * c4 + t < keep) orow[4 * c4 + t] = o[t];
       }
     }
   }
@@ -733,8 +996,11 @@ template <typename TW>
 cudaError_t launch_isvd(Ctl* ctl, void* const* dbufs, void* const* vbufs, double* part_p,
                         double* part_e, double* p, double* es, void* evec, const double* S,
                         SecWork w, int grid, cudaStream_t st) {
+  k_isvd_p_rows<TW><<<grid, ROWS_NT, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p);
   k_isvd_p<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p);
   k_reduce_vec<<<(TK_STREAM_CAP_MAX + 2 + 31) / 32, 256, 0, st>>>(ctl, part_p, grid, TK_STREAM_CAP_MAX, 0, p);
+  k_isvd_e_rows<TW><<<grid, ROWS_NT, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p,
+                                               (TW*)evec, part_e);
   k_isvd_e<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p, (TW*)evec,
                                      part_e);
   k_reduce_vec<<<(TK_STREAM_CAP_MAX + 2 + 31) / 32, 256, 0, st>>>(ctl, part_e, grid, TK_STREAM_CAP_MAX + 2, 1, es);
@@ -763,6 +1029,10 @@ template <typename TW>
 cudaError_t launch_cv(Ctl* ctl, void* const* dbufs, void* const* cbufs, void* const* vbufs,
                       SecWork w, const void* Bc, const void* cu, const void* Bv, const void* wv,
                       int ldb, const void* evec, int grid_cv, cudaStream_t st) {
+  k_cv_rows<TW><<<dim3(grid_cv, 2), ROWS_NT, 0, st>>>(ctl, (TW* const*)cbufs, (TW* const*)vbufs,
+                                                      (const TW*)Bc, (const TW*)Bv, ldb,
+                                                      (const TW*)cu, (const TW*)wv,
+                                                      (const TW*)evec, (TW* const*)dbufs, w);
   k_cv_update<TW><<<grid_cv, 256, 0, st>>>(ctl, (TW* const*)cbufs, (TW* const*)cbufs,
                                            (const TW*)Bc, ldb, (const TW*)cu, nullptr,
                                            (TW* const*)dbufs, w);
