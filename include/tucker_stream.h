@@ -117,6 +117,28 @@ tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* str
 tucker_status tucker_reconstruct(tucker_state* s, int64_t t_begin, int64_t t_end,
                                  void* out_dev, void* stream);
 
+/* Allocation-free form of tucker_reconstruct. The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory at the time they reconstruct. Examples are a
+ * process whose device memory is already reserved in full by another allocator, code on a
+ * device or under a virtualisation layer without stream-ordered memory pools (cudaMallocAsync,
+ * which tucker_reconstruct uses, is unsupported there), and latency-critical loops that must not
+ * pay for an allocation. Arguments, layout, output and errors are those of tucker_reconstruct.
+ * The temporaries live in one fixed device array of TUCKER_NOALLOC_SCRATCH_BYTES, which every GPU
+ * that loads this library holds until the process exits; each of the two temporaries may use
+ * half of it. A call whose largest temporary, C x_d U_d(t_begin:t_end, :) or a partial expansion
+ * C x_d U_d x_1 U_1 ... x_k U_k (k < d-1), needs more than half returns TUCKER_EINVAL before
+ * any device work. Reconstruct fewer slices per call in that case. The call allocates nothing:
+ * no cudaMalloc, no cudaFree, no pool or library allocation. The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current, so make that
+ * first call outside any stream capture. Every call, on every state, shares the one array and
+ * keeps its last contents. Nothing in it needs to start at zero, because each call writes every
+ * element it reads. Calls whose device work overlaps (on different streams or host threads)
+ * race on the array and must be serialised by the caller. Synchronizes `stream` once before
+ * its launches, to read the ranks. */
+#define TUCKER_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+tucker_status tucker_reconstruct_noalloc(tucker_state* s, int64_t t_begin, int64_t t_end,
+                                         void* out_dev, void* stream);
+
 /* Running error bound and data norm (Prop. 1, Prop. 2, App. D): *err_bound_host is the square
  * root of the accumulated squared truncation error (initial ST-HOSVD + every update), an upper
  * bound of ||X - X^||_F; *data_norm_host = ||X||_F over every slice seen. Synchronizes. */

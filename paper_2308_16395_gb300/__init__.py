@@ -24,7 +24,9 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ENUMERIC", 5: "
 EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info", "tucker_copy_factor",
            "tucker_copy_core", "tucker_copy_sv", "tucker_last_error", "tucker_destroy",
-           "tucker_version", "tucker_profile_enable", "tucker_profile_read"]
+           "tucker_version", "tucker_profile_enable", "tucker_profile_read",
+           "tucker_reconstruct_noalloc"]
+NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
 
@@ -74,6 +76,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_init_sthosvd.argtypes = [ctypes.POINTER(TuckerConfig), vp, i64, vp, ctypes.POINTER(vp)]
     lib.tucker_stream_update.argtypes = [vp, vp, vp]
     lib.tucker_reconstruct.argtypes = [vp, i64, i64, vp, vp]
+    lib.tucker_reconstruct_noalloc.argtypes = [vp, i64, i64, vp, vp]
     lib.tucker_error_norm.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.tucker_get_ranks.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.tucker_get_step_info.argtypes = [vp, ctypes.POINTER(StepInfo)]
@@ -88,7 +91,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_profile_enable.argtypes = [vp, i32]
     lib.tucker_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
     for name in ("tucker_profile_enable", "tucker_profile_read", "tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
-                 "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
+                 "tucker_reconstruct_noalloc", "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
                  "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv"):
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
@@ -140,6 +143,12 @@ def tucker_stream_update(h: int, Y_ptr: int, stream: int = 0) -> None:
 def tucker_reconstruct(h: int, t0: int, t1: int, out_ptr: int, stream: int = 0) -> None:
     _check(load_library().tucker_reconstruct(h, int(t0), int(t1), ctypes.c_void_p(out_ptr),
                                              ctypes.c_void_p(stream)), h)
+
+
+def tucker_reconstruct_noalloc(h: int, t0: int, t1: int, out_ptr: int, stream: int = 0) -> None:
+    """Allocation-free reconstruction (temporaries in the library's fixed device array)."""
+    _check(load_library().tucker_reconstruct_noalloc(h, int(t0), int(t1), ctypes.c_void_p(out_ptr),
+                                                     ctypes.c_void_p(stream)), h)
 
 
 def tucker_error_norm(h: int) -> tuple[float, float]:

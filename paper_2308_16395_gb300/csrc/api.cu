@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "../../include/tucker_stream.h"
@@ -638,6 +639,94 @@ tucker_status do_reconstruct(tucker_state* s, int64_t t0, int64_t t1, void* out,
 
 bool usable(tucker_state* s) { return s && !s->latched; }
 
+// ---------------------------------------------------------------------------------------------
+// allocation-free reconstruction: the two ping-pong temporaries live in one fixed device array
+// ---------------------------------------------------------------------------------------------
+constexpr size_t kNoallocScratchBytes = (size_t)TUCKER_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+}  // namespace
+
+// Every GPU that loads this library holds this array until the process exits. Host code must not
+// use its name as a device address: the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TUCKER_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+tucker_status noalloc_scratch(tucker_state* s, void** out) {
+  *out = nullptr;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) {
+    set_err(s, "allocation-free reconstruction supports device ordinals below %s%lld", "", kNoallocMaxDevices);
+    return TUCKER_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return TUCKER_OK;
+}
+
+// Same launch sequence as do_reconstruct; the temporaries are the two halves of the fixed array.
+template <typename TW>
+tucker_status do_reconstruct_noalloc(tucker_state* s, int64_t t0, int64_t t1, void* out,
+                                     cudaStream_t st) {
+  const Ctl& c = *s->hctl;
+  const int d = s->d;
+  const long long T = t1 - t0;
+  long long R = 1;
+  for (int i = 0; i < d - 1; ++i) R *= c.r[i];
+  const int rd = c.r[d - 1];
+  // largest temporary: C x_d U_d(t0:t1, :) (R x T), then every partial expansion but the last
+  long long need = R * T;
+  for (int k = 0; k + 1 < d - 1; ++k) {
+    long long e = T;
+    for (int i = 0; i <= k; ++i) e *= s->n[i];
+    for (int i = k + 1; i < d - 1; ++i) e *= c.r[i];
+    need = std::max(need, e);
+  }
+  const size_t half = kNoallocScratchBytes / 2;
+  if ((size_t)need * (size_t)s->tw > half) {
+    snprintf(s->err, sizeof(s->err),
+             "tucker_reconstruct_noalloc: slices [%lld, %lld) need %lld bytes per temporary, above "
+             "the fixed %zu-byte half of the scratch array; reconstruct fewer slices per call",
+             (long long)t0, (long long)t1, need * (long long)s->tw, half);
+    return TUCKER_EINVAL;
+  }
+  void* base = nullptr;
+  tucker_status rc = noalloc_scratch(s, &base);
+  if (rc != TUCKER_OK) return rc;
+  void* tmp[2] = {base, (void*)((unsigned char*)base + half)};
+  CK(launch_core_times_ud<TW>(s->Cb[c.cbuf], R, rd, s->ldc, s->Ud[c.ubuf], t0, T, tmp[0], st));
+  int cur = 0;
+  for (int k = 0; k < d - 1; ++k) {
+    long long A = 1, B = T;
+    for (int i = 0; i < k; ++i) A *= s->n[i];
+    for (int i = k + 1; i < d - 1; ++i) B *= c.r[i];
+    const bool last = (k == d - 2);
+    void* dst = last ? out : tmp[cur ^ 1];
+    cudaError_t e;
+    if (s->tw == 4) {
+      if (last && s->tx == 8) e = launch_expand<float, float, double>(tmp[cur], A, c.r[k], B, s->Uw[k], s->n[k], s->n[k], dst, st);
+      else e = launch_expand<float, float, float>(tmp[cur], A, c.r[k], B, s->Uw[k], s->n[k], s->n[k], dst, st);
+    } else {
+      if (last && s->tx == 4) e = launch_expand<double, double, float>(tmp[cur], A, c.r[k], B, s->U[k], s->n[k], s->n[k], dst, st);
+      else e = launch_expand<double, double, double>(tmp[cur], A, c.r[k], B, s->U[k], s->n[k], s->n[k], dst, st);
+    }
+    CK(e);
+    cur ^= 1;
+  }
+  return TUCKER_OK;
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -710,6 +799,21 @@ tucker_status tucker_reconstruct(tucker_state* s, int64_t t_begin, int64_t t_end
   }
   if (s->tw == 4) return do_reconstruct<float>(s, t_begin, t_end, out_dev, (cudaStream_t)stream);
   return do_reconstruct<double>(s, t_begin, t_end, out_dev, (cudaStream_t)stream);
+}
+
+tucker_status tucker_reconstruct_noalloc(tucker_state* s, int64_t t_begin, int64_t t_end,
+                                         void* out_dev, void* stream) {
+  if (!s || !out_dev) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  s->last_stream = (cudaStream_t)stream;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  if (t_begin < 0 || t_end > s->hctl->nd || t_begin >= t_end) {
+    set_err(s, "slice range out of bounds%s (n_d = %lld)", "", s->hctl->nd);
+    return TUCKER_EINVAL;
+  }
+  if (s->tw == 4) return do_reconstruct_noalloc<float>(s, t_begin, t_end, out_dev, (cudaStream_t)stream);
+  return do_reconstruct_noalloc<double>(s, t_begin, t_end, out_dev, (cudaStream_t)stream);
 }
 
 tucker_status tucker_error_norm(tucker_state* s, double* err_bound, double* data_norm) {
