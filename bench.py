@@ -295,8 +295,116 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_adjoint(args):
+    """Gradient evaluations of L = ||(Y x_n U_n^T) x_n U_n - T||^2 with respect to Y and every
+    U_n: 128 x 128 x 64 FP32 slices, ranks (20, 20, 12); forward and backward through the C ABI
+    (tucker_ttm_*), timed eagerly and as one captured CUDA graph per evaluation."""
+    import torch
+
+    from paper_2308_16395_gb300 import autograd as ag
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, r = (128, 128, 64), (20, 20, 12)
+    g = torch.Generator(device="cpu").manual_seed(230816395 + 3)
+    Yh_host = torch.randn(tuple(reversed(n)), generator=g).pin_memory()
+    Th_host = torch.randn(tuple(reversed(n)), generator=g).pin_memory()
+    Us = []
+    for nk, rk in zip(n, r):
+        q, _ = torch.linalg.qr(torch.randn(nk, rk, generator=g, dtype=torch.float64))
+        Us.append(q.float().t().contiguous().to(dev).t().requires_grad_(True))   # column-major
+    Y = Yh_host.to(dev).permute(2, 1, 0).requires_grad_(True)
+    T = Th_host.to(dev).permute(2, 1, 0)
+
+    def step():
+        G = ag.project(Y, Us)
+        L = ((ag.reconstruct(G, Us) - T) ** 2).sum()
+        L.backward()
+        return L
+
+    for _ in range(max(args.warmup, 3)):
+        Y.grad = None
+        for U in Us:
+            U.grad = None
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(K):
+        Y.grad = None
+        for U in Us:
+            U.grad = None
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_eager = e0.elapsed_time(e1) / K
+    # one CUDA graph per gradient evaluation
+    side = torch.cuda.Stream()
+    side.wait_stream(st)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            Y.grad = None
+            for U in Us:
+                U.grad = None
+            step()
+    st.wait_stream(side)
+    Y.grad = None
+    for U in Us:
+        U.grad = None
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        Ls = step()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0.record(st)
+    for _ in range(K):
+        graph.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms_graph = e0.elapsed_time(e1) / K
+    # end to end: host Y and T copied in, the loss read back, every evaluation
+    Yin = Y.detach()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(st)
+    for _ in range(K):
+        Yin.permute(2, 1, 0).copy_(Yh_host, non_blocking=True)
+        T.permute(2, 1, 0).copy_(Th_host, non_blocking=True)
+        graph.replay()
+        float(Ls.item())
+    f1.record(st)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1) / K
+    N = n[0] * n[1] * n[2]
+    # algorithmic bytes of one evaluation: Y and T read, dL/dY written, each mode product over a
+    # full-size operand reads or writes N values (3 forward, 3 for dL/dG, 2 partial chains of the
+    # factor gradients, 3 for dL/dY), FP32
+    alg_bytes = 4 * N * (3 + 11)
+    line = {
+        "metric": METRIC, "value": 1e3 / ms_graph, "unit": "slices/s", "n_gpus": 1, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "adjoint: gradient of ||(Y x U^T) x U - T||^2 w.r.t. Y and U_n, "
+                               "128x128x64 fp32, ranks (20,20,12)", "parallelism": "1 gpu",
+                   "l2": "8 MB working set, L2-resident (latency-bound by design)"},
+        "eager_ms_per_eval": ms_eager, "graph_ms_per_eval": ms_graph,
+        "gbs_effective": alg_bytes / (ms_graph / 1e3) / 1e9,
+        "e2e": {"value": 1e3 / ms_e2e, "unit": "slices/s", "h2d_bytes_per_step": 8 * N,
+                "d2h_bytes_per_step": 4},
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="stream", choices=["stream", "adjoint"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
@@ -310,6 +418,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

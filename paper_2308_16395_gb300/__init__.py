@@ -25,7 +25,8 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info", "tucker_copy_factor",
            "tucker_copy_core", "tucker_copy_sv", "tucker_last_error", "tucker_destroy",
            "tucker_version", "tucker_profile_enable", "tucker_profile_read",
-           "tucker_reconstruct_noalloc"]
+           "tucker_reconstruct_noalloc", "tucker_ttm_workspace_bytes", "tucker_ttm_project",
+           "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint", "tucker_ttm_reconstruct_adjoint"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -35,6 +36,11 @@ class TuckerConfig(ctypes.Structure):
                 ("reserved0", ctypes.c_int32), ("n", ctypes.c_int64 * MAX_MODES),
                 ("rank_cap", ctypes.c_int64 * MAX_MODES), ("steps_cap", ctypes.c_int64),
                 ("core_cap", ctypes.c_int64), ("tau", ctypes.c_double), ("eps_m", ctypes.c_double)]
+
+
+class TtmDesc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("n", ctypes.c_int64 * MAX_MODES), ("r", ctypes.c_int64 * MAX_MODES)]
 
 
 class StepInfo(ctypes.Structure):
@@ -90,6 +96,16 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_version.restype = ctypes.c_char_p
     lib.tucker_profile_enable.argtypes = [vp, i32]
     lib.tucker_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
+    pdesc = ctypes.POINTER(TtmDesc)
+    lib.tucker_ttm_workspace_bytes.argtypes = [pdesc]
+    lib.tucker_ttm_workspace_bytes.restype = i64
+    lib.tucker_ttm_project.argtypes = [pdesc, vp, vp, vp, vp, i64, vp]
+    lib.tucker_ttm_reconstruct.argtypes = [pdesc, vp, vp, vp, vp, i64, vp]
+    lib.tucker_ttm_project_adjoint.argtypes = [pdesc, vp, vp, vp, vp, vp, vp, i64, vp]
+    lib.tucker_ttm_reconstruct_adjoint.argtypes = [pdesc, vp, vp, vp, vp, vp, vp, i64, vp]
+    for name in ("tucker_ttm_project", "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint",
+                 "tucker_ttm_reconstruct_adjoint"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("tucker_profile_enable", "tucker_profile_read", "tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
                  "tucker_reconstruct_noalloc", "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
                  "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv"):
@@ -194,6 +210,63 @@ def tucker_profile_read(h: int) -> dict:
     _check(load_library().tucker_profile_read(h, ctypes.byref(p)), h)
     return dict(ms=[p.ms[i] for i in range(NPHASES)], bytes=[p.bytes[i] for i in range(NPHASES)],
                 launches=int(p.launches), updates=int(p.updates))
+
+
+# --- projection / reconstruction chains and adjoints (include/tucker_ttm.h) --------------------
+
+def ttm_desc(n, r, dtype="f32") -> TtmDesc:
+    d = TtmDesc()
+    d.ndim = len(n)
+    d.dtype = TUCKER_F32 if dtype in ("f32", "float32") else TUCKER_F64
+    for i, (a, b) in enumerate(zip(n, r)):
+        d.n[i] = int(a)
+        d.r[i] = int(b)
+    return d
+
+
+def _ptrs(ps):
+    """Host array of device pointers (NULL entries allowed)."""
+    if ps is None:
+        return None
+    arr = (ctypes.c_void_p * MAX_MODES)()
+    for i, p in enumerate(ps):
+        arr[i] = p or None
+    return arr
+
+
+def tucker_ttm_workspace_bytes(desc: TtmDesc) -> int:
+    v = load_library().tucker_ttm_workspace_bytes(ctypes.byref(desc))
+    if v < 0:
+        raise TuckerError(1, "invalid ttm descriptor")
+    return int(v)
+
+
+def tucker_ttm_project(desc, U_ptrs, Y_ptr, G_ptr, work_ptr, work_bytes, stream=0) -> None:
+    _check(load_library().tucker_ttm_project(ctypes.byref(desc), _ptrs(U_ptrs), ctypes.c_void_p(Y_ptr),
+                                             ctypes.c_void_p(G_ptr), ctypes.c_void_p(work_ptr),
+                                             int(work_bytes), ctypes.c_void_p(stream)))
+
+
+def tucker_ttm_reconstruct(desc, U_ptrs, G_ptr, Y_ptr, work_ptr, work_bytes, stream=0) -> None:
+    _check(load_library().tucker_ttm_reconstruct(ctypes.byref(desc), _ptrs(U_ptrs), ctypes.c_void_p(G_ptr),
+                                                 ctypes.c_void_p(Y_ptr), ctypes.c_void_p(work_ptr),
+                                                 int(work_bytes), ctypes.c_void_p(stream)))
+
+
+def tucker_ttm_project_adjoint(desc, U_ptrs, Y_ptr, Gbar_ptr, Ybar_ptr, Ubar_ptrs, work_ptr,
+                               work_bytes, stream=0) -> None:
+    _check(load_library().tucker_ttm_project_adjoint(
+        ctypes.byref(desc), _ptrs(U_ptrs), ctypes.c_void_p(Y_ptr), ctypes.c_void_p(Gbar_ptr),
+        ctypes.c_void_p(Ybar_ptr), _ptrs(Ubar_ptrs), ctypes.c_void_p(work_ptr), int(work_bytes),
+        ctypes.c_void_p(stream)))
+
+
+def tucker_ttm_reconstruct_adjoint(desc, U_ptrs, G_ptr, Yhbar_ptr, Gbar_ptr, Ubar_ptrs, work_ptr,
+                                   work_bytes, stream=0) -> None:
+    _check(load_library().tucker_ttm_reconstruct_adjoint(
+        ctypes.byref(desc), _ptrs(U_ptrs), ctypes.c_void_p(G_ptr), ctypes.c_void_p(Yhbar_ptr),
+        ctypes.c_void_p(Gbar_ptr), _ptrs(Ubar_ptrs), ctypes.c_void_p(work_ptr), int(work_bytes),
+        ctypes.c_void_p(stream)))
 
 
 def tucker_last_error(h: int) -> str:

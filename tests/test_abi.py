@@ -74,3 +74,16 @@ def test_version_string(lib):
     import paper_2308_16395_gb300 as pkg
 
     assert "sm_103a" in pkg.tucker_version()
+
+
+def test_ttm_workspace_query_is_host_only(lib):
+    """tucker_ttm_workspace_bytes: 4 buffers of max_k N r_k / n_k elements, 256-byte rounded;
+    -1 for an invalid descriptor (no device call)."""
+    import paper_2308_16395_gb300 as pkg
+
+    d = pkg.ttm_desc((128, 128, 64), (20, 20, 12), "f32")
+    M = max(128 * 128 * 64 // n * r for n, r in zip((128, 128, 64), (20, 20, 12)))
+    assert pkg.tucker_ttm_workspace_bytes(d) == 4 * ((M * 4 + 255) // 256 * 256)
+    for n, r in [((8, 8), (9, 2)), ((8, 0), (2, 0)), ((), ())]:
+        with pytest.raises(pkg.TuckerError):
+            pkg.tucker_ttm_workspace_bytes(pkg.ttm_desc(n, r, "f64"))
