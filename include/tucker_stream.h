@@ -111,6 +111,36 @@ tucker_status tucker_init_sthosvd(const tucker_config* cfg, const void* X_dev, i
  * conditions are latched (see above). */
 tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* stream);
 
+/* Batched form: many independent streams, each updated by Alg. 5, advanced together by one
+ * CUDA-graph launch per time step.
+ *
+ * tucker_batch_create captures one tucker_stream_update of every state into one CUDA graph, one
+ * branch per state, so the updates of different streams run concurrently on the device. The
+ * graph reads state i's next slice from the caller-owned device buffer Y_slots_dev[i] (layout and
+ * type of that state's config), at every tucker_batch_update: the caller writes each time step's
+ * slices into the slots (e.g. a simulation writes them there, or a host copy lands there), then
+ * calls tucker_batch_update. Each update's device-side branches and ranks stay per state. The
+ * states may differ in d, sizes, tau, dtype and precision; a state appears at most once.
+ * Synchronizes each state's last stream once; enqueues no work.
+ * Errors: EINVAL (NULL, count outside 1..4096, a repeated state), ESTATE (a state holds a latched
+ * error), ECUDA (capture or instantiation failed). The states must outlive the batch; the slots
+ * must stay allocated while it is used. tucker_stream_update may still be called on a state
+ * between batch launches (on any stream; the caller orders the two). */
+typedef struct tucker_batch tucker_batch;
+tucker_status tucker_batch_create(tucker_state* const* states, const void* const* Y_slots_dev,
+                                  int32_t count, tucker_batch** out);
+
+/* One update of every state of the batch (one graph launch on `stream`, no host synchronization).
+ * Device-side errors latch in the state that met them (the other states proceed) and are
+ * reported by that state's next synchronizing call. Errors: EINVAL, ESTATE, ECUDA. */
+tucker_status tucker_batch_update(tucker_batch* b, void* stream);
+
+/* Kernel launches (graph kernel nodes) per tucker_batch_update; -1 for NULL. */
+int64_t tucker_batch_kernels(const tucker_batch* b);
+
+/* Release the graph (the states are not touched). */
+void tucker_batch_destroy(tucker_batch* b);
+
 /* Reconstruction X^(:, ..., t) = C x_1 U_1 ... x_{d-1} U_{d-1} x_d U_d(t, :) for slices
  * t in [t_begin, t_end) (0-based) into out_dev (n_1 x ... x n_{d-1} x (t_end - t_begin),
  * column-major, element type cfg->dtype). Enqueued on `stream`. Errors: EINVAL, ESTATE. */

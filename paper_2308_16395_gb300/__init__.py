@@ -26,7 +26,8 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_copy_core", "tucker_copy_sv", "tucker_last_error", "tucker_destroy",
            "tucker_version", "tucker_profile_enable", "tucker_profile_read",
            "tucker_reconstruct_noalloc", "tucker_ttm_workspace_bytes", "tucker_ttm_project",
-           "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint", "tucker_ttm_reconstruct_adjoint"]
+           "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint", "tucker_ttm_reconstruct_adjoint",
+           "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -96,6 +97,14 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_version.restype = ctypes.c_char_p
     lib.tucker_profile_enable.argtypes = [vp, i32]
     lib.tucker_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
+    lib.tucker_batch_create.argtypes = [vp, vp, i32, ctypes.POINTER(vp)]
+    lib.tucker_batch_create.restype = ctypes.c_int
+    lib.tucker_batch_update.argtypes = [vp, vp]
+    lib.tucker_batch_update.restype = ctypes.c_int
+    lib.tucker_batch_kernels.argtypes = [vp]
+    lib.tucker_batch_kernels.restype = i64
+    lib.tucker_batch_destroy.argtypes = [vp]
+    lib.tucker_batch_destroy.restype = None
     pdesc = ctypes.POINTER(TtmDesc)
     lib.tucker_ttm_workspace_bytes.argtypes = [pdesc]
     lib.tucker_ttm_workspace_bytes.restype = i64
@@ -210,6 +219,73 @@ def tucker_profile_read(h: int) -> dict:
     _check(load_library().tucker_profile_read(h, ctypes.byref(p)), h)
     return dict(ms=[p.ms[i] for i in range(NPHASES)], bytes=[p.bytes[i] for i in range(NPHASES)],
                 launches=int(p.launches), updates=int(p.updates))
+
+
+# --- batched form -----------------------------------------------------------------------------
+
+def tucker_batch_create(handles, slot_ptrs) -> int:
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*handles)
+    ys = (ctypes.c_void_p * n)(*slot_ptrs)
+    b = ctypes.c_void_p()
+    _check(load_library().tucker_batch_create(hs, ys, n, ctypes.byref(b)))
+    return b.value
+
+
+def tucker_batch_update(b: int, stream: int = 0) -> None:
+    _check(load_library().tucker_batch_update(b, ctypes.c_void_p(stream)))
+
+
+def tucker_batch_kernels(b: int) -> int:
+    return int(load_library().tucker_batch_kernels(b))
+
+
+def tucker_batch_destroy(b: int) -> None:
+    if b:
+        load_library().tucker_batch_destroy(b)
+
+
+class TuckerBatch:
+    """Independent TuckerStream states advanced together, one CUDA-graph launch per time step.
+
+    ``slots[i]`` is the device tensor the graph reads state i's next slice from (allocated here,
+    shape and dtype of that stream's slices): write the time step's slices into the slots, then
+    call :meth:`update`.
+    """
+
+    def __init__(self, streams, stream=None):
+        import torch
+
+        self.streams = list(streams)
+        self.slots = [torch.empty(tuple(reversed(s.n)), dtype=s.dtype, device="cuda") for s in self.streams]
+        self._stream = stream
+        self.b = tucker_batch_create([s.h for s in self.streams], [y.data_ptr() for y in self.slots])
+
+    def _sp(self) -> int:
+        import torch
+
+        s = self._stream if self._stream is not None else torch.cuda.current_stream()
+        return s.cuda_stream
+
+    @property
+    def kernels(self) -> int:
+        return tucker_batch_kernels(self.b)
+
+    def update(self) -> None:
+        tucker_batch_update(self.b, self._sp())
+        for s in self.streams:
+            s._stream = self._stream
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            tucker_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --- projection / reconstruction chains and adjoints (include/tucker_ttm.h) --------------------

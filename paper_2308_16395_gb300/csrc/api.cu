@@ -454,7 +454,7 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
     if (e == cudaSuccess) e = launch_append<TW>(s->ctl, k, 1, s->eW, Uk, (s->tw == 8) ? nullptr : Uwk, nv, nv, st);
     if (e == cudaSuccess && k < d - 1 && ((s->tcmask >> k) & 1))
       e = launch_split_u(s->ctl, k, 0, s->U[k], s->n[k], s->usplit[k], st);
-    if (e != cudaSuccess) { set_err(s, "CUDA error: %s", cudaGetErrorString(e)); rc = TUCKER_ECUDA; break; }
+    if (e != cudaSuccess) { set_err(s, "CUDA error (%s) in the Gram/eig/append step of mode %lld", cudaGetErrorString(e), k + 1); rc = TUCKER_ECUDA; break; }
     s->last_stream = st;
     rc = sync_ctl(s);
     if (rc != TUCKER_OK) break;
@@ -467,7 +467,7 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
     if (k == 0) e = launch_proj<TX, TW>(s->ctl, k, 1, 0, X, d_ib, Uwk, nv, rk, nullptr, nullptr, kGridP, st);
     else e = launch_proj<TW, TW>(s->ctl, k, 1, 0, X, d_ib, Uwk, nv, rk, nullptr, nullptr, kGridP, st);
     if (e == cudaSuccess) e = launch_mode_end(s->ctl, k, st);
-    if (e != cudaSuccess) { set_err(s, "CUDA error: %s", cudaGetErrorString(e)); rc = TUCKER_ECUDA; break; }
+    if (e != cudaSuccess) { set_err(s, "CUDA error (%s) in the projection of mode %lld", cudaGetErrorString(e), k + 1); rc = TUCKER_ECUDA; break; }
   }
   if (rc == TUCKER_OK) rc = sync_ctl(s);
   if (rc == TUCKER_OK) {
@@ -477,7 +477,7 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
     const int rd = c.r[d - 1];
     cudaError_t e = launch_init_finish<TW>(s->ctl, ib[c.xbuf], R, rd, s->elam, Utmp, (int)n_init, s->Cb[0], s->Vb[0],
                                            s->Ud[0], s->S, s->ldc, st);
-    if (e != cudaSuccess) { set_err(s, "CUDA error: %s", cudaGetErrorString(e)); rc = TUCKER_ECUDA; }
+    if (e != cudaSuccess) { set_err(s, "CUDA error (%s) in the core factorization (R = %lld)", cudaGetErrorString(e), R); rc = TUCKER_ECUDA; }
     if (rc == TUCKER_OK) {
       double err2 = 0.0;
       for (int k = 0; k < d; ++k) err2 += c.disc[k];
@@ -729,6 +729,73 @@ tucker_status do_reconstruct_noalloc(tucker_state* s, int64_t t0, int64_t t1, vo
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------------
+// batched form: one update of many independent states captured as one CUDA graph
+// ---------------------------------------------------------------------------------------------
+struct tucker_batch {
+  std::vector<tucker_state*> states;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;   // kernel nodes per graph launch
+  char err[256] = "ok";
+};
+
+namespace {
+
+tucker_status update_dispatch(tucker_state* s, const void* Y, cudaStream_t st) {
+  const bool mixed = s->cfg.precision == TUCKER_PREC_MIXED;
+  const bool f32 = s->cfg.dtype == TUCKER_F32;
+  if (mixed) return f32 ? do_update<float, float, float>(s, Y, st) : do_update<double, float, float>(s, Y, st);
+  return f32 ? do_update<float, double, double>(s, Y, st) : do_update<double, double, double>(s, Y, st);
+}
+
+// Capture: origin stream -> fork event -> one branch stream per state (its whole update) ->
+// join events -> origin. Streams and events exist only during the capture.
+tucker_status capture_batch(tucker_batch* b, const void* const* Y, cudaStream_t* streams,
+                            cudaEvent_t* evs) {
+  const int count = (int)b->states.size();
+  cudaStream_t origin = streams[count];
+  if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return TUCKER_ECUDA;
+  tucker_status rc = TUCKER_OK;
+  if (cudaEventRecord(evs[count], origin) != cudaSuccess) rc = TUCKER_ECUDA;
+  for (int i = 0; i < count && rc == TUCKER_OK; ++i) {
+    tucker_state* s = b->states[i];
+    if (cudaStreamWaitEvent(streams[i], evs[count], 0) != cudaSuccess) { rc = TUCKER_ECUDA; break; }
+    const bool prof = s->prof;
+    s->prof = false;
+    rc = update_dispatch(s, Y[i], streams[i]);
+    s->prof = prof;
+    if (rc != TUCKER_OK) {
+      snprintf(b->err, sizeof(b->err), "state %d: %s", i, s->err);
+      break;
+    }
+    if (cudaEventRecord(evs[i], streams[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(origin, evs[i], 0) != cudaSuccess) rc = TUCKER_ECUDA;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(origin, &g);
+  if (rc != TUCKER_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (rc == TUCKER_OK) rc = TUCKER_ECUDA;
+    return rc;
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) return TUCKER_ECUDA;
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess) {
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) b->launches++;
+      }
+    }
+  }
+  return TUCKER_OK;
+}
+
+}  // namespace
+
 // =============================================================================================
 // C ABI
 // =============================================================================================
@@ -899,6 +966,63 @@ tucker_status tucker_copy_sv(tucker_state* s, double* S_dev, double* V_dev) {
   }
   CK(cudaStreamSynchronize(s->last_stream));
   return TUCKER_OK;
+}
+
+tucker_status tucker_batch_create(tucker_state* const* states, const void* const* Y_slots_dev,
+                                  int32_t count, tucker_batch** out) {
+  if (!out) return TUCKER_EINVAL;
+  *out = nullptr;
+  if (!states || !Y_slots_dev || count < 1 || count > 4096) return TUCKER_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!states[i] || !Y_slots_dev[i]) return TUCKER_EINVAL;
+    if (!usable(states[i])) return TUCKER_ESTATE;
+    for (int j = 0; j < i; ++j)
+      if (states[j] == states[i]) return TUCKER_EINVAL;   // a state updates once per launch
+  }
+  tucker_batch* b = new tucker_batch();
+  b->states.assign(states, states + count);
+  std::vector<cudaStream_t> streams(count + 1, nullptr);
+  std::vector<cudaEvent_t> evs(count + 1, nullptr);
+  tucker_status rc = TUCKER_OK;
+  for (int i = 0; i <= count && rc == TUCKER_OK; ++i) {
+    if (cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming) != cudaSuccess) rc = TUCKER_ECUDA;
+  }
+  // the states' earlier work must be complete before the graph is first launched; the capture
+  // itself enqueues nothing
+  for (int i = 0; i < count && rc == TUCKER_OK; ++i)
+    if (cudaStreamSynchronize(states[i]->last_stream) != cudaSuccess) rc = TUCKER_ECUDA;
+  if (rc == TUCKER_OK) rc = capture_batch(b, Y_slots_dev, streams.data(), evs.data());
+  for (int i = 0; i <= count; ++i) {
+    if (streams[i]) cudaStreamDestroy(streams[i]);
+    if (evs[i]) cudaEventDestroy(evs[i]);
+  }
+  if (rc != TUCKER_OK) {
+    fprintf(stderr, "tucker_batch_create: %s\n", b->err);
+    tucker_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_batch_update(tucker_batch* b, void* stream) {
+  if (!b || !b->exec) return TUCKER_EINVAL;
+  for (tucker_state* s : b->states)
+    if (!usable(s)) return TUCKER_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return TUCKER_ECUDA;
+  for (tucker_state* s : b->states) s->last_stream = st;
+  return TUCKER_OK;
+}
+
+int64_t tucker_batch_kernels(const tucker_batch* b) { return b ? b->launches : -1; }
+
+void tucker_batch_destroy(tucker_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  delete b;
 }
 
 tucker_status tucker_profile_enable(tucker_state* s, int32_t on) {

@@ -639,10 +639,23 @@ template <typename TE>
 cudaError_t launch_eig(Ctl* ctl, int k, int mode, const double* G, void* Aw, void* Z, void* LD,
                        double* W, double* lam, int mcap, int n, cudaStream_t st) {
   EigArgs ea{G, Aw, Z, LD, W, lam, mcap};
+  // dynamic shared memory may use what the kernel's static arrays leave of the opt-in maximum
+  static size_t dyn_max[2] = {0, 0};
+  size_t& lim = dyn_max[sizeof(TE) == 8 ? 1 : 0];
+  if (lim == 0) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_eig_topk<TE>);
+    if (e != cudaSuccess) return e;
+    lim = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
+    lim = std::min(lim, EIG_SMEM_MAX);
+  }
   const size_t mat = (size_t)n * n * sizeof(TE);
   const size_t vec = (size_t)EIG_SMEM_VECS * 3 * n * sizeof(TE);
-  const int use_vec = (vec <= 150 * 1024) ? 1 : 0;
-  const int use_amat = (use_vec && mat + vec <= EIG_SMEM_MAX) ? 1 : 0;
+  const int use_vec = (vec <= std::min<size_t>(150 * 1024, lim)) ? 1 : 0;
+  const int use_amat = (use_vec && mat + vec <= lim) ? 1 : 0;
   const size_t sm = (use_amat ? mat : 0) + (use_vec ? vec : 0);
   if (sm) cudaFuncSetAttribute(k_eig_topk<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   // FP32 Grams up to 192 x 192 are tridiagonalized by the register kernel first; the reflectors

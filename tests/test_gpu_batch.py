@@ -1,0 +1,116 @@
+"""Batched form: independent streams of uneven sizes, ranks and tolerances advanced by one
+CUDA-graph launch per time step (tucker_batch_*), against the same states updated one by one
+through tucker_stream_update and against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.parity import decision_margins, to_device
+from workloads import LowRankStream, batched_streams
+
+pytestmark = pytest.mark.gpu
+
+DELTA_DEC = 1e-3
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2308_16395_gb300 as p
+    from paper_2308_16395_gb300 import build as b
+
+    b.build()
+    p.load_library()
+    return p
+
+
+def _streams():
+    """Five uneven mixed-form FP32 streams (sizes 8..40, ranks 2..6, tau from {1e-2, 1e-3, 1e-4})
+    plus one FP64-form stream of FP64 slices."""
+    out = [(s, tau, "mixed", "f32") for s, tau in
+           batched_streams(nstreams=5, steps=16, size_range=(8, 40), rank_range=(2, 6), seed=21)]
+    out.append((LowRankStream((20, 13, 9), (3, 4, 2, 3), 16, 1e-4, seed=22), 1e-3, "fp64", "f64"))
+    return out
+
+
+def test_batch_matches_single_updates_and_oracle(pkg):
+    import torch
+
+    n_init, T = 5, 16
+    entries = []
+    for s, tau, prec, dt in _streams():
+        tdt = torch.float32 if dt == "f32" else torch.float64
+        X = s.tensor(0, T).astype(np.float64)
+        Xs = X.astype(np.float32).astype(np.float64) if dt == "f32" else X
+        Xg = to_device(Xs, tdt)
+        kw = dict(precision=prec, steps_cap=T + 4)
+        a = pkg.TuckerStream(Xg[:n_init].contiguous(), tau, **kw)
+        b = pkg.TuckerStream(Xg[:n_init].contiguous(), tau, **kw)
+        st = O.init_stream(Xs[..., :n_init].copy(order="F"), tau)
+        entries.append(dict(a=a, b=b, st=st, Xg=Xg, Xs=Xs, prec=prec, tau=tau, ok=True))
+    batch = pkg.TuckerBatch([e["a"] for e in entries])
+    assert batch.kernels > 0
+    for t in range(n_init, T):
+        for e, slot in zip(entries, batch.slots):
+            slot.copy_(e["Xg"][t])
+        batch.update()
+        for e in entries:
+            e["b"].update(e["Xg"][t].contiguous())
+            if e["ok"]:
+                O.stream_update(e["st"], e["Xs"][..., t].copy(order="F"))
+        for e in entries:
+            ra, rb = e["a"].ranks, e["b"].ranks
+            assert ra == rb, (t, ra, rb)
+            if e["ok"] and ra != e["st"].ranks:
+                margin = decision_margins(e["st"].log[-1])
+                assert margin < DELTA_DEC, (t, ra, e["st"].ranks, margin)
+                e["ok"] = False          # a near-cutoff decision flipped: stop the oracle comparison
+    for e in entries:
+        Ra = e["a"].reconstruct(0, T).double()
+        Rb = e["b"].reconstruct(0, T).double()
+        assert float(torch.linalg.norm(Ra - Rb) / torch.linalg.norm(Rb)) <= 1e-12
+        if e["ok"]:
+            Xh = O.reconstruct(e["st"].C, e["st"].Us)
+            rel = np.linalg.norm(pkg.paper_order(Ra).cpu().numpy() - Xh) / np.linalg.norm(Xh)
+            assert rel < (1e-5 if e["prec"] == "mixed" else 1e-9), rel
+        ea, da = e["a"].error_norm()
+        eb, db = e["b"].error_norm()
+        assert abs(ea - eb) <= 1e-12 * max(eb, 1e-300) and abs(da - db) <= 1e-12 * db
+    batch.close()
+    for e in entries:
+        e["a"].close()
+        e["b"].close()
+
+
+def test_batch_error_latches_in_one_state(pkg):
+    import torch
+
+    s1 = LowRankStream((16, 12, 10), (3, 3, 2, 4), 12, 1e-4, seed=5)
+    s2 = LowRankStream((14, 11, 9), (2, 3, 2, 3), 12, 1e-4, seed=6)
+    X1 = to_device(s1.tensor(0, 12), torch.float64)
+    X2 = to_device(s2.tensor(0, 12), torch.float64)
+    a = pkg.TuckerStream(X1[:6].contiguous(), 1e-3, precision="fp64", steps_cap=7)   # room for 1 update
+    b = pkg.TuckerStream(X2[:6].contiguous(), 1e-3, precision="fp64", steps_cap=16)
+    ref = pkg.TuckerStream(X2[:6].contiguous(), 1e-3, precision="fp64", steps_cap=16)
+    batch = pkg.TuckerBatch([a, b])
+    for t in range(6, 9):
+        batch.slots[0].copy_(X1[t])
+        batch.slots[1].copy_(X2[t])
+        batch.update()
+        ref.update(X2[t].contiguous())
+    with pytest.raises(pkg.TuckerError) as ei:
+        a.ranks
+    assert ei.value.code == 3                      # ECAPACITY latched in the first state only
+    assert b.ranks == ref.ranks and b.n_d == 9
+    Rb, Rr = b.reconstruct(0, 9), ref.reconstruct(0, 9)
+    assert float(torch.linalg.norm(Rb - Rr) / torch.linalg.norm(Rr)) <= 1e-12
+    with pytest.raises(pkg.TuckerError) as ei:      # the batch refuses once a state has reported
+        batch.update()
+    assert ei.value.code == 7
+    batch.close()
+    for x in (a, b, ref):
+        x.close()

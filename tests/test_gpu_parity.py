@@ -239,3 +239,23 @@ def test_capacity_and_bad_input_errors(pkg):
     with pytest.raises(pkg.TuckerError) as ei:
         pkg.TuckerStream(torch.zeros_like(Xg[:6]).contiguous(), 1e-3, precision="fp64")
     assert ei.value.code == 1
+
+
+@pytest.mark.parametrize("precision,dtype", [("fp64", "f64"), ("mixed", "f32")])
+def test_eigensolver_at_the_shared_memory_limit(pkg, precision, dtype):
+    """n_1 = 136: the FP64 eigensolver's matrix and vectors (200 KB) fill shared memory together
+    with its static arrays; every eigensolve of this stream runs at that size."""
+    rng = np.random.default_rng(17)
+    n, T = (136, 10, 8), 12
+    A = [np.linalg.qr(rng.standard_normal((m, 4)))[0] for m in n]
+    X = np.zeros(n + (T,), order="F")
+    for t in range(T):
+        r_use = 2 if t < 6 else 4
+        G = rng.standard_normal((r_use,) * 3)
+        X[..., t] = O.reconstruct(G, [a[:, :r_use] for a in A])
+    X += 1e-6 * rng.standard_normal(X.shape)
+    st, ts, Xs, recs, div = _run(pkg, X, 6, 1e-3, precision, dtype)
+    assert not div
+    assert st.ranks[0] == 4
+    _compare_final(pkg, st, ts, Xs, precision)
+    ts.close()
