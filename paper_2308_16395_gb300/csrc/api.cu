@@ -945,8 +945,9 @@ tucker_status tucker_copy_core(tucker_state* s, double* dst) {
   const Ctl& c = *s->hctl;
   long long R = 1;
   for (int i = 0; i < s->d - 1; ++i) R *= c.r[i];
-  if (s->tw == 4) CK(launch_state_to_colmajor<float>(s->Cb[c.cbuf], R, c.r[s->d - 1], s->ldc, dst, s->last_stream));
-  else CK(launch_state_to_colmajor<double>(s->Cb[c.cbuf], R, c.r[s->d - 1], s->ldc, dst, s->last_stream));
+  const int ls = tk_cv_stride(c.r[s->d - 1], s->ldc, s->tw);
+  if (s->tw == 4) CK(launch_state_to_colmajor<float>(s->Cb[c.cbuf], R, c.r[s->d - 1], ls, dst, s->last_stream));
+  else CK(launch_state_to_colmajor<double>(s->Cb[c.cbuf], R, c.r[s->d - 1], ls, dst, s->last_stream));
   CK(cudaStreamSynchronize(s->last_stream));
   return TUCKER_OK;
 }
@@ -961,8 +962,9 @@ tucker_status tucker_copy_sv(tucker_state* s, double* S_dev, double* V_dev) {
   if (V_dev) {
     long long R = 1;
     for (int i = 0; i < s->d - 1; ++i) R *= c.r[i];
-    if (s->tw == 4) CK(launch_state_to_colmajor<float>(s->Vb[c.cbuf], R, rd, s->ldc, V_dev, s->last_stream));
-    else CK(launch_state_to_colmajor<double>(s->Vb[c.cbuf], R, rd, s->ldc, V_dev, s->last_stream));
+    const int ls = tk_cv_stride(rd, s->ldc, s->tw);
+    if (s->tw == 4) CK(launch_state_to_colmajor<float>(s->Vb[c.cbuf], R, rd, ls, V_dev, s->last_stream));
+    else CK(launch_state_to_colmajor<double>(s->Vb[c.cbuf], R, rd, ls, V_dev, s->last_stream));
   }
   CK(cudaStreamSynchronize(s->last_stream));
   return TUCKER_OK;

@@ -233,11 +233,24 @@ __device__ __forceinline__ bool rows_cv_ok(const Ctl* ctl, int keep) {
   return rows_isvd_ok(ctl) && keep >= 1 && keep <= ROWS_RMAX;
 }
 
+// Row stride of the C and V state rows at streaming rank r: compact (r rounded up to 16 bytes)
+// while the per-lane row passes handle the rank, the capacity ldc above it (the stride the
+// tensor-core path's TMA maps describe). Every reader and writer of C and V derives the stride
+// from the rank the rows hold, so a buffer is always read with the stride it was written with.
+__host__ __device__ __forceinline__ int tk_cv_stride(int r, int ldc, int tw) {
+  const int a = 16 / tw;
+  if (r > ROWS_RMAX) return ldc;
+  const int s = (r + a - 1) / a * a;
+  return s < ldc ? s : ldc;
+}
+
+// The tensor-core core/V update keeps both strides at ldc: streaming rank above ROWS_RMAX before
+// and after the update (an update that crosses ROWS_RMAX runs on the SIMT kernel).
 __device__ __forceinline__ bool tc_cv_ok(const Ctl* ctl, int keep) {
   if (rows_cv_ok(ctl, keep)) return false;
   if (ctl->tw != 4) return false;
   const int r = ctl->r[ctl->d - 1];
-  if (r < 1 || keep < 1) return false;
+  if (r <= ROWS_RMAX || keep <= ROWS_RMAX) return false;
   const int kc = (r + TC_KC - 1) / TC_KC;
   const int np = (keep + 15) / 16 * 16;
   if (np > 256) return false;

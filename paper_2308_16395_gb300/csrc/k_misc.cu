@@ -6,13 +6,14 @@
 namespace tk {
 
 // After the batch ST-HOSVD: Ccol is the core as a column-major (R x r_d) array (C_(d)^T).
-// State: C[j*ldc + i] = C(j, i), V[j*ldc + i] = C(j, i) / S_i (V_(d) = S^-1 C_(d), Assumption
-// 1(c)), S_i = sqrt(lambda_i) of the streaming-mode Gram, U_d row-major from Utmp (nt x r_d,
-// column-major).
+// State: C[j*ls + i] = C(j, i), V[j*ls + i] = C(j, i) / S_i (V_(d) = S^-1 C_(d), Assumption
+// 1(c)), ls = tk_cv_stride(r_d); S_i = sqrt(lambda_i) of the streaming-mode Gram; U_d row-major
+// (ld ldc) from Utmp (nt x r_d, column-major).
 template <typename TW>
 __global__ void k_init_finish(const TW* Ccol, long long R, int rd, const double* lam,
                               const double* Utmp, int nt, TW* C, TW* V, double* Ud, double* S,
                               int ldc) {
+  const int ls = tk_cv_stride(rd, ldc, (int)sizeof(TW));
   const long long total = R * rd;
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
        L += (long long)gridDim.x * blockDim.x) {
@@ -20,8 +21,8 @@ __global__ void k_init_finish(const TW* Ccol, long long R, int rd, const double*
     const int i = (int)(L / R);
     const TW c = Ccol[L];
     const double s = sqrt(fmax(lam[i], 0.0));
-    C[j * ldc + i] = c;
-    V[j * ldc + i] = (TW)((double)c / s);
+    C[j * ls + i] = c;
+    V[j * ls + i] = (TW)((double)c / s);
   }
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < rd; i += blockDim.x) S[i] = sqrt(fmax(lam[i], 0.0));
@@ -46,15 +47,17 @@ cudaError_t launch_init_finish(Ctl* ctl, const void* Ccol, long long R, int rd, 
 }
 
 // out(j, t) = sum_i C(j, i) U_d(t0 + t, i): the core contracted with rows of U_d, as a
-// column-major (R x T) array (the first step of X^ = C x_d U_d x_{d-1} ... x_1 U_1).
+// column-major (R x T) array (the first step of X^ = C x_d U_d x_{d-1} ... x_1 U_1). C rows have
+// stride tk_cv_stride(r_d), U_d rows stride ldc.
 template <typename TW>
 __global__ void k_core_times_ud(const TW* C, long long R, int rd, int ldc, const double* Ud,
                                 long long t0, long long T, TW* out) {
+  const int ls = tk_cv_stride(rd, ldc, (int)sizeof(TW));
   const long long total = R * T;
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
        L += (long long)gridDim.x * blockDim.x) {
     const long long j = L % R, t = L / R;
-    const TW* row = C + j * ldc;
+    const TW* row = C + j * ls;
     const double* u = Ud + (t0 + t) * ldc;
     double s = 0.0;
     for (int i = 0; i < rd; ++i) s += (double)row[i] * u[i];
@@ -72,7 +75,8 @@ cudaError_t launch_core_times_ud(const void* C, long long R, int rd, int ldc, co
   return cudaGetLastError();
 }
 
-// State rows (R x rd, ld = ldc, type TW) -> FP64 column-major (R x rd).
+// Rows (R x rd, row stride ldc, type TW) -> FP64 column-major (R x rd). For the C and V state the
+// caller passes tk_cv_stride(r_d) as the stride.
 template <typename TW>
 __global__ void k_state_to_col(const TW* Src, long long R, int rd, int ldc, double* dst) {
   const long long total = R * rd;

@@ -3,7 +3,8 @@
 //
 // State layout (device): C and V are stored "row per spatial index": row j (the column-major
 // linear index of (i_1..i_{d-1}) over the current spatial ranks) holds the r_d streaming-mode
-// coefficients contiguously, row stride ldc = streaming-rank capacity. So C_(d) = C^T and the
+// coefficients contiguously, row stride tk_cv_stride(r_d) (compact up to r_d = 32, the
+// streaming-rank capacity ldc above). So C_(d) = C^T and the
 // matrix V of Alg. 3 (V = V_(d)^T) is exactly the stored R x r_d array. U_d is row-major
 // (steps_cap x ldc). Zero padding of C and V in spatial modes (Alg. 4, PadWithZeros) is never
 // materialised: kernels read old rows through the new->old index map (missing rows are zero).
@@ -37,7 +38,7 @@ __global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW*
   if (rows_isvd_ok(ctl)) return;   // k_isvd_p_rows does this pass
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
-  const int ldc = ctl->ldc;
+  const int ldc = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));
   const TW* V = vbufs[ctl->cbuf];
   const TW* dv = dbufs[ctl->xbuf];
   long long Ro = 1;
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) k_isvd_e(const Ctl* __restrict__ ctl, TW*
   if (rows_isvd_ok(ctl)) return;   // k_isvd_e_rows does this pass
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
-  const int ldc = ctl->ldc;
+  const int ldc = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));
   const TW* V = vbufs[ctl->cbuf];
   const TW* dv = dbufs[ctl->xbuf];
   long long Rn = 1;
@@ -603,7 +604,8 @@ __global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, 
   const int d = ctl->d, mm = d - 1;
   const int r = ctl->r[d - 1];
   const int keep = w.meta[2];
-  const int ldc = ctl->ldc;
+  const int ldi = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));      // rows read (rank r)
+  const int ldo = tk_cv_stride(keep, ctl->ldc, (int)sizeof(TW));   // rows written (rank keep)
   long long Rn = 1;
   for (int i = 0; i < mm; ++i) Rn *= ctl->r[i];
   const TW* In = ibufs[ctl->cbuf];
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, 
       for (int L = tid; L < CV_TM * CV_TK; L += 256) {
         const int row = L / CV_TK, kk = L % CV_TK;
         const long long src = rowsrc[row];
-        As[kk][row] = (src >= 0 && k0 + kk < r) ? In[src * ldc + k0 + kk] : TW(0);
+        As[kk][row] = (src >= 0 && k0 + kk < r) ? In[src * ldi + k0 + kk] : TW(0);
       }
       for (int L = tid; L < CV_TK * CV_TN; L += 256) {
         const int kk = L / CV_TN, cc = L % CV_TN;
@@ -662,7 +664,7 @@ __global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, 
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int c = n0 + tx + 16 * q;
-        if (c < keep) Out[j * ldc + c] = acc[p][q] + xj * cvec[c];
+        if (c < keep) Out[j * ldo + c] = acc[p][q] + xj * cvec[c];
       }
     }
   }
@@ -671,7 +673,7 @@ __global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, 
 // ---------------------------------------------------------------------------------------------
 // Row passes with one row per lane (r_d <= 32). Each lane owns rows jn = g, g + G, ... of the new
 // spatial layout, maps each to its old row (zero padding has none), reads that row's r_d
-// coefficients as 16-byte pieces (the row start is aligned when ldc is a multiple of 4 floats /
+// coefficients as 16-byte pieces (the row start is aligned when the stride is a multiple of 4 floats /
 // 2 doubles) and keeps them in registers. Nothing is recomputed across lanes, so the index map
 // costs one mixed-radix decomposition per row. FP32 partial sums cover at most ROWS_FLUSH rows
 // before they are added into FP64 shared-memory slots.
@@ -744,7 +746,7 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_p_rows(const Ctl* __restrict__
   if (!rows_isvd_ok(ctl)) return;
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
-  const int ldc = ctl->ldc;
+  const int ldc = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));
   const bool vec = (ldc % (16 / (int)sizeof(TW))) == 0;
   const TW* V = vbufs[ctl->cbuf];
   const TW* dv = dbufs[ctl->xbuf];
@@ -793,7 +795,7 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_e_rows(const Ctl* __restrict__
   if (!rows_isvd_ok(ctl)) return;
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
-  const int ldc = ctl->ldc;
+  const int ldc = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));
   const bool vec = (ldc % (16 / (int)sizeof(TW))) == 0;
   const TW* V = vbufs[ctl->cbuf];
   const TW* dv = dbufs[ctl->xbuf];
@@ -867,8 +869,9 @@ __global__ void __launch_bounds__(ROWS_NT) k_cv_rows(const Ctl* __restrict__ ctl
   if (!rows_cv_ok(ctl, keep)) return;
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
-  const int ldc = ctl->ldc;
-  const bool vec = (ldc % (16 / (int)sizeof(TW))) == 0;
+  const int ldi = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));      // rows read (rank r)
+  const int ldo = tk_cv_stride(keep, ctl->ldc, (int)sizeof(TW));   // rows written (rank keep)
+  const bool vec = (ldi % (16 / (int)sizeof(TW))) == 0 && (ldo % (16 / (int)sizeof(TW))) == 0;
   const bool isV = blockIdx.y == 1;
   const TW* In = (isV ? vbufs : cbufs)[ctl->cbuf];
   TW* Out = (isV ? vbufs : cbufs)[ctl->cbuf ^ 1];
@@ -896,13 +899,13 @@ __global__ void __launch_bounds__(ROWS_NT) k_cv_rows(const Ctl* __restrict__ ctl
   for (long long jn = (long long)blockIdx.x * ROWS_NT + threadIdx.x; jn < Rn; jn += G) {
     const int jo = same ? (int)jn : map_new_to_old_reg((int)jn, rn, ro, m);
     TW v[ROWS_RMAX];
-    if (jo >= 0) load_row<TW>(In + (long long)jo * ldc, r, vec, v);
+    if (jo >= 0) load_row<TW>(In + (long long)jo * ldi, r, vec, v);
     else {
 #pragma unroll
       for (int c = 0; c < ROWS_RMAX; ++c) v[c] = TW(0);
     }
     const TW xj = X[jn];
-    TW* orow = Out + jn * ldc;
+    TW* orow = Out + jn * ldo;
 #pragma unroll
     for (int c4 = 0; c4 < ROWS_RMAX / 4; ++c4) {
       if (4 * c4 >= keep) break;
@@ -916,7 +919,7 @@ __global__ void __launch_bounds__(ROWS_NT) k_cv_rows(const Ctl* __restrict__ ctl
         for (int t = 0; t < 4; ++t) o[t] += v[k] * Bs[k][4 * c4 + t];
       }
       if (vec && sizeof(TW) == 4) {
-        // columns keep.. of the last piece are zero (B and c are zero-padded); ldc % 4 == 0
+        // columns keep.. of the last piece are zero (B and c are zero-padded); ldo % 4 == 0
         // keeps the piece inside the row
         *reinterpret_cast<float4*>(orow + 4 * c4) = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
       } else {
