@@ -19,7 +19,7 @@ using namespace tk;
 namespace {
 
 constexpr int kGridP = 152 * 2;    // projection kernel grid (persistent-style, grid-stride)
-constexpr int kGridI = 152 * 4;    // ISVD row-pass grid
+constexpr int kGridI = 152 * 2;    // ISVD row-pass grid (one wave at two blocks per SM)
 constexpr int kGridCV = 152 * 4;   // core / V update grid
 constexpr int kGramBlocks = 600;   // target blocks of the residual-Gram kernel
 constexpr int kSecMax = TK_STREAM_CAP_MAX + 2;
@@ -570,7 +570,7 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
     CK(launch_isvd<TW>(s->ctl, s->d_dbufs, s->d_vbufs, s->part_p, s->part_e, s->pvec, s->esvec,
                        s->evec, s->S, s->sw, kGridI, st));
     CK(launch_secular_vectors(s->ctl, s->S, s->sw, s->Snew, st));
-    launches += 7;
+    launches += 6;
   }
   {
     PhaseMark pm(s, st, TK_PH_FACT);

@@ -60,6 +60,8 @@ struct Ctl {
   long long nupdates;
   // ---- algorithmic bytes per phase, accumulated by every update (see k_end_update) ----
   double acc_bytes[8];
+  // ---- completion tickets of the cross-block reductions (zero between launches) ----
+  unsigned ticket[4];
 };
 
 // Phases of one update (profiling and byte accounting).
@@ -123,6 +125,48 @@ __host__ __device__ inline long long tk_prod(const int* v, int a, int b) {
 // ---------------------------------------------------------------------------------------------
 // warp / block reductions
 // ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v);
+
+// Cross-block reduction in a fixed order. Every block has written its partial vector
+// part[blockIdx.x * stride + c] (c < len); the last block to finish (completion ticket) sums the
+// partials of all blocks into out[c], warps taking blocks w, w + W, ... in increasing order and
+// the warp sums added in warp order, so the result does not depend on which block finished last.
+// Returns true in that block (all its threads), after out[] is written; resets the ticket.
+__device__ __forceinline__ bool tk_last_block_reduce(const double* part, long long stride, int len,
+                                                     double* out, unsigned* ticket) {
+  __shared__ int s_last;
+  __shared__ double s_red[32][33];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nb = gridDim.x;
+  for (int c0 = 0; c0 < len; c0 += 32) {
+    const int c = c0 + lane;
+    double acc = 0.0;
+    if (c < len) {
+      const volatile double* vp = part;
+      for (int b = wid; b < nb; b += nw) acc += vp[(long long)b * stride + c];
+    }
+    s_red[wid][lane] = acc;
+    __syncthreads();
+    if (wid == 0 && c < len) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += s_red[w][lane];
+      out[c] = t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  __threadfence();
+  __syncthreads();
+  return true;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

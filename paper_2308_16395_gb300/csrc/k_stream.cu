@@ -13,7 +13,7 @@
 //   k_isvd_e       e = d - V p, ||e||^2, s = V^T e              (Alg. 3, second step + one
 //                  classical Gram-Schmidt re-orthogonalisation of e against V, the QR of Alg. 3
 //                  specialised to orthonormal V)
-//   k_isvd_small   q, the q <= eps branch, the compact SVD of S' through the secular equation
+//   isvd_small_body q, the q <= eps branch, the compact SVD of S' through the secular equation
 //                  of S'^T S' = diag(S^2[,0]) + z z^T (O(r^2) instead of O(r^3))
 //   k_ud_update    U~_d = [U_d U''(1:r,:); U''(r+1,:)]          (Alg. 3)
 //   k_core_m       M = U~_d(1:n_d,:)^T U_d                      (Alg. 5, last step)
@@ -32,8 +32,9 @@ constexpr int RB = 8;   // rows per warp batch
 
 // p = V_pad^T d over the old rows; partials per block (TK_STREAM_CAP_MAX doubles each).
 template <typename TW>
-__global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW* const* dbufs,
-                                               TW* const* vbufs, double* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_isvd_p(Ctl* __restrict__ ctl, TW* const* dbufs,
+                                               TW* const* vbufs, double* __restrict__ part,
+                                               double* __restrict__ pout) {
   if (ctl->status) return;
   if (rows_isvd_ok(ctl)) return;   // k_isvd_p_rows does this pass
   const int d = ctl->d, m = d - 1;
@@ -105,37 +106,90 @@ __global__ void __launch_bounds__(256) k_isvd_p(const Ctl* __restrict__ ctl, TW*
     for (int w = 0; w < 8; ++w) s += sh[w][c];
     part[(long long)blockIdx.x * TK_STREAM_CAP_MAX + c] = s;
   }
+  tk_last_block_reduce(part, TK_STREAM_CAP_MAX, r, pout, &ctl->ticket[0]);
 }
 
-// Fixed-order reduction of per-block vectors: out[c] = sum_b part[b * stride + c] for
-// c < r_d + len_extra. One block per 32 columns, warps split the partials.
-__global__ void __launch_bounds__(256) k_reduce_vec(const Ctl* ctl, const double* part, int nparts,
-                                                   int stride, int len_extra, double* out) {
-  if (ctl->status) return;
-  const int len = ctl->r[ctl->d - 1] + len_extra;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int c = blockIdx.x * 32 + lane;
-  if (blockIdx.x * 32 >= len) return;
-  double s = 0.0;
-  if (c < len)
-    for (int b = wid; b < nparts; b += 8) s += part[(long long)b * stride + c];
-  __shared__ double sh[8][32];
-  sh[wid][lane] = s;
-  __syncthreads();
-  if (wid == 0 && c < len) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += sh[w][lane];
-    out[c] = t;
+// q, the q <= eps branch of Alg. 3 and the deflated secular problem of S'^T S' (one thread of
+// the e-pass's last block, once the cross-block sums p and [s; ||e||^2] are complete).
+__device__ void isvd_small_body(Ctl* ctl, const double* p, const double* es, const double* S,
+                                const SecWork& w) {
+  const int d = ctl->d;
+  const int r = ctl->r[d - 1];
+  // CGS-corrected projection: p' = p + s, q'^2 = ||e||^2 - ||s||^2
+  double s2 = 0.0;
+  for (int c = 0; c < r; ++c) s2 += es[c] * es[c];
+  double q2 = es[r] - s2;
+  if (q2 < 0.0) q2 = 0.0;
+  const double q = sqrt(q2);
+  for (int c = 0; c < r; ++c) w.pq[c] = p[c] + es[c];
+  w.pq[r] = q;
+  ctl->q2 = q2;
+  ctl->q = q;
+  const int aug = q > ctl->eps ? 1 : 0;   // Alg. 3: ignore e if q <= eps
+  ctl->aug = aug;
+  if (aug && r + 1 > ctl->cap[d - 1]) { ctl->status = TK_ECAPACITY; return; }
+  long long Rn = 1;
+  for (int i = 0; i < d - 1; ++i) Rn *= ctl->r[i];
+  if (Rn > ctl->core_cap) { ctl->status = TK_ECAPACITY; return; }
+  const int m = r + aug;
+  // poles (descending since S is descending) and weights
+  double zn2 = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double zi = (i < r) ? w.pq[i] : q;
+    zn2 += zi * zi;
   }
+  const double u = 1.1102230246251565e-16;
+  const double d1 = (r > 0) ? S[0] * S[0] : 0.0;
+  const double scale = fmax(d1, zn2) > 0.0 ? fmax(d1, zn2) : 1.0;
+  const double tol = 8.0 * u * scale;
+  const double zn = sqrt(zn2);
+  int mk = 0, nl = 0, nr = 0;
+  // deflation of tiny weights, merge of (nearly) equal poles by a Givens rotation
+  double pz = 0.0, pd = 0.0;
+  int pidx = -1;
+  for (int i = 0; i < m; ++i) {
+    const double di = (i < r) ? S[i] * S[i] : 0.0;
+    double zi = (i < r) ? w.pq[i] : q;
+    if (fabs(zi) * zn <= tol) {   // deflate: eigenpair (di, e_i)
+      w.lam[nl] = di;
+      w.lsrc[nl] = -(i + 1);
+      ++nl;
+      continue;
+    }
+    if (pidx >= 0 && fabs(pd - di) <= tol) {
+      // rotate (pz at pidx, zi at i) so that the weight of pole i vanishes
+      const double h = hypot(pz, zi);
+      const double c = pz / h, s = zi / h;
+      w.rot[4 * nr + 0] = pidx; w.rot[4 * nr + 1] = i; w.rot[4 * nr + 2] = c; w.rot[4 * nr + 3] = s;
+      ++nr;
+      pz = h;
+      w.z[mk - 1] = h;
+      w.lam[nl] = di;
+      w.lsrc[nl] = -(i + 1);
+      ++nl;
+      continue;
+    }
+    w.delta[mk] = di;
+    w.z[mk] = zi;
+    w.idx[mk] = i;
+    pz = zi; pd = di; pidx = i;
+    ++mk;
+  }
+  w.nrot[0] = nr;
+  w.meta[0] = m;
+  w.meta[1] = mk;
+  w.meta[3] = nl;
 }
 
 // ---------------------------------------------------------------------------------------------
 // e = d - V_pad p over the new rows (stored), ||e||^2 and s = V_pad^T e; partials (r + 1).
 // ---------------------------------------------------------------------------------------------
 template <typename TW>
-__global__ void __launch_bounds__(256) k_isvd_e(const Ctl* __restrict__ ctl, TW* const* dbufs,
+__global__ void __launch_bounds__(256) k_isvd_e(Ctl* __restrict__ ctl, TW* const* dbufs,
                                                TW* const* vbufs, const double* __restrict__ p,
-                                               TW* __restrict__ evec, double* __restrict__ part) {
+                                               TW* __restrict__ evec, double* __restrict__ part,
+                                               double* __restrict__ es, const double* __restrict__ S,
+                                               SecWork w) {
   if (ctl->status) return;
   if (rows_isvd_ok(ctl)) return;   // k_isvd_e_rows does this pass
   const int d = ctl->d, m = d - 1;
@@ -229,9 +283,12 @@ __global__ void __launch_bounds__(256) k_isvd_e(const Ctl* __restrict__ ctl, TW*
   for (int c = threadIdx.x; c <= r; c += blockDim.x) {
     const int src = (c == r) ? TK_STREAM_CAP_MAX : c;
     double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += sh[w][src];
+    for (int ww = 0; ww < 8; ++ww) s += sh[ww][src];
     part[(long long)blockIdx.x * (TK_STREAM_CAP_MAX + 2) + c] = s;
   }
+  if (tk_last_block_reduce(part, TK_STREAM_CAP_MAX + 2, r + 1, es, &ctl->ticket[1]) &&
+      threadIdx.x == 0)
+    isvd_small_body(ctl, p, es, S, w);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -242,78 +299,6 @@ __global__ void __launch_bounds__(256) k_isvd_e(const Ctl* __restrict__ ctl, TW*
 // weights of Gu & Eisenstat (SIAM J. Matrix Anal. Appl. 15, 1994), which keep them orthogonal.
 // ---------------------------------------------------------------------------------------------
 
-
-__global__ void k_isvd_small(Ctl* ctl, const double* p, const double* es, const double* S,
-                             SecWork w) {
-  if (ctl->status) return;
-  if (threadIdx.x != 0) return;   // O(r) bookkeeping on one thread
-  const int d = ctl->d;
-  const int r = ctl->r[d - 1];
-  // CGS-corrected projection: p' = p + s, q'^2 = ||e||^2 - ||s||^2
-  double s2 = 0.0;
-  for (int c = 0; c < r; ++c) s2 += es[c] * es[c];
-  double q2 = es[r] - s2;
-  if (q2 < 0.0) q2 = 0.0;
-  const double q = sqrt(q2);
-  for (int c = 0; c < r; ++c) w.pq[c] = p[c] + es[c];
-  w.pq[r] = q;
-  ctl->q2 = q2;
-  ctl->q = q;
-  const int aug = q > ctl->eps ? 1 : 0;   // Alg. 3: ignore e if q <= eps
-  ctl->aug = aug;
-  if (aug && r + 1 > ctl->cap[d - 1]) { ctl->status = TK_ECAPACITY; return; }
-  long long Rn = 1;
-  for (int i = 0; i < d - 1; ++i) Rn *= ctl->r[i];
-  if (Rn > ctl->core_cap) { ctl->status = TK_ECAPACITY; return; }
-  const int m = r + aug;
-  // poles (descending since S is descending) and weights
-  double zn2 = 0.0;
-  for (int i = 0; i < m; ++i) {
-    const double zi = (i < r) ? w.pq[i] : q;
-    zn2 += zi * zi;
-  }
-  const double u = 1.1102230246251565e-16;
-  const double d1 = (r > 0) ? S[0] * S[0] : 0.0;
-  const double scale = fmax(d1, zn2) > 0.0 ? fmax(d1, zn2) : 1.0;
-  const double tol = 8.0 * u * scale;
-  const double zn = sqrt(zn2);
-  int mk = 0, nl = 0, nr = 0;
-  // deflation of tiny weights, merge of (nearly) equal poles by a Givens rotation
-  double pz = 0.0, pd = 0.0;
-  int pidx = -1;
-  for (int i = 0; i < m; ++i) {
-    const double di = (i < r) ? S[i] * S[i] : 0.0;
-    double zi = (i < r) ? w.pq[i] : q;
-    if (fabs(zi) * zn <= tol) {   // deflate: eigenpair (di, e_i)
-      w.lam[nl] = di;
-      w.lsrc[nl] = -(i + 1);
-      ++nl;
-      continue;
-    }
-    if (pidx >= 0 && fabs(pd - di) <= tol) {
-      // rotate (pz at pidx, zi at i) so that the weight of pole i vanishes
-      const double h = hypot(pz, zi);
-      const double c = pz / h, s = zi / h;
-      w.rot[4 * nr + 0] = pidx; w.rot[4 * nr + 1] = i; w.rot[4 * nr + 2] = c; w.rot[4 * nr + 3] = s;
-      ++nr;
-      pz = h;
-      w.z[mk - 1] = h;
-      w.lam[nl] = di;
-      w.lsrc[nl] = -(i + 1);
-      ++nl;
-      continue;
-    }
-    w.delta[mk] = di;
-    w.z[mk] = zi;
-    w.idx[mk] = i;
-    pz = zi; pd = di; pidx = i;
-    ++mk;
-  }
-  w.nrot[0] = nr;
-  w.meta[0] = m;
-  w.meta[1] = mk;
-  w.meta[3] = nl;
-}
 
 __device__ double sec_f(const double* delta, const double* z, int mk, double dorg, double tau,
                         double* fp, int lane) {
@@ -330,20 +315,46 @@ __device__ double sec_f(const double* delta, const double* z, int mk, double dor
   return 1.0 + f;
 }
 
-// One warp per root of 1 + sum z_i^2 / (delta_i - lambda) = 0.
-__global__ void k_secular_roots(const Ctl* ctl, SecWork w) {
+// FP32 form of sec_f on scaled, origin-shifted data: df[i] = (delta_i - delta_o) / scale,
+// zf2[i] = z_i^2 / scale, t = tau / scale.
+__device__ __forceinline__ float sec_f32(const float* df, const float* zf2, int mk, float t,
+                                         float* fp, int lane) {
+  float f = 0.f, g = 0.f;
+  for (int i = lane; i < mk; i += 32) {
+    const float den = df[i] - t;
+    const float q = zf2[i] / den;
+    f += q;
+    g += q / den;
+  }
+  f = warp_sum(f);
+  g = warp_sum(g);
+  *fp = g;
+  return 1.f + f;
+}
+
+constexpr int SEC_WARPS = 4;       // roots per block of k_secular_roots
+constexpr int SEC_PAIR_MAX = 48;   // pair-parallel Loewner weights up to this many poles
+
+// One warp per root of 1 + sum z_i^2 / (delta_i - lambda) = 0. The root is first located in FP32
+// (bisection with Newton steps on the origin-shifted, scaled equation, about 24 bits), then
+// polished in FP64 by safeguarded Newton steps inside a bracket checked in FP64: FP64 runs at a
+// small fraction of the FP32 rate here, and from a 24-bit start Newton needs two or three steps.
+__global__ void __launch_bounds__(32 * SEC_WARPS) k_secular_roots(const Ctl* ctl, SecWork w) {
   if (ctl->status) return;
   const int mk = w.meta[1];
-  const int lane = threadIdx.x & 31;
-  const int root = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int root = blockIdx.x * SEC_WARPS + wl;
   if (root >= mk) return;
+  __shared__ float s_df[SEC_WARPS][TK_STREAM_CAP_MAX + 1];
+  __shared__ float s_z2[SEC_WARPS][TK_STREAM_CAP_MAX + 1];
   double zn2 = 0.0;
   for (int i = lane; i < mk; i += 32) zn2 += w.z[i] * w.z[i];
   zn2 = warp_sum(zn2);
-  // interval of lambda_root: (delta_root, delta_{root-1}) or (delta_0, delta_0 + ||z||^2]
+  double fp;
+  // interval of lambda_root: (delta_root, delta_{root-1}) or (delta_0, delta_0 + ||z||^2]; the
+  // origin is the nearer pole (sign of f at the midpoint)
   int o;
   double lo, hi;   // offsets relative to delta[o]
-  double fp;
   if (root == 0) {
     o = 0; lo = 0.0; hi = zn2;
   } else {
@@ -354,9 +365,31 @@ __global__ void k_secular_roots(const Ctl* ctl, SecWork w) {
     else { o = root - 1; lo = a - b + mid; hi = 0.0; }   // lo = -(b - a)/2 relative to b
   }
   const double dorg = w.delta[o];
-  double tau = 0.5 * (lo + hi);
-  // bisection with Newton acceleration (bracket kept)
-  for (int it = 0; it < 120; ++it) {
+  // ---- FP32 search ----
+  const double scale = fmax(fmax(fabs(w.delta[0]), zn2), 1e-300);
+  const double inv = 1.0 / scale;
+  for (int i = lane; i < mk; i += 32) {
+    s_df[wl][i] = (float)((w.delta[i] - dorg) * inv);
+    s_z2[wl][i] = (float)(w.z[i] * w.z[i] * inv);
+  }
+  __syncwarp();
+  float lf = (float)(lo * inv), hf = (float)(hi * inv);
+  float t = 0.5f * (lf + hf);
+  for (int it = 0; it < 80; ++it) {
+    float gp;
+    const float f = sec_f32(s_df[wl], s_z2[wl], mk, t, &gp, lane);
+    if (f == 0.f) break;
+    if (f > 0.f) hf = t; else lf = t;
+    float tn = t - f / gp;
+    if (!(tn > lf && tn < hf)) tn = 0.5f * (lf + hf);
+    if (hf - lf <= 4.f * 5.9604645e-08f * fmaxf(fabsf(lf), fabsf(hf)) ||
+        fabsf(tn - t) <= 2.f * 5.9604645e-08f * fabsf(t)) { t = tn; break; }
+    t = tn;
+  }
+  // ---- FP64 polish ----
+  double tau = (double)t * scale;
+  if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
     const double f = sec_f(w.delta, w.z, mk, dorg, tau, &fp, lane);
     if (f == 0.0) break;
     if (f > 0.0) hi = tau; else lo = tau;
@@ -385,6 +418,7 @@ __global__ void __launch_bounds__(1024) k_secular_vectors(Ctl* ctl, const double
   __shared__ int src_all[TK_STREAM_CAP_MAX + 1];
   __shared__ int order[TK_STREAM_CAP_MAX + 1];
   __shared__ int s_keep;
+  __shared__ double s_fac[SEC_PAIR_MAX][SEC_PAIR_MAX];
   // roots first (index k -> lambda = delta[org] + tau), then deflated
   for (int k = tid; k < mk; k += nt) {
     lam_all[k] = w.delta[w.org[k]] + w.tau[k];
@@ -395,16 +429,36 @@ __global__ void __launch_bounds__(1024) k_secular_vectors(Ctl* ctl, const double
     src_all[mk + k] = w.lsrc[k];
   }
   __syncthreads();
-  // Loewner weights of the non-deflated problem
-  for (int i = tid; i < mk; i += nt) {
-    // zhat_i^2 = (lambda_i - delta_i) prod_{j != i} (lambda_j - delta_i) / (delta_j - delta_i)
-    double prod = (w.delta[w.org[i]] - w.delta[i]) + w.tau[i];
-    for (int j = 0; j < mk; ++j) {
-      if (j == i) continue;
-      const double num = (w.delta[w.org[j]] - w.delta[i]) + w.tau[j];
-      prod *= num / (w.delta[j] - w.delta[i]);
+  // Loewner weights of the non-deflated problem:
+  // zhat_i^2 = (lambda_i - delta_i) prod_{j != i} (lambda_j - delta_i) / (delta_j - delta_i)
+  if (mk <= SEC_PAIR_MAX) {
+    // every factor in parallel (one FP64 division each), then one warp per product
+    for (int L = tid; L < mk * mk; L += nt) {
+      const int i = L / mk, j = L - i * mk;
+      double f;
+      if (j == i) f = (w.delta[w.org[i]] - w.delta[i]) + w.tau[i];
+      else f = ((w.delta[w.org[j]] - w.delta[i]) + w.tau[j]) / (w.delta[j] - w.delta[i]);
+      s_fac[i][j] = f;
     }
-    zhat[i] = copysign(sqrt(fabs(prod)), w.z[i]);
+    __syncthreads();
+    const int lane = tid & 31, nwarp = nt >> 5;
+    for (int i = tid >> 5; i < mk; i += nwarp) {
+      double prod = 1.0;
+      for (int j = lane; j < mk; j += 32) prod *= s_fac[i][j];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) prod *= __shfl_xor_sync(0xffffffffu, prod, off);
+      if (lane == 0) zhat[i] = copysign(sqrt(fabs(prod)), w.z[i]);
+    }
+  } else {
+    for (int i = tid; i < mk; i += nt) {
+      double prod = (w.delta[w.org[i]] - w.delta[i]) + w.tau[i];
+      for (int j = 0; j < mk; ++j) {
+        if (j == i) continue;
+        const double num = (w.delta[w.org[j]] - w.delta[i]) + w.tau[j];
+        prod *= num / (w.delta[j] - w.delta[i]);
+      }
+      zhat[i] = copysign(sqrt(fabs(prod)), w.z[i]);
+    }
   }
   // descending order of all m eigenvalues (rank sort; ties by position)
   for (int a = tid; a < m; a += nt) {
@@ -440,37 +494,49 @@ __global__ void __launch_bounds__(1024) k_secular_vectors(Ctl* ctl, const double
     w.V2[(long long)k * m + i] = 0.0;
   }
   __syncthreads();
-  for (int k = tid; k < keep; k += nt) {
-    const int a = order[k];
-    const int src = src_all[a];
-    double* col = w.V2 + (long long)k * m;
-    if (src >= 0) {
-      const int o = w.org[src];
-      const double tau = w.tau[src];
-      double nrm = 0.0;
-      for (int i = 0; i < mk; ++i) {
-        const double den = (w.delta[i] - w.delta[o]) - tau;
-        const double v = zhat[i] / den;
-        col[w.idx[i]] = v;
-        nrm += v * v;
+  // eigenvector entries of the non-deflated columns, one division per (column, row) pair
+  for (long long L = tid; L < (long long)keep * mk; L += nt) {
+    const int k = (int)(L / mk), i = (int)(L % mk);
+    const int src = src_all[order[k]];
+    if (src < 0) continue;
+    const double den = (w.delta[i] - w.delta[w.org[src]]) - w.tau[src];
+    w.V2[(long long)k * m + w.idx[i]] = zhat[i] / den;
+  }
+  __syncthreads();
+  // one warp per column: normalise (or the unit vector of a deflated pair), undo the Givens
+  // merges (in reverse order), singular value
+  {
+    const int lane = tid & 31, nwarp = nt >> 5;
+    for (int k = tid >> 5; k < keep; k += nwarp) {
+      const int a = order[k];
+      const int src = src_all[a];
+      double* col = w.V2 + (long long)k * m;
+      if (src >= 0) {
+        double nrm = 0.0;
+        for (int i = lane; i < mk; i += 32) {
+          const double v = col[w.idx[i]];
+          nrm += v * v;
+        }
+        nrm = sqrt(warp_sum(nrm));
+        for (int i = lane; i < mk; i += 32) col[w.idx[i]] /= nrm;
+      } else if (lane == 0) {
+        col[-src - 1] = 1.0;
       }
-      nrm = sqrt(nrm);
-      for (int i = 0; i < mk; ++i) col[w.idx[i]] /= nrm;
-    } else {
-      col[-src - 1] = 1.0;
+      __syncwarp();
+      if (lane == 0) {
+        for (int t = w.nrot[0] - 1; t >= 0; --t) {
+          const int i = (int)w.rot[4 * t + 0], j = (int)w.rot[4 * t + 1];
+          const double c = w.rot[4 * t + 2], sn = w.rot[4 * t + 3];
+          const double xi = col[i], xj = col[j];
+          // merged weight lives on i: original (z_i, z_j) = h (c, s); x_orig = G^T x_rot
+          col[i] = c * xi - sn * xj;
+          col[j] = sn * xi + c * xj;
+        }
+        const double sig = sqrt(fmax(lam_all[a], 0.0));
+        w.sv[k] = sig;
+        Sout[k] = sig;
+      }
     }
-    // undo the Givens merges (applied in reverse order)
-    for (int t = w.nrot[0] - 1; t >= 0; --t) {
-      const int i = (int)w.rot[4 * t + 0], j = (int)w.rot[4 * t + 1];
-      const double c = w.rot[4 * t + 2], s = w.rot[4 * t + 3];
-      const double xi = col[i], xj = col[j];
-      // merged weight lives on i: original (z_i, z_j) = h (c, s); x_orig = G^T x_rot
-      col[i] = c * xi - s * xj;
-      col[j] = s * xi + c * xj;
-    }
-    const double sig = sqrt(fmax(lam_all[a], 0.0));
-    w.sv[k] = sig;
-    Sout[k] = sig;
   }
   __syncthreads();
   // U'' = S' V'' / sigma: rows 0..r-1: S_i V''(i,k); row r: p'^T V''(0:r,k) + q' V''(r,k)
@@ -714,13 +780,18 @@ __device__ __forceinline__ void load_row(const TW* __restrict__ row, int r, bool
   for (int c = 0; c < ROWS_RMAX; ++c) v[c] = (c < r) ? v[c] : TW(0);
 }
 
-// Adds the warp's FP32 partial sums acc[c] (c < ROWS_RMAX) into the FP64 slots sw[c] (lane 0).
+// Adds the warp's partial sums acc[c] (live columns c < r) into the FP64 slots sw[c] (lane 0).
+// The sum across lanes runs in the work type (FP32 in the mixed form: the FP64 pipe is a small
+// fraction of the FP32 rate, and a 32-term FP32 sum of 32-row FP32 partials keeps the 1e-7
+// relative accuracy of the products); only the per-warp totals are added in FP64.
 template <typename TW>
-__device__ __forceinline__ void rows_flush(TW (&acc)[ROWS_RMAX], double* sw, int lane) {
+__device__ __forceinline__ void rows_flush(TW (&acc)[ROWS_RMAX], double* sw, int lane, int r) {
 #pragma unroll
   for (int c = 0; c < ROWS_RMAX; ++c) {
-    const double t = warp_sum((double)acc[c]);
-    if (lane == 0) sw[c] += t;
+    if (c < r) {
+      const TW t = warp_sum(acc[c]);
+      if (lane == 0) sw[c] += (double)t;
+    }
     acc[c] = TW(0);
   }
 }
@@ -739,9 +810,10 @@ __device__ __forceinline__ void rows_block_sum(double (*sw)[ROWS_RMAX + 1], int 
 // p = V_pad^T d: partials per block in the layout of k_isvd_p. Warps walk 32 consecutive new
 // rows at a time (a warp-uniform loop, so the periodic FP64 flush is a warp reduction).
 template <typename TW>
-__global__ void __launch_bounds__(ROWS_NT) k_isvd_p_rows(const Ctl* __restrict__ ctl,
+__global__ void __launch_bounds__(ROWS_NT) k_isvd_p_rows(Ctl* __restrict__ ctl,
                                                         TW* const* dbufs, TW* const* vbufs,
-                                                        double* __restrict__ part) {
+                                                        double* __restrict__ part,
+                                                        double* __restrict__ pout) {
   if (ctl->status) return;
   if (!rows_isvd_ok(ctl)) return;
   const int d = ctl->d, m = d - 1;
@@ -777,20 +849,24 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_p_rows(const Ctl* __restrict__
 #pragma unroll
       for (int c = 0; c < ROWS_RMAX; ++c) acc[c] += v[c] * dj;
     }
-    if (++it == ROWS_FLUSH) { rows_flush<TW>(acc, sw[wid], lane); it = 0; }
+    if (++it == ROWS_FLUSH) { rows_flush<TW>(acc, sw[wid], lane, r); it = 0; }
   }
-  rows_flush<TW>(acc, sw[wid], lane);
+  rows_flush<TW>(acc, sw[wid], lane, r);
   rows_block_sum(sw, r, part, TK_STREAM_CAP_MAX);
+  tk_last_block_reduce(part, TK_STREAM_CAP_MAX, r, pout, &ctl->ticket[0]);
 }
 
 // e = d - V_pad p (stored), ||e||^2 and s = V_pad^T e: partials in the layout of k_isvd_e
 // (s in columns 0..r-1, ||e||^2 in column r).
 template <typename TW>
-__global__ void __launch_bounds__(ROWS_NT) k_isvd_e_rows(const Ctl* __restrict__ ctl,
+__global__ void __launch_bounds__(ROWS_NT) k_isvd_e_rows(Ctl* __restrict__ ctl,
                                                         TW* const* dbufs, TW* const* vbufs,
                                                         const double* __restrict__ p,
                                                         TW* __restrict__ evec,
-                                                        double* __restrict__ part) {
+                                                        double* __restrict__ part,
+                                                        double* __restrict__ es,
+                                                        const double* __restrict__ S,
+                                                        SecWork w) {
   if (ctl->status) return;
   if (!rows_isvd_ok(ctl)) return;
   const int d = ctl->d, m = d - 1;
@@ -839,9 +915,9 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_e_rows(const Ctl* __restrict__
       evec[jn] = e;
       eacc.add(e * e);
     }
-    if (++it == ROWS_FLUSH) { rows_flush<TW>(acc, sw[wid], lane); it = 0; }
+    if (++it == ROWS_FLUSH) { rows_flush<TW>(acc, sw[wid], lane, r); it = 0; }
   }
-  rows_flush<TW>(acc, sw[wid], lane);
+  rows_flush<TW>(acc, sw[wid], lane, r);
   const double e2 = warp_sum(eacc.value());
   if (lane == 0) sw[wid][ROWS_RMAX] = e2;
   __syncthreads();
@@ -850,6 +926,9 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_e_rows(const Ctl* __restrict__
     sw[threadIdx.x][r] = sw[threadIdx.x][ROWS_RMAX];
   }
   rows_block_sum(sw, r + 1, part, TK_STREAM_CAP_MAX + 2);
+  if (tk_last_block_reduce(part, TK_STREAM_CAP_MAX + 2, r + 1, es, &ctl->ticket[1]) &&
+      threadIdx.x == 0)
+    isvd_small_body(ctl, p, es, S, w);
 }
 
 // C~ = C_pad B_c + d c_c^T (blockIdx.y = 0) and V~ = V_pad B_v + e w_v^T (blockIdx.y = 1), one
@@ -999,16 +1078,15 @@ template <typename TW>
 cudaError_t launch_isvd(Ctl* ctl, void* const* dbufs, void* const* vbufs, double* part_p,
                         double* part_e, double* p, double* es, void* evec, const double* S,
                         SecWork w, int grid, cudaStream_t st) {
-  k_isvd_p_rows<TW><<<grid, ROWS_NT, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p);
-  k_isvd_p<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p);
-  k_reduce_vec<<<(TK_STREAM_CAP_MAX + 2 + 31) / 32, 256, 0, st>>>(ctl, part_p, grid, TK_STREAM_CAP_MAX, 0, p);
+  // p = V^T d, then e = d - V p with [s; ||e||^2] and the small ISVD bookkeeping; each pass
+  // finishes its cross-block sum in its last block
+  k_isvd_p_rows<TW><<<grid, ROWS_NT, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p, p);
+  k_isvd_p<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p, p);
   k_isvd_e_rows<TW><<<grid, ROWS_NT, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p,
-                                               (TW*)evec, part_e);
+                                               (TW*)evec, part_e, es, S, w);
   k_isvd_e<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p, (TW*)evec,
-                                     part_e);
-  k_reduce_vec<<<(TK_STREAM_CAP_MAX + 2 + 31) / 32, 256, 0, st>>>(ctl, part_e, grid, TK_STREAM_CAP_MAX + 2, 1, es);
-  k_isvd_small<<<1, 32, 0, st>>>(ctl, p, es, S, w);
-  k_secular_roots<<<(TK_STREAM_CAP_MAX + 1 + 7) / 8, 256, 0, st>>>(ctl, w);
+                                     part_e, es, S, w);
+  k_secular_roots<<<(TK_STREAM_CAP_MAX + 1 + SEC_WARPS - 1) / SEC_WARPS, 32 * SEC_WARPS, 0, st>>>(ctl, w);
   return cudaGetLastError();
 }
 
