@@ -385,7 +385,22 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   for (int i = tid; i < n - 1; i += nt) sb2[i] = sb[i] * sb[i];
   __syncthreads();
 
-  // ---- eigenvalues by bisection (one thread per eigenvalue, ascending index) ----
+  // ---- Alg. 1's cut from the top eigenvalues ----
+  // tails[l] = lam_l + ... + lam_{n-1} = trace(G) - (lam_0 + ... + lam_{l-1}), with the trace
+  // summed in FP64 from G's diagonal, so only the eigenvalues above the cut are computed: largest
+  // first, one warp per eigenvalue, each by multisection of the Sturm count at 32 shifts per
+  // sweep (33 sub-intervals, five bits per sweep); batches of one eigenvalue per warp until the
+  // cut is found. The error of a tail is then that of a few eigenvalues (a few u ||G||), not of
+  // the sum of all the small ones.
+  __shared__ double stails[TK_N_MAX + 1];   // stails[l] = trace - (lam_0 + ... + lam_{l-1})
+  __shared__ int s_cnt, s_cut;
+  __shared__ double s_trace;
+  if (wid == 0) {
+    double t = 0.0;
+    for (int i = lane; i < n; i += 32) t += ea.G[(long long)i * n + i];
+    t = warp_sum(t);
+    if (lane == 0) { s_trace = t; stails[0] = t; s_cnt = 0; s_cut = -1; }
+  }
   {
     TE gl = sa[0], gu = sa[0], bmax2 = TE(0);
     for (int i = 0; i < n; ++i) {
@@ -400,70 +415,72 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     gu += TE(2) * u * scale * n + Eps<TE>::tiny();
     const TE pivmin = max(Eps<TE>::tiny(), u * u * bmax2);
     // absolute floor u |T|: the reduction to tridiagonal form already moves every eigenvalue by
-    // that much, so refining eigenvalues near zero (the residual Gram has r_k of them) further
-    // buys nothing and costs most of the sweeps
+    // that much
     const TE atol = max(pivmin, u * scale);
-    for (int i = tid; i < n; i += nt) {
-      TE lo = gl, hi = gu;
-      constexpr int NS = 3;   // 4-way multisection: two bits per sweep
-      for (int it = 0; it < 60; ++it) {
-        const TE w = hi - lo;
-        if (w <= TE(2) * u * max(fabs(lo), fabs(hi)) + atol) break;
-        TE x[NS];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) x[s] = lo + TE(s + 1) * TE(0.25) * w;
-        if (!(x[0] > lo && x[NS - 1] < hi)) break;
-        int cnt[NS];
-        sturm_countN<TE, NS>(sa, sb2, n, x, pivmin, cnt);
-        // the eigenvalue of ascending index i lies in the first sub-interval whose right end
-        // counts more than i eigenvalues below it
-        TE nlo = x[NS - 1], nhi = hi;
-#pragma unroll
-        for (int s = NS - 1; s >= 0; --s)
-          if (cnt[s] > i) { nhi = x[s]; nlo = (s > 0) ? x[s - 1] : lo; }
-        lo = nlo;
-        hi = nhi;
+    const double eps2 = ctl->eps * ctl->eps;
+    __syncthreads();
+    if (tid == 0 && s_trace <= eps2) s_cut = 0;
+    __syncthreads();
+    // the first batch always runs (the initial ST-HOSVD keeps at least one eigenpair)
+    for (int j0 = 0; j0 < n && (j0 == 0 || s_cut < 0); j0 += nwarp) {
+      const int j = j0 + wid;            // descending index of this warp's eigenvalue
+      if (j < n) {
+        const int i = n - 1 - j;         // ascending index
+        TE lo = gl, hi = gu;
+        for (int it = 0; it < 40; ++it) {
+          const TE w = hi - lo;
+          if (w <= TE(2) * u * max(fabs(lo), fabs(hi)) + atol) break;
+          const TE step = w / TE(33);
+          TE x[1] = {lo + TE(lane + 1) * step};
+          if (!(lo + step > lo && lo + TE(32) * step < hi)) break;
+          int cnt[1];
+          sturm_countN<TE, 1>(sa, sb2, n, x, pivmin, cnt);
+          // the eigenvalue lies in the first sub-interval whose right end counts more than i
+          // eigenvalues below it
+          const unsigned above = __ballot_sync(0xffffffffu, cnt[0] > i);
+          const int l = above ? __ffs(above) - 1 : 32;
+          const TE nlo = (l == 0) ? lo : lo + TE(l) * step;
+          const TE nhi = (l == 32) ? hi : lo + TE(l + 1) * step;
+          lo = nlo;
+          hi = nhi;
+        }
+        if (lane == 0) slam[j] = TE(0.5) * (lo + hi);
       }
-      slam[n - 1 - i] = TE(0.5) * (lo + hi);   // store descending
+      __syncthreads();
+      if (tid == 0) {
+        const int jend = min(n, j0 + nwarp);
+        for (int jj = j0; jj < jend; ++jj) {
+          stails[jj + 1] = stails[jj] - (double)slam[jj];
+          if (s_cut < 0 && stails[jj + 1] <= eps2) s_cut = jj + 1;
+        }
+        s_cnt = jend;
+        if (s_cut < 0 && jend == n) s_cut = n;   // every eigenvalue is kept
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
 
-  // ---- rank decision (Alg. 1) in FP64: tails[l] = lam_l + ... + lam_{n-1}, first l with
-  // tails[l] <= eps^2 ----
-  __shared__ double stails[TK_N_MAX + 1];
+  // ---- rank decision (Alg. 1) in FP64: the first l with tails[l] <= eps^2 ----
   if (tid == 0) {
-    const double eps2 = ctl->eps * ctl->eps;
-    stails[n] = 0.0;
-    for (int l = n - 1; l >= 0; --l) stails[l] = stails[l + 1] + (double)slam[l];
-    int m = n;
-    for (int l = 0; l <= n; ++l) {
-      if (stails[l] <= eps2) { m = l; break; }
-    }
-    double disc = 0.0;
-    for (int i = m; i < n; ++i) disc += (double)slam[i];
+    int m = s_cut;
     int status = 0;
     if (mode == 0) {
       const int rk = ctl->r[k];
       if (m > n - rk) m = n - rk;
-      disc = 0.0;
-      for (int i = m; i < n; ++i) disc += (double)slam[i];
       if (rk + m > ctl->cap[k]) status = TK_ECAPACITY;
     } else {
       if (m < 1) m = 1;
-      disc = 0.0;
-      for (int i = m; i < n; ++i) disc += (double)slam[i];
       if (m > ctl->cap[k] || m > ea.mcap) status = TK_ECAPACITY;
     }
     if (m > ea.mcap) status = TK_ECAPACITY;
     if (status) ctl->status = status;
     s_m = status ? 0 : m;
-    s_disc = disc;
+    s_disc = (m <= s_cnt) ? stails[m] : 0.0;
   }
   __syncthreads();
   const int m = s_m;
   if (ea.lam_out)
-    for (int i = tid; i < n; i += nt) ea.lam_out[i] = (double)slam[i];
+    for (int i = tid; i < s_cnt; i += nt) ea.lam_out[i] = (double)slam[i];
   if (m == 0) {
     if (tid == 0) {
       if (mode == 0) { ctl->radd[k] = 0; ctl->disc[k] = s_disc; }
