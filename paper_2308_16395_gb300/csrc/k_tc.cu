@@ -357,6 +357,13 @@ namespace tk {
 // =============================================================================================
 constexpr int TP_STAGE = 48 * 1024;                // X hi | X lo | U chunk hi | U chunk lo
 constexpr int TP_S = 2;
+constexpr int TP_PF = 12;                           // X chunks prefetched into L2 ahead
+// warps: 0 TMA producer, 1 MMA issuer, 2 .. 2+TP_SPLIT_WARPS-1 TF32 splitters of the X chunks,
+// then 4 epilogue warps (TMEM lane quarter = warp % 4, so the first is a multiple of 4)
+constexpr int TP_SPLIT_WARPS = 6;
+constexpr int TP_EPI_W0 = 2 + TP_SPLIT_WARPS;
+constexpr int TP_NT = 32 * (TP_EPI_W0 + 4);
+static_assert(TP_EPI_W0 % 4 == 0, "epilogue warps must start at a TMEM lane quarter boundary");
 constexpr size_t TP_SMEM = (size_t)TP_S * TP_STAGE + 128 * 1024 + 1024 + 256;
 
 struct TcProjArgs {
@@ -372,7 +379,7 @@ struct TcProjArgs {
 };
 
 template <bool RESID, bool WRITE_ET>
-__global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl, int pred,
+__global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ctl, int pred,
                                                    const __grid_constant__ CUtensorMap mY,
                                                    const __grid_constant__ CUtensorMap mD0,
                                                    const __grid_constant__ CUtensorMap mD1,
@@ -415,7 +422,9 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl,
   uint64_t* mma2done = d2free + 1;
   uint64_t* bload = mma2done + 1;
   uint64_t* done = bload + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* ybar = done + 1;                       // [2] Y chunk loaded (residual epilogue)
+  uint64_t* yfree = ybar + 2;                      // [2] Y chunk consumed by the 4 epilogue warps
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(yfree + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* red = reinterpret_cast<double*>(tmem_slot + 4);   // [8] doubles
 
@@ -423,7 +432,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl,
   if (threadIdx.x == 0) {
     for (int s = 0; s < TP_S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 64);
+      mbar_init(&conv[s], 32 * TP_SPLIT_WARPS);
       mbar_init(&empty[s], 1);
     }
     mbar_init(d1full, 1);
@@ -433,6 +442,10 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl,
     mbar_init(mma2done, 1);
     mbar_init(bload, 1);
     mbar_init(done, 1);
+    mbar_init(&ybar[0], 1);
+    mbar_init(&ybar[1], 1);
+    mbar_init(&yfree[0], 4);
+    mbar_init(&yfree[1], 4);
     *abort = 0;
     fence_barrier_init();
   }
@@ -462,10 +475,20 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl,
             tma_load_2d(&mUrlo, bload, B2lo + ((size_t)kc * n1p + n0) * TC_KC, kc * TC_KC, n0);
           }
       }
+      // the X chunk TP_PF chunks ahead of the one loaded is prefetched into L2, so the two
+      // stages wait on L2 rather than on DRAM latency
+      const long long nq = (long long)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x) * Kc1;
+      auto prefetch_chunk = [&](long long qq) {
+        if (qq >= nq) return;
+        const long long tt = blockIdx.x + (qq / Kc1) * (long long)gridDim.x;
+        tma_prefetch_l2_2d(mX, (int)(qq % Kc1) * TC_KC, (int)(tt * TC_M));
+      };
+      for (long long qq = 0; qq < TP_PF; ++qq) prefetch_chunk(qq);
       long long q = 0;
       for (long long t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
         for (int kc = 0; kc < Kc1; ++kc, ++q) {
           const int s = (int)(q % TP_S);
+          prefetch_chunk(q + TP_PF);
           if (!wait_bar(&empty[s], (uint32_t)(((q / TP_S) & 1) ^ 1), abort)) break;
           unsigned char* st = base + (size_t)s * TP_STAGE;
           mbar_arrive_expect_tx(&full[s], (uint32_t)(TC_M * TC_KC * 4 + Rp * TC_KC * 4 * 2));
@@ -534,7 +557,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl,
       wait_bar(done, 0, abort);
     }
     __syncwarp();
-  } else if (warp == 2 || warp == 3) {
+  } else if (warp >= 2 && warp < 2 + TP_SPLIT_WARPS) {
     // ---------------- X splitters ----------------
     const int ct = threadIdx.x - 64;
     long long q = 0;
@@ -545,7 +568,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl,
         float4* hi = reinterpret_cast<float4*>(base + (size_t)s * TP_STAGE);
         float4* lo = hi + TC_M * TC_KC / 4;
 #pragma unroll 4
-        for (int i = ct; i < TC_M * TC_KC / 4; i += 64) {
+        for (int i = ct; i < TC_M * TC_KC / 4; i += 32 * TP_SPLIT_WARPS) {
           float4 v = hi[i], h, l;
           tf32_split(v.x, h.x, l.x);
           tf32_split(v.y, h.y, l.y);
@@ -558,13 +581,33 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl,
         mbar_arrive(&conv[s]);
       }
     }
-  } else if (warp >= 4 && warp < 8) {
+  } else if (warp >= TP_EPI_W0 && warp < TP_EPI_W0 + 4) {
     // ---------------- epilogue ----------------
-    const int wq = warp - 4;
+    const int wq = warp - TP_EPI_W0;   // TMEM lane quarter (warp % 4)
     const uint32_t lq = (uint32_t)(wq * 32) << 16;
     double eacc = 0.0, yacc = 0.0;
+    // The residual needs the tile's Y again: when the resident U copy leaves 32 KB, the epilogue
+    // reloads Y by 32-column chunks (TMA, an L2 hit: the tile was streamed moments before) into
+    // two swizzled buffers, instead of 128 strided row reads per chunk from global memory.
+    const int nck = (n1 + TC_KC - 1) / TC_KC;
+    const bool ysm = RESID && (size_t)2 * Kc2 * n1p * TC_KC * 4 + 2 * TC_M * TC_KC * 4 <= 128 * 1024;
+    float* ybuf = B2lo + (size_t)Kc2 * n1p * TC_KC;   // [2][TC_M][TC_KC], 1024-byte aligned
+    const bool yleader = (wq == 0 && lane == 0);
+    long long yq = 0;                                 // Y chunks consumed so far
+    // chunk seq goes to buffer seq & 1 once the 4 warps have consumed chunk seq - 2 (bounded
+    // wait of the issuing thread); returns false if that wait gave up
+    auto issue_y = [&](long long t_, int ci, long long seq) -> bool {
+      if (seq >= 2 && !wait_bar(&yfree[seq & 1], (uint32_t)(((seq - 2) >> 1) & 1), abort)) return false;
+      mbar_arrive_expect_tx(&ybar[seq & 1], (uint32_t)(TC_M * TC_KC * 4));
+      tma_load_2d(mX, &ybar[seq & 1], ybuf + (size_t)(seq & 1) * TC_M * TC_KC, ci * TC_KC, (int)(t_ * TC_M));
+      return true;
+    };
     int it = 0;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      if (ysm && yleader) {
+        if (issue_y(t, 0, yq) && nck > 1) issue_y(t, 1, yq + 1);
+      }
+      __syncwarp();
       bool okw = wait_bar(d1full, (uint32_t)(it & 1), abort);
       okw = __all_sync(0xffffffffu, okw);
       if (!okw) break;
@@ -596,16 +639,24 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl,
         if (!okw) break;
         tc_fence_after();
         const float* xrow = Xg + f * n1;
-        for (int c0 = 0; c0 < n1p; c0 += 32) {
+        const int row = wq * 32 + lane;
+        for (int c0 = 0, ci = 0; c0 < n1p; c0 += 32, ++ci) {
           float v[32];
           tmem_ld32(tD2 + lq + c0, v);
-          if (live) {
+          const float4* ych = reinterpret_cast<const float4*>(ybuf + (size_t)(yq & 1) * TC_M * TC_KC) + row * 8;
+          if (ysm) {
+            okw = wait_bar(&ybar[yq & 1], (uint32_t)((yq >> 1) & 1), abort);
+            okw = __all_sync(0xffffffffu, okw);
+          }
+          if (live && okw) {
             // FP32 partial sums over 32 elements, flushed to FP64 per chunk
             float es = 0.f, ys = 0.f;
 #pragma unroll
             for (int i = 0; i < 32; i += 4) {
               if (c0 + i < n1) {
-                const float4 y = *reinterpret_cast<const float4*>(xrow + c0 + i);
+                // SWIZZLE_128B: 16-byte piece j of row `row` sits at piece j ^ (row & 7)
+                const float4 y = ysm ? ych[(i >> 2) ^ (row & 7)]
+                                     : *reinterpret_cast<const float4*>(xrow + c0 + i);
                 const float e0 = y.x - v[i], e1 = y.y - v[i + 1], e2 = y.z - v[i + 2], e3 = y.w - v[i + 3];
                 es = fmaf(e0, e0, es); es = fmaf(e1, e1, es); es = fmaf(e2, e2, es); es = fmaf(e3, e3, es);
                 ys = fmaf(y.x, y.x, ys); ys = fmaf(y.y, y.y, ys); ys = fmaf(y.z, y.z, ys); ys = fmaf(y.w, y.w, ys);
@@ -624,6 +675,15 @@ __global__ void __launch_bounds__(256, 1) k_tc_proj(const Ctl* __restrict__ ctl,
             // zero the padding fibers the Gram's last K chunk reads
             for (int i = 0; i < 32; ++i)
               if (c0 + i < n1) a.Et[(long long)(c0 + i) * a.et_stride + f] = 0.f;
+          }
+          if (ysm) {
+            // this warp is done with the buffer; it is refilled with chunk ci + 2 once all four
+            // epilogue warps are
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&yfree[yq & 1]);
+            if (yleader && ci + 2 < nck) issue_y(t, ci + 2, yq + 2);
+            __syncwarp();   // the next tcgen05.ld is warp-collective: lane 0 may have waited
+            ++yq;
           }
         }
         tc_fence_before();
@@ -695,13 +755,13 @@ cudaError_t launch_tc_proj(const Ctl* ctl, int k, int mode, int pred, const floa
   static bool attr[3] = {false, false, false};
   if (mode == 0) {
     if (!attr[0]) { cudaFuncSetAttribute(k_tc_proj<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[0] = true; }
-    k_tc_proj<false, false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
+    k_tc_proj<false, false><<<grid, TP_NT, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
   } else if (mode == 1) {
     if (!attr[1]) { cudaFuncSetAttribute(k_tc_proj<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[1] = true; }
-    k_tc_proj<true, false><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
+    k_tc_proj<true, false><<<grid, TP_NT, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
   } else {
     if (!attr[2]) { cudaFuncSetAttribute(k_tc_proj<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[2] = true; }
-    k_tc_proj<true, true><<<grid, 256, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
+    k_tc_proj<true, true><<<grid, TP_NT, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
   }
   return cudaGetLastError();
 }
