@@ -273,6 +273,8 @@ struct EigArgs {
 // mode 1: data Gram of mode k in the batch ST-HOSVD (Alg. 2): r >= 1.
 // use_smem: the n x n working matrix lives in (dynamic) shared memory instead of global memory.
 constexpr int EIG_SMEM_VECS = 16;
+constexpr int EIG_FIRST_BATCH = 8;   // top eigenvalues computed before the first cut test
+constexpr int EIG_WY = 8;            // reflectors per compact-WY group of the back-transform
 
 // use_smem: dynamic shared memory holds the eigenvector workspaces (up to EIG_SMEM_VECS vectors)
 // after the n x n working matrix when use_amat, else at its start.
@@ -401,14 +403,30 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     t = warp_sum(t);
     if (lane == 0) { s_trace = t; stails[0] = t; s_cnt = 0; s_cut = -1; }
   }
-  {
-    TE gl = sa[0], gu = sa[0], bmax2 = TE(0);
-    for (int i = 0; i < n; ++i) {
+  // Gershgorin interval, largest b_i^2 and |T|_inf of the tridiagonal matrix (one warp)
+  __shared__ TE s_gl, s_gu, s_bmax2, s_tnorm;
+  if (wid == 0) {
+    TE gl = sa[0], gu = sa[0], bmax2 = TE(0), tn = TE(0);
+    for (int i = lane; i < n; i += 32) {
       const TE rad = (i > 0 ? fabs(sb[i - 1]) : TE(0)) + (i < n - 1 ? fabs(sb[i]) : TE(0));
       gl = min(gl, sa[i] - rad);
       gu = max(gu, sa[i] + rad);
+      tn = max(tn, fabs(sa[i]) + rad);
       if (i < n - 1) bmax2 = max(bmax2, sb2[i]);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gl = min(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+      gu = max(gu, __shfl_xor_sync(0xffffffffu, gu, o));
+      tn = max(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+      bmax2 = max(bmax2, __shfl_xor_sync(0xffffffffu, bmax2, o));
+    }
+    if (lane == 0) { s_gl = gl; s_gu = gu; s_bmax2 = bmax2; s_tnorm = tn; }
+  }
+  __syncthreads();
+  {
+    TE gl = s_gl, gu = s_gu;
+    const TE bmax2 = s_bmax2;
     const TE scale = max(fabs(gl), fabs(gu));
     const TE u = Eps<TE>::u();
     gl -= TE(2) * u * scale * n + Eps<TE>::tiny();
@@ -421,10 +439,14 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     __syncthreads();
     if (tid == 0 && s_trace <= eps2) s_cut = 0;
     __syncthreads();
-    // the first batch always runs (the initial ST-HOSVD keeps at least one eigenpair)
-    for (int j0 = 0; j0 < n && (j0 == 0 || s_cut < 0); j0 += nwarp) {
+    // the first batch always runs (the initial ST-HOSVD keeps at least one eigenpair); it is
+    // small because the cut of a residual Gram usually keeps a few eigenpairs. The initial
+    // ST-HOSVD (mode 1) computes every eigenvalue: its discarded energy is a tiny fraction of the
+    // trace, so it is summed from the bottom of the spectrum below instead.
+    for (int j0 = 0; j0 < n && (j0 == 0 || s_cut < 0 || mode == 1); j0 += (j0 == 0 ? EIG_FIRST_BATCH : nwarp)) {
+      const int bs = (j0 == 0) ? EIG_FIRST_BATCH : nwarp;
       const int j = j0 + wid;            // descending index of this warp's eigenvalue
-      if (j < n) {
+      if (wid < bs && j < n) {
         const int i = n - 1 - j;         // ascending index
         TE lo = gl, hi = gu;
         for (int it = 0; it < 40; ++it) {
@@ -448,7 +470,7 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
       }
       __syncthreads();
       if (tid == 0) {
-        const int jend = min(n, j0 + nwarp);
+        const int jend = min(n, j0 + bs);
         for (int jj = j0; jj < jend; ++jj) {
           stails[jj + 1] = stails[jj] - (double)slam[jj];
           if (s_cut < 0 && stails[jj + 1] <= eps2) s_cut = jj + 1;
@@ -461,6 +483,17 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   }
 
   // ---- rank decision (Alg. 1) in FP64: the first l with tails[l] <= eps^2 ----
+  if (tid == 0 && mode == 1) {
+    // all eigenvalues are known: tails summed from the smallest eigenvalue up
+    const double eps2 = ctl->eps * ctl->eps;
+    stails[n] = 0.0;
+    for (int l = n - 1; l >= 0; --l) stails[l] = stails[l + 1] + (double)slam[l];
+    int cut = n;
+    for (int l = 0; l <= n; ++l)
+      if (stails[l] <= eps2) { cut = l; break; }
+    s_cut = cut;
+    s_cnt = n;
+  }
   if (tid == 0) {
     int m = s_cut;
     int status = 0;
@@ -495,8 +528,7 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   TE* zbase = reinterpret_cast<TE*>(eig_dyn) + (size_t)n * n * use_amat;
   TE* Z = zsm ? zbase : reinterpret_cast<TE*>(ea.Z);                       // n x m
   TE* LD = zsm ? zbase + (size_t)EIG_SMEM_VECS * n : reinterpret_cast<TE*>(ea.LD);  // L, D
-  TE tnorm = TE(0);
-  for (int i = 0; i < n; ++i) tnorm = max(tnorm, fabs(sa[i]) + (i < n - 1 ? fabs(sb[i]) : TE(0)) + (i > 0 ? fabs(sb[i - 1]) : TE(0)));
+  const TE tnorm = s_tnorm;
   const TE u = Eps<TE>::u();
   const TE pivt = max(u * tnorm, Eps<TE>::tiny());
   for (int v = tid; v < m; v += nt) {
@@ -577,19 +609,97 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     }
     __syncthreads();
   }
-  // ---- back-transform: x = H_0 H_1 ... H_{n-3} z (one warp per vector) ----
-  for (int v = wid; v < m; v += nwarp) {
-    TE* z = Z + (long long)v * n;
-    for (int c = n - 3; c >= 0; --c) {
-      const TE tau = stau[c];
-      if (tau == TE(0)) continue;
-      const TE* hv = A + (long long)c * n + c + 1;
-      const int len = n - c - 1;
-      TE s = TE(0);
-      for (int i = lane; i < len; i += 32) s += hv[i] * z[c + 1 + i];
-      s = warp_sum(s) * tau;
-      for (int i = lane; i < len; i += 32) z[c + 1 + i] -= s * hv[i];
-      __syncwarp();
+  // ---- back-transform: x = H_0 H_1 ... H_{n-3} z ----
+  // Groups of EIG_WY consecutive reflectors in compact WY form, H_a ... H_b = I - V T V^T with T
+  // upper triangular (Schreiber & Van Loan, SIAM J. Sci. Stat. Comput. 10, 1989), applied last
+  // group first: one round of dot products (V^T V and V^T Z) over all warps, T and T (V^T Z) on
+  // one warp, then Z -= V (T V^T Z) over all threads. Reflector c is column c of A below the
+  // diagonal, with its leading 1 stored at row c + 1.
+  if (m <= EIG_SMEM_VECS) {
+    __shared__ TE wy_s[EIG_WY][EIG_WY];            // v_a^T v_b, a < b
+    __shared__ TE wy_w[EIG_WY][EIG_SMEM_VECS];     // V^T Z, then T V^T Z
+    const int nref = n - 2;
+    for (int g0 = nref > 0 ? ((nref - 1) / EIG_WY) * EIG_WY : -1; g0 >= 0; g0 -= EIG_WY) {
+      const int gl = min(EIG_WY, nref - g0);
+      const int npair = gl * (gl - 1) / 2;
+      for (int t = wid; t < npair + gl * m; t += nwarp) {
+        TE s = TE(0);
+        if (t < npair) {
+          int b = 1;
+          while (b * (b + 1) / 2 <= t) ++b;
+          const int a = t - b * (b - 1) / 2;
+          const TE* va = A + (long long)(g0 + a) * n;
+          const TE* vb = A + (long long)(g0 + b) * n;
+          for (int i = g0 + b + 1 + lane; i < n; i += 32) s += va[i] * vb[i];
+          s = warp_sum(s);
+          if (lane == 0) wy_s[a][b] = s;
+        } else {
+          const int a = (t - npair) % gl, v = (t - npair) / gl;
+          const TE* va = A + (long long)(g0 + a) * n;
+          const TE* z = Z + (long long)v * n;
+          for (int i = g0 + a + 1 + lane; i < n; i += 32) s += va[i] * z[i];
+          s = warp_sum(s);
+          if (lane == 0) wy_w[a][v] = s;
+        }
+      }
+      __syncthreads();
+      if (wid == 0) {
+        // lane i holds row i of T in registers: column j is T(i, j) = -tau_j sum_{i<=k<j}
+        // T(i, k) v_k^T v_j for i < j, tau_j on the diagonal
+        TE trow[EIG_WY];
+#pragma unroll
+        for (int j = 0; j < EIG_WY; ++j) {
+          TE acc = TE(0);
+#pragma unroll
+          for (int k = 0; k < EIG_WY; ++k)
+            if (k < j && k >= lane) acc += trow[k] * wy_s[k][j];
+          const TE tj = (j < gl) ? stau[g0 + j] : TE(0);
+          trow[j] = (lane < j) ? -tj * acc : (lane == j ? tj : TE(0));
+        }
+        // (T V^T Z)(i, v) for the lane's row i, every vector
+        TE outv[EIG_SMEM_VECS];
+#pragma unroll
+        for (int v = 0; v < EIG_SMEM_VECS; ++v) {
+          TE acc = TE(0);
+          if (v < m) {
+#pragma unroll
+            for (int k = 0; k < EIG_WY; ++k)
+              if (k < gl) acc += trow[k] * wy_w[k][v];
+          }
+          outv[v] = acc;
+        }
+        __syncwarp();
+        if (lane < gl) {
+#pragma unroll
+          for (int v = 0; v < EIG_SMEM_VECS; ++v)
+            if (v < m) wy_w[lane][v] = outv[v];
+        }
+      }
+      __syncthreads();
+      for (long long L = tid; L < (long long)m * n; L += nt) {
+        const int v = (int)(L / n), i = (int)(L % n);
+        if (i <= g0) continue;
+        TE acc = TE(0);
+        for (int a = 0; a < gl && g0 + a + 1 <= i; ++a) acc += A[(long long)(g0 + a) * n + i] * wy_w[a][v];
+        Z[(long long)v * n + i] -= acc;
+      }
+      __syncthreads();
+    }
+  } else {
+    // one warp per vector, reflectors applied one at a time
+    for (int v = wid; v < m; v += nwarp) {
+      TE* z = Z + (long long)v * n;
+      for (int c = n - 3; c >= 0; --c) {
+        const TE tau = stau[c];
+        if (tau == TE(0)) continue;
+        const TE* hv = A + (long long)c * n + c + 1;
+        const int len = n - c - 1;
+        TE s = TE(0);
+        for (int i = lane; i < len; i += 32) s += hv[i] * z[c + 1 + i];
+        s = warp_sum(s) * tau;
+        for (int i = lane; i < len; i += 32) z[c + 1 + i] -= s * hv[i];
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
