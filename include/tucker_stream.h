@@ -212,6 +212,16 @@ tucker_status tucker_profile_enable(tucker_state* s, int32_t on);
 /* Accumulated profile since tucker_profile_enable. Synchronizes. */
 tucker_status tucker_profile_read(tucker_state* s, tucker_profile* out_host);
 
+/* Execution form of tucker_stream_update. Without phase profiling, the first update of a state
+ * captures the update as a CUDA graph: every data-dependent branch stays on the device, each
+ * spatial mode's growth chain (residual Gram, eigensolve, augmentation, re-projection) becomes a
+ * conditional IF node whose condition the device sets from ||E_k|| > eps, and each later call
+ * writes the slice address (and its TMA descriptor) into the state with one small host-to-device
+ * copy and launches the graph. With profiling on, updates are issued as individual launches.
+ * Returns the kernel nodes of the captured update graph (conditional bodies included: an upper
+ * bound of the kernels one update runs), 0 before the first capture, -1 for NULL. */
+int64_t tucker_graph_kernels(const tucker_state* s);
+
 /* Message for the last error on this state (static storage owned by the state; never NULL). */
 const char* tucker_last_error(const tucker_state* s);
 

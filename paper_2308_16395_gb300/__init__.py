@@ -27,7 +27,8 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_version", "tucker_profile_enable", "tucker_profile_read",
            "tucker_reconstruct_noalloc", "tucker_ttm_workspace_bytes", "tucker_ttm_project",
            "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint", "tucker_ttm_reconstruct_adjoint",
-           "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy"]
+           "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy",
+           "tucker_graph_kernels"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -101,6 +102,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_batch_create.restype = ctypes.c_int
     lib.tucker_batch_update.argtypes = [vp, vp]
     lib.tucker_batch_update.restype = ctypes.c_int
+    lib.tucker_graph_kernels.argtypes = [vp]
+    lib.tucker_graph_kernels.restype = i64
     lib.tucker_batch_kernels.argtypes = [vp]
     lib.tucker_batch_kernels.restype = i64
     lib.tucker_batch_destroy.argtypes = [vp]
@@ -343,6 +346,10 @@ def tucker_ttm_reconstruct_adjoint(desc, U_ptrs, G_ptr, Yhbar_ptr, Gbar_ptr, Uba
         ctypes.byref(desc), _ptrs(U_ptrs), ctypes.c_void_p(G_ptr), ctypes.c_void_p(Yhbar_ptr),
         ctypes.c_void_p(Gbar_ptr), _ptrs(Ubar_ptrs), ctypes.c_void_p(work_ptr), int(work_bytes),
         ctypes.c_void_p(stream)))
+
+
+def tucker_graph_kernels(h: int) -> int:
+    return int(load_library().tucker_graph_kernels(h))
 
 
 def tucker_last_error(h: int) -> str:

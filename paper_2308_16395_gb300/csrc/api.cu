@@ -5,6 +5,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stddef.h>
+
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -96,6 +98,20 @@ struct tucker_state {
   cudaStream_t last_stream = nullptr;
   int latched = 0;
   char err[512] = "ok";
+  // graph form of the update (device-side branches as conditional nodes)
+  bool gform = false;                 // capturing: open an IF node around each growth chain
+  bool body_open = false;
+  cudaStream_t body_st = nullptr;     // captures the IF bodies
+  cudaStream_t cap_st = nullptr;      // captures the single-state update graph
+  cudaGraph_t ugraph = nullptr;
+  cudaGraphExec_t uexec = nullptr;
+  bool graph_failed = false;          // capture or instantiation failed once: stay eager
+  long long graph_kernels = 0;        // kernel nodes of the update graph (bodies included)
+  std::vector<cudaGraph_t> bodies;    // IF bodies created by the last capture
+  struct {
+    unsigned char map[128];
+    const void* y;
+  } yslot_host{};
 };
 
 namespace {
@@ -498,6 +514,63 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
 }
 
 // ---------------------------------------------------------------------------------------------
+// graph form: an IF node (condition set on the device) around a chain of launches
+// ---------------------------------------------------------------------------------------------
+cudaError_t cond_handle(cudaStream_t st, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  // the condition is 0 at every launch unless a kernel sets it
+  return cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault);
+}
+
+// Appends the IF node to the capture of st and starts capturing its body on body_st (the body
+// graph is appended to `bodies`).
+cudaError_t cond_begin(cudaStream_t st, cudaStream_t body_st, cudaGraphConditionalHandle h,
+                       std::vector<cudaGraph_t>* bodies) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  if (bodies) bodies->push_back(p.conditional.phGraph_out[0]);
+  return cudaStreamBeginCaptureToGraph(body_st, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal);
+}
+
+cudaError_t cond_end(cudaStream_t body_st) {
+  cudaGraph_t g = nullptr;
+  return cudaStreamEndCapture(body_st, &g);
+}
+
+// Kernel nodes directly in g (the bodies of its conditional nodes are separate graphs).
+long long count_kernel_nodes(cudaGraph_t g) {
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) return 0;
+  long long c = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++c;
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------------------------
 // streaming update (Alg. 5): fixed launch sequence, device-side branches
 // ---------------------------------------------------------------------------------------------
 template <typename TX, typename TW, typename TE>
@@ -525,11 +598,20 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       else
         CK((launch_proj<TW, TW>(s->ctl, k, 1, 0, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], s->part_e2,
                                 nullptr, kGridP, st)));
-      CK(launch_decide(s->ctl, k, s->part_e2, s->part_y2, kGridP, st));
+      cudaGraphConditionalHandle hc = 0;
+      if (s->gform) CK(cond_handle(st, &hc));
+      CK(launch_decide(s->ctl, k, s->part_e2, s->part_y2, kGridP, hc, st));
+      if (s->gform) {
+        // graph form: the growth chain below is the body of an IF node on grew[k]
+        CK(cond_begin(st, s->body_st, hc, &s->bodies));
+        s->body_open = true;
+      }
     }
     {
       // ||E_k|| > eps: residual Gram, eig + rank cut (Alg. 1), augmentation, then
       // pass C: D*_k = D*_{k-1} x_k U~_k^T (= Concatenate(P_k, L_k), App. C)
+      const cudaStream_t main_st = st;
+      cudaStream_t st = s->gform ? s->body_st : main_st;
       PhaseMark pm(s, st, TK_PH_GROW);
       if ((s->etmask >> k) & 1) {
         // residual E^T of mode k, then its Gram on the tensor cores (only if mode k grew)
@@ -560,7 +642,11 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       else
         CK((launch_proj<TW, TW>(s->ctl, k, 2, 1, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], nullptr,
                                 nullptr, kGridP, st)));
-      CK(launch_mode_end(s->ctl, k, st));
+      if (s->gform) {
+        CK(cond_end(s->body_st));
+        s->body_open = false;
+      }
+      CK(launch_mode_end(s->ctl, k, main_st));
     }
     launches += 8;
   }
@@ -749,6 +835,50 @@ tucker_status update_dispatch(tucker_state* s, const void* Y, cudaStream_t st) {
   return f32 ? do_update<float, double, double>(s, Y, st) : do_update<double, double, double>(s, Y, st);
 }
 
+tucker_status ensure_streams(tucker_state* s) {
+  if (!s->cap_st) CK(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
+  if (!s->body_st) CK(cudaStreamCreateWithFlags(&s->body_st, cudaStreamNonBlocking));
+  return TUCKER_OK;
+}
+
+// One update of s, slice read from the control block's slot, captured as a CUDA graph whose
+// growth chains are IF nodes on grew[k] (set by k_decide).
+tucker_status capture_update(tucker_state* s) {
+  tucker_status rc = ensure_streams(s);
+  if (rc != TUCKER_OK) return rc;
+  s->bodies.clear();
+  CK(cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
+  const bool prof = s->prof;
+  s->prof = false;
+  s->gform = true;
+  rc = update_dispatch(s, nullptr, s->cap_st);
+  s->gform = false;
+  s->prof = prof;
+  if (s->body_open) {
+    cudaGraph_t gb = nullptr;
+    cudaStreamEndCapture(s->body_st, &gb);
+    s->body_open = false;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s->cap_st, &g);
+  if (rc != TUCKER_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != TUCKER_OK ? rc : TUCKER_ECUDA;
+  }
+  if (cudaGraphInstantiate(&s->uexec, g, 0) != cudaSuccess) {
+    s->uexec = nullptr;
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return TUCKER_ECUDA;
+  }
+  s->ugraph = g;
+  s->graph_kernels = count_kernel_nodes(g);
+  for (cudaGraph_t b : s->bodies) s->graph_kernels += count_kernel_nodes(b);
+  s->bodies.clear();
+  return TUCKER_OK;
+}
+
 // Capture: origin stream -> fork event -> one branch stream per state (its whole update) ->
 // join events -> origin. Streams and events exist only during the capture.
 tucker_status capture_batch(tucker_batch* b, const void* const* Y, cudaStream_t* streams,
@@ -762,9 +892,19 @@ tucker_status capture_batch(tucker_batch* b, const void* const* Y, cudaStream_t*
     tucker_state* s = b->states[i];
     if (cudaStreamWaitEvent(streams[i], evs[count], 0) != cudaSuccess) { rc = TUCKER_ECUDA; break; }
     const bool prof = s->prof;
+    rc = ensure_streams(s);
+    if (rc != TUCKER_OK) break;
     s->prof = false;
+    s->gform = true;
+    s->bodies.clear();
     rc = update_dispatch(s, Y[i], streams[i]);
+    s->gform = false;
     s->prof = prof;
+    if (s->body_open) {
+      cudaGraph_t gb = nullptr;
+      cudaStreamEndCapture(s->body_st, &gb);
+      s->body_open = false;
+    }
     if (rc != TUCKER_OK) {
       snprintf(b->err, sizeof(b->err), "state %d: %s", i, s->err);
       break;
@@ -781,15 +921,10 @@ tucker_status capture_batch(tucker_batch* b, const void* const* Y, cudaStream_t*
   }
   b->graph = g;
   if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) return TUCKER_ECUDA;
-  size_t nn = 0;
-  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) {
-    std::vector<cudaGraphNode_t> nodes(nn);
-    if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess) {
-      for (cudaGraphNode_t nd : nodes) {
-        cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) b->launches++;
-      }
-    }
+  b->launches = count_kernel_nodes(g);
+  for (tucker_state* s : b->states) {
+    for (cudaGraph_t bg : s->bodies) b->launches += count_kernel_nodes(bg);
+    s->bodies.clear();
   }
   return TUCKER_OK;
 }
@@ -804,6 +939,8 @@ extern "C" {
 const char* tucker_version(void) { return kVersion; }
 
 const char* tucker_last_error(const tucker_state* s) { return s ? s->err : "null state"; }
+
+int64_t tucker_graph_kernels(const tucker_state* s) { return s ? s->graph_kernels : -1; }
 
 tucker_status tucker_init_sthosvd(const tucker_config* cfg, const void* X_dev, int64_t n_init,
                                   void* stream, tucker_state** out) {
@@ -847,10 +984,29 @@ tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* str
   if (!usable(s)) return TUCKER_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
-  const bool mixed = s->cfg.precision == TUCKER_PREC_MIXED;
-  const bool f32 = s->cfg.dtype == TUCKER_F32;
-  if (mixed) return f32 ? do_update<float, float, float>(s, Y_dev, st) : do_update<double, float, float>(s, Y_dev, st);
-  return f32 ? do_update<float, double, double>(s, Y_dev, st) : do_update<double, double, double>(s, Y_dev, st);
+  // Graph form (unless phase profiling is on): the update is captured once; each call writes
+  // the slice's address (and its TMA descriptor) into the control block and launches the graph.
+  if (!s->prof && !s->graph_failed) {
+    if (!s->uexec && capture_update(s) != TUCKER_OK) s->graph_failed = true;
+    if (s->uexec) {
+      memset(&s->yslot_host, 0, sizeof(s->yslot_host));
+      if ((s->tcmask & 1) && s->tx == 4) {
+        CUtensorMap m;
+        if (!make_map_2d_f32(&m, Y_dev, s->N / s->n[0], s->n[0], s->n[0], 32, 128)) {
+          set_err(s, "slice address unusable for TMA (16-byte alignment)%s%lld", "", 0);
+          return TUCKER_EINVAL;
+        }
+        memcpy(s->yslot_host.map, &m, sizeof(m));
+      }
+      s->yslot_host.y = Y_dev;
+      static_assert(offsetof(Ctl, yptr) == offsetof(Ctl, ymap) + 128, "slot layout");
+      CK(cudaMemcpyAsync(reinterpret_cast<unsigned char*>(s->ctl) + offsetof(Ctl, ymap), &s->yslot_host,
+                         128 + sizeof(const void*), cudaMemcpyHostToDevice, st));
+      CK(cudaGraphLaunch(s->uexec, st));
+      return TUCKER_OK;
+    }
+  }
+  return update_dispatch(s, Y_dev, st);
 }
 
 tucker_status tucker_reconstruct(tucker_state* s, int64_t t_begin, int64_t t_end, void* out_dev,
@@ -1059,6 +1215,10 @@ tucker_status tucker_profile_read(tucker_state* s, tucker_profile* out) {
 void tucker_destroy(tucker_state* s) {
   if (!s) return;
   cudaStreamSynchronize(s->last_stream);
+  if (s->uexec) cudaGraphExecDestroy(s->uexec);
+  if (s->ugraph) cudaGraphDestroy(s->ugraph);
+  if (s->cap_st) cudaStreamDestroy(s->cap_st);
+  if (s->body_st) cudaStreamDestroy(s->body_st);
   free_all(s);
   delete s;
 }

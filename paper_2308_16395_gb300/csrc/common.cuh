@@ -62,6 +62,11 @@ struct Ctl {
   double acc_bytes[8];
   // ---- completion tickets of the cross-block reductions (zero between launches) ----
   unsigned ticket[4];
+  // ---- slice of the current update when the update runs as a CUDA graph (written by one
+  // host-to-device copy before each launch): TMA descriptor of the slice as a row-major
+  // (N / n_1) x n_1 FP32 matrix (only with the tensor-core mode-1 pass) and its address ----
+  alignas(128) unsigned char ymap[128];
+  const void* yptr;
 };
 
 // Phases of one update (profiling and byte accounting).

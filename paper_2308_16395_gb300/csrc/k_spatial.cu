@@ -62,7 +62,9 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
   const long long F = A * B;
   const long long pstr = out_stride(ctl, A, F);
   const int xb = ctl->xbuf;
-  const TX* X = (xb < 0) ? Xext : reinterpret_cast<const TX*>(dbufs[xb]);
+  // the slice: the launch argument, or the graph update's slot in the control block
+  const TX* X = (xb < 0) ? (Xext ? Xext : reinterpret_cast<const TX*>(ctl->yptr))
+                         : reinterpret_cast<const TX*>(dbufs[xb]);
   TW* P = dbufs[(xb + out_off + 3) % 3];
 
   TW* Xs = reinterpret_cast<TW*>(smem_raw);                 // JC * FT
@@ -177,8 +179,13 @@ __global__ void __launch_bounds__(NT) k_ttm_proj(const Ctl* __restrict__ ctl, in
 
 // Reduce the per-block partials of mode k and take Alg. 4's branch: grew = ||E_k|| > eps.
 // For k = 0 also ||Y||^2 and eps = tau ||Y|| / sqrt(d) (Alg. 5, first step).
-__global__ void k_decide(Ctl* ctl, int k, const double* part_e2, const double* part_y2, int nparts) {
-  if (ctl->status) return;
+// hcond (graph form): the conditional handle of mode k's growth body, set to grew[k].
+__global__ void k_decide(Ctl* ctl, int k, const double* part_e2, const double* part_y2, int nparts,
+                         cudaGraphConditionalHandle hcond) {
+  if (ctl->status) {
+    if (hcond && threadIdx.x == 0) cudaGraphSetConditional(hcond, 0u);
+    return;
+  }
   __shared__ double red[32];
   double se = 0.0, sy = 0.0;
   // fixed-order reduction (deterministic)
@@ -199,6 +206,7 @@ __global__ void k_decide(Ctl* ctl, int k, const double* part_e2, const double* p
     ctl->grew[k] = g;
     ctl->radd[k] = 0;
     ctl->disc[k] = g ? 0.0 : se;
+    if (hcond) cudaGraphSetConditional(hcond, g ? 1u : 0u);
   }
 }
 
@@ -238,7 +246,9 @@ __global__ void __launch_bounds__(NT) k_resid_gram(const Ctl* __restrict__ ctl, 
   const long long F = A * B;
   const long long pstr = out_stride(ctl, A, F);
   const int xb = ctl->xbuf;
-  const TX* X = (xb < 0) ? Xext : reinterpret_cast<const TX*>(dbufs[xb]);
+  // the slice: the launch argument, or the graph update's slot in the control block
+  const TX* X = (xb < 0) ? (Xext ? Xext : reinterpret_cast<const TX*>(ctl->yptr))
+                         : reinterpret_cast<const TX*>(dbufs[xb]);
   const TW* P = data_only ? nullptr : dbufs[(xb + 1 + 3) % 3];
 
   const int T = (n + GT - 1) / GT;
@@ -444,8 +454,8 @@ cudaError_t launch_resid_gram(const Ctl* ctl, int k, int n, const void* Xext, vo
 }
 
 cudaError_t launch_decide(Ctl* ctl, int k, const double* pe, const double* py, int nparts,
-                          cudaStream_t st) {
-  k_decide<<<1, 256, 0, st>>>(ctl, k, pe, py, nparts);
+                          cudaGraphConditionalHandle hcond, cudaStream_t st) {
+  k_decide<<<1, 256, 0, st>>>(ctl, k, pe, py, nparts, hcond);
   return cudaGetLastError();
 }
 

@@ -367,6 +367,7 @@ static_assert(TP_EPI_W0 % 4 == 0, "epilogue warps must start at a TMEM lane quar
 constexpr size_t TP_SMEM = (size_t)TP_S * TP_STAGE + 128 * 1024 + 1024 + 256;
 
 struct TcProjArgs {
+  const CUtensorMap* mYg;   // slice descriptor in the control block (graph form), else NULL
   float* const* dbufs;
   int out_off;
   double* part_e2;
@@ -402,8 +403,8 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
   const int Kc2 = (Rp + TC_KC - 1) / TC_KC;
   const long long ntiles = (F + TC_M - 1) / TC_M;
   const int xb = ctl->xbuf;
-  const CUtensorMap* mX = xb < 0 ? &mY : (xb == 0 ? &mD0 : (xb == 1 ? &mD1 : &mD2));
-  const float* Xg = xb < 0 ? a.Y : a.dbufs[xb];
+  const CUtensorMap* mX = xb < 0 ? (a.mYg ? a.mYg : &mY) : (xb == 0 ? &mD0 : (xb == 1 ? &mD1 : &mD2));
+  const float* Xg = xb < 0 ? (a.Y ? a.Y : reinterpret_cast<const float*>(ctl->yptr)) : a.dbufs[xb];
   float* P = a.dbufs[(xb + a.out_off + 3) % 3];
 
   extern __shared__ __align__(1024) unsigned char psm_raw[];
@@ -462,6 +463,7 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
+      if (xb < 0 && a.mYg) tensormap_acquire(a.mYg);   // written by a copy before the launch
       tma_prefetch(mX);
       tma_prefetch(&mUhi);
       tma_prefetch(&mUlo);
@@ -593,6 +595,7 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
     const bool ysm = RESID && (size_t)2 * Kc2 * n1p * TC_KC * 4 + 2 * TC_M * TC_KC * 4 <= 128 * 1024;
     float* ybuf = B2lo + (size_t)Kc2 * n1p * TC_KC;   // [2][TC_M][TC_KC], 1024-byte aligned
     const bool yleader = (wq == 0 && lane == 0);
+    if (ysm && yleader && xb < 0 && a.mYg) tensormap_acquire(a.mYg);
     long long yq = 0;                                 // Y chunks consumed so far
     // chunk seq goes to buffer seq & 1 once the 4 warps have consumed chunk seq - 2 (bounded
     // wait of the issuing thread); returns false if that wait gave up
@@ -746,12 +749,15 @@ cudaError_t launch_tc_proj(const Ctl* ctl, int k, int mode, int pred, const floa
                            int out_off, double* part_e2, double* part_y2, int nparts, float* Et,
                            long long et_stride, int grid, cudaStream_t st) {
   CUtensorMap mY;
-  if (k == 0) {
+  const CUtensorMap* mYg = nullptr;
+  if (k == 0 && Y) {
     if (!make_map_2d_f32(&mY, Y, F0, n0, n0, 32, 128)) return cudaErrorInvalidValue;
   } else {
     mY = m.d[0];   // unused for k >= 1 (the input is a D buffer)
+    // graph form (Y == NULL): the slice descriptor is read from the control block
+    if (k == 0) mYg = reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const unsigned char*>(ctl) + offsetof(Ctl, ymap));
   }
-  TcProjArgs a{(float* const*)dbufs, out_off, part_e2, part_y2, nparts, Y, Et, et_stride, k};
+  TcProjArgs a{mYg, (float* const*)dbufs, out_off, part_e2, part_y2, nparts, Y, Et, et_stride, k};
   static bool attr[3] = {false, false, false};
   if (mode == 0) {
     if (!attr[0]) { cudaFuncSetAttribute(k_tc_proj<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[0] = true; }

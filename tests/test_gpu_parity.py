@@ -259,3 +259,26 @@ def test_eigensolver_at_the_shared_memory_limit(pkg, precision, dtype):
     assert st.ranks[0] == 4
     _compare_final(pkg, st, ts, Xs, precision)
     ts.close()
+
+
+def test_graph_form_equals_launch_sequence(pkg):
+    """The captured-graph update (conditional growth bodies) and the launch-by-launch update
+    (phase profiling on) give the same state on a stream whose spatial ranks grow."""
+    import torch
+
+    X = _growth_stream(n=(40, 28, 12))
+    Xg = to_device(X.astype(np.float32).astype(np.float64), torch.float32)
+    a = pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="mixed", steps_cap=24)
+    b = pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="mixed", steps_cap=24)
+    pkg.tucker_profile_enable(b.h, 1)
+    for t in range(6, X.shape[-1]):
+        a.update(Xg[t].contiguous())
+        b.update(Xg[t].contiguous())
+        assert a.ranks == b.ranks, t
+    assert pkg.tucker_graph_kernels(a.h) > 0 and pkg.tucker_graph_kernels(b.h) == 0
+    assert a.ranks[:3] == (5, 5, 5)
+    Ra, Rb = a.reconstruct(0, a.n_d).double(), b.reconstruct(0, b.n_d).double()
+    assert float(torch.linalg.norm(Ra - Rb) / torch.linalg.norm(Rb)) <= 1e-12
+    assert a.error_norm() == b.error_norm()
+    a.close()
+    b.close()
