@@ -174,6 +174,14 @@ tucker_status tucker_reconstruct_noalloc(tucker_state* s, int64_t t_begin, int64
  * bound of ||X - X^||_F; *data_norm_host = ||X||_F over every slice seen. Synchronizes. */
 tucker_status tucker_error_norm(tucker_state* s, double* err_bound_host, double* data_norm_host);
 
+/* Asynchronous form of tucker_error_norm for pipelined callers: enqueues on `stream` a copy of
+ * the squared running error bound and the squared data norm, as they stand after the work
+ * enqueued so far, into out2_host[0] and out2_host[1] (host memory, preferably pinned). No
+ * synchronization: the values are valid once `stream` has reached this point. A latched device
+ * error is not reported here (the next synchronizing call reports it). Errors: EINVAL, ESTATE,
+ * ECUDA. */
+tucker_status tucker_error_norm_async(tucker_state* s, double* out2_host, void* stream);
+
 /* Current ranks r_1..r_d (d entries) and n_d. Synchronizes. */
 tucker_status tucker_get_ranks(tucker_state* s, int64_t* ranks_host, int64_t* n_d_host);
 

@@ -28,7 +28,7 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_reconstruct_noalloc", "tucker_ttm_workspace_bytes", "tucker_ttm_project",
            "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint", "tucker_ttm_reconstruct_adjoint",
            "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy",
-           "tucker_graph_kernels"]
+           "tucker_graph_kernels", "tucker_error_norm_async"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -102,6 +102,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_batch_create.restype = ctypes.c_int
     lib.tucker_batch_update.argtypes = [vp, vp]
     lib.tucker_batch_update.restype = ctypes.c_int
+    lib.tucker_error_norm_async.argtypes = [vp, vp, vp]
+    lib.tucker_error_norm_async.restype = ctypes.c_int
     lib.tucker_graph_kernels.argtypes = [vp]
     lib.tucker_graph_kernels.restype = i64
     lib.tucker_batch_kernels.argtypes = [vp]
@@ -183,6 +185,11 @@ def tucker_error_norm(h: int) -> tuple[float, float]:
     e, n = ctypes.c_double(), ctypes.c_double()
     _check(load_library().tucker_error_norm(h, ctypes.byref(e), ctypes.byref(n)), h)
     return e.value, n.value
+
+
+def tucker_error_norm_async(h: int, out_ptr: int, stream: int = 0) -> None:
+    """Enqueue a copy of (err^2, ||X||^2) into host memory at out_ptr (2 doubles); no sync."""
+    _check(load_library().tucker_error_norm_async(h, ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)), h)
 
 
 def tucker_get_ranks(h: int, d: int) -> tuple[tuple, int]:

@@ -108,10 +108,6 @@ struct tucker_state {
   bool graph_failed = false;          // capture or instantiation failed once: stay eager
   long long graph_kernels = 0;        // kernel nodes of the update graph (bodies included)
   std::vector<cudaGraph_t> bodies;    // IF bodies created by the last capture
-  struct {
-    unsigned char map[128];
-    const void* y;
-  } yslot_host{};
 };
 
 namespace {
@@ -985,23 +981,23 @@ tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* str
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
   // Graph form (unless phase profiling is on): the update is captured once; each call writes
-  // the slice's address (and its TMA descriptor) into the control block and launches the graph.
+  // the slice's address (and its TMA descriptor) into the control block with a one-block kernel
+  // and launches the graph.
   if (!s->prof && !s->graph_failed) {
     if (!s->uexec && capture_update(s) != TUCKER_OK) s->graph_failed = true;
     if (s->uexec) {
-      memset(&s->yslot_host, 0, sizeof(s->yslot_host));
+      SlotArgs sa{};
       if ((s->tcmask & 1) && s->tx == 4) {
         CUtensorMap m;
         if (!make_map_2d_f32(&m, Y_dev, s->N / s->n[0], s->n[0], s->n[0], 32, 128)) {
           set_err(s, "slice address unusable for TMA (16-byte alignment)%s%lld", "", 0);
           return TUCKER_EINVAL;
         }
-        memcpy(s->yslot_host.map, &m, sizeof(m));
+        static_assert(sizeof(m) == sizeof(sa.map), "descriptor size");
+        memcpy(sa.map, &m, sizeof(m));
       }
-      s->yslot_host.y = Y_dev;
-      static_assert(offsetof(Ctl, yptr) == offsetof(Ctl, ymap) + 128, "slot layout");
-      CK(cudaMemcpyAsync(reinterpret_cast<unsigned char*>(s->ctl) + offsetof(Ctl, ymap), &s->yslot_host,
-                         128 + sizeof(const void*), cudaMemcpyHostToDevice, st));
+      sa.y = Y_dev;
+      CK(launch_set_slot(s->ctl, sa, st));
       CK(cudaGraphLaunch(s->uexec, st));
       return TUCKER_OK;
     }
@@ -1045,6 +1041,15 @@ tucker_status tucker_error_norm(tucker_state* s, double* err_bound, double* data
   if (rc != TUCKER_OK) return rc;
   *err_bound = std::sqrt(std::max(s->hctl->err2, 0.0));
   *data_norm = std::sqrt(std::max(s->hctl->data2, 0.0));
+  return TUCKER_OK;
+}
+
+tucker_status tucker_error_norm_async(tucker_state* s, double* out2, void* stream) {
+  if (!s || !out2) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  static_assert(offsetof(Ctl, data2) == offsetof(Ctl, err2) + sizeof(double), "err2, data2 adjacent");
+  CK(cudaMemcpyAsync(out2, reinterpret_cast<unsigned char*>(s->ctl) + offsetof(Ctl, err2),
+                     2 * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   return TUCKER_OK;
 }
 

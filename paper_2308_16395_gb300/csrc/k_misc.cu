@@ -103,6 +103,22 @@ cudaError_t launch_ud_to_colmajor(const double* Ud, int nd, int rd, int ldc, dou
   return launch_state_to_colmajor<double>(Ud, nd, rd, ldc, dst, st);
 }
 
+// Graph form of the update: the slice's TMA descriptor and address, passed as kernel parameters,
+// written into the control block's slot (a kernel rather than a host-to-device copy, so that the
+// write never queues behind a large slice transfer on a copy engine).
+__global__ void k_set_slot(Ctl* ctl, const __grid_constant__ SlotArgs a) {
+  const int t = threadIdx.x;
+  if (t < 32) reinterpret_cast<unsigned*>(ctl->ymap)[t] = a.map[t];
+  if (t == 32) ctl->yptr = a.y;
+  // the descriptor is read by the tensor-map proxy of later kernels (which acquire it)
+  asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+}
+
+cudaError_t launch_set_slot(Ctl* ctl, const SlotArgs& a, cudaStream_t st) {
+  k_set_slot<<<1, 64, 0, st>>>(ctl, a);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_init_finish<float>(Ctl*, const void*, long long, int, const double*,
                                                const double*, int, void*, void*, double*, double*,
                                                int, cudaStream_t);

@@ -103,6 +103,11 @@ cudaError_t launch_tc_gram(const Ctl* ctl, int k, const TcProjMaps& m, int n1, d
                            double* G, int nsm, cudaStream_t st);
 
 // ---- k_misc.cu ----
+struct SlotArgs {
+  unsigned map[32];        // TMA descriptor of the slice (128 bytes)
+  const void* y;           // slice address
+};
+cudaError_t launch_set_slot(Ctl* ctl, const SlotArgs& a, cudaStream_t st);
 template <typename TW>
 cudaError_t launch_init_finish(Ctl* ctl, const void* Ccol, long long R, int rd, const double* lam,
                                const double* Utmp, int nt, void* C, void* V, double* Ud, double* S,

@@ -282,3 +282,62 @@ def test_graph_form_equals_launch_sequence(pkg):
     assert a.error_norm() == b.error_norm()
     a.close()
     b.close()
+
+
+@pytest.mark.slow
+def test_full_size_blob_stream_as_benchmarked(pkg):
+    """The benchmark's workload at full size and in its launch configuration: advected blobs
+    192 x 192 x 96 x 12 FP32 (170 MB slices), tau = 1e-4, n_init = 10, mixed form, the graph form
+    of the update, the bench's capacities. Ranks are compared every step (flips allowed only at
+    decisions within DELTA_DEC of eps^2); the reconstructions of sampled slices (first initial
+    slice, last update) against the FP64 oracle within 1e-5 relative; the running error bound
+    stays within tau."""
+    import torch
+
+    bf = BlobField(grid=(192, 192, 96), nvar=12, nblobs=40, noise=1e-5, seed=2)
+    T = 14
+    dev = torch.device("cuda")
+    gs = [bf.slice_torch(t, dev) for t in range(T)]                      # (12, 96, 192, 192)
+    xs = [g.cpu().numpy().T.astype(np.float64) for g in gs]              # paper order, FP64
+    st = O.init_stream(np.asfortranarray(np.stack(xs[:10], axis=-1)), 1e-4)
+    ts = pkg.TuckerStream(torch.stack(gs[:10]).contiguous(), 1e-4, precision="mixed",
+                          rank_cap=[0, 0, 0, 0, 24], steps_cap=T + 4, core_cap=4 << 20)
+    assert ts.ranks == st.ranks
+    ok = True
+    for t in range(10, T):
+        O.stream_update(st, xs[t])
+        ts.update(gs[t])
+        if ts.ranks != st.ranks:
+            assert decision_margins(st.log[-1]) < DELTA_DEC, (t, ts.ranks, st.ranks)
+            ok = False
+            break
+    assert pkg.tucker_graph_kernels(ts.h) > 0
+    if ok:
+        for t in (0, T - 1):
+            g = pkg.paper_order(ts.reconstruct(t, t + 1)[0]).cpu().numpy().astype(np.float64)
+            o = O.reconstruct_slices(st, t, t + 1)[..., 0]
+            rel = np.linalg.norm(g - o) / np.linalg.norm(o)
+            assert rel < 1e-5, (t, rel)
+    eb, dn = ts.error_norm()
+    assert eb <= 1e-4 * dn * (1 + 1e-6)
+    ts.close()
+
+
+def test_async_error_norm_read(pkg):
+    """tucker_error_norm_async copies (err^2, ||X||^2) into pinned host memory in stream order."""
+    import torch
+
+    s = LowRankStream((16, 12, 10), (3, 3, 2, 4), 12, 1e-4, seed=5)
+    Xg = to_device(s.tensor(0, 12), torch.float64)
+    ts = pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="fp64", steps_cap=16)
+    out = torch.zeros((6, 2), dtype=torch.float64).pin_memory()
+    st = torch.cuda.current_stream()
+    for i, t in enumerate(range(6, 12)):
+        ts.update(Xg[t].contiguous())
+        pkg.tucker_error_norm_async(ts.h, out[i].data_ptr(), st.cuda_stream)
+    torch.cuda.synchronize()
+    eb, dn = ts.error_norm()
+    assert abs(float(out[5, 0]) - eb * eb) <= 1e-14 * max(eb * eb, 1e-300)
+    assert abs(float(out[5, 1]) - dn * dn) <= 1e-14 * dn * dn
+    assert all(float(out[i + 1, 1]) > float(out[i, 1]) for i in range(5))   # data norm grows
+    ts.close()
