@@ -486,8 +486,11 @@ def run_batched(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
+    from paper_2308_16395_gb300.autotune import CANDIDATES, tune_batch
+
     K, W = args.steps, max(args.warmup, 3)
-    T = N_INIT + W + K
+    W_TUNE = 2 * len(CANDIDATES)          # launch-shape tuning steps (untimed, before warm-up)
+    T = N_INIT + W_TUNE + W + K
     all_specs = batched_streams(nstreams=64, steps=100)
     # independent streams: each rank updates its own balanced share (no data-path collective)
     mine = assign_streams([stream_cost(s.spatial) for s, _ in all_specs], ws)[rank]
@@ -517,9 +520,18 @@ def run_batched(args):
         states.append(pkg.TuckerStream(X0, tau, precision="mixed", steps_cap=T + 4,
                                        rank_cap=[0, 0, 0, (T + 4 + 7) // 8 * 8]))
         del X0
+    # per-stream launch shapes: the share multiplier is tuned on the streams' next time steps
+    tstep = [N_INIT]
+
+    def feed(b):
+        for gi, slot in enumerate(b.slots):
+            make_slice(gi, tstep[0], slot)
+        tstep[0] += 1
+
+    best_c, tune_ms = tune_batch(states, feed)
     batch = pkg.TuckerBatch(states)
     stream = torch.cuda.current_stream()
-    for t in range(N_INIT, N_INIT + W):
+    for t in range(N_INIT + W_TUNE, N_INIT + W_TUNE + W):
         for gi, slot in enumerate(batch.slots):
             make_slice(gi, t, slot)
         batch.update()
@@ -528,7 +540,7 @@ def run_batched(args):
     clocks = ClockSampler(local)
     clocks.start()
     ms = 0.0
-    for t in range(N_INIT + W, T):
+    for t in range(N_INIT + W_TUNE + W, T):
         for gi, slot in enumerate(batch.slots):
             make_slice(gi, t, slot)                 # new slices land in the slots (untimed)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -559,6 +571,8 @@ def run_batched(args):
         "gbs_ingested": slice_bytes * K / (ms / 1e3) / 1e9,
         "time_steps_per_s": K / (ms / 1e3),
         "graph_kernels_per_step": batch.kernels,
+        "launch_shape": {"share_multiplier": best_c,
+                         "tuning_ms_per_step": {str(c): round(v, 3) for c, v in tune_ms.items()}},
         "gpu_launches": batch.kernels,
         "rank_range": [min(min(r[:3]) for r in ranks), max(max(r[:3]) for r in ranks),
                        min(r[3] for r in ranks), max(r[3] for r in ranks)],

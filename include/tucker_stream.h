@@ -230,6 +230,27 @@ tucker_status tucker_profile_read(tucker_state* s, tucker_profile* out_host);
  * bound of the kernels one update runs), 0 before the first capture, -1 for NULL. */
 int64_t tucker_graph_kernels(const tucker_state* s);
 
+/* Launch shape of the update's kernels: CTA counts of its grid-stride passes. The defaults fill
+ * the whole GPU (two CTAs per SM for the projection and ISVD passes, one per SM for the
+ * tensor-core passes, four per SM for the core/V update); states updated concurrently (the batched
+ * form) run faster with smaller shares, which bench.py's batched workload chooses with the
+ * autotuner in paper_2308_16395_gb300/autotune.py. A plan changes no result, only how the work
+ * is split. Zero fields keep the default. */
+typedef struct {
+  int32_t grid_proj;   /* SIMT projection / residual passes and norm partial sums, 1..4096 */
+  int32_t grid_tc;     /* tensor-core passes (projection, E^T, Gram, core/V), 1..SM count */
+  int32_t grid_isvd;   /* ISVD row passes, 1..304 */
+  int32_t grid_cv;     /* core / V update, 1..65535 */
+} tucker_launch_plan;
+
+/* Set the plan. Takes effect at the next update (a captured update graph is discarded and
+ * captured again); a batch must be created after its states' plans are set. Synchronizes the
+ * state's last stream. Errors: EINVAL (field out of range), ESTATE. */
+tucker_status tucker_set_launch_plan(tucker_state* s, const tucker_launch_plan* plan);
+
+/* The plan in effect (defaults resolved). */
+tucker_status tucker_get_launch_plan(const tucker_state* s, tucker_launch_plan* plan_host);
+
 /* Message for the last error on this state (static storage owned by the state; never NULL). */
 const char* tucker_last_error(const tucker_state* s);
 

@@ -28,7 +28,8 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_reconstruct_noalloc", "tucker_ttm_workspace_bytes", "tucker_ttm_project",
            "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint", "tucker_ttm_reconstruct_adjoint",
            "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy",
-           "tucker_graph_kernels", "tucker_error_norm_async"]
+           "tucker_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
+           "tucker_get_launch_plan"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -43,6 +44,11 @@ class TuckerConfig(ctypes.Structure):
 class TtmDesc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("n", ctypes.c_int64 * MAX_MODES), ("r", ctypes.c_int64 * MAX_MODES)]
+
+
+class LaunchPlan(ctypes.Structure):
+    _fields_ = [("grid_proj", ctypes.c_int32), ("grid_tc", ctypes.c_int32),
+                ("grid_isvd", ctypes.c_int32), ("grid_cv", ctypes.c_int32)]
 
 
 class StepInfo(ctypes.Structure):
@@ -102,6 +108,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_batch_create.restype = ctypes.c_int
     lib.tucker_batch_update.argtypes = [vp, vp]
     lib.tucker_batch_update.restype = ctypes.c_int
+    lib.tucker_set_launch_plan.argtypes = [vp, ctypes.POINTER(LaunchPlan)]
+    lib.tucker_set_launch_plan.restype = ctypes.c_int
+    lib.tucker_get_launch_plan.argtypes = [vp, ctypes.POINTER(LaunchPlan)]
+    lib.tucker_get_launch_plan.restype = ctypes.c_int
     lib.tucker_error_norm_async.argtypes = [vp, vp, vp]
     lib.tucker_error_norm_async.restype = ctypes.c_int
     lib.tucker_graph_kernels.argtypes = [vp]
@@ -353,6 +363,17 @@ def tucker_ttm_reconstruct_adjoint(desc, U_ptrs, G_ptr, Yhbar_ptr, Gbar_ptr, Uba
         ctypes.byref(desc), _ptrs(U_ptrs), ctypes.c_void_p(G_ptr), ctypes.c_void_p(Yhbar_ptr),
         ctypes.c_void_p(Gbar_ptr), _ptrs(Ubar_ptrs), ctypes.c_void_p(work_ptr), int(work_bytes),
         ctypes.c_void_p(stream)))
+
+
+def tucker_set_launch_plan(h: int, grid_proj=0, grid_tc=0, grid_isvd=0, grid_cv=0) -> None:
+    p = LaunchPlan(int(grid_proj), int(grid_tc), int(grid_isvd), int(grid_cv))
+    _check(load_library().tucker_set_launch_plan(h, ctypes.byref(p)), h)
+
+
+def tucker_get_launch_plan(h: int) -> dict:
+    p = LaunchPlan()
+    _check(load_library().tucker_get_launch_plan(h, ctypes.byref(p)), h)
+    return dict(grid_proj=p.grid_proj, grid_tc=p.grid_tc, grid_isvd=p.grid_isvd, grid_cv=p.grid_cv)
 
 
 def tucker_graph_kernels(h: int) -> int:

@@ -85,6 +85,11 @@ struct tucker_state {
   float* et = nullptr;            // E^T of the growing mode (n_k x Fs_k) for the Gram
   long long et_stride[TK_MAXD]{};
   int nsm = 152;
+  // launch shape of the update's kernels (tucker_set_launch_plan)
+  int grid_p = kGridP;   // SIMT projection / residual passes; partial-sum slots of the norms
+  int grid_tc = 152;     // tensor-core passes (one CTA per SM at most)
+  int grid_i = kGridI;   // ISVD row passes
+  int grid_cv = kGridCV; // core / V update
   void* cu = nullptr;
   void* wv = nullptr;
   std::vector<void*> allocs;
@@ -318,6 +323,7 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev));
+  s->grid_tc = s->nsm;
   if (tw == 4 && s->ldc % 4 == 0) {
     for (int i = 0; i < 4; ++i) CK(dalloc(s, (void**)&s->bsplit[i], sizeof(float) * 512 * 512));
     CK(dalloc(s, (void**)&s->d_bsplit, sizeof(void*) * 4));
@@ -584,19 +590,19 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       PhaseMark pm(s, st, k == 0 ? TK_PH_PROJ1 : TK_PH_PROJN);
       if (tck) {
         CK(launch_tc_proj(s->ctl, k, 1, 0, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
-                          s->d_dbufs, 1, s->part_e2, k == 0 ? s->part_y2 : nullptr, kGridP,
-                          nullptr, 0, s->nsm, st));
+                          s->d_dbufs, 1, s->part_e2, k == 0 ? s->part_y2 : nullptr, s->grid_p,
+                          nullptr, 0, s->grid_tc, st));
         launches += 1;
       }
       if (k == 0)
         CK((launch_proj<TX, TW>(s->ctl, k, 1, 0, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], s->part_e2,
-                                s->part_y2, kGridP, st)));
+                                s->part_y2, s->grid_p, st)));
       else
         CK((launch_proj<TW, TW>(s->ctl, k, 1, 0, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], s->part_e2,
-                                nullptr, kGridP, st)));
+                                nullptr, s->grid_p, st)));
       cudaGraphConditionalHandle hc = 0;
       if (s->gform) CK(cond_handle(st, &hc));
-      CK(launch_decide(s->ctl, k, s->part_e2, s->part_y2, kGridP, hc, st));
+      CK(launch_decide(s->ctl, k, s->part_e2, s->part_y2, s->grid_p, hc, st));
       if (s->gform) {
         // graph form: the growth chain below is the body of an IF node on grew[k]
         CK(cond_begin(st, s->body_st, hc, &s->bodies));
@@ -612,9 +618,9 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       if ((s->etmask >> k) & 1) {
         // residual E^T of mode k, then its Gram on the tensor cores (only if mode k grew)
         CK(launch_tc_proj(s->ctl, k, 2, 1, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
-                          s->d_dbufs, 1, nullptr, nullptr, kGridP, s->et, s->et_stride[k],
-                          s->nsm, st));
-        CK(launch_tc_gram(s->ctl, k, s->pmaps[k], n, s->gpart, s->G, s->nsm, st));
+                          s->d_dbufs, 1, nullptr, nullptr, s->grid_p, s->et, s->et_stride[k],
+                          s->grid_tc, st));
+        CK(launch_tc_gram(s->ctl, k, s->pmaps[k], n, s->gpart, s->G, s->grid_tc, st));
         launches += 3;
       }
       if (k == 0)
@@ -629,15 +635,15 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       if (tck) {
         CK(launch_split_u(s->ctl, k, 1, s->U[k], n, s->usplit[k], st));
         CK(launch_tc_proj(s->ctl, k, 0, 1, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
-                          s->d_dbufs, 2, nullptr, nullptr, kGridP, nullptr, 0, s->nsm, st));
+                          s->d_dbufs, 2, nullptr, nullptr, s->grid_p, nullptr, 0, s->grid_tc, st));
         launches += 2;
       }
       if (k == 0)
         CK((launch_proj<TX, TW>(s->ctl, k, 2, 1, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], nullptr,
-                                nullptr, kGridP, st)));
+                                nullptr, s->grid_p, st)));
       else
         CK((launch_proj<TW, TW>(s->ctl, k, 2, 1, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], nullptr,
-                                nullptr, kGridP, st)));
+                                nullptr, s->grid_p, st)));
       if (s->gform) {
         CK(cond_end(s->body_st));
         s->body_open = false;
@@ -650,7 +656,7 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
     // streaming mode: incremental SVD (Alg. 3)
     PhaseMark pm(s, st, TK_PH_ISVD);
     CK(launch_isvd<TW>(s->ctl, s->d_dbufs, s->d_vbufs, s->part_p, s->part_e, s->pvec, s->esvec,
-                       s->evec, s->S, s->sw, kGridI, st));
+                       s->evec, s->S, s->sw, s->grid_i, st));
     CK(launch_secular_vectors(s->ctl, s->S, s->sw, s->Snew, st));
     launches += 6;
   }
@@ -665,11 +671,11 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
     PhaseMark pm(s, st, TK_PH_CV);
     if (s->tc) {
       CK(launch_tc_cv(s->ctl, s->sw, s->maps, s->Cb, s->Vb, s->d_cbufs, s->d_vbufs, s->cu, s->wv,
-                      s->evec, s->d_dbufs, s->ldc, s->nsm, st));
+                      s->evec, s->d_dbufs, s->ldc, s->grid_tc, st));
       launches += 3;
     }
     CK(launch_cv<TW>(s->ctl, s->d_dbufs, s->d_cbufs, s->d_vbufs, s->sw, s->Bc, s->cu, s->Bv, s->wv,
-                     s->ldc, s->evec, kGridCV, st));
+                     s->ldc, s->evec, s->grid_cv, st));
     launches += 2;
   }
   CK(launch_end(s->ctl, s->Snew, s->S, st));
@@ -937,6 +943,38 @@ const char* tucker_version(void) { return kVersion; }
 const char* tucker_last_error(const tucker_state* s) { return s ? s->err : "null state"; }
 
 int64_t tucker_graph_kernels(const tucker_state* s) { return s ? s->graph_kernels : -1; }
+
+tucker_status tucker_set_launch_plan(tucker_state* s, const tucker_launch_plan* p) {
+  if (!s || !p) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  const int gp = p->grid_proj ? p->grid_proj : kGridP;
+  const int gt = p->grid_tc ? p->grid_tc : s->nsm;
+  const int gi = p->grid_isvd ? p->grid_isvd : kGridI;
+  const int gc = p->grid_cv ? p->grid_cv : kGridCV;
+  if (gp < 1 || gp > 4096 || gt < 1 || gt > s->nsm || gi < 1 || gi > kGridI || gc < 1 || gc > 65535) {
+    set_err(s, "launch plan out of range%s%lld", "", 0);
+    return TUCKER_EINVAL;
+  }
+  s->grid_p = gp;
+  s->grid_tc = gt;
+  s->grid_i = gi;
+  s->grid_cv = gc;
+  // the captured update graph holds the old launch shapes: capture again at the next update
+  if (s->last_stream) cudaStreamSynchronize(s->last_stream);
+  if (s->uexec) { cudaGraphExecDestroy(s->uexec); s->uexec = nullptr; }
+  if (s->ugraph) { cudaGraphDestroy(s->ugraph); s->ugraph = nullptr; }
+  s->graph_kernels = 0;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_get_launch_plan(const tucker_state* s, tucker_launch_plan* p) {
+  if (!s || !p) return TUCKER_EINVAL;
+  p->grid_proj = s->grid_p;
+  p->grid_tc = s->grid_tc;
+  p->grid_isvd = s->grid_i;
+  p->grid_cv = s->grid_cv;
+  return TUCKER_OK;
+}
 
 tucker_status tucker_init_sthosvd(const tucker_config* cfg, const void* X_dev, int64_t n_init,
                                   void* stream, tucker_state** out) {

@@ -943,7 +943,7 @@ __global__ void k_syrk_reduce(const Ctl* ctl, int k, const double* gpart, int S,
 cudaError_t launch_tc_gram(const Ctl* ctl, int k, const TcProjMaps& m, int n1, double* gpart,
                            double* G, int nsm, cudaStream_t st) {
   const int MT = (n1 + TC_M - 1) / TC_M;
-  const int S = nsm / MT;
+  const int S = nsm / MT > 0 ? nsm / MT : 1;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_tc_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM); attr = true; }
   k_tc_syrk<<<dim3(S, MT), 256, TS_SMEM, st>>>(ctl, k, m.eta, m.etb, gpart);

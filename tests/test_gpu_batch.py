@@ -114,3 +114,25 @@ def test_batch_error_latches_in_one_state(pkg):
     batch.close()
     for x in (a, b, ref):
         x.close()
+
+
+def test_launch_plan_changes_no_result(pkg):
+    """A small launch plan (a few CTAs per pass) gives the same state as the default plan."""
+    import torch
+
+    s = LowRankStream((40, 28, 12), (3, 3, 2, 3), 14, 1e-4, seed=8)
+    Xg = to_device(s.tensor(0, 14).astype(np.float32).astype(np.float64), torch.float32)
+    a = pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="mixed", steps_cap=20)
+    b = pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="mixed", steps_cap=20)
+    pkg.tucker_set_launch_plan(b.h, grid_proj=3, grid_tc=1, grid_isvd=2, grid_cv=5)
+    assert pkg.tucker_get_launch_plan(b.h) == dict(grid_proj=3, grid_tc=1, grid_isvd=2, grid_cv=5)
+    with pytest.raises(pkg.TuckerError):
+        pkg.tucker_set_launch_plan(b.h, grid_isvd=100000)
+    for t in range(6, 14):
+        a.update(Xg[t].contiguous())
+        b.update(Xg[t].contiguous())
+    assert a.ranks == b.ranks
+    Ra, Rb = a.reconstruct(0, 14).double(), b.reconstruct(0, 14).double()
+    assert float(torch.linalg.norm(Ra - Rb) / torch.linalg.norm(Ra)) <= 1e-6
+    a.close()
+    b.close()
