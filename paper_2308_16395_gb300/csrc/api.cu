@@ -366,7 +366,6 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
       const long long fs = (s->dbuf_elems / nk + 32 + 3) / 4 * 4;
       s->et_stride[k] = fs;
       bool oke = make_map_2d_f32(&m.eta, s->et, nk, fs, fs, 32, 128);
-      oke &= make_map_2d_f32(&m.etb, s->et, nk, fs, fs, 32, 16);
       if (oke) s->etmask |= 1 << k;
     }
   }

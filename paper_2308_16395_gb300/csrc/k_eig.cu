@@ -17,6 +17,8 @@
 namespace tk {
 
 constexpr int EIG_NT = 1024;
+// FP32 solves run 512 threads (16 warps), so the warp-per-vector path has 128 registers a thread
+constexpr int EIG_NT_F32 = 512;
 
 template <typename TE> struct Eps;
 template <> struct Eps<double> { static __device__ double u() { return 1.1102230246251565e-16; } static __device__ double tiny() { return 1e-290; } };
@@ -25,14 +27,14 @@ template <> struct Eps<float> { static __device__ float u() { return 5.9604645e-
 // Sturm counts at NS shifts in one sweep (NS independent recurrences per step). The quotient
 // b_i^2 / q uses the fast hardware reciprocal in FP32: the count only needs the sign of q, and a
 // relative error of a few ulp in one term moves it no more than the rounding of the subtraction.
-// The reciprocal unit (a quarter of the FMA rate) bounds the sweep, so three shifts per sweep
-// (two bits) balance its throughput against the latency of the recurrence.
+// Each step is a dependent chain (reciprocal, FMA, pivot guard), so a lane runs NS recurrences
+// interleaved: the second costs little extra time per sweep.
 template <typename TE> __device__ __forceinline__ TE sturm_recip(TE q) { return TE(1) / q; }
 template <> __device__ __forceinline__ float sturm_recip<float>(float q) { return __fdividef(1.f, q); }
 
 template <typename TE, int NS>
-__device__ void sturm_countN(const TE* a, const TE* b2, int n, const TE (&x)[NS], TE pivmin,
-                             int (&cnt)[NS]) {
+__device__ void sturm_countN(const TE* __restrict__ a, const TE* __restrict__ b2, int n,
+                             const TE (&x)[NS], TE pivmin, int (&cnt)[NS]) {
   TE q[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -40,6 +42,7 @@ __device__ void sturm_countN(const TE* a, const TE* b2, int n, const TE (&x)[NS]
     if (fabs(q[s]) < pivmin) q[s] = -pivmin;
     cnt[s] = q[s] < TE(0);
   }
+#pragma unroll 4
   for (int i = 1; i < n; ++i) {
     const TE ai = a[i], bi = b2[i - 1];
 #pragma unroll
@@ -52,8 +55,9 @@ __device__ void sturm_countN(const TE* a, const TE* b2, int n, const TE (&x)[NS]
 }
 
 // Householder tridiagonalization of an FP32 Gram matrix held in registers (n <= 192), one CTA of
-// 12 warps run before the eigensolver. Thread (warp w, lane l) owns A(w + 12a, l + 32b) for
-// a < RA, b < CB. Step c: every warp forms reflector c (LAPACK convention H = I - tau v v^T,
+// NW = 12 warps run before the eigensolver (24 warps measured slower: every warp repeats the
+// reflector and w computations). Thread (warp w, lane l) owns A(w + NW a, l + 32b) for a < RA,
+// b < CB. Step c: every warp forms reflector c (LAPACK convention H = I - tau v v^T,
 // v_0 = 1) from column c in shared memory; p = tau A22 v is reduced across a warp's lanes by a
 // butterfly that halves the rows a lane carries at each level (RA rows cost RA shuffles rather
 // than 5 RA); after one barrier every warp forms w = p - (tau/2)(p^T v) v itself, applies
@@ -61,8 +65,9 @@ __device__ void sturm_countN(const TE* a, const TE* b2, int n, const TE (&x)[NS]
 // The step body is instantiated per first live column block CB0 = (c+1)/32, so blocks of rows
 // and columns left of the trailing matrix drop out at compile time and the loops carry no
 // branches; entries outside the trailing matrix are masked by selects.
-// Output: reflector c in V[c n + c + 1 ...]; tri = [diagonal (n), off-diagonal (n), tau (n)].
-constexpr int TRI_NW = 12;
+// Output: reflector c in V[c n + c + 1 ...] (zeros elsewhere in the n x n block); tri = [diagonal
+// (n), off-diagonal (n), tau (n)].
+constexpr int TRI_NMAX = 192;   // largest n of the register kernel (12 warps x 16 rows)
 
 // p ? x : y through PTX selp. Picking register areg[a][b] for a run-time b with a plain
 // comparison lets the compiler turn the unrolled choice into an indexed access, which moves the
@@ -83,12 +88,19 @@ struct TriSmem {
   float* stau;
 };
 
-template <int RA, int CB, int CB0>
-__device__ __forceinline__ void tri_step(float (&areg)[RA][CB], int c, int n, int lane, int wid,
+// Packed FP32 pairs: rows 2h and 2h+1 of a thread's register block share one 64-bit register
+// pair, so the matrix-vector product and the rank-2 update issue one paired FMA (__ffma2_rn,
+// round-to-nearest in each half) per two entries.
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+template <int NW, int RA, int CB, int CB0>
+__device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], int c, int n, int lane, int wid,
                                          float* V, const TriSmem& sm) {
   constexpr int LOGRA = RA == 16 ? 4 : RA == 8 ? 3 : RA == 4 ? 2 : RA == 2 ? 1 : 0;
-  // row blocks a whose rows w + 12a all lie left of column 32 CB0 - 1 <= c are dead
-  constexpr int A0 = CB0 == 0 ? 0 : (32 * CB0 - TRI_NW) / TRI_NW + 1;
+  // row blocks a whose rows w + 12a all lie left of column 32 CB0 - 1 <= c are dead; pairs
+  // start at an even row block (a dead row in a live pair is updated by zero and never stored)
+  constexpr int A0 = CB0 == 0 ? 0 : (32 * CB0 - NW) / NW + 1;
+  constexpr int H0 = A0 / 2;
   const float* x = (c & 1) ? sm.sx1 : sm.sx0;
   float* xn = (c & 1) ? sm.sx0 : sm.sx1;
   // reflector from x = A(c+1:n, c); the same in every warp (same inputs and reduction order)
@@ -125,11 +137,14 @@ __device__ __forceinline__ void tri_step(float (&areg)[RA][CB], int c, int n, in
   }
   float acc[RA];
 #pragma unroll
-  for (int a = 0; a < RA; ++a) {
-    acc[a] = 0.f;
-    if (a < A0) continue;
+  for (int h = 0; h < RA / 2; ++h) {
+    float2 s2 = f2(0.f, 0.f);
+    if (h >= H0) {
 #pragma unroll
-    for (int b = CB0; b < CB; ++b) acc[a] = fmaf(areg[a][b], vc[b], acc[a]);
+      for (int b = CB0; b < CB; ++b) s2 = __ffma2_rn(a2[h][b], f2(vc[b], vc[b]), s2);
+    }
+    acc[2 * h] = s2.x;
+    acc[2 * h + 1] = s2.y;
   }
   // butterfly reduce-scatter: at level M the lanes with bit M set keep the upper half
 #pragma unroll
@@ -149,7 +164,7 @@ __device__ __forceinline__ void tri_step(float (&areg)[RA][CB], int c, int n, in
   {
     const int my_a = lane >> (5 - LOGRA);
     const bool writer = (lane & ((1 << (5 - LOGRA)) - 1)) == 0;
-    const int i = wid + TRI_NW * my_a;
+    const int i = wid + NW * my_a;
     if (writer && i > c && i < n) sm.sw[i] = tau * acc[0];
   }
   __syncthreads();
@@ -171,80 +186,101 @@ __device__ __forceinline__ void tri_step(float (&areg)[RA][CB], int c, int n, in
     wc[b] = sel_f32(j > c && j < n, swc[b] + K * vc[b], 0.f);
   }
 #pragma unroll
-  for (int a = A0; a < RA; ++a) {
-    const int i = wid + TRI_NW * a;
-    const bool live = i > c && i < n;
-    const float vi = sel_f32(i == c + 1, 1.f, sel_f32(live, x[i] * scal, 0.f));
-    const float wi = sel_f32(live, sm.sw[i] + K * vi, 0.f);
+  for (int h = H0; h < RA / 2; ++h) {
+    float nv[2], nw[2];
 #pragma unroll
-    for (int b = CB0; b < CB; ++b) areg[a][b] = fmaf(-vi, wc[b], fmaf(-wi, vc[b], areg[a][b]));
+    for (int e = 0; e < 2; ++e) {
+      const int i = wid + NW * (2 * h + e);
+      const bool live = i > c && i < n;
+      const float vi = sel_f32(i == c + 1, 1.f, sel_f32(live, x[i] * scal, 0.f));
+      nv[e] = -vi;
+      nw[e] = -sel_f32(live, sm.sw[i] + K * vi, 0.f);
+    }
+    const float2 mv = f2(nv[0], nv[1]), mw = f2(nw[0], nw[1]);
+#pragma unroll
+    for (int b = CB0; b < CB; ++b)
+      a2[h][b] = __ffma2_rn(mv, f2(wc[b], wc[b]), __ffma2_rn(mw, f2(vc[b], vc[b]), a2[h][b]));
   }
   // column c+1 (block CB0) from its owners
   if (lane == ((c + 1) & 31)) {
 #pragma unroll
-    for (int a = A0; a < RA; ++a) {
-      const int i = wid + TRI_NW * a;
-      if (i == c + 1) sm.sa[c + 1] = areg[a][CB0];
-      else if (i > c + 1 && i < n) xn[i] = areg[a][CB0];
-    }
+    for (int h = H0; h < RA / 2; ++h)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int i = wid + NW * (2 * h + e);
+        const float val = e ? a2[h][CB0].y : a2[h][CB0].x;
+        if (i == c + 1) sm.sa[c + 1] = val;
+        else if (i > c + 1 && i < n) xn[i] = val;
+      }
   }
   __syncthreads();
 }
 
-template <int RA, int CB, int CB0>
-__device__ __forceinline__ void tri_steps(float (&areg)[RA][CB], int n, int lane, int wid, float* V,
-                                          const TriSmem& sm) {
+template <int NW, int RA, int CB, int CB0>
+__device__ __forceinline__ void tri_steps(float2 (&a2)[RA / 2][CB], int n, int lane, int wid,
+                                          float* V, const TriSmem& sm) {
   // steps whose next column c+1 lies in block CB0
   const int c_lo = CB0 == 0 ? 0 : 32 * CB0 - 1;
   const int c_hi = min(32 * CB0 + 30, n - 3);
-  for (int c = c_lo; c <= c_hi; ++c) tri_step<RA, CB, CB0>(areg, c, n, lane, wid, V, sm);
-  if constexpr (CB0 + 1 < CB) tri_steps<RA, CB, CB0 + 1>(areg, n, lane, wid, V, sm);
+  for (int c = c_lo; c <= c_hi; ++c) tri_step<NW, RA, CB, CB0>(a2, c, n, lane, wid, V, sm);
+  if constexpr (CB0 + 1 < CB) tri_steps<NW, RA, CB, CB0 + 1>(a2, n, lane, wid, V, sm);
 }
 
-template <int RA, int CB>
-__global__ void __launch_bounds__(TRI_NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int mode,
-                                                              const double* __restrict__ G, float* V,
-                                                              float* tri) {
+template <int NW, int RA, int CB>
+__global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int mode,
+                                                          const double* __restrict__ G, float* V,
+                                                          float* tri) {
+  static_assert(RA % 2 == 0, "register rows are paired");
   if (ctl->status) return;
   if (mode == 0 && !ctl->grew[k]) return;
   const int d = ctl->d;
   const int n = (k == d - 1) ? ctl->init_nt : ctl->n[k];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int SZ = TRI_NW * RA + 32;
+  constexpr int SZ = NW * RA + 32;
   static_assert(SZ > 32 * CB, "shared vectors must cover every column index");
   __shared__ float sx[2][SZ];
   __shared__ float sw[SZ];
   __shared__ float sa[SZ], sb[SZ], stau[SZ];
   for (int i = tid; i < SZ; i += blockDim.x) { sx[0][i] = 0.f; sx[1][i] = 0.f; sw[i] = 0.f; }
-  float areg[RA][CB];
+  // the reflector block starts as zeros: entries above each reflector's leading 1 and the
+  // columns n-2, n-1 (no reflector) then read as zero (the steps write rows c+1.. of column c)
+  for (int L = tid; L < n * n; L += blockDim.x) V[L] = 0.f;
+  float2 a2[RA / 2][CB];
 #pragma unroll
-  for (int a = 0; a < RA; ++a)
+  for (int h = 0; h < RA / 2; ++h)
 #pragma unroll
     for (int b = 0; b < CB; ++b) {
-      const int i = wid + TRI_NW * a, j = lane + 32 * b;
-      areg[a][b] = (i < n && j < n) ? (float)G[(long long)i * n + j] : 0.f;
+      const int i0 = wid + NW * (2 * h), i1 = i0 + NW, j = lane + 32 * b;
+      a2[h][b] = f2((i0 < n && j < n) ? (float)G[(long long)i0 * n + j] : 0.f,
+                    (i1 < n && j < n) ? (float)G[(long long)i1 * n + j] : 0.f);
     }
   __syncthreads();
   // column 0
   if (lane == 0) {
 #pragma unroll
-    for (int a = 0; a < RA; ++a) {
-      const int i = wid + TRI_NW * a;
-      if (i == 0) sa[0] = areg[a][0];
-      else if (i < n) sx[0][i] = areg[a][0];
-    }
+    for (int h = 0; h < RA / 2; ++h)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int i = wid + NW * (2 * h + e);
+        const float val = e ? a2[h][0].y : a2[h][0].x;
+        if (i == 0) sa[0] = val;
+        else if (i < n) sx[0][i] = val;
+      }
   }
   __syncthreads();
   const TriSmem sm{sx[0], sx[1], sw, sa, sb, stau};
-  tri_steps<RA, CB, 0>(areg, n, lane, wid, V, sm);
+  tri_steps<NW, RA, CB, 0>(a2, n, lane, wid, V, sm);
   // trailing entries: column n-2 is in buffer (n-2)&1; A(n-1, n-1) with its owner
-  if (lane == ((n - 1) & 31) && wid == (n - 1) % TRI_NW) {
-    const int a0 = (n - 1) / TRI_NW, b0 = (n - 1) >> 5;
+  if (lane == ((n - 1) & 31) && wid == (n - 1) % NW) {
+    const int a0 = (n - 1) / NW, b0 = (n - 1) >> 5;
     float v = 0.f;
 #pragma unroll
-    for (int a = 0; a < RA; ++a)
+    for (int h = 0; h < RA / 2; ++h)
 #pragma unroll
-      for (int b = 0; b < CB; ++b) v = sel_f32(a == a0 && b == b0, areg[a][b], v);
+      for (int b = 0; b < CB; ++b) {
+        v = sel_f32(2 * h == a0 && b == b0, a2[h][b].x, v);
+        v = sel_f32(2 * h + 1 == a0 && b == b0, a2[h][b].y, v);
+      }
     sa[n - 1] = v;
   }
   if (tid == 0) {
@@ -274,12 +310,115 @@ struct EigArgs {
 // use_smem: the n x n working matrix lives in (dynamic) shared memory instead of global memory.
 constexpr int EIG_SMEM_VECS = 16;
 constexpr int EIG_FIRST_BATCH = 8;   // top eigenvalues computed before the first cut test
+constexpr int EIG_FIRST_BATCH_FV = 4;
 constexpr int EIG_WY = 8;            // reflectors per compact-WY group of the back-transform
+
+// Warp-per-vector eigenvector path for FP32 Grams tridiagonalized by k_tridiag_reg (n <= 192,
+// up to EIG_SMEM_VECS vectors). Inverse iteration solves the bidiagonal systems of the LDL^T
+// factors as first-order linear recurrences, which compose as affine maps: each lane runs the
+// recurrence over EIG_FV_SEG consecutive rows, a warp scan composes the lanes' maps, and one more
+// pass evaluates every row. The back-transform applies the reflectors in compact-WY groups of
+// EIG_FV_GW whose triangular factors T are formed beforehand by the warps that do not bisect.
+constexpr int EIG_FV_NMAX = 192;
+constexpr int EIG_FV_SEG = EIG_FV_NMAX / 32;
+constexpr int EIG_FV_GW = 16;
+constexpr int EIG_FV_GMAX = (EIG_FV_NMAX - 2 + EIG_FV_GW - 1) / EIG_FV_GW;
+
+// Butterfly reduce-scatter of 16 per-lane partial sums: returns the warp total of p[lane >> 1]
+// (lanes 2a and 2a + 1 both hold the sum for a).
+__device__ __forceinline__ float warp_rs16(float (&p)[16], int lane) {
+#pragma unroll
+  for (int lev = 0; lev < 4; ++lev) {
+    const int M = 16 >> lev;
+    const int H = 16 >> (lev + 1);
+    const bool up = (lane & M) != 0;
+#pragma unroll
+    for (int t = 0; t < H; ++t) {
+      const float keep = up ? p[H + t] : p[t];
+      const float send = up ? p[t] : p[H + t];
+      p[t] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+    }
+  }
+  return p[0] + __shfl_xor_sync(0xffffffffu, p[0], 1);
+}
+
+// T - sig I = L D L^T of the symmetric tridiagonal T (diagonal a, off-diagonal b) for inverse
+// iteration: L (n, L[n-1] = 0) and the reciprocal pivots 1/D (n); pivots smaller than pivt in
+// magnitude are replaced by +-pivt so the factorization is always defined. One thread.
+__device__ __forceinline__ void fv_ldl(const float* __restrict__ a, const float* __restrict__ b,
+                                       int n, float sig, float pivt, float* __restrict__ L,
+                                       float* __restrict__ Dinv) {
+  float dcur = a[0] - sig;
+  if (fabsf(dcur) < pivt) dcur = copysignf(pivt, dcur == 0.f ? 1.f : dcur);
+  float dinv = __fdividef(1.f, dcur);
+  Dinv[0] = dinv;
+#pragma unroll 4
+  for (int i = 0; i < n - 1; ++i) {
+    const float bi = b[i];
+    const float l = bi * dinv;
+    L[i] = l;
+    dcur = fmaf(-l, bi, a[i + 1] - sig);
+    if (fabsf(dcur) < pivt) dcur = copysignf(pivt, dcur == 0.f ? 1.f : dcur);
+    dinv = __fdividef(1.f, dcur);
+    Dinv[i + 1] = dinv;
+  }
+  L[n - 1] = 0.f;
+}
+
+// T factor of reflector group g (reflectors 16g .. 16g+gl-1; reflector c is column c of V, zero
+// at rows <= c, 1 at row c + 1; the columns n-2, n-1 hold zeros): H_{16g} ... H_{16g+gl-1} =
+// I - V T V^T, T upper triangular with T(j, j) = tau_j and T(0:j, j) = -tau_j T(0:j, 0:j)
+// V(:, 0:j)^T v_j (Schreiber & Van Loan). One warp. Reflector indices past the last column are
+// clamped to column n-1 (zeros), rows past n are clamped to row n-1 and masked, so the loops carry
+// no branches. The products v_a^T v_b go through the 16 x 16 scratch sc; T outside gl x gl is 0.
+__device__ void fv_wy_factor(const float* V, const float* tau, int n, int g,
+                             float (*wt)[EIG_FV_GW], float* sc, int lane) {
+  const int g0 = EIG_FV_GW * g;
+  const int gl = min(EIG_FV_GW, n - 2 - g0);
+#pragma unroll 1
+  for (int b = 1; b < 16; ++b) {
+    const float* vb = V + min(g0 + b, n - 1) * n;
+    float xb[EIG_FV_SEG];
+#pragma unroll
+    for (int t = 0; t < EIG_FV_SEG; ++t) {
+      const int i = lane + 32 * t;
+      xb[t] = i < n ? vb[i] : 0.f;
+    }
+    float p[16];
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {
+      const float* va = V + min(g0 + a, n - 1) * n;
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t < EIG_FV_SEG; ++t) acc = fmaf(va[min(lane + 32 * t, n - 1)], xb[t], acc);
+      p[a] = acc;
+    }
+    const float s = warp_rs16(p, lane);
+    const int a = lane >> 1;
+    if ((lane & 1) == 0 && a < b) sc[a * 16 + b] = s;
+  }
+  __syncwarp();
+  float trow[EIG_FV_GW];   // row `lane` of T (lanes 0..15)
+#pragma unroll
+  for (int j = 0; j < EIG_FV_GW; ++j) {
+    float sacc = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < j; ++kk)
+      if (kk >= lane) sacc = fmaf(trow[kk], sc[kk * 16 + j], sacc);
+    const float tj = (j < gl) ? tau[g0 + j] : 0.f;
+    trow[j] = (lane < j) ? -tj * sacc : (lane == j ? tj : 0.f);
+  }
+  if (lane < EIG_FV_GW) {
+#pragma unroll
+    for (int j = 0; j < EIG_FV_GW; ++j) wt[lane][j] = trow[j];
+  }
+  __syncwarp();
+}
 
 // use_smem: dynamic shared memory holds the eigenvector workspaces (up to EIG_SMEM_VECS vectors)
 // after the n x n working matrix when use_amat, else at its start.
 template <typename TE>
-__global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, EigArgs ea,
+__global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, EigArgs ea,
                                                     int use_smem, int use_amat, int pre) {
   extern __shared__ __align__(16) unsigned char eig_dyn[];
   if (ctl->status) return;
@@ -297,12 +436,23 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
 
   __shared__ TE svb[2][TK_N_MAX];
   __shared__ int s_skip[2];
+  // FP32 warp-per-vector path (the reflector copy and the WY factors are prepared by the warps
+  // that do not bisect in the first batch)
+  const bool fastv = sizeof(TE) == 4 && pre && use_amat && use_smem && n >= 8 && n <= EIG_FV_NMAX;
+  // the WY scratch (256 floats per group) fits in the eigenvector area, so the first batch's
+  // vector workspaces after it are free while the bisection runs
+  const bool fv_spec = fastv && ((n - 2 + EIG_FV_GW - 1) / EIG_FV_GW) * 256 <= EIG_SMEM_VECS * n;
+  // first bisection batch: fewer eigenvalues on the FP32 path, so more warps prepare the WY
+  // factors meanwhile (one group each at n = 192)
+  const int bs0 = fastv ? EIG_FIRST_BATCH_FV : EIG_FIRST_BATCH;
+  __shared__ float wy_t[EIG_FV_GMAX][EIG_FV_GW][EIG_FV_GW];
+  static_assert(EIG_SMEM_VECS <= EIG_NT_F32 / 32, "one warp per vector");
   if (pre) {
     // tridiagonal form and reflectors from k_tridiag_reg: tri follows the n x n reflector block
     const TE* V = reinterpret_cast<const TE*>(ea.Aw);
     const TE* tri = V + (long long)n * n;
     for (int i = tid; i < n; i += nt) { sa[i] = tri[i]; sb[i] = tri[n + i]; stau[i] = tri[2 * n + i]; }
-    if (use_amat)
+    if (use_amat && !fastv)
       for (long long L = tid; L < (long long)n * n; L += nt) A[L] = V[L];
     __syncthreads();
   } else {
@@ -390,9 +540,9 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
   // ---- Alg. 1's cut from the top eigenvalues ----
   // tails[l] = lam_l + ... + lam_{n-1} = trace(G) - (lam_0 + ... + lam_{l-1}), with the trace
   // summed in FP64 from G's diagonal, so only the eigenvalues above the cut are computed: largest
-  // first, one warp per eigenvalue, each by multisection of the Sturm count at 32 shifts per
-  // sweep (33 sub-intervals, five bits per sweep); batches of one eigenvalue per warp until the
-  // cut is found. The error of a tail is then that of a few eigenvalues (a few u ||G||), not of
+  // first, one warp per eigenvalue, each by multisection of the Sturm count at 64 shifts per
+  // sweep (two per lane, 65 sub-intervals, six bits per sweep); batches of one eigenvalue per
+  // warp until the cut is found. The error of a tail is then that of a few eigenvalues (a few u ||G||), not of
   // the sum of all the small ones.
   __shared__ double stails[TK_N_MAX + 1];   // stails[l] = trace - (lam_0 + ... + lam_{l-1})
   __shared__ int s_cnt, s_cut;
@@ -443,8 +593,8 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     // small because the cut of a residual Gram usually keeps a few eigenpairs. The initial
     // ST-HOSVD (mode 1) computes every eigenvalue: its discarded energy is a tiny fraction of the
     // trace, so it is summed from the bottom of the spectrum below instead.
-    for (int j0 = 0; j0 < n && (j0 == 0 || s_cut < 0 || mode == 1); j0 += (j0 == 0 ? EIG_FIRST_BATCH : nwarp)) {
-      const int bs = (j0 == 0) ? EIG_FIRST_BATCH : nwarp;
+    for (int j0 = 0; j0 < n && (j0 == 0 || s_cut < 0 || mode == 1); j0 += (j0 == 0 ? bs0 : nwarp)) {
+      const int bs = (j0 == 0) ? bs0 : nwarp;
       const int j = j0 + wid;            // descending index of this warp's eigenvalue
       if (wid < bs && j < n) {
         const int i = n - 1 - j;         // ascending index
@@ -452,21 +602,58 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
         for (int it = 0; it < 40; ++it) {
           const TE w = hi - lo;
           if (w <= TE(2) * u * max(fabs(lo), fabs(hi)) + atol) break;
-          const TE step = w / TE(33);
-          TE x[1] = {lo + TE(lane + 1) * step};
-          if (!(lo + step > lo && lo + TE(32) * step < hi)) break;
-          int cnt[1];
-          sturm_countN<TE, 1>(sa, sb2, n, x, pivmin, cnt);
+          // 64 shifts per sweep, two independent recurrences per lane (65 sub-intervals)
+          const TE step = w / TE(65);
+          TE x[2] = {lo + TE(lane + 1) * step, lo + TE(lane + 33) * step};
+          if (!(lo + step > lo && lo + TE(64) * step < hi)) break;
+          int cnt[2];
+          sturm_countN<TE, 2>(sa, sb2, n, x, pivmin, cnt);
           // the eigenvalue lies in the first sub-interval whose right end counts more than i
           // eigenvalues below it
-          const unsigned above = __ballot_sync(0xffffffffu, cnt[0] > i);
-          const int l = above ? __ffs(above) - 1 : 32;
+          const unsigned above0 = __ballot_sync(0xffffffffu, cnt[0] > i);
+          const unsigned above1 = __ballot_sync(0xffffffffu, cnt[1] > i);
+          const int l = above0 ? __ffs(above0) - 1 : (above1 ? 32 + __ffs(above1) - 1 : 64);
           const TE nlo = (l == 0) ? lo : lo + TE(l) * step;
-          const TE nhi = (l == 32) ? hi : lo + TE(l + 1) * step;
+          const TE nhi = (l == 64) ? hi : lo + TE(l + 1) * step;
           lo = nlo;
           hi = nhi;
         }
         if (lane == 0) slam[j] = TE(0.5) * (lo + hi);
+        if (fv_spec && j0 == 0 && lane == 0) {
+          // inverse-iteration factors for this eigenvalue while the other warps still bisect
+          const float uf = 5.9604645e-08f, tnf = (float)s_tnorm;
+          float* LDj = reinterpret_cast<float*>(eig_dyn) + (size_t)n * n + (size_t)EIG_SMEM_VECS * n + (size_t)j * 2 * n;
+          fv_ldl(reinterpret_cast<const float*>(sa), reinterpret_cast<const float*>(sb), n,
+                 (float)slam[j] + 4.f * uf * tnf, fmaxf(uf * tnf, 1e-35f), LDj, LDj + n);
+        }
+      } else if (fastv && j0 == 0 && wid >= bs) {
+        // reflectors into shared memory, WY factors of every group
+        // reflectors into shared memory (k_tridiag_reg wrote them with their zeros), four
+        // 16-byte loads in flight per thread, then the WY factors of every group; the T scratch
+        // of group g is 256 floats of the (still unused) eigenvector workspace
+        const float* Vg = reinterpret_cast<const float*>(ea.Aw);
+        float* Af = reinterpret_cast<float*>(eig_dyn);   // == A (use_amat): shared, not generic
+        const int pw = wid - bs, np = nwarp - bs;
+        const int nn = n * n, n4 = nn / 4, pt = pw * 32 + lane, ps = np * 32;
+        const float4* V4 = reinterpret_cast<const float4*>(Vg);
+        float4* A4 = reinterpret_cast<float4*>(Af);
+        for (int q = pt; q < n4; q += 4 * ps) {
+          float4 r[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (q + u * ps < n4) r[u] = V4[q + u * ps];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (q + u * ps < n4) A4[q + u * ps] = r[u];
+        }
+        for (int L = 4 * n4 + pt; L < nn; L += ps) Af[L] = Vg[L];
+        // the copy is complete among these warps (named barrier 1; the bisecting warps do not
+        // take part)
+        asm volatile("bar.sync 1, %0;" ::"r"(np * 32) : "memory");
+        const int ng = (n - 2 + EIG_FV_GW - 1) / EIG_FV_GW;
+        float* scr = Af + (size_t)n * n;
+        for (int g = pw; g < ng; g += np)
+          fv_wy_factor(Af, reinterpret_cast<const float*>(stau), n, g, wy_t[g], scr + (size_t)g * 256, lane);
       }
       __syncthreads();
       if (tid == 0) {
@@ -518,6 +705,193 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_topk(Ctl* ctl, int k, int mode, 
     if (tid == 0) {
       if (mode == 0) { ctl->radd[k] = 0; ctl->disc[k] = s_disc; }
       else { ctl->r[k] = 0; ctl->disc[k] = s_disc; }
+    }
+    return;
+  }
+
+  if (fastv && m <= EIG_SMEM_VECS) {
+    // ---- eigenvectors of the top m eigenvalues, one warp per vector ----
+    // inverse iteration (Golub & Van Loan, Sec. 8.2.2) on T - sig I = L D L^T, sig slightly
+    // above the computed eigenvalue; 3 iterations with modified Gram-Schmidt across vectors
+    float* Af = reinterpret_cast<float*>(eig_dyn);   // == A (use_amat): shared, not generic
+    float* Zs = Af + (size_t)n * n;                      // vector v: Zs[v n + row]
+    float* LDs = Zs + (size_t)EIG_SMEM_VECS * n;         // vector v: L (n), 1/D (n)
+    const float* saf = reinterpret_cast<const float*>(sa);
+    const float* sbf = reinterpret_cast<const float*>(sb);
+    const float uf = 5.9604645e-08f;
+    const float tnf = (float)s_tnorm;
+    const float pivt = fmaxf(uf * tnf, 1e-35f);
+    const bool mine = wid < m;
+    const int v = wid;
+    float* Lv = LDs + (size_t)(mine ? v : 0) * 2 * n;
+    float* Dv = Lv + n;
+    constexpr int SEG = EIG_FV_SEG;
+    const int r0 = SEG * lane;
+    const unsigned FULL = 0xffffffffu;
+    // factors of the first batch's vectors were formed by their bisection warps
+    if (mine && lane == 0 && !(fv_spec && v < bs0))
+      fv_ldl(saf, sbf, n, (float)slam[v] + 4.f * uf * tnf, pivt, Lv, Dv);
+    __syncwarp();
+    float z[SEG];
+#pragma unroll
+    for (int q = 0; q < SEG; ++q) {
+      const int r = r0 + q;
+      // deterministic start vector with entries in [1, 1.5]
+      unsigned h = (unsigned)(r * 2654435761u) ^ (unsigned)((v + 1) * 40503u);
+      h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
+      z[q] = (r < n) ? 1.f + (0.5f / 65535.f) * (float)(h & 0xffffu) : 0.f;
+    }
+    for (int iter = 0; iter < 3; ++iter) {
+      if (mine) {
+        // L y = z: y_r = z_r - L_{r-1} y_{r-1}; per lane y_r = al_r y_in + be_r
+        float al[SEG], be[SEG];
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) {
+          const int r = r0 + q;
+          const float lm = (r >= 1 && r < n) ? Lv[r - 1] : 0.f;
+          al[q] = (q == 0) ? -lm : -lm * al[q - 1];
+          be[q] = (q == 0) ? z[0] : fmaf(-lm, be[q - 1], z[q]);
+        }
+        float Am = al[SEG - 1], Bm = be[SEG - 1];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const float A2 = __shfl_up_sync(FULL, Am, off), B2 = __shfl_up_sync(FULL, Bm, off);
+          if (lane >= off) { Bm = fmaf(Am, B2, Bm); Am *= A2; }
+        }
+        float yin = __shfl_up_sync(FULL, Bm, 1);
+        if (lane == 0) yin = 0.f;
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) z[q] = fmaf(al[q], yin, be[q]);
+        // D L^T x = y: x_r = y_r / d_r - L_r x_{r+1}; per lane x_r = ga_r x_in + de_r
+        float ga[SEG], de[SEG];
+#pragma unroll
+        for (int q = SEG - 1; q >= 0; --q) {
+          const int r = r0 + q;
+          const float lr = (r < n) ? Lv[r] : 0.f;
+          const float dr = (r < n) ? Dv[r] : 0.f;
+          ga[q] = (q == SEG - 1) ? -lr : -lr * ga[q + 1];
+          de[q] = (q == SEG - 1) ? z[q] * dr : fmaf(-lr, de[q + 1], z[q] * dr);
+        }
+        float Cm = ga[0], Em = de[0];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const float C2 = __shfl_down_sync(FULL, Cm, off), E2 = __shfl_down_sync(FULL, Em, off);
+          if (lane + off < 32) { Em = fmaf(Cm, E2, Em); Cm *= C2; }
+        }
+        float xin = __shfl_down_sync(FULL, Em, 1);
+        if (lane == 31) xin = 0.f;
+        float amax = 0.f;
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) {
+          z[q] = fmaf(ga[q], xin, de[q]);
+          amax = fmaxf(amax, fabsf(z[q]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, o));
+        // the solve amplifies by up to 1/(4 u |T|): back to unit max-norm
+        const float sc = amax > 0.f ? 1.f / amax : 0.f;
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) z[q] *= sc;
+      }
+      if (m > 1) {
+        // modified Gram-Schmidt in vector order through shared memory
+        if (mine) {
+#pragma unroll
+          for (int q = 0; q < SEG; ++q)
+            if (r0 + q < n) Zs[(size_t)v * n + r0 + q] = z[q];
+        }
+        __syncthreads();
+        for (int vv = 0; vv + 1 < m; ++vv) {
+          if (mine && v > vv) {
+            float sdot = 0.f, zz = 0.f, zv[SEG];
+#pragma unroll
+            for (int q = 0; q < SEG; ++q) {
+              zv[q] = (r0 + q < n) ? Zs[(size_t)vv * n + r0 + q] : 0.f;
+              sdot = fmaf(zv[q], z[q], sdot);
+              zz = fmaf(zv[q], zv[q], zz);
+            }
+            sdot = warp_sum(sdot);
+            zz = warp_sum(zz);
+            const float coef = zz > 0.f ? sdot / zz : 0.f;
+#pragma unroll
+            for (int q = 0; q < SEG; ++q) {
+              z[q] = fmaf(-coef, zv[q], z[q]);
+              if (r0 + q < n) Zs[(size_t)v * n + r0 + q] = z[q];
+            }
+          }
+          __syncthreads();
+        }
+      }
+      if (mine) {
+        float part = 0.f;
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) part = fmaf(z[q], z[q], part);
+        const float nrm = sqrtf(warp_sum(part));
+        const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) z[q] *= inv;
+      }
+    }
+    // ---- back-transform x = H_0 H_1 ... H_{n-3} z, last WY group first ----
+    if (mine) {
+#pragma unroll
+      for (int q = 0; q < SEG; ++q)
+        if (r0 + q < n) Zs[(size_t)v * n + r0 + q] = z[q];
+      __syncwarp();
+      float zr[SEG];   // rows lane + 32 t
+#pragma unroll
+      for (int t = 0; t < SEG; ++t) {
+        const int i = lane + 32 * t;
+        zr[t] = (i < n) ? Zs[(size_t)v * n + i] : 0.f;
+      }
+      const int ng = (n - 2 + EIG_FV_GW - 1) / EIG_FV_GW;
+      // branch-free group loop: reflector columns past n-1 clamp to column n-1 (zeros), rows
+      // past n clamp to row n-1 and are masked out of the update (zr stays 0 there)
+      const int am = lane >> 1;
+#pragma unroll 1
+      for (int g = ng - 1; g >= 0; --g) {
+        const int g0 = EIG_FV_GW * g;
+        // s = V^T z
+        float p[16];
+#pragma unroll
+        for (int a = 0; a < 16; ++a) {
+          const float* va = Af + min(g0 + a, n - 1) * n;
+          float x[SEG];
+#pragma unroll
+          for (int t = 0; t < SEG; ++t) x[t] = va[min(lane + 32 * t, n - 1)];
+          float acc = 0.f;
+#pragma unroll
+          for (int t = 0; t < SEG; ++t) acc = fmaf(x[t], zr[t], acc);
+          p[a] = acc;
+        }
+        const float s_mine = warp_rs16(p, lane);          // s_{lane >> 1}
+        // u = T s (T upper triangular, zero below the diagonal): lanes 2a, 2a + 1 form u_a
+        float u_mine = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          u_mine = fmaf(wy_t[g][am][j], __shfl_sync(FULL, s_mine, 2 * j), u_mine);
+        // z -= V u
+#pragma unroll
+        for (int a = 0; a < 16; ++a) {
+          const float ua = __shfl_sync(FULL, u_mine, 2 * a);
+          const float* va = Af + min(g0 + a, n - 1) * n;
+#pragma unroll
+          for (int t = 0; t < SEG; ++t) {
+            const int i = lane + 32 * t;
+            const float dz = va[min(i, n - 1)] * ua;
+            zr[t] = i < n ? zr[t] - dz : zr[t];
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < SEG; ++t) {
+        const int i = lane + 32 * t;
+        if (i < n) ea.W[(long long)v * n + i] = (double)zr[t];
+      }
+    }
+    if (tid == 0) {
+      if (mode == 0) { ctl->radd[k] = m; ctl->disc[k] = s_disc; }
+      else { ctl->r[k] = m; ctl->disc[k] = s_disc; }
     }
     return;
   }
@@ -788,17 +1162,16 @@ cudaError_t launch_eig(Ctl* ctl, int k, int mode, const double* G, void* Aw, voi
   // FP32 Grams up to 192 x 192 are tridiagonalized by the register kernel first; the reflectors
   // (n x n floats) and the tridiagonal (3n floats) fit in Aw, which holds n x n doubles
   int pre = 0;
-  if (sizeof(TE) == 4 && n >= 3 && n <= TRI_NW * 16) {
+  if (sizeof(TE) == 4 && n >= 3 && n <= TRI_NMAX) {
     float* V = reinterpret_cast<float*>(Aw);
     float* tri = V + (size_t)n * n;
-    constexpr int T = TRI_NW * 32;
-    if (n <= 24) k_tridiag_reg<2, 1><<<1, T, 0, st>>>(ctl, k, mode, G, V, tri);
-    else if (n <= 48) k_tridiag_reg<4, 2><<<1, T, 0, st>>>(ctl, k, mode, G, V, tri);
-    else if (n <= 96) k_tridiag_reg<8, 3><<<1, T, 0, st>>>(ctl, k, mode, G, V, tri);
-    else k_tridiag_reg<16, 6><<<1, T, 0, st>>>(ctl, k, mode, G, V, tri);
+    if (n <= 24) k_tridiag_reg<12, 2, 1><<<1, 12 * 32, 0, st>>>(ctl, k, mode, G, V, tri);
+    else if (n <= 48) k_tridiag_reg<12, 4, 2><<<1, 12 * 32, 0, st>>>(ctl, k, mode, G, V, tri);
+    else if (n <= 96) k_tridiag_reg<12, 8, 3><<<1, 12 * 32, 0, st>>>(ctl, k, mode, G, V, tri);
+    else k_tridiag_reg<12, 16, 6><<<1, 12 * 32, 0, st>>>(ctl, k, mode, G, V, tri);
     pre = 1;
   }
-  k_eig_topk<TE><<<1, EIG_NT, sm, st>>>(ctl, k, mode, ea, use_vec, use_amat, pre);
+  k_eig_topk<TE><<<1, sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT, sm, st>>>(ctl, k, mode, ea, use_vec, use_amat, pre);
   return cudaGetLastError();
 }
 

@@ -774,24 +774,30 @@ cudaError_t launch_tc_proj(const Ctl* ctl, int k, int mode, int pred, const floa
 
 // =============================================================================================
 // k_tc_syrk: partial Gram G = E^T E of the mode-k residual unfolding (Alg. 1's Gram of E_(k)),
-// split over the fibers (K). E^T (n_k x Fs, row stride Fs) streams by TMA in 32-fiber chunks;
-// both operands are split on chip into TF32 hi/lo (3xTF32); one CTA per (128-row block of G, K
-// split); partial blocks are summed in FP64 by k_syrk_reduce.
+// split over the fibers (K). One CTA per K split computes every block of G it needs from one
+// stream of E^T chunks: a chunk is the n_k rows x 32 fibers of E^T (TMA, 128-row boxes, rows past
+// n_k zero-filled), split on chip into TF32 hi/lo (3xTF32); the MMA operands are row ranges of
+// that one buffer: block 0 = rows 0..127 x columns 0..n_k, block 1 (n_k > 128) = rows 128..255 x
+// columns 128..n_k (the block below it is the transpose of block 0's right part). FP32 partial
+// blocks per split are summed in FP64 by k_syrk_reduce, in a fixed split order.
+// Warps: 0 TMA producer, 1 MMA issuer, 2..11 splitters; 4..7 also read the accumulators out.
 // =============================================================================================
-constexpr int TS_STAGE = 96 * 1024;    // A hi | A lo | B hi | B lo (B up to 256 rows)
-constexpr int TS_S = 2;
+constexpr int TS_ROWS = 256;                          // E^T rows per stage (n_k <= 256)
+constexpr int TS_STAGE = 2 * TS_ROWS * TC_KC * 4;     // hi | lo: 64 KB
+constexpr int TS_S = 3;
+constexpr int TS_SPLIT_W = 10;
+constexpr int TS_NT = 32 * (2 + TS_SPLIT_W);
 constexpr size_t TS_SMEM = (size_t)TS_S * TS_STAGE + 1024 + 256;
 
-__global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl, int k,
-                                                   const __grid_constant__ CUtensorMap mEa,
-                                                   const __grid_constant__ CUtensorMap mEb,
-                                                   double* __restrict__ gpart) {
+__global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ctl, int k,
+                                                     const __grid_constant__ CUtensorMap mEa,
+                                                     float* __restrict__ gpart) {
   if (ctl->status) return;
   if (!tc_gram_ok(ctl, k)) return;
   const int n1 = ctl->n[k];
   const long long F = view_B(ctl, k);
   const int n1p = (n1 + 15) / 16 * 16;
-  const int MT = gridDim.y, mt = blockIdx.y;
+  const int MT = (n1p + TC_M - 1) / TC_M;             // 1 or 2 row blocks
   const int S = gridDim.x, sp = blockIdx.x;
   const long long KC = (F + TC_KC - 1) / TC_KC;
   const long long per = (KC + S - 1) / S;
@@ -813,7 +819,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl,
   if (threadIdx.x == 0) {
     for (int s = 0; s < TS_S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 64);
+      mbar_init(&conv[s], 32 * TS_SPLIT_W);
       mbar_init(&empty[s], 1);
     }
     mbar_init(accfull, 1);
@@ -822,27 +828,26 @@ __global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl,
     fence_barrier_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, 256);
+    tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // stage layout: A hi [0,16K) A lo [16K,32K) B hi [32K,64K) B lo [64K,96K)
+  const uint32_t t0 = tmem, t1 = tmem + 256;          // block 0 (<= 256 cols), block 1 (<= 128)
+  // stage layout: hi rows [0, 256) x 128 B, then lo rows [0, 256) x 128 B
   if (warp == 0) {
     if (lane == 0) {
       tma_prefetch(&mEa);
-      tma_prefetch(&mEb);
       for (int c = 0; c < nchunks && !*abort; ++c) {
         const int s = c % TS_S;
         if (!wait_bar(&empty[s], (uint32_t)(((c / TS_S) & 1) ^ 1), abort)) break;
         unsigned char* st = base + (size_t)s * TS_STAGE;
         const int x = (int)((c_beg + c) * TC_KC);
-        mbar_arrive_expect_tx(&full[s], (uint32_t)(TC_M * TC_KC * 4 + n1p * TC_KC * 4));
-        tma_load_2d(&mEa, &full[s], st, x, mt * TC_M);
-        for (int n0 = 0; n0 < n1p; n0 += 16)
-          tma_load_2d(&mEb, &full[s], st + 32 * 1024 + n0 * 128, x, n0);
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(MT * TC_M * TC_KC * 4));
+        for (int mt = 0; mt < MT; ++mt)
+          tma_load_2d(&mEa, &full[s], st + (size_t)mt * TC_M * 128, x, mt * TC_M);
       }
       for (int j = (nchunks > TS_S ? nchunks - TS_S : 0); j < nchunks; ++j)
         wait_bar(&empty[j % TS_S], (uint32_t)((j / TS_S) & 1), abort);
@@ -850,21 +855,28 @@ __global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl,
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc_tf32(TC_M, n1p);
+      const uint32_t id0 = idesc_tf32(TC_M, n1p);
+      const uint32_t id1 = idesc_tf32(TC_M, MT > 1 ? n1p - TC_M : 16);
       bool ok = true;
       for (int c = 0; c < nchunks; ++c) {
         const int s = c % TS_S;
         if (!wait_bar(&conv[s], (uint32_t)((c / TS_S) & 1), abort)) { ok = false; break; }
         tc_fence_after();
         unsigned char* st = base + (size_t)s * TS_STAGE;
-        const uint64_t ahi = desc_sw128(st), alo = desc_sw128(st + 16 * 1024);
-        const uint64_t bhi = desc_sw128(st + 32 * 1024), blo = desc_sw128(st + 64 * 1024);
+        const uint64_t h0 = desc_sw128(st), l0 = desc_sw128(st + TS_ROWS * 128);
+        const uint64_t h1 = desc_sw128(st + TC_M * 128), l1 = desc_sw128(st + TS_ROWS * 128 + TC_M * 128);
 #pragma unroll
         for (int k4 = 0; k4 < TC_KC / 8; ++k4) {
           const uint64_t o = (uint64_t)(k4 * 32) >> 4;
-          mma_tf32(tmem, ahi + o, bhi + o, id, (c | k4) ? 1u : 0u);
-          mma_tf32(tmem, ahi + o, blo + o, id, 1u);
-          mma_tf32(tmem, alo + o, bhi + o, id, 1u);
+          const uint32_t acc = (c | k4) ? 1u : 0u;
+          mma_tf32(t0, h0 + o, h0 + o, id0, acc);
+          mma_tf32(t0, h0 + o, l0 + o, id0, 1u);
+          mma_tf32(t0, l0 + o, h0 + o, id0, 1u);
+          if (MT > 1) {
+            mma_tf32(t1, h1 + o, h1 + o, id1, acc);
+            mma_tf32(t1, h1 + o, l1 + o, id1, 1u);
+            mma_tf32(t1, l1 + o, h1 + o, id1, 1u);
+          }
         }
         tc_commit(&empty[s]);
       }
@@ -873,81 +885,93 @@ __global__ void __launch_bounds__(256, 1) k_tc_syrk(const Ctl* __restrict__ ctl,
       wait_bar(done, 0, abort);
     }
     __syncwarp();
-  } else if (warp == 2 || warp == 3) {
+  } else {
+    // splitters: rows [0, n1p) of the chunk (rows n1p.. are only read into accumulator rows
+    // that are never stored)
     const int ct = threadIdx.x - 64;
+    const int nv4 = n1p * TC_KC / 4;
     for (int c = 0; c < nchunks && !*abort; ++c) {
       const int s = c % TS_S;
       if (!wait_bar(&full[s], (uint32_t)((c / TS_S) & 1), abort)) break;
       unsigned char* st = base + (size_t)s * TS_STAGE;
-      float4* ahi = reinterpret_cast<float4*>(st);
-      float4* alo = reinterpret_cast<float4*>(st + 16 * 1024);
-      float4* bhi = reinterpret_cast<float4*>(st + 32 * 1024);
-      float4* blo = reinterpret_cast<float4*>(st + 64 * 1024);
-      for (int i = ct; i < TC_M * TC_KC / 4; i += 64) {
-        float4 v = ahi[i], h, l;
+      float4* hi = reinterpret_cast<float4*>(st);
+      float4* lo = reinterpret_cast<float4*>(st + TS_ROWS * 128);
+      for (int i = ct; i < nv4; i += 32 * TS_SPLIT_W) {
+        float4 v = hi[i], h, l;
         tf32_split(v.x, h.x, l.x); tf32_split(v.y, h.y, l.y);
         tf32_split(v.z, h.z, l.z); tf32_split(v.w, h.w, l.w);
-        ahi[i] = h; alo[i] = l;
-      }
-      for (int i = ct; i < n1p * TC_KC / 4; i += 64) {
-        float4 v = bhi[i], h, l;
-        tf32_split(v.x, h.x, l.x); tf32_split(v.y, h.y, l.y);
-        tf32_split(v.z, h.z, l.z); tf32_split(v.w, h.w, l.w);
-        bhi[i] = h; blo[i] = l;
+        hi[i] = h; lo[i] = l;
       }
       fence_proxy_async_smem();
       mbar_arrive(&conv[s]);
     }
-  } else if (warp >= 4 && warp < 8) {
-    const int wq = warp - 4;
-    bool okw = nchunks > 0 ? wait_bar(accfull, 0, abort) : false;
-    okw = __all_sync(0xffffffffu, okw);
-    const int row = wq * 32 + lane;   // row of the 128-row block
-    double* out = gpart + (((long long)sp * MT + mt) * TC_M + row) * n1p;
-    if (okw) {
-      tc_fence_after();
-      for (int c0 = 0; c0 < n1p; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
+    if (warp >= 4 && warp < 8) {
+      // partial blocks out: gpart[sp][row][col] (row-major, n1p x n1p FP32); block 0 rows
+      // 0..127 every column, block 1 rows 128.. columns 128..
+      const int wq = warp - 4;
+      bool okw = nchunks > 0 ? wait_bar(accfull, 0, abort) : false;
+      okw = __all_sync(0xffffffffu, okw);
+      float* outp = gpart + (long long)sp * n1p * n1p;
+      for (int mt = 0; mt < MT; ++mt) {
+        const int row = mt * TC_M + wq * 32 + lane;
+        const int cb = mt * TC_M;                    // first column of the block
+        const uint32_t tb = (mt ? t1 : t0) + ((uint32_t)(wq * 32) << 16);
+        for (int c0 = 0; c0 < n1p - cb; c0 += 32) {
+          float v[32];
+          if (okw) {
+            tc_fence_after();
+            tmem_ld32(tb + (uint32_t)c0, v);
+          } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (c0 + i < n1p) out[c0 + i] = (double)v[i];
+            for (int i = 0; i < 32; ++i) v[i] = 0.f;
+          }
+          if (row < n1p) {
+            float* o = outp + (long long)row * n1p + cb + c0;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (cb + c0 + i < n1p) o[i] = v[i];
+          }
+        }
       }
-    } else {
-      for (int c0 = 0; c0 < n1p; ++c0) out[c0] = 0.0;
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, 256);
+  if (warp == 1) tmem_dealloc(tmem, 512);
   if (threadIdx.x == 0 && *abort) const_cast<Ctl*>(ctl)->status = 5;
 }
 
-// G (n_k x n_k, FP64, column-major) = sum over K splits of the partial 128-row blocks.
-__global__ void k_syrk_reduce(const Ctl* ctl, int k, const double* gpart, int S, int MT, double* G) {
+// G (n_k x n_k, FP64, column-major) = sum over the K splits of the partial blocks, in split
+// order. Entry (i, j) is read as partial (j, i) (consecutive threads, consecutive i: contiguous)
+// except in the block rows < 128, columns >= 128 of G's lower-left mirror, which only block 0
+// holds (as (i, j)).
+__global__ void k_syrk_reduce(const Ctl* ctl, int k, const float* gpart, int S, double* G) {
   if (ctl->status) return;
   if (!tc_gram_ok(ctl, k)) return;
   const int n1 = ctl->n[k];
   const int n1p = (n1 + 15) / 16 * 16;
+  const long long plane = (long long)n1p * n1p;
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < (long long)n1 * n1;
        L += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(L % n1), j = (int)(L / n1);
-    const int mt = i / TC_M, row = i % TC_M;
+    const bool direct = (j < TC_M) || (i >= TC_M);
+    const long long off = direct ? (long long)j * n1p + i : (long long)i * n1p + j;
     double acc = 0.0;
-    for (int sp = 0; sp < S; ++sp) acc += gpart[(((long long)sp * MT + mt) * TC_M + row) * n1p + j];
+    for (int sp = 0; sp < S; ++sp) acc += (double)gpart[sp * plane + off];
     G[(long long)j * n1 + i] = acc;
   }
 }
 
 cudaError_t launch_tc_gram(const Ctl* ctl, int k, const TcProjMaps& m, int n1, double* gpart,
                            double* G, int nsm, cudaStream_t st) {
-  const int MT = (n1 + TC_M - 1) / TC_M;
-  const int S = nsm / MT > 0 ? nsm / MT : 1;
+  (void)n1;
+  const int S = nsm > 0 ? nsm : 1;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_tc_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM); attr = true; }
-  k_tc_syrk<<<dim3(S, MT), 256, TS_SMEM, st>>>(ctl, k, m.eta, m.etb, gpart);
-  k_syrk_reduce<<<64, 256, 0, st>>>(ctl, k, gpart, S, MT, G);
+  float* gp = reinterpret_cast<float*>(gpart);
+  k_tc_syrk<<<S, TS_NT, TS_SMEM, st>>>(ctl, k, m.eta, gp);
+  k_syrk_reduce<<<144, 256, 0, st>>>(ctl, k, gp, S, G);
   return cudaGetLastError();
 }
 

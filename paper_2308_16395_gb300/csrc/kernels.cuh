@@ -89,7 +89,7 @@ struct TcProjMaps {
   CUtensorMap uhi, ulo;     // U_k TF32 splits, column-major n_k x cap (rows of B1 = columns of U)
   CUtensorMap urhi, urlo;   // U_k TF32 splits, row-major n_k x 64
   CUtensorMap d[3];         // the D* buffers viewed as row-major (rows x n_k), box 32 x 128
-  CUtensorMap eta, etb;     // E^T (n_k x Fs), boxes 32 x 128 and 32 x 16
+  CUtensorMap eta;          // E^T (n_k x Fs), box 32 x 128
 };
 cudaError_t launch_split_u(const Ctl* ctl, int k, int pred, const double* U, int ldu,
                            float* const* sp, cudaStream_t st);
