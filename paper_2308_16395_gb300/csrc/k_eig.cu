@@ -82,11 +82,17 @@ __device__ __forceinline__ float sel_f32(bool p, float x, float y) {
 struct TriSmem {
   float* sx0;
   float* sx1;
-  float* sw;
+  float* svp;    // v of the current step, row-permuted (see tri_perm)
+  float* swp;    // p = tau A22 v, row-permuted
   float* sa;
   float* sb;
   float* stau;
 };
+
+// Row i of the register block (warp i % NW, block i / NW) stored at (i % NW) RA + i / NW, so a
+// warp's RA rows are contiguous and its row pairs load as float2.
+template <int NW, int RA>
+__device__ __forceinline__ int tri_perm(int i) { return (i % NW) * RA + i / NW; }
 
 // Packed FP32 pairs: rows 2h and 2h+1 of a thread's register block share one 64-bit register
 // pair, so the matrix-vector product and the rank-2 update issue one paired FMA (__ffma2_rn,
@@ -130,9 +136,10 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], int c, int n,
   if (wid == 0) {
     if (lane == 0) { sm.stau[c] = tau; sm.sb[c] = beta; }
 #pragma unroll
-    for (int b = CB0; b < CB; ++b) {
+    for (int b = 0; b < CB; ++b) {
       const int j = lane + 32 * b;
-      if (j > c && j < n) V[(long long)c * n + j] = vc[b];
+      if (b >= CB0 && j > c && j < n) V[(long long)c * n + j] = vc[b];
+      if (j < n) sm.svp[tri_perm<NW, RA>(j)] = b >= CB0 ? vc[b] : 0.f;
     }
   }
   float acc[RA];
@@ -165,7 +172,7 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], int c, int n,
     const int my_a = lane >> (5 - LOGRA);
     const bool writer = (lane & ((1 << (5 - LOGRA)) - 1)) == 0;
     const int i = wid + NW * my_a;
-    if (writer && i > c && i < n) sm.sw[i] = tau * acc[0];
+    if (writer && i < n) sm.swp[wid * RA + my_a] = (i > c) ? tau * acc[0] : 0.f;
   }
   __syncthreads();
   // w = p - (tau/2)(p^T v) v, again the same in every warp
@@ -174,32 +181,29 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], int c, int n,
 #pragma unroll
   for (int b = CB0; b < CB; ++b) {
     const int j = lane + 32 * b;
-    swc[b] = sm.sw[j];
+    swc[b] = j < n ? sm.swp[tri_perm<NW, RA>(j)] : 0.f;
     pv += sel_f32(j > c && j < n, swc[b] * vc[b], 0.f);
   }
   pv = warp_sum(pv);
   const float K = -0.5f * tau * pv;
-  float wc[CB];
+  float wn[CB], vn[CB];   // -w and -v at the thread's columns
 #pragma unroll
   for (int b = CB0; b < CB; ++b) {
     const int j = lane + 32 * b;
-    wc[b] = sel_f32(j > c && j < n, swc[b] + K * vc[b], 0.f);
+    wn[b] = -sel_f32(j > c && j < n, swc[b] + K * vc[b], 0.f);
+    vn[b] = -vc[b];
   }
+  // rows: v and p of the warp's rows as pairs (zero at dead rows and rows >= n), w = p + K v
+  const float2* v2p = reinterpret_cast<const float2*>(sm.svp + wid * RA);
+  const float2* p2p = reinterpret_cast<const float2*>(sm.swp + wid * RA);
+  const float2 K2 = f2(K, K);
 #pragma unroll
   for (int h = H0; h < RA / 2; ++h) {
-    float nv[2], nw[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int i = wid + NW * (2 * h + e);
-      const bool live = i > c && i < n;
-      const float vi = sel_f32(i == c + 1, 1.f, sel_f32(live, x[i] * scal, 0.f));
-      nv[e] = -vi;
-      nw[e] = -sel_f32(live, sm.sw[i] + K * vi, 0.f);
-    }
-    const float2 mv = f2(nv[0], nv[1]), mw = f2(nw[0], nw[1]);
+    const float2 vi = v2p[h];
+    const float2 wi = __ffma2_rn(K2, vi, p2p[h]);
 #pragma unroll
     for (int b = CB0; b < CB; ++b)
-      a2[h][b] = __ffma2_rn(mv, f2(wc[b], wc[b]), __ffma2_rn(mw, f2(vc[b], vc[b]), a2[h][b]));
+      a2[h][b] = __ffma2_rn(vi, f2(wn[b], wn[b]), __ffma2_rn(wi, f2(vn[b], vn[b]), a2[h][b]));
   }
   // column c+1 (block CB0) from its owners
   if (lane == ((c + 1) & 31)) {
@@ -239,9 +243,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
   constexpr int SZ = NW * RA + 32;
   static_assert(SZ > 32 * CB, "shared vectors must cover every column index");
   __shared__ float sx[2][SZ];
-  __shared__ float sw[SZ];
+  __shared__ __align__(16) float svp[SZ];
+  __shared__ __align__(16) float swp[SZ];
   __shared__ float sa[SZ], sb[SZ], stau[SZ];
-  for (int i = tid; i < SZ; i += blockDim.x) { sx[0][i] = 0.f; sx[1][i] = 0.f; sw[i] = 0.f; }
+  for (int i = tid; i < SZ; i += blockDim.x) { sx[0][i] = 0.f; sx[1][i] = 0.f; svp[i] = 0.f; swp[i] = 0.f; }
   // the reflector block starts as zeros: entries above each reflector's leading 1 and the
   // columns n-2, n-1 (no reflector) then read as zero (the steps write rows c+1.. of column c)
   for (int L = tid; L < n * n; L += blockDim.x) V[L] = 0.f;
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
       }
   }
   __syncthreads();
-  const TriSmem sm{sx[0], sx[1], sw, sa, sb, stau};
+  const TriSmem sm{sx[0], sx[1], svp, swp, sa, sb, stau};
   tri_steps<NW, RA, CB, 0>(a2, n, lane, wid, V, sm);
   // trailing entries: column n-2 is in buffer (n-2)&1; A(n-1, n-1) with its owner
   if (lane == ((n - 1) & 31) && wid == (n - 1) % NW) {
