@@ -18,6 +18,7 @@
 #define TK_OK 0
 #define TK_ECAPACITY 3
 #define TK_ENUMERIC 4
+#define TK_ETIMEOUT 5
 
 struct Ctl {
   // ---- configuration (written at creation) ----
@@ -138,6 +139,20 @@ __device__ __forceinline__ T warp_sum(T v);
 // partials of all blocks into out[c], warps taking blocks w, w + W, ... in increasing order and
 // the warp sums added in warp order, so the result does not depend on which block finished last.
 // Returns true in that block (all its threads), after out[] is written; resets the ticket.
+// true in every thread of the last block of the grid to arrive (completion ticket, reset by
+// that block); the writes of the other blocks before their arrival are visible to it.
+__device__ __forceinline__ bool tk_block_ticket(unsigned* ticket) {
+  __shared__ int s_lastb;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_lastb = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (!s_lastb) return false;
+  __threadfence();
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
 __device__ __forceinline__ bool tk_last_block_reduce(const double* part, long long stride, int len,
                                                      double* out, unsigned* ticket) {
   __shared__ int s_last;
@@ -154,8 +169,16 @@ __device__ __forceinline__ bool tk_last_block_reduce(const double* part, long lo
     const int c = c0 + lane;
     double acc = 0.0;
     if (c < len) {
-      const volatile double* vp = part;
-      for (int b = wid; b < nb; b += nw) acc += vp[(long long)b * stride + c];
+      // L2 loads (.cg: the partials come from other blocks), eight independent sums so that
+      // the loads overlap instead of waiting on one another
+      double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      int b = wid;
+      for (; b + 7 * nw < nb; b += 8 * nw) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] += __ldcg(part + (long long)(b + u * nw) * stride + c);
+      }
+      for (; b < nb; b += nw) a[0] += __ldcg(part + (long long)b * stride + c);
+      acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     }
     s_red[wid][lane] = acc;
     __syncthreads();

@@ -20,6 +20,7 @@
 //   k_cv_update    C~ = C M^T + d u^T and V~ = V' V''           (Alg. 5 / Alg. 3)
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc_common.cuh"
 
 namespace tk {
 
@@ -111,33 +112,22 @@ __global__ void __launch_bounds__(256) k_isvd_p(Ctl* __restrict__ ctl, TW* const
 
 // q, the q <= eps branch of Alg. 3 and the deflated secular problem of S'^T S' (one thread of
 // the e-pass's last block, once the cross-block sums p and [s; ||e||^2] are complete).
-__device__ void isvd_small_body(Ctl* ctl, const double* p, const double* es, const double* S,
-                                const SecWork& w) {
-  const int d = ctl->d;
-  const int r = ctl->r[d - 1];
-  // CGS-corrected projection: p' = p + s, q'^2 = ||e||^2 - ||s||^2
-  double s2 = 0.0;
-  for (int c = 0; c < r; ++c) s2 += es[c] * es[c];
-  double q2 = es[r] - s2;
-  if (q2 < 0.0) q2 = 0.0;
-  const double q = sqrt(q2);
-  for (int c = 0; c < r; ++c) w.pq[c] = p[c] + es[c];
-  w.pq[r] = q;
+// The part of the small ISVD step after its sums: the q <= eps decision of Alg. 3, the poles
+// S_i^2 and weights z = [p'; q] of S'^T S' = diag(S^2[, 0]) + z z^T, deflation of tiny weights
+// and merges of (nearly) equal poles (one thread). pq = [p'; q] (may be shared memory); zr2 =
+// sum_{i<r} pq_i^2; Rn the new spatial core size; eps and capd ctl->eps and ctl->cap[d - 1].
+__device__ void isvd_small_tail(Ctl* ctl, const double* S, const SecWork& w, const double* pq,
+                                int r, double q2, double q, double zr2, long long Rn, double eps,
+                                int capd) {
   ctl->q2 = q2;
   ctl->q = q;
-  const int aug = q > ctl->eps ? 1 : 0;   // Alg. 3: ignore e if q <= eps
+  const int aug = q > eps ? 1 : 0;   // Alg. 3: ignore e if q <= eps
   ctl->aug = aug;
-  if (aug && r + 1 > ctl->cap[d - 1]) { ctl->status = TK_ECAPACITY; return; }
-  long long Rn = 1;
-  for (int i = 0; i < d - 1; ++i) Rn *= ctl->r[i];
+  if (aug && r + 1 > capd) { ctl->status = TK_ECAPACITY; return; }
   if (Rn > ctl->core_cap) { ctl->status = TK_ECAPACITY; return; }
   const int m = r + aug;
   // poles (descending since S is descending) and weights
-  double zn2 = 0.0;
-  for (int i = 0; i < m; ++i) {
-    const double zi = (i < r) ? w.pq[i] : q;
-    zn2 += zi * zi;
-  }
+  const double zn2 = zr2 + (aug ? q * q : 0.0);
   const double u = 1.1102230246251565e-16;
   const double d1 = (r > 0) ? S[0] * S[0] : 0.0;
   const double scale = fmax(d1, zn2) > 0.0 ? fmax(d1, zn2) : 1.0;
@@ -149,7 +139,7 @@ __device__ void isvd_small_body(Ctl* ctl, const double* p, const double* es, con
   int pidx = -1;
   for (int i = 0; i < m; ++i) {
     const double di = (i < r) ? S[i] * S[i] : 0.0;
-    double zi = (i < r) ? w.pq[i] : q;
+    double zi = (i < r) ? pq[i] : q;
     if (fabs(zi) * zn <= tol) {   // deflate: eigenpair (di, e_i)
       w.lam[nl] = di;
       w.lsrc[nl] = -(i + 1);
@@ -179,6 +169,25 @@ __device__ void isvd_small_body(Ctl* ctl, const double* p, const double* es, con
   w.meta[0] = m;
   w.meta[1] = mk;
   w.meta[3] = nl;
+}
+
+// The small ISVD step on one thread (the SIMT passes, streaming rank above ROWS_RMAX):
+// CGS-corrected projection p' = p + s, q'^2 = ||e||^2 - ||s||^2, then isvd_small_tail.
+__device__ void isvd_small_body(Ctl* ctl, const double* p, const double* es, const double* S,
+                                const SecWork& w, int r, long long Rn, double eps, int capd) {
+  double s2 = 0.0;
+  for (int c = 0; c < r; ++c) s2 += es[c] * es[c];
+  double q2 = es[r] - s2;
+  if (q2 < 0.0) q2 = 0.0;
+  const double q = sqrt(q2);
+  double zr2 = 0.0;
+  for (int c = 0; c < r; ++c) {
+    const double v = p[c] + es[c];
+    w.pq[c] = v;
+    zr2 += v * v;
+  }
+  w.pq[r] = q;
+  isvd_small_tail(ctl, S, w, w.pq, r, q2, q, zr2, Rn, eps, capd);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -287,8 +296,11 @@ __global__ void __launch_bounds__(256) k_isvd_e(Ctl* __restrict__ ctl, TW* const
     part[(long long)blockIdx.x * (TK_STREAM_CAP_MAX + 2) + c] = s;
   }
   if (tk_last_block_reduce(part, TK_STREAM_CAP_MAX + 2, r + 1, es, &ctl->ticket[1]) &&
-      threadIdx.x == 0)
-    isvd_small_body(ctl, p, es, S, w);
+      threadIdx.x == 0) {
+    long long Rn = 1;
+    for (int i = 0; i < d - 1; ++i) Rn *= ctl->r[i];
+    isvd_small_body(ctl, p, es, S, w, r, Rn, ctl->eps, ctl->cap[d - 1]);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -569,19 +581,23 @@ __global__ void k_ud_update(const Ctl* ctl, double* const* udbufs, SecWork w) {
   const double* Ud = udbufs[ctl->ubuf];
   double* Un = udbufs[ctl->ubuf ^ 1];
   const long long total = (long long)(nd + 1) * keep;
-  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
-       L += (long long)gridDim.x * blockDim.x) {
+  // one warp per entry, lanes over the r terms (see k_core_m)
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwt = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long L = gw; L < total; L += nwt) {
     const int t = (int)(L / keep), c = (int)(L % keep);
     const double* u2 = w.U2 + (long long)c * (r + 1);
     double s;
     if (t < nd) {
       s = 0.0;
       const double* row = Ud + (long long)t * ldc;
-      for (int i = 0; i < r; ++i) s += row[i] * u2[i];
+      for (int i = lane; i < r; i += 32) s += row[i] * u2[i];
+      s = warp_sum(s);
     } else {
       s = u2[r];
     }
-    Un[(long long)t * ldc + c] = s;
+    if (lane == 0) Un[(long long)t * ldc + c] = s;
   }
 }
 
@@ -605,11 +621,17 @@ __global__ void k_core_m(const Ctl* ctl, double* const* udbufs, SecWork w, const
   const double* Ud = udbufs[ctl->ubuf];
   const double* Un = udbufs[ctl->ubuf ^ 1];
   const long long total = (long long)keep * r;
-  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
-       L += (long long)gridDim.x * blockDim.x) {
+  // one warp per entry of M: lanes split the sum over the n_d rows (FP64 is long-latency: a
+  // 32-way split and a tree replace a chain of n_d dependent FMAs)
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwt = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long L = gw; L < total; L += nwt) {
     const int a = (int)(L / r), b = (int)(L % r);   // M(a, b)
     double s = 0.0;
-    for (int t = 0; t < nd; ++t) s += Un[(long long)t * ldc + a] * Ud[(long long)t * ldc + b];
+    for (int t = lane; t < nd; t += 32) s += Un[(long long)t * ldc + a] * Ud[(long long)t * ldc + b];
+    s = warp_sum(s);
+    if (lane != 0) continue;
     Bc[(long long)b * ldb + a] = (TW)s;              // Bc(b, a) = M(a, b), row-major r x keep
     const double* col = w.V2 + (long long)a * m;
     double bv = col[b];
@@ -736,6 +758,52 @@ __global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, 
   }
 }
 
+// The small ISVD step run by the last block of the e pass (r <= ROWS_RMAX): the block loads p,
+// [s; ||e||^2], S and the ranks in parallel into shared memory (one round of loads instead of a
+// chain of dependent ones on one thread), warp 0 forms p' and the sums as warp reductions, then
+// thread 0 runs isvd_small_tail.
+__device__ void isvd_small_block(Ctl* ctl, const double* p, const double* es, const double* S,
+                                 const SecWork& w) {
+  __shared__ double sp_[ROWS_RMAX + 1], ses_[ROWS_RMAX + 2], sS_[ROWS_RMAX + 1], spq_[ROWS_RMAX + 2];
+  __shared__ int srk_[TK_MAXD];
+  __shared__ double seps_, sq2_, sq_, szr2_;
+  __shared__ int scap_;
+  const int d = ctl->d;
+  const int r = ctl->r[d - 1];
+  for (int i = threadIdx.x; i <= r; i += blockDim.x) {
+    ses_[i] = __ldcg(es + i);   // written by other blocks of the calling kernel
+    if (i < r) { sp_[i] = p[i]; sS_[i] = S[i]; }
+  }
+  if (threadIdx.x < d - 1) srk_[threadIdx.x] = ctl->r[threadIdx.x];
+  if (threadIdx.x == 32) { seps_ = ctl->eps; scap_ = ctl->cap[d - 1]; }
+  __syncthreads();
+  // warp 0: p' = p + s, ||s||^2, q'^2 and ||p'||^2 as warp sums (r <= 32: one entry per lane)
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const double sc = lane < r ? ses_[lane] : 0.0;
+    const double pc = lane < r ? sp_[lane] + sc : 0.0;
+    if (lane < r) { spq_[lane] = pc; w.pq[lane] = pc; }
+    const double s2 = warp_sum(sc * sc);
+    const double zr2 = warp_sum(pc * pc);
+    if (lane == 0) {
+      double q2 = ses_[r] - s2;
+      if (q2 < 0.0) q2 = 0.0;
+      const double q = sqrt(q2);
+      spq_[r] = q;
+      w.pq[r] = q;
+      sq2_ = q2;
+      sq_ = q;
+      szr2_ = zr2;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long Rn = 1;
+    for (int i = 0; i < d - 1; ++i) Rn *= srk_[i];
+    isvd_small_tail(ctl, sS_, w, spq_, r, sq2_, sq_, szr2_, Rn, seps_, scap_);
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Row passes with one row per lane (r_d <= 32). Each lane owns rows jn = g, g + G, ... of the new
 // spatial layout, maps each to its old row (zero padding has none), reads that row's r_d
@@ -746,6 +814,13 @@ __global__ void __launch_bounds__(256) k_cv_update(const Ctl* __restrict__ ctl, 
 // ---------------------------------------------------------------------------------------------
 constexpr int ROWS_NT = 256;
 constexpr int ROWS_FLUSH = 32;
+
+// The bulk-tile passes (below) take the update when the slice rows are FP32 work rows and no
+// spatial rank grew (old row j is new row j).
+__device__ __forceinline__ bool bulk_rows_ok(const Ctl* ctl) {
+  return ctl->tw == 4 && rows_isvd_ok(ctl) && !spatial_grew(ctl);
+}
+
 
 template <typename TW>
 __device__ __forceinline__ void load_row(const TW* __restrict__ row, int r, bool vec, TW (&v)[ROWS_RMAX]) {
@@ -816,6 +891,7 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_p_rows(Ctl* __restrict__ ctl,
                                                         double* __restrict__ pout) {
   if (ctl->status) return;
   if (!rows_isvd_ok(ctl)) return;
+  if (sizeof(TW) == 4 && bulk_rows_ok(ctl)) return;   // the bulk-tile pass ran
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
   const int ldc = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));
@@ -852,8 +928,8 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_p_rows(Ctl* __restrict__ ctl,
     if (++it == ROWS_FLUSH) { rows_flush<TW>(acc, sw[wid], lane, r); it = 0; }
   }
   rows_flush<TW>(acc, sw[wid], lane, r);
-  rows_block_sum(sw, r, part, TK_STREAM_CAP_MAX);
-  tk_last_block_reduce(part, TK_STREAM_CAP_MAX, r, pout, &ctl->ticket[0]);
+  rows_block_sum(sw, r, part, TK_STREAM_CAP_MAX);   // k_col_reduce finishes p
+  (void)pout;
 }
 
 // e = d - V_pad p (stored), ||e||^2 and s = V_pad^T e: partials in the layout of k_isvd_e
@@ -869,6 +945,7 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_e_rows(Ctl* __restrict__ ctl,
                                                         SecWork w) {
   if (ctl->status) return;
   if (!rows_isvd_ok(ctl)) return;
+  if (sizeof(TW) == 4 && bulk_rows_ok(ctl)) return;   // the bulk-tile pass ran
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
   const int ldc = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));
@@ -925,10 +1002,253 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_e_rows(Ctl* __restrict__ ctl,
   if (threadIdx.x < ROWS_NT / 32 && r < ROWS_RMAX) {
     sw[threadIdx.x][r] = sw[threadIdx.x][ROWS_RMAX];
   }
-  rows_block_sum(sw, r + 1, part, TK_STREAM_CAP_MAX + 2);
-  if (tk_last_block_reduce(part, TK_STREAM_CAP_MAX + 2, r + 1, es, &ctl->ticket[1]) &&
-      threadIdx.x == 0)
-    isvd_small_body(ctl, p, es, S, w);
+  rows_block_sum(sw, r + 1, part, TK_STREAM_CAP_MAX + 2);   // k_col_reduce finishes [s; ||e||^2]
+  (void)es; (void)S; (void)w;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Bulk-tile row passes: mixed form, streaming rank <= ROWS_RMAX, no spatial growth in this update
+// (old row j is new row j, so the rows of a tile are one contiguous range of V). Tiles of BR_NT
+// rows, one per thread, move into shared memory by 1D TMA bulk copies, BR_S stages deep (BR_S - 1
+// tiles in flight per block), and each thread reads its row there: V streams from global memory
+// at full sector efficiency whatever the row stride. The arithmetic and the FP32 -> FP64 flush
+// schedule are those of the lane-per-row passes above.
+// ---------------------------------------------------------------------------------------------
+constexpr int BR_NT = ROWS_NT;
+constexpr int BR_S = 3;
+constexpr int BR_TILE = BR_NT * ROWS_RMAX * 4;        // bytes of a tile at the largest row stride
+constexpr size_t BR_SMEM = (size_t)BR_S * BR_TILE + 128;
+
+struct BulkTiles {
+  const unsigned char* src;   // first row of V
+  unsigned char* sm;          // BR_S stages of BR_TILE bytes
+  uint64_t* full;             // BR_S mbarriers
+  long long R;                // rows
+  int rowbytes;               // row stride in bytes (a multiple of 16)
+  long long nmine;            // tiles of this block: blockIdx.x, blockIdx.x + gridDim.x, ...
+  __device__ void issue(long long i) const {
+    const long long row0 = (blockIdx.x + i * (long long)gridDim.x) * BR_NT;
+    const long long rows = R - row0 < BR_NT ? R - row0 : BR_NT;
+    const uint32_t bytes = (uint32_t)(rows * rowbytes);
+    const int st = (int)(i % BR_S);
+    tc::mbar_arrive_expect_tx(&full[st], bytes);
+    tc::bulk_load(sm + (size_t)st * BR_TILE, src + row0 * rowbytes, bytes, &full[st]);
+  }
+};
+
+// Set-up common to the bulk passes: barriers, tile counts, the first BR_S - 1 copies.
+__device__ __forceinline__ BulkTiles bulk_begin(const float* V, long long R, int s,
+                                                unsigned char* dyn, volatile int* abort) {
+  BulkTiles bt;
+  bt.sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
+  bt.full = reinterpret_cast<uint64_t*>(bt.sm + (size_t)BR_S * BR_TILE);
+  bt.src = reinterpret_cast<const unsigned char*>(V);
+  bt.R = R;
+  bt.rowbytes = s * 4;
+  const long long ntiles = (R + BR_NT - 1) / BR_NT;
+  bt.nmine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < BR_S; ++st) tc::mbar_init(&bt.full[st], 1);
+    *abort = 0;
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (long long i = 0; i < BR_S - 1 && i < bt.nmine; ++i) bt.issue(i);
+  return bt;
+}
+
+// After an aborted wait: thread 0 waits (bounded) for the copies still in flight, tiles
+// consumed .. issued - 1, so none lands after the block has exited.
+__device__ __forceinline__ void bulk_drain(const BulkTiles& bt, long long consumed) {
+  if (threadIdx.x != 0) return;
+  const long long issued = consumed + BR_S - 1 < bt.nmine ? consumed + BR_S - 1 : bt.nmine;
+  for (long long i = consumed; i < issued; ++i)
+    for (long long k = 0; k < tc::kWaitLimit; ++k)
+      if (tc::mbar_try_wait(&bt.full[i % BR_S], (uint32_t)((i / BR_S) & 1))) break;
+}
+
+// Adds the per-thread FP32 partials acc[c] (c < r) into the FP64 slots of the warp.
+template <int C>
+__device__ __forceinline__ void bulk_flush(float (&acc)[C], double* sw, int lane, int r) {
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    if (c < r) {
+      const float t = warp_sum(acc[c]);
+      if (lane == 0) sw[c] += (double)t;
+    }
+    acc[c] = 0.f;
+  }
+}
+
+// p = V^T d, S4 = row stride / 4.
+template <int S4>
+__device__ __forceinline__ long long isvd_p_tiles(const BulkTiles& bt, const float* __restrict__ dv,
+                                                  int r, double* sw, volatile int* abort) {
+  constexpr int C = 4 * S4;
+  float acc[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc[c] = 0.f;
+  const int tid = threadIdx.x, lane = tid & 31;
+  int it = 0;
+  long long i = 0;
+  for (; i < bt.nmine; ++i) {
+    if (tid == 0 && i + BR_S - 1 < bt.nmine) bt.issue(i + BR_S - 1);
+    const long long row = (blockIdx.x + i * (long long)gridDim.x) * BR_NT + tid;
+    const float dj = row < bt.R ? dv[row] : 0.f;
+    const int st = (int)(i % BR_S);
+    const bool ok = tc::mbar_wait(&bt.full[st], (uint32_t)((i / BR_S) & 1), abort);
+    if (ok && row < bt.R) {
+      const float4* rp = reinterpret_cast<const float4*>(bt.sm + (size_t)st * BR_TILE) + tid * S4;
+#pragma unroll
+      for (int q = 0; q < S4; ++q) {
+        const float4 v = rp[q];
+        acc[4 * q] = fmaf(v.x, dj, acc[4 * q]);
+        acc[4 * q + 1] = fmaf(v.y, dj, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(v.z, dj, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(v.w, dj, acc[4 * q + 3]);
+      }
+    }
+    if (++it == ROWS_FLUSH) { bulk_flush<C>(acc, sw, lane, r); it = 0; }
+    if (!__syncthreads_and(ok)) { ++i; break; }
+  }
+  bulk_flush<C>(acc, sw, lane, r);
+  return i;
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(BR_NT) k_isvd_p_bulk(Ctl* __restrict__ ctl, TW* const* dbufs,
+                                                      TW* const* vbufs, double* __restrict__ part,
+                                                      double* __restrict__ pout) {
+  if (ctl->status) return;
+  if (sizeof(TW) != 4 || !bulk_rows_ok(ctl)) return;
+  extern __shared__ __align__(128) unsigned char br_dyn[];
+  __shared__ double sw[ROWS_NT / 32][ROWS_RMAX + 1];
+  __shared__ int s_abort;
+  const int d = ctl->d, m = d - 1;
+  const int r = ctl->r[d - 1];
+  const int s = tk_cv_stride(r, ctl->ldc, 4);
+  long long R = 1;
+  for (int i = 0; i < m; ++i) R *= ctl->r[i];
+  const float* V = reinterpret_cast<const float*>(vbufs[ctl->cbuf]);
+  const float* dv = reinterpret_cast<const float*>(dbufs[ctl->xbuf]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = lane; c <= ROWS_RMAX; c += 32) sw[wid][c] = 0.0;
+  volatile int* abort = &s_abort;
+  const BulkTiles bt = bulk_begin(V, R, s, br_dyn, abort);
+  long long done = 0;
+  switch (s >> 2) {
+    case 1: done = isvd_p_tiles<1>(bt, dv, r, sw[wid], abort); break;
+    case 2: done = isvd_p_tiles<2>(bt, dv, r, sw[wid], abort); break;
+    case 3: done = isvd_p_tiles<3>(bt, dv, r, sw[wid], abort); break;
+    case 4: done = isvd_p_tiles<4>(bt, dv, r, sw[wid], abort); break;
+    case 5: done = isvd_p_tiles<5>(bt, dv, r, sw[wid], abort); break;
+    case 6: done = isvd_p_tiles<6>(bt, dv, r, sw[wid], abort); break;
+    case 7: done = isvd_p_tiles<7>(bt, dv, r, sw[wid], abort); break;
+    default: done = isvd_p_tiles<8>(bt, dv, r, sw[wid], abort); break;
+  }
+  if (*abort) {
+    bulk_drain(bt, done);
+    if (threadIdx.x == 0) ctl->status = TK_ETIMEOUT;
+  }
+  rows_block_sum(sw, r, part, TK_STREAM_CAP_MAX);   // k_col_reduce finishes p
+  (void)pout;
+}
+
+// e = d - V p (stored), ||e||^2 (compensated) and s = V^T e; the last block to finish then runs
+// the small ISVD step, as k_isvd_e_rows does.
+template <int S4>
+__device__ __forceinline__ long long isvd_e_tiles(const BulkTiles& bt, const float* __restrict__ dv,
+                                                  const float* pl, float* __restrict__ evec, int r,
+                                                  double* sw, KahanF& eacc, volatile int* abort) {
+  constexpr int C = 4 * S4;
+  float acc[C], pr[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) { acc[c] = 0.f; pr[c] = pl[c]; }
+  const int tid = threadIdx.x, lane = tid & 31;
+  int it = 0;
+  long long i = 0;
+  for (; i < bt.nmine; ++i) {
+    if (tid == 0 && i + BR_S - 1 < bt.nmine) bt.issue(i + BR_S - 1);
+    const long long row = (blockIdx.x + i * (long long)gridDim.x) * BR_NT + tid;
+    const float dj = row < bt.R ? dv[row] : 0.f;
+    const int st = (int)(i % BR_S);
+    const bool ok = tc::mbar_wait(&bt.full[st], (uint32_t)((i / BR_S) & 1), abort);
+    if (ok && row < bt.R) {
+      const float4* rp = reinterpret_cast<const float4*>(bt.sm + (size_t)st * BR_TILE) + tid * S4;
+      float v[C];
+#pragma unroll
+      for (int q = 0; q < S4; ++q) {
+        const float4 t = rp[q];
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+      }
+      // columns r.. of the last piece are not part of the state (possibly never written)
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] = c < r ? v[c] : 0.f;
+      float dot = 0.f;
+#pragma unroll
+      for (int c = 0; c < C; ++c) dot = fmaf(v[c], pr[c], dot);
+      const float e = dj - dot;
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = fmaf(v[c], e, acc[c]);
+      evec[row] = e;
+      eacc.add(e * e);
+    }
+    if (++it == ROWS_FLUSH) { bulk_flush<C>(acc, sw, lane, r); it = 0; }
+    if (!__syncthreads_and(ok)) { ++i; break; }
+  }
+  bulk_flush<C>(acc, sw, lane, r);
+  return i;
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(BR_NT) k_isvd_e_bulk(Ctl* __restrict__ ctl, TW* const* dbufs,
+                                                      TW* const* vbufs, const double* __restrict__ p,
+                                                      TW* __restrict__ evec, double* __restrict__ part,
+                                                      double* __restrict__ es,
+                                                      const double* __restrict__ S, SecWork w) {
+  if (ctl->status) return;
+  if (sizeof(TW) != 4 || !bulk_rows_ok(ctl)) return;
+  extern __shared__ __align__(128) unsigned char br_dyn[];
+  __shared__ double sw[ROWS_NT / 32][ROWS_RMAX + 1];
+  __shared__ float pl[ROWS_RMAX];
+  __shared__ int s_abort;
+  const int d = ctl->d, m = d - 1;
+  const int r = ctl->r[d - 1];
+  const int s = tk_cv_stride(r, ctl->ldc, 4);
+  long long R = 1;
+  for (int i = 0; i < m; ++i) R *= ctl->r[i];
+  const float* V = reinterpret_cast<const float*>(vbufs[ctl->cbuf]);
+  const float* dv = reinterpret_cast<const float*>(dbufs[ctl->xbuf]);
+  float* ev = reinterpret_cast<float*>(evec);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = lane; c <= ROWS_RMAX; c += 32) sw[wid][c] = 0.0;
+  if (threadIdx.x < ROWS_RMAX) pl[threadIdx.x] = threadIdx.x < r ? (float)p[threadIdx.x] : 0.f;
+  volatile int* abort = &s_abort;
+  const BulkTiles bt = bulk_begin(V, R, s, br_dyn, abort);   // barrier inside: pl is visible
+  KahanF eacc;
+  long long done = 0;
+  switch (s >> 2) {
+    case 1: done = isvd_e_tiles<1>(bt, dv, pl, ev, r, sw[wid], eacc, abort); break;
+    case 2: done = isvd_e_tiles<2>(bt, dv, pl, ev, r, sw[wid], eacc, abort); break;
+    case 3: done = isvd_e_tiles<3>(bt, dv, pl, ev, r, sw[wid], eacc, abort); break;
+    case 4: done = isvd_e_tiles<4>(bt, dv, pl, ev, r, sw[wid], eacc, abort); break;
+    case 5: done = isvd_e_tiles<5>(bt, dv, pl, ev, r, sw[wid], eacc, abort); break;
+    case 6: done = isvd_e_tiles<6>(bt, dv, pl, ev, r, sw[wid], eacc, abort); break;
+    case 7: done = isvd_e_tiles<7>(bt, dv, pl, ev, r, sw[wid], eacc, abort); break;
+    default: done = isvd_e_tiles<8>(bt, dv, pl, ev, r, sw[wid], eacc, abort); break;
+  }
+  if (*abort) {
+    bulk_drain(bt, done);
+    if (threadIdx.x == 0) ctl->status = TK_ETIMEOUT;
+  }
+  const double e2 = warp_sum(eacc.value());
+  if (lane == 0) sw[wid][ROWS_RMAX] = e2;
+  __syncthreads();
+  // ||e||^2 moves to column r (columns r.. of the slots hold zeros)
+  if (threadIdx.x < ROWS_NT / 32 && r < ROWS_RMAX) sw[threadIdx.x][r] = sw[threadIdx.x][ROWS_RMAX];
+  rows_block_sum(sw, r + 1, part, TK_STREAM_CAP_MAX + 2);   // k_col_reduce finishes [s; ||e||^2]
+  (void)es; (void)S; (void)w;
 }
 
 // C~ = C_pad B_c + d c_c^T (blockIdx.y = 0) and V~ = V_pad B_v + e w_v^T (blockIdx.y = 1), one
@@ -1013,44 +1333,58 @@ __global__ void __launch_bounds__(ROWS_NT) k_cv_rows(const Ctl* __restrict__ ctl
 // End of the update: S <- S~, ranks, n_d, buffers, error bookkeeping (Prop. 1, Prop. 2).
 __global__ void k_end_update(Ctl* ctl, const double* Snew, double* S) {
   if (ctl->status) return;
-  const int d = ctl->d;
-  const int keep = ctl->rnew_d;
-  for (int i = threadIdx.x; i < keep; i += blockDim.x) S[i] = Snew[i];
+  // the whole control block is copied to shared memory in one round of loads by all threads;
+  // thread 0 then reads it there (its updates go to global memory) instead of waiting on a
+  // chain of dependent global loads
+  __shared__ __align__(128) unsigned char cbuf_[sizeof(Ctl)];
+  static_assert(sizeof(Ctl) % 16 == 0, "control block copied in 16-byte words");
+  for (int i = threadIdx.x; i < (int)(sizeof(Ctl) / 16); i += blockDim.x)
+    reinterpret_cast<uint4*>(cbuf_)[i] = __ldcg(reinterpret_cast<const uint4*>(ctl) + i);
   __syncthreads();
+  const Ctl& c = *reinterpret_cast<const Ctl*>(cbuf_);
+  const int d = c.d;
+  const int keep = c.rnew_d;
+  for (int i = threadIdx.x; i < keep; i += blockDim.x) S[i] = Snew[i];
   if (threadIdx.x == 0) {
-    // algorithmic bytes of this update (each operand read or written once per pass)
-    const double tw = ctl->tw, tx = ctl->tx;
-    const int r = ctl->r[d - 1];
-    double Ro = 1.0, Rn = 1.0;
-    for (int k = 0; k < d - 1; ++k) { Ro *= ctl->rold[k]; Rn *= ctl->r[k]; }
-    double A = 1.0;
+    // algorithmic bytes of this update (each operand read or written once per pass), in integer
+    // arithmetic (FP64 operations are long-latency on this part and this is one thread)
+    const long long tw = c.tw, tx = c.tx;
+    const long long r = c.r[d - 1];
+    long long Ro = 1, Rn = 1;
+    for (int k = 0; k < d - 1; ++k) { Ro *= c.rold[k]; Rn *= c.r[k]; }
+    long long A = 1;
+    long long bp1 = 0, bpn = 0, bgr = 0;
     for (int k = 0; k < d - 1; ++k) {
-      double B = 1.0;
-      for (int i = k + 1; i < d - 1; ++i) B *= ctl->n[i];
-      const double in_el = A * ctl->n[k] * B;
-      const double in_b = (k == 0 ? tx : tw) * in_el;
-      const double p_b = tw * A * ctl->rold[k] * B;
-      ctl->acc_bytes[k == 0 ? TK_PH_PROJ1 : TK_PH_PROJN] += in_b + p_b;
-      if (ctl->grew[k]) ctl->acc_bytes[TK_PH_GROW] += 2.0 * in_b + p_b + tw * A * ctl->r[k] * B;
-      A *= ctl->r[k];
+      long long B = 1;
+      for (int i = k + 1; i < d - 1; ++i) B *= c.n[i];
+      const long long in_b = (k == 0 ? tx : tw) * A * c.n[k] * B;
+      const long long p_b = tw * A * c.rold[k] * B;
+      if (k == 0) bp1 += in_b + p_b; else bpn += in_b + p_b;
+      if (c.grew[k]) bgr += 2 * in_b + p_b + tw * A * c.r[k] * B;
+      A *= c.r[k];
     }
-    ctl->acc_bytes[TK_PH_ISVD] += tw * (2.0 * Ro * r + 3.0 * Rn);
-    ctl->acc_bytes[TK_PH_FACT] += 8.0 * 2.0 * ((double)ctl->nd * r + (double)(ctl->nd + 1) * keep);
-    ctl->acc_bytes[TK_PH_CV] += tw * (2.0 * Ro * r + 2.0 * Rn * keep + 2.0 * Rn);
+    const long long nd = c.nd;
+    ctl->acc_bytes[TK_PH_PROJ1] = c.acc_bytes[TK_PH_PROJ1] + (double)bp1;
+    ctl->acc_bytes[TK_PH_PROJN] = c.acc_bytes[TK_PH_PROJN] + (double)bpn;
+    ctl->acc_bytes[TK_PH_GROW] = c.acc_bytes[TK_PH_GROW] + (double)bgr;
+    ctl->acc_bytes[TK_PH_ISVD] = c.acc_bytes[TK_PH_ISVD] + (double)(tw * (2 * Ro * r + 3 * Rn));
+    ctl->acc_bytes[TK_PH_FACT] = c.acc_bytes[TK_PH_FACT] + (double)(16 * (nd * r + (nd + 1) * keep));
+    ctl->acc_bytes[TK_PH_CV] = c.acc_bytes[TK_PH_CV] + (double)(tw * (2 * Ro * r + 2 * Rn * keep + 2 * Rn));
+    // error bookkeeping (Prop. 1, Prop. 2, App. D): discarded energies of this update
     double disc = 0.0;
-    for (int k = 0; k < d - 1; ++k) disc += ctl->disc[k];
-    disc += ctl->aug ? 0.0 : ctl->q2;
-    disc += ctl->dropped;
-    ctl->err2 += disc;
-    ctl->data2 += ctl->y2;
+    for (int k = 0; k < d - 1; ++k) disc += c.disc[k];
+    disc += c.aug ? 0.0 : c.q2;
+    disc += c.dropped;
+    ctl->err2 = c.err2 + disc;
+    ctl->data2 = c.data2 + c.y2;
     // the tensor-core path after spatial growth expands into the other buffer and writes back
     // into this one; every other path writes the other buffer
-    const bool stay = tc_cv_ok(ctl, keep) && spatial_grew(ctl);
+    const bool stay = tc_cv_ok(&c, keep) && spatial_grew(&c);
     ctl->r[d - 1] = keep;
-    ctl->nd += 1;
-    if (!stay) ctl->cbuf ^= 1;
-    ctl->ubuf ^= 1;
-    ctl->nupdates += 1;
+    ctl->nd = c.nd + 1;
+    if (!stay) ctl->cbuf = c.cbuf ^ 1;
+    ctl->ubuf = c.ubuf ^ 1;
+    ctl->nupdates = c.nupdates + 1;
   }
 }
 
@@ -1074,16 +1408,68 @@ __global__ void k_begin_update(Ctl* ctl) {
 // ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
+// Cross-block sums of the lane-per-row and bulk-tile passes (streaming rank <= ROWS_RMAX; the
+// SIMT passes sum in their own last block): out[c] = sum over blocks b < nb of part[b stride + c]
+// for c < len, one block per column, every partial loaded in one round, added in a fixed order
+// (per-thread, then warp, then block). which = 1 (the e pass, len = r + 1): the last block to
+// finish then runs the small ISVD step.
+constexpr int CR_NT = 256;
+__global__ void __launch_bounds__(CR_NT) k_col_reduce(Ctl* __restrict__ ctl, const double* __restrict__ part,
+                                                     long long stride, int nb, double* __restrict__ out,
+                                                     int which, const double* __restrict__ p,
+                                                     const double* __restrict__ S, SecWork w) {
+  if (ctl->status) return;
+  if (!rows_isvd_ok(ctl)) return;
+  const int r = ctl->r[ctl->d - 1];
+  const int len = which ? r + 1 : r;
+  const int c = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ double red[CR_NT / 32];
+  if (c < len) {
+    double a0 = 0.0, a1 = 0.0;
+    int b = threadIdx.x;
+    for (; b + CR_NT < nb; b += 2 * CR_NT) {
+      a0 += __ldcg(part + (long long)b * stride + c);
+      a1 += __ldcg(part + (long long)(b + CR_NT) * stride + c);
+    }
+    if (b < nb) a0 += __ldcg(part + (long long)b * stride + c);
+    const double t = warp_sum(a0 + a1);
+    if (lane == 0) red[wid] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double u = 0.0;
+#pragma unroll
+      for (int i = 0; i < CR_NT / 32; ++i) u += red[i];
+      out[c] = u;
+    }
+  }
+  if (which && tk_block_ticket(&ctl->ticket[2])) isvd_small_block(ctl, p, out, S, w);
+}
+
 template <typename TW>
 cudaError_t launch_isvd(Ctl* ctl, void* const* dbufs, void* const* vbufs, double* part_p,
                         double* part_e, double* p, double* es, void* evec, const double* S,
                         SecWork w, int grid, cudaStream_t st) {
   // p = V^T d, then e = d - V p with [s; ||e||^2] and the small ISVD bookkeeping; each pass
-  // finishes its cross-block sum in its last block
+  // finishes its cross-block sum in its last block. Exactly one of the bulk-tile, lane-per-row
+  // and SIMT kernels of each pass does the work (device-side conditions).
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_isvd_p_bulk<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM);
+    cudaFuncSetAttribute(k_isvd_e_bulk<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM);
+    attr = true;
+  }
+  if (sizeof(TW) == 4)
+    k_isvd_p_bulk<TW><<<grid, BR_NT, BR_SMEM, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p, p);
   k_isvd_p_rows<TW><<<grid, ROWS_NT, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p, p);
   k_isvd_p<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p, p);
+  k_col_reduce<<<ROWS_RMAX + 1, CR_NT, 0, st>>>(ctl, part_p, TK_STREAM_CAP_MAX, grid, p, 0, nullptr, nullptr, w);
+  if (sizeof(TW) == 4)
+    k_isvd_e_bulk<TW><<<grid, BR_NT, BR_SMEM, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p,
+                                                    (TW*)evec, part_e, es, S, w);
   k_isvd_e_rows<TW><<<grid, ROWS_NT, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p,
                                                (TW*)evec, part_e, es, S, w);
+  k_col_reduce<<<ROWS_RMAX + 1, CR_NT, 0, st>>>(ctl, part_e, TK_STREAM_CAP_MAX + 2, grid, es, 1, p, S, w);
   k_isvd_e<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p, (TW*)evec,
                                      part_e, es, S, w);
   k_secular_roots<<<(TK_STREAM_CAP_MAX + 1 + SEC_WARPS - 1) / SEC_WARPS, 32 * SEC_WARPS, 0, st>>>(ctl, w);

@@ -942,36 +942,56 @@ __global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ct
   if (threadIdx.x == 0 && *abort) const_cast<Ctl*>(ctl)->status = 5;
 }
 
-// G (n_k x n_k, FP64, column-major) = sum over the K splits of the partial blocks, in split
-// order. Entry (i, j) is read as partial (j, i) (consecutive threads, consecutive i: contiguous)
-// except in the block rows < 128, columns >= 128 of G's lower-left mirror, which only block 0
-// holds (as (i, j)).
-__global__ void k_syrk_reduce(const Ctl* ctl, int k, const float* gpart, int S, double* G) {
+// G (n_k x n_k, FP64, column-major) = sum over the K splits of the partial blocks. Block: 32
+// consecutive entries of G (lanes) x 8 warps; warp w sums the splits w, w + 8, ... in FP64 and
+// the 8 warp sums are added in warp order (a fixed summation order). Entry (i, j) is read as
+// partial (j, i) (consecutive lanes, consecutive i: contiguous) except in the block rows < 128,
+// columns >= 128 of G's lower-left mirror, which only block 0 holds (as (i, j)).
+constexpr int SR_W = 8;
+__global__ void __launch_bounds__(32 * SR_W) k_syrk_reduce(const Ctl* ctl, int k, const float* gpart,
+                                                          int S, double* G) {
   if (ctl->status) return;
   if (!tc_gram_ok(ctl, k)) return;
   const int n1 = ctl->n[k];
   const int n1p = (n1 + 15) / 16 * 16;
   const long long plane = (long long)n1p * n1p;
-  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < (long long)n1 * n1;
-       L += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ double red[SR_W][33];
+  const long long L = (long long)blockIdx.x * 32 + lane;
+  const bool live = L < (long long)n1 * n1;
+  double acc = 0.0;
+  long long off = 0;
+  if (live) {
     const int i = (int)(L % n1), j = (int)(L / n1);
     const bool direct = (j < TC_M) || (i >= TC_M);
-    const long long off = direct ? (long long)j * n1p + i : (long long)i * n1p + j;
-    double acc = 0.0;
-    for (int sp = 0; sp < S; ++sp) acc += (double)gpart[sp * plane + off];
-    G[(long long)j * n1 + i] = acc;
+    off = direct ? (long long)j * n1p + i : (long long)i * n1p + j;
+    double a0 = 0.0, a1 = 0.0;
+    int sp = wid;
+    for (; sp + SR_W < S; sp += 2 * SR_W) {
+      a0 += (double)gpart[sp * plane + off];
+      a1 += (double)gpart[(sp + SR_W) * plane + off];
+    }
+    if (sp < S) a0 += (double)gpart[sp * plane + off];
+    acc = a0 + a1;
+  }
+  red[wid][lane] = acc;
+  __syncthreads();
+  if (wid == 0 && live) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < SR_W; ++w) t += red[w][lane];
+    G[L] = t;   // L = j n1 + i: column-major
   }
 }
 
 cudaError_t launch_tc_gram(const Ctl* ctl, int k, const TcProjMaps& m, int n1, double* gpart,
                            double* G, int nsm, cudaStream_t st) {
-  (void)n1;
   const int S = nsm > 0 ? nsm : 1;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_tc_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM); attr = true; }
   float* gp = reinterpret_cast<float*>(gpart);
   k_tc_syrk<<<S, TS_NT, TS_SMEM, st>>>(ctl, k, m.eta, gp);
-  k_syrk_reduce<<<144, 256, 0, st>>>(ctl, k, gp, S, G);
+  k_syrk_reduce<<<(n1 * n1 + 31) / 32, 32 * SR_W, 0, st>>>(ctl, k, gp, S, G);
   return cudaGetLastError();
 }
 
