@@ -948,6 +948,7 @@ __global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ct
 // partial (j, i) (consecutive lanes, consecutive i: contiguous) except in the block rows < 128,
 // columns >= 128 of G's lower-left mirror, which only block 0 holds (as (i, j)).
 constexpr int SR_W = 8;
+constexpr int SR_SMAX = 160;   // K splits (grid of k_tc_syrk) at most
 __global__ void __launch_bounds__(32 * SR_W) k_syrk_reduce(const Ctl* ctl, int k, const float* gpart,
                                                           int S, double* G) {
   if (ctl->status) return;
@@ -965,13 +966,19 @@ __global__ void __launch_bounds__(32 * SR_W) k_syrk_reduce(const Ctl* ctl, int k
     const int i = (int)(L % n1), j = (int)(L / n1);
     const bool direct = (j < TC_M) || (i >= TC_M);
     off = direct ? (long long)j * n1p + i : (long long)i * n1p + j;
-    double a0 = 0.0, a1 = 0.0;
-    int sp = wid;
-    for (; sp + SR_W < S; sp += 2 * SR_W) {
-      a0 += (double)gpart[sp * plane + off];
-      a1 += (double)gpart[(sp + SR_W) * plane + off];
+    // every partial of this warp's splits is loaded before the first add (one round of L2
+    // latency rather than one per split)
+    constexpr int PER = (SR_SMAX + SR_W - 1) / SR_W;
+    float v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int sp = wid + u * SR_W;
+      v[u] = sp < S ? gpart[sp * plane + off] : 0.f;
     }
-    if (sp < S) a0 += (double)gpart[sp * plane + off];
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int u = 0; u + 1 < PER; u += 2) { a0 += (double)v[u]; a1 += (double)v[u + 1]; }
+    if (PER & 1) a0 += (double)v[PER - 1];
     acc = a0 + a1;
   }
   red[wid][lane] = acc;
@@ -986,7 +993,7 @@ __global__ void __launch_bounds__(32 * SR_W) k_syrk_reduce(const Ctl* ctl, int k
 
 cudaError_t launch_tc_gram(const Ctl* ctl, int k, const TcProjMaps& m, int n1, double* gpart,
                            double* G, int nsm, cudaStream_t st) {
-  const int S = nsm > 0 ? nsm : 1;
+  const int S = nsm > 0 ? (nsm < SR_SMAX ? nsm : SR_SMAX) : 1;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(k_tc_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM); attr = true; }
   float* gp = reinterpret_cast<float*>(gpart);
