@@ -312,12 +312,25 @@ __global__ void __launch_bounds__(256) k_isvd_e(Ctl* __restrict__ ctl, TW* const
 // ---------------------------------------------------------------------------------------------
 
 
+// 1/x in FP64 from the FP32 reciprocal refined by two Newton steps r <- r + r (1 - x r) (each
+// doubles the correct bits: ~2^-24 -> 2^-48 -> below FP64 rounding); about half the latency of an
+// FP64 division on this GPU. Outside the normal FP32 range it divides.
+__device__ __forceinline__ double drcp(double x) {
+  const float xf = (float)x;
+  const float ax = fabsf(xf);
+  if (!(ax > 1e-36f && ax < 1e36f)) return 1.0 / x;
+  double r = (double)__frcp_rn(xf);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
 __device__ double sec_f(const double* delta, const double* z, int mk, double dorg, double tau,
                         double* fp, int lane) {
   double f = 0.0, g = 0.0;
   for (int i = lane; i < mk; i += 32) {
     const double den = (delta[i] - dorg) - tau;
-    const double t = z[i] / den;
+    const double t = z[i] * drcp(den);
     f += z[i] * t;
     g += t * t;
   }
@@ -333,10 +346,11 @@ __device__ __forceinline__ float sec_f32(const float* df, const float* zf2, int 
                                          float* fp, int lane) {
   float f = 0.f, g = 0.f;
   for (int i = lane; i < mk; i += 32) {
-    const float den = df[i] - t;
-    const float q = zf2[i] / den;
+    // fast reciprocal: the FP32 search only seeds the FP64 polish (scaled data, |den| <= ~1)
+    const float rd = __fdividef(1.f, df[i] - t);
+    const float q = zf2[i] * rd;
     f += q;
-    g += q / den;
+    g += q * rd;
   }
   f = warp_sum(f);
   g = warp_sum(g);
@@ -392,7 +406,7 @@ __global__ void __launch_bounds__(32 * SEC_WARPS) k_secular_roots(const Ctl* ctl
     const float f = sec_f32(s_df[wl], s_z2[wl], mk, t, &gp, lane);
     if (f == 0.f) break;
     if (f > 0.f) hf = t; else lf = t;
-    float tn = t - f / gp;
+    float tn = t - __fdividef(f, gp);
     if (!(tn > lf && tn < hf)) tn = 0.5f * (lf + hf);
     if (hf - lf <= 4.f * 5.9604645e-08f * fmaxf(fabsf(lf), fabsf(hf)) ||
         fabsf(tn - t) <= 2.f * 5.9604645e-08f * fabsf(t)) { t = tn; break; }
@@ -405,7 +419,7 @@ __global__ void __launch_bounds__(32 * SEC_WARPS) k_secular_roots(const Ctl* ctl
     const double f = sec_f(w.delta, w.z, mk, dorg, tau, &fp, lane);
     if (f == 0.0) break;
     if (f > 0.0) hi = tau; else lo = tau;
-    double tn = tau - f / fp;
+    double tn = tau - f * drcp(fp);
     if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
     const double width = hi - lo;
     if (width <= 4.0 * 1.1102230246251565e-16 * fmax(fabs(lo), fabs(hi)) ||

@@ -356,7 +356,13 @@ namespace tk {
 //         per-block partials; WRITE_ET: E^T (n_k x Fs, row stride Fs) for the residual Gram.
 // =============================================================================================
 constexpr int TP_STAGE = 48 * 1024;                // X hi | X lo | U chunk hi | U chunk lo
-constexpr int TP_S = 2;
+// stages: 2 when the residual runs (the resident U rows for MMA2 and the Y buffers take 128 KB),
+// 4 for the re-projection (pass C), which needs neither
+template <bool RESID> struct TpCfg {
+  static constexpr int S = RESID ? 2 : 4;
+  static constexpr size_t B2 = RESID ? 128 * 1024 : 0;
+  static constexpr size_t SMEM = (size_t)S * TP_STAGE + B2 + 1024 + 256;
+};
 constexpr int TP_PF = 12;                           // X chunks prefetched into L2 ahead
 // warps: 0 TMA producer, 1 MMA issuer, 2 .. 2+TP_SPLIT_WARPS-1 TF32 splitters of the X chunks,
 // then 4 epilogue warps (TMEM lane quarter = warp % 4, so the first is a multiple of 4)
@@ -364,7 +370,6 @@ constexpr int TP_SPLIT_WARPS = 6;
 constexpr int TP_EPI_W0 = 2 + TP_SPLIT_WARPS;
 constexpr int TP_NT = 32 * (TP_EPI_W0 + 4);
 static_assert(TP_EPI_W0 % 4 == 0, "epilogue warps must start at a TMEM lane quarter boundary");
-constexpr size_t TP_SMEM = (size_t)TP_S * TP_STAGE + 128 * 1024 + 1024 + 256;
 
 struct TcProjArgs {
   const CUtensorMap* mYg;   // slice descriptor in the control block (graph form), else NULL
@@ -410,9 +415,10 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
   extern __shared__ __align__(1024) unsigned char psm_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(psm_raw) + 1023) & ~uintptr_t(1023));
-  float* B2hi = reinterpret_cast<float*>(base + TP_S * TP_STAGE);   // [Kc2][n1p][32]
+  constexpr int TP_S = TpCfg<RESID>::S;
+  float* B2hi = reinterpret_cast<float*>(base + TP_S * TP_STAGE);   // [Kc2][n1p][32] (RESID)
   float* B2lo = B2hi + (size_t)Kc2 * n1p * TC_KC;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TP_S * TP_STAGE + 128 * 1024);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TP_S * TP_STAGE + TpCfg<RESID>::B2);
   uint64_t* full = bars;
   uint64_t* conv = bars + TP_S;
   uint64_t* empty = bars + 2 * TP_S;
@@ -760,14 +766,14 @@ cudaError_t launch_tc_proj(const Ctl* ctl, int k, int mode, int pred, const floa
   TcProjArgs a{mYg, (float* const*)dbufs, out_off, part_e2, part_y2, nparts, Y, Et, et_stride, k};
   static bool attr[3] = {false, false, false};
   if (mode == 0) {
-    if (!attr[0]) { cudaFuncSetAttribute(k_tc_proj<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[0] = true; }
-    k_tc_proj<false, false><<<grid, TP_NT, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
+    if (!attr[0]) { cudaFuncSetAttribute(k_tc_proj<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TpCfg<false>::SMEM); attr[0] = true; }
+    k_tc_proj<false, false><<<grid, TP_NT, TpCfg<false>::SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
   } else if (mode == 1) {
-    if (!attr[1]) { cudaFuncSetAttribute(k_tc_proj<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[1] = true; }
-    k_tc_proj<true, false><<<grid, TP_NT, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
+    if (!attr[1]) { cudaFuncSetAttribute(k_tc_proj<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TpCfg<true>::SMEM); attr[1] = true; }
+    k_tc_proj<true, false><<<grid, TP_NT, TpCfg<true>::SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
   } else {
-    if (!attr[2]) { cudaFuncSetAttribute(k_tc_proj<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TP_SMEM); attr[2] = true; }
-    k_tc_proj<true, true><<<grid, TP_NT, TP_SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
+    if (!attr[2]) { cudaFuncSetAttribute(k_tc_proj<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TpCfg<true>::SMEM); attr[2] = true; }
+    k_tc_proj<true, true><<<grid, TP_NT, TpCfg<true>::SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.uhi, m.ulo, m.urhi, m.urlo, a);
   }
   return cudaGetLastError();
 }
