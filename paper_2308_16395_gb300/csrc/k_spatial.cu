@@ -196,17 +196,32 @@ __global__ void k_decide(Ctl* ctl, int k, const double* part_e2, const double* p
   se = block_sum(se, red);
   sy = block_sum(sy, red);
   if (threadIdx.x == 0) {
+    // Alg. 4: skip if ||E_k|| <= eps, taken as ||E_k||^2 <= eps^2 (eps^2 = tau^2 ||Y||^2 / d) so
+    // that the branch does not wait on square roots and a division (FP64 is long-latency here)
+    double eps2;
     if (k == 0) {
-      ctl->y2 = sy;
-      if (!isfinite(sy)) { ctl->status = TK_ENUMERIC; return; }
-      ctl->eps = ctl->tau * sqrt(sy) / sqrt((double)ctl->d);
+      if (!isfinite(sy)) {
+        ctl->y2 = sy;
+        ctl->status = TK_ENUMERIC;
+        if (hcond) cudaGraphSetConditional(hcond, 0u);
+        return;
+      }
+      const double tau = ctl->tau;
+      eps2 = tau * tau * sy * (1.0 / (double)ctl->d);
+    } else {
+      const double e = ctl->eps;
+      eps2 = e * e;
     }
+    const int g = se > eps2 ? 1 : 0;
+    if (hcond) cudaGraphSetConditional(hcond, g ? 1u : 0u);
     ctl->e2[k] = se;
-    const int g = sqrt(se) > ctl->eps ? 1 : 0;   // Alg. 4: skip if ||E_k|| <= eps
     ctl->grew[k] = g;
     ctl->radd[k] = 0;
     ctl->disc[k] = g ? 0.0 : se;
-    if (hcond) cudaGraphSetConditional(hcond, g ? 1u : 0u);
+    if (k == 0) {
+      ctl->y2 = sy;
+      ctl->eps = ctl->tau * sqrt(sy) / sqrt((double)ctl->d);
+    }
   }
 }
 

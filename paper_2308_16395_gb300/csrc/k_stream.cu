@@ -497,20 +497,33 @@ __global__ void __launch_bounds__(1024) k_secular_vectors(Ctl* ctl, const double
     order[rank] = a;
   }
   __syncthreads();
-  if (tid == 0) {
-    // numerical rank of the compact SVD: keep lambda > (r+1) u lambda_max, at most #columns
+  {
+    // numerical rank of the compact SVD: keep lambda > (r+1) u lambda_max (a count over the
+    // sorted eigenvalues, which are descending, so the kept ones come first), the rest dropped;
+    // count and dropped energy by block reductions in a fixed order (FP64 is long-latency: no
+    // serial loop on one thread)
     const double lmax = m > 0 ? lam_all[order[0]] : 0.0;
     const double thr = (double)(r + 1) * 1.1102230246251565e-16 * lmax;
-    int keep = 0;
     double drop = 0.0;
-    for (int k = 0; k < m; ++k) {
-      const double l = lam_all[order[k]];
-      if (keep < m && l > thr && lmax > 0.0) ++keep; else drop += fmax(l, 0.0);
+    int kept = 0;
+    if (tid < m) {
+      const double l = lam_all[order[tid]];
+      if (l > thr && lmax > 0.0) kept = 1; else drop = fmax(l, 0.0);
     }
-    s_keep = keep;
-    w.meta[2] = keep;
-    ctl->rnew_d = keep;
-    ctl->dropped = drop;
+    const int keep = __syncthreads_count(kept);
+    __shared__ double s_drop[32];
+    const int lane = tid & 31, wid = tid >> 5;
+    drop = warp_sum(drop);
+    if (lane == 0) s_drop[wid] = drop;
+    __syncthreads();
+    if (tid == 0) {
+      double dsum = 0.0;
+      for (int i = 0; i < (nt >> 5); ++i) dsum += s_drop[i];
+      s_keep = keep;
+      w.meta[2] = keep;
+      ctl->rnew_d = keep;
+      ctl->dropped = dsum;
+    }
   }
   __syncthreads();
   const int keep = s_keep;
@@ -543,8 +556,8 @@ __global__ void __launch_bounds__(1024) k_secular_vectors(Ctl* ctl, const double
           const double v = col[w.idx[i]];
           nrm += v * v;
         }
-        nrm = sqrt(warp_sum(nrm));
-        for (int i = lane; i < mk; i += 32) col[w.idx[i]] /= nrm;
+        const double inv = drcp(sqrt(warp_sum(nrm)));
+        for (int i = lane; i < mk; i += 32) col[w.idx[i]] *= inv;
       } else if (lane == 0) {
         col[-src - 1] = 1.0;
       }
@@ -565,20 +578,27 @@ __global__ void __launch_bounds__(1024) k_secular_vectors(Ctl* ctl, const double
     }
   }
   __syncthreads();
-  // U'' = S' V'' / sigma: rows 0..r-1: S_i V''(i,k); row r: p'^T V''(0:r,k) + q' V''(r,k)
-  for (long long L = tid; L < (long long)(r + 1) * keep; L += nt) {
-    const int k = (int)(L / (r + 1)), i = (int)(L % (r + 1));
+  // U'' = S' V'' / sigma: rows 0..r-1: S_i V''(i,k); row r: p'^T V''(0:r,k) + q' V''(r,k) (one
+  // warp per column k, lanes over the r terms)
+  for (long long L = tid; L < (long long)r * keep; L += nt) {
+    const int k = (int)(L / r), i = (int)(L % r);
     const double* col = w.V2 + (long long)k * m;
-    double val;
-    if (i < r) {
-      val = S[i] * col[i];
-    } else {
-      val = 0.0;
-      for (int c = 0; c < r; ++c) val += w.pq[c] * col[c];
-      if (aug) val += w.pq[r] * col[r];
-    }
     const double sig = w.sv[k];
-    w.U2[(long long)k * (r + 1) + i] = sig > 0.0 ? val / sig : 0.0;
+    w.U2[(long long)k * (r + 1) + i] = sig > 0.0 ? S[i] * col[i] * drcp(sig) : 0.0;
+  }
+  {
+    const int lane = tid & 31, nwarp = nt >> 5;
+    for (int k = tid >> 5; k < keep; k += nwarp) {
+      const double* col = w.V2 + (long long)k * m;
+      double val = 0.0;
+      for (int c = lane; c < r; c += 32) val += w.pq[c] * col[c];
+      val = warp_sum(val);
+      if (lane == 0) {
+        if (aug) val += w.pq[r] * col[r];
+        const double sig = w.sv[k];
+        w.U2[(long long)k * (r + 1) + r] = sig > 0.0 ? val * drcp(sig) : 0.0;
+      }
+    }
   }
 }
 
