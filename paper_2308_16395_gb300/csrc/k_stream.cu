@@ -615,23 +615,40 @@ __global__ void k_ud_update(const Ctl* ctl, double* const* udbufs, SecWork w) {
   const double* Ud = udbufs[ctl->ubuf];
   double* Un = udbufs[ctl->ubuf ^ 1];
   const long long total = (long long)(nd + 1) * keep;
-  // one warp per entry, lanes over the r terms (see k_core_m)
-  const int lane = threadIdx.x & 31;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwt = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long L = gw; L < total; L += nwt) {
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  if (total * 32 <= nthr) {
+    // few entries (short streams): one warp per entry, lanes over the r terms (see k_core_m)
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (long long L = gw; L < total; L += nthr >> 5) {
+      const int t = (int)(L / keep), c = (int)(L % keep);
+      const double* u2 = w.U2 + (long long)c * (r + 1);
+      double s;
+      if (t < nd) {
+        s = 0.0;
+        const double* row = Ud + (long long)t * ldc;
+        for (int i = lane; i < r; i += 32) s += row[i] * u2[i];
+        s = warp_sum(s);
+      } else {
+        s = u2[r];
+      }
+      if (lane == 0) Un[(long long)t * ldc + c] = s;
+    }
+    return;
+  }
+  // many entries (long streams, n_d large): one thread per entry
+  for (long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x; L < total; L += nthr) {
     const int t = (int)(L / keep), c = (int)(L % keep);
     const double* u2 = w.U2 + (long long)c * (r + 1);
     double s;
     if (t < nd) {
       s = 0.0;
       const double* row = Ud + (long long)t * ldc;
-      for (int i = lane; i < r; i += 32) s += row[i] * u2[i];
-      s = warp_sum(s);
+      for (int i = 0; i < r; ++i) s += row[i] * u2[i];
     } else {
       s = u2[r];
     }
-    if (lane == 0) Un[(long long)t * ldc + c] = s;
+    Un[(long long)t * ldc + c] = s;
   }
 }
 
