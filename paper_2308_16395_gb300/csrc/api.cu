@@ -578,6 +578,8 @@ template <typename TX, typename TW, typename TE>
 tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
   const int d = s->d;
   long long launches = 0;
+  // (an IF node costs more than the empty launch of a predicated kernel on this GPU, so only the
+  // 11-kernel growth chains below are conditional nodes)
   CK(launch_begin(s->ctl, st));
   launches += 1;
   for (int k = 0; k < d - 1; ++k) {

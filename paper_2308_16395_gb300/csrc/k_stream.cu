@@ -936,7 +936,7 @@ __device__ __forceinline__ void rows_block_sum(double (*sw)[ROWS_RMAX + 1], int 
 // p = V_pad^T d: partials per block in the layout of k_isvd_p. Warps walk 32 consecutive new
 // rows at a time (a warp-uniform loop, so the periodic FP64 flush is a warp reduction).
 template <typename TW>
-__global__ void __launch_bounds__(ROWS_NT) k_isvd_p_rows(Ctl* __restrict__ ctl,
+__device__ __forceinline__ void isvd_p_rows(Ctl* __restrict__ ctl,
                                                         TW* const* dbufs, TW* const* vbufs,
                                                         double* __restrict__ part,
                                                         double* __restrict__ pout) {
@@ -986,7 +986,7 @@ __global__ void __launch_bounds__(ROWS_NT) k_isvd_p_rows(Ctl* __restrict__ ctl,
 // e = d - V_pad p (stored), ||e||^2 and s = V_pad^T e: partials in the layout of k_isvd_e
 // (s in columns 0..r-1, ||e||^2 in column r).
 template <typename TW>
-__global__ void __launch_bounds__(ROWS_NT) k_isvd_e_rows(Ctl* __restrict__ ctl,
+__device__ __forceinline__ void isvd_e_rows(Ctl* __restrict__ ctl,
                                                         TW* const* dbufs, TW* const* vbufs,
                                                         const double* __restrict__ p,
                                                         TW* __restrict__ evec,
@@ -1168,7 +1168,7 @@ __device__ __forceinline__ long long isvd_p_tiles(const BulkTiles& bt, const flo
 }
 
 template <typename TW>
-__global__ void __launch_bounds__(BR_NT) k_isvd_p_bulk(Ctl* __restrict__ ctl, TW* const* dbufs,
+__device__ __forceinline__ void isvd_p_bulk(Ctl* __restrict__ ctl, TW* const* dbufs,
                                                       TW* const* vbufs, double* __restrict__ part,
                                                       double* __restrict__ pout) {
   if (ctl->status) return;
@@ -1253,7 +1253,7 @@ __device__ __forceinline__ long long isvd_e_tiles(const BulkTiles& bt, const flo
 }
 
 template <typename TW>
-__global__ void __launch_bounds__(BR_NT) k_isvd_e_bulk(Ctl* __restrict__ ctl, TW* const* dbufs,
+__device__ __forceinline__ void isvd_e_bulk(Ctl* __restrict__ ctl, TW* const* dbufs,
                                                       TW* const* vbufs, const double* __restrict__ p,
                                                       TW* __restrict__ evec, double* __restrict__ part,
                                                       double* __restrict__ es,
@@ -1459,6 +1459,30 @@ __global__ void k_begin_update(Ctl* ctl) {
 // ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
+// One launch for the bulk-tile and lane-per-row bodies of each pass, chosen on the device (one
+// kernel node instead of two in the update graph); both take 256 threads and the pass's grid.
+// The SIMT pass (streaming rank above ROWS_RMAX) stays a kernel of its own: its shared tiles
+// would leave this launch one block per SM.
+template <typename TW>
+__global__ void __launch_bounds__(256) k_isvd_p_all(Ctl* __restrict__ ctl, TW* const* dbufs,
+                                                   TW* const* vbufs, double* __restrict__ part,
+                                                   double* __restrict__ pout) {
+  if (ctl->status) return;
+  if (sizeof(TW) == 4 && bulk_rows_ok(ctl)) isvd_p_bulk<TW>(ctl, dbufs, vbufs, part, pout);
+  else if (rows_isvd_ok(ctl)) isvd_p_rows<TW>(ctl, dbufs, vbufs, part, pout);
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(256) k_isvd_e_all(Ctl* __restrict__ ctl, TW* const* dbufs,
+                                                   TW* const* vbufs, const double* __restrict__ p,
+                                                   TW* __restrict__ evec, double* __restrict__ part,
+                                                   double* __restrict__ es,
+                                                   const double* __restrict__ S, SecWork w) {
+  if (ctl->status) return;
+  if (sizeof(TW) == 4 && bulk_rows_ok(ctl)) isvd_e_bulk<TW>(ctl, dbufs, vbufs, p, evec, part, es, S, w);
+  else if (rows_isvd_ok(ctl)) isvd_e_rows<TW>(ctl, dbufs, vbufs, p, evec, part, es, S, w);
+}
+
 // Cross-block sums of the lane-per-row and bulk-tile passes (streaming rank <= ROWS_RMAX; the
 // SIMT passes sum in their own last block): out[c] = sum over blocks b < nb of part[b stride + c]
 // for c < len, one block per column, every partial loaded in one round, added in a fixed order
@@ -1504,25 +1528,22 @@ cudaError_t launch_isvd(Ctl* ctl, void* const* dbufs, void* const* vbufs, double
   // p = V^T d, then e = d - V p with [s; ||e||^2] and the small ISVD bookkeeping; each pass
   // finishes its cross-block sum in its last block. Exactly one of the bulk-tile, lane-per-row
   // and SIMT kernels of each pass does the work (device-side conditions).
+  // dynamic shared memory: the bulk-tile stages (FP32 work type only)
+  const size_t dyn = sizeof(TW) == 4 ? BR_SMEM : 0;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_isvd_p_bulk<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM);
-    cudaFuncSetAttribute(k_isvd_e_bulk<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM);
+    cudaFuncSetAttribute(k_isvd_p_all<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM);
+    cudaFuncSetAttribute(k_isvd_e_all<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM);
     attr = true;
   }
-  if (sizeof(TW) == 4)
-    k_isvd_p_bulk<TW><<<grid, BR_NT, BR_SMEM, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p, p);
-  k_isvd_p_rows<TW><<<grid, ROWS_NT, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p, p);
+  k_isvd_p_all<TW><<<grid, 256, dyn, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p, p);
   k_isvd_p<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, part_p, p);
   k_col_reduce<<<ROWS_RMAX + 1, CR_NT, 0, st>>>(ctl, part_p, TK_STREAM_CAP_MAX, grid, p, 0, nullptr, nullptr, w);
-  if (sizeof(TW) == 4)
-    k_isvd_e_bulk<TW><<<grid, BR_NT, BR_SMEM, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p,
-                                                    (TW*)evec, part_e, es, S, w);
-  k_isvd_e_rows<TW><<<grid, ROWS_NT, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p,
-                                               (TW*)evec, part_e, es, S, w);
-  k_col_reduce<<<ROWS_RMAX + 1, CR_NT, 0, st>>>(ctl, part_e, TK_STREAM_CAP_MAX + 2, grid, es, 1, p, S, w);
+  k_isvd_e_all<TW><<<grid, 256, dyn, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p,
+                                           (TW*)evec, part_e, es, S, w);
   k_isvd_e<TW><<<grid, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW* const*)vbufs, p, (TW*)evec,
                                      part_e, es, S, w);
+  k_col_reduce<<<ROWS_RMAX + 1, CR_NT, 0, st>>>(ctl, part_e, TK_STREAM_CAP_MAX + 2, grid, es, 1, p, S, w);
   k_secular_roots<<<(TK_STREAM_CAP_MAX + 1 + SEC_WARPS - 1) / SEC_WARPS, 32 * SEC_WARPS, 0, st>>>(ctl, w);
   return cudaGetLastError();
 }
