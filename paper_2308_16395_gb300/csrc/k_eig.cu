@@ -57,14 +57,19 @@ __device__ void sturm_countN(const TE* __restrict__ a, const TE* __restrict__ b2
 // Householder tridiagonalization of an FP32 Gram matrix held in registers (n <= 192), one CTA of
 // NW = 12 warps run before the eigensolver (24 warps measured slower: every warp repeats the
 // reflector and w computations). Thread (warp w, lane l) owns A(w + NW a, l + 32b) for a < RA,
-// b < CB. Step c: every warp forms reflector c (LAPACK convention H = I - tau v v^T,
-// v_0 = 1) from column c in shared memory; p = tau A22 v is reduced across a warp's lanes by a
-// butterfly that halves the rows a lane carries at each level (RA rows cost RA shuffles rather
-// than 5 RA); after one barrier every warp forms w = p - (tau/2)(p^T v) v itself, applies
-// A22 -= v w^T + w v^T to its registers and the owners of column c+1 publish it; second barrier.
-// The step body is instantiated per first live column block CB0 = (c+1)/32, so blocks of rows
-// and columns left of the trailing matrix drop out at compile time and the loops carry no
-// branches; entries outside the trailing matrix are masked by selects.
+// b < CB. LAPACK convention: reflector c is H = I - tau v v^T with v_{c+1} = 1, p = tau A22 v,
+// w = p - (tau/2)(p^T v) v, A22 -= v w^T + w v^T (Golub & Van Loan, Sec. 8.3.1).
+// Look-ahead order, one barrier per step: the rank-2 update of step c-1 is applied in step c,
+// fused with the matrix-vector product of step c (update an entry, then multiply it by v_c).
+// Column c of A after step c-1 is rebuilt by every warp from the published column c of A after
+// step c-2 and the vectors of step c-1 (A(:,c) - v w_c - w v_c, v_c = 1), so the column never
+// waits for the update: after the barrier of step c-1 a warp reads p_{c-1}, forms w_{c-1} at
+// its columns, then column c, reflector c, and runs the fused loop. p of one step, v of one step
+// and the published columns alternate between two buffers. p = tau A22 v is reduced across a
+// warp's lanes by a butterfly that halves the rows a lane carries at each level (RA rows cost
+// RA shuffles rather than 5 RA). The step body is instantiated per column block CB0 = c / 32, so
+// blocks of rows and columns left of the trailing matrix drop out at compile time; entries
+// outside it are masked by selects.
 // Output: reflector c in V[c n + c + 1 ...] (zeros elsewhere in the n x n block); tri = [diagonal
 // (n), off-diagonal (n), tau (n)].
 constexpr int TRI_NMAX = 192;   // largest n of the register kernel (12 warps x 16 rows)
@@ -79,11 +84,12 @@ __device__ __forceinline__ float sel_f32(bool p, float x, float y) {
   return r;
 }
 
+// Two buffers of SZ floats each, buffer c & 1 for step c (base + (c & 1) SZ: a run-time index
+// into an array of pointers would put the array in local memory).
 struct TriSmem {
-  float* sx0;
-  float* sx1;
-  float* svp;    // v of the current step, row-permuted (see tri_perm)
-  float* swp;    // p = tau A22 v, row-permuted
+  float* scol;   // column c of A after step c-2, natural row order
+  float* svp;    // v of step c, row-permuted (see tri_perm)
+  float* swp;    // p = tau A22 v of step c, row-permuted
   float* sa;
   float* sb;
   float* stau;
@@ -99,34 +105,68 @@ __device__ __forceinline__ int tri_perm(int i) { return (i % NW) * RA + i / NW; 
 // round-to-nearest in each half) per two entries.
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 
+// Loop-carried vectors of the previous step at the thread's columns.
+template <int CB> struct TriPrev {
+  float v[CB];   // v_{c-1}
+  float tau;     // tau_{c-1}
+};
+
+// w_{c-1} = p_{c-1} - (tau_{c-1}/2)(p_{c-1}^T v_{c-1}) v_{c-1} at the thread's columns (blocks
+// >= B0); returns the scalar -(tau/2) p^T v. p and v vanish outside the trailing matrix of step
+// c-1 (rows >= n included), so no mask is needed.
+template <int NW, int RA, int CB, int B0>
+__device__ __forceinline__ float tri_w(const TriPrev<CB>& pr, const float* pp, int n, int lane,
+                                       float (&wc)[CB]) {
+  float pc[CB];
+  float pv = 0.f;
+#pragma unroll
+  for (int b = B0; b < CB; ++b) {
+    const int j = lane + 32 * b;
+    pc[b] = j < n ? pp[tri_perm<NW, RA>(j)] : 0.f;
+    pv = fmaf(pc[b], pr.v[b], pv);
+  }
+  const float K = -0.5f * pr.tau * warp_sum(pv);
+#pragma unroll
+  for (int b = B0; b < CB; ++b) wc[b] = fmaf(K, pr.v[b], pc[b]);
+  return K;
+}
+
 template <int NW, int RA, int CB, int CB0>
-__device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], int c, int n, int lane, int wid,
-                                         float* V, const TriSmem& sm) {
+__device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], TriPrev<CB>& pr, int c, int n,
+                                         int lane, int wid, float* V, const TriSmem& sm) {
   constexpr int LOGRA = RA == 16 ? 4 : RA == 8 ? 3 : RA == 4 ? 2 : RA == 2 ? 1 : 0;
-  // row blocks a whose rows w + 12a all lie left of column 32 CB0 - 1 <= c are dead; pairs
-  // start at an even row block (a dead row in a live pair is updated by zero and never stored)
-  constexpr int A0 = CB0 == 0 ? 0 : (32 * CB0 - NW) / NW + 1;
+  // rows <= c are not needed after step c and c >= 32 CB0: row blocks a whose rows w + NW a are
+  // all <= 32 CB0 are dead; pairs start at an even row block (a dead row in a live pair is
+  // updated and multiplied harmlessly, and its p entry is stored as zero)
+  constexpr int A0 = 32 * CB0 >= NW - 1 ? (32 * CB0 - NW + 1) / NW + 1 : 0;
   constexpr int H0 = A0 / 2;
-  const float* x = (c & 1) ? sm.sx1 : sm.sx0;
-  float* xn = (c & 1) ? sm.sx0 : sm.sx1;
-  // reflector from x = A(c+1:n, c); the same in every warp (same inputs and reduction order)
+  constexpr int SZ = NW * RA + 32;
+  const int par = (c & 1) * SZ, prv = SZ - par;
+  // w_{c-1} at the thread's columns (the barrier of step c-1 published p_{c-1})
+  float wc[CB];
+  const float K = tri_w<NW, RA, CB, CB0>(pr, sm.swp + prv, n, lane, wc);
+  const float wcc = __shfl_sync(0xffffffffu, wc[CB0], c & 31);   // w_{c-1}(c); column c in CB0
+  // column c of A after step c-1: A(:,c) - v w(c) - w v(c), v(c) = 1
+  const float* col = sm.scol + par;
   float xc[CB];
   float part = 0.f;
 #pragma unroll
   for (int b = CB0; b < CB; ++b) {
     const int j = lane + 32 * b;
-    xc[b] = x[j];
+    xc[b] = fmaf(-pr.v[b], wcc, col[j]) - wc[b];
     part += sel_f32(j >= c + 2 && j < n, xc[b] * xc[b], 0.f);
   }
   const float xn2 = warp_sum(part);
-  const float alpha = x[c + 1];
+  float asrc = xc[CB0];
+  if constexpr (CB0 + 1 < CB) asrc = sel_f32(((c + 1) >> 5) != CB0, xc[CB0 + 1], asrc);
+  const float alpha = __shfl_sync(0xffffffffu, asrc, (c + 1) & 31);
   float tau = 0.f, scal = 0.f, beta = alpha;
   if (xn2 != 0.f) {
     beta = -copysignf(sqrtf(alpha * alpha + xn2), alpha);
     tau = __fdividef(beta - alpha, beta);
     scal = __fdividef(1.f, alpha - beta);
   }
-  // tau = 0 leaves v = e_1 and p = w = 0: the step is an exact no-op
+  // tau = 0 leaves v = e_{c+1} and p = w = 0: step c is an exact no-op
   float vc[CB];
 #pragma unroll
   for (int b = CB0; b < CB; ++b) {
@@ -134,21 +174,34 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], int c, int n,
     vc[b] = sel_f32(j == c + 1, 1.f, sel_f32(j > c + 1 && j < n, xc[b] * scal, 0.f));
   }
   if (wid == 0) {
-    if (lane == 0) { sm.stau[c] = tau; sm.sb[c] = beta; }
+    if (lane == 0) { sm.stau[c] = tau; sm.sb[c] = beta; sm.sa[c] = col[c] - 2.f * wcc; }
 #pragma unroll
     for (int b = 0; b < CB; ++b) {
       const int j = lane + 32 * b;
       if (b >= CB0 && j > c && j < n) V[(long long)c * n + j] = vc[b];
-      if (j < n) sm.svp[tri_perm<NW, RA>(j)] = b >= CB0 ? vc[b] : 0.f;
+      if (j < n) sm.svp[par + tri_perm<NW, RA>(j)] = b >= CB0 ? vc[b] : 0.f;
     }
   }
+  // fused: A22 -= v_{c-1} w_{c-1}^T + w_{c-1} v_{c-1}^T, then p = A22 v_c
+  float wn[CB], vn[CB], vv[CB];
+#pragma unroll
+  for (int b = CB0; b < CB; ++b) { wn[b] = -wc[b]; vn[b] = -pr.v[b]; vv[b] = vc[b]; }
+  const float2* v2p = reinterpret_cast<const float2*>(sm.svp + prv + wid * RA);
+  const float2* p2p = reinterpret_cast<const float2*>(sm.swp + prv + wid * RA);
+  const float2 K2 = f2(K, K);
   float acc[RA];
 #pragma unroll
   for (int h = 0; h < RA / 2; ++h) {
     float2 s2 = f2(0.f, 0.f);
     if (h >= H0) {
+      const float2 vi = v2p[h];
+      const float2 wi = __ffma2_rn(K2, vi, p2p[h]);
 #pragma unroll
-      for (int b = CB0; b < CB; ++b) s2 = __ffma2_rn(a2[h][b], f2(vc[b], vc[b]), s2);
+      for (int b = CB0; b < CB; ++b) {
+        const float2 a = __ffma2_rn(vi, f2(wn[b], wn[b]), __ffma2_rn(wi, f2(vn[b], vn[b]), a2[h][b]));
+        a2[h][b] = a;
+        s2 = __ffma2_rn(a, f2(vv[b], vv[b]), s2);
+      }
     }
     acc[2 * h] = s2.x;
     acc[2 * h + 1] = s2.y;
@@ -172,62 +225,36 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], int c, int n,
     const int my_a = lane >> (5 - LOGRA);
     const bool writer = (lane & ((1 << (5 - LOGRA)) - 1)) == 0;
     const int i = wid + NW * my_a;
-    if (writer && i < n) sm.swp[wid * RA + my_a] = (i > c) ? tau * acc[0] : 0.f;
+    if (writer && i < n) sm.swp[par + wid * RA + my_a] = (i > c) ? tau * acc[0] : 0.f;
   }
-  __syncthreads();
-  // w = p - (tau/2)(p^T v) v, again the same in every warp
-  float swc[CB];
-  float pv = 0.f;
-#pragma unroll
-  for (int b = CB0; b < CB; ++b) {
-    const int j = lane + 32 * b;
-    swc[b] = j < n ? sm.swp[tri_perm<NW, RA>(j)] : 0.f;
-    pv += sel_f32(j > c && j < n, swc[b] * vc[b], 0.f);
-  }
-  pv = warp_sum(pv);
-  const float K = -0.5f * tau * pv;
-  float wn[CB], vn[CB];   // -w and -v at the thread's columns
-#pragma unroll
-  for (int b = CB0; b < CB; ++b) {
-    const int j = lane + 32 * b;
-    wn[b] = -sel_f32(j > c && j < n, swc[b] + K * vc[b], 0.f);
-    vn[b] = -vc[b];
-  }
-  // rows: v and p of the warp's rows as pairs (zero at dead rows and rows >= n), w = p + K v
-  const float2* v2p = reinterpret_cast<const float2*>(sm.svp + wid * RA);
-  const float2* p2p = reinterpret_cast<const float2*>(sm.swp + wid * RA);
-  const float2 K2 = f2(K, K);
-#pragma unroll
-  for (int h = H0; h < RA / 2; ++h) {
-    const float2 vi = v2p[h];
-    const float2 wi = __ffma2_rn(K2, vi, p2p[h]);
-#pragma unroll
-    for (int b = CB0; b < CB; ++b)
-      a2[h][b] = __ffma2_rn(vi, f2(wn[b], wn[b]), __ffma2_rn(wi, f2(vn[b], vn[b]), a2[h][b]));
-  }
-  // column c+1 (block CB0) from its owners
+  // publish column c+1 of A after step c-1 (rows >= c+1 all lie in live pairs; other rows of
+  // the buffer are never read)
   if (lane == ((c + 1) & 31)) {
+    float* nc = sm.scol + prv;
 #pragma unroll
-    for (int h = H0; h < RA / 2; ++h)
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int i = wid + NW * (2 * h + e);
-        const float val = e ? a2[h][CB0].y : a2[h][CB0].x;
-        if (i == c + 1) sm.sa[c + 1] = val;
-        else if (i > c + 1 && i < n) xn[i] = val;
+    for (int h = H0; h < RA / 2; ++h) {
+      float2 val = a2[h][CB0];
+      if constexpr (CB0 + 1 < CB) {
+        const bool hi = ((c + 1) >> 5) != CB0;
+        val = f2(sel_f32(hi, a2[h][CB0 + 1].x, val.x), sel_f32(hi, a2[h][CB0 + 1].y, val.y));
       }
+      nc[wid + NW * (2 * h)] = val.x;
+      nc[wid + NW * (2 * h + 1)] = val.y;
+    }
   }
+#pragma unroll
+  for (int b = CB0; b < CB; ++b) pr.v[b] = vc[b];
+  pr.tau = tau;
   __syncthreads();
 }
 
 template <int NW, int RA, int CB, int CB0>
-__device__ __forceinline__ void tri_steps(float2 (&a2)[RA / 2][CB], int n, int lane, int wid,
-                                          float* V, const TriSmem& sm) {
-  // steps whose next column c+1 lies in block CB0
-  const int c_lo = CB0 == 0 ? 0 : 32 * CB0 - 1;
-  const int c_hi = min(32 * CB0 + 30, n - 3);
-  for (int c = c_lo; c <= c_hi; ++c) tri_step<NW, RA, CB, CB0>(a2, c, n, lane, wid, V, sm);
-  if constexpr (CB0 + 1 < CB) tri_steps<NW, RA, CB, CB0 + 1>(a2, n, lane, wid, V, sm);
+__device__ __forceinline__ void tri_steps(float2 (&a2)[RA / 2][CB], TriPrev<CB>& pr, int n,
+                                          int lane, int wid, float* V, const TriSmem& sm) {
+  // steps c = 32 CB0 .. 32 CB0 + 31 (reflectors exist for c <= n - 3)
+  const int c_hi = min(32 * CB0 + 31, n - 3);
+  for (int c = 32 * CB0; c <= c_hi; ++c) tri_step<NW, RA, CB, CB0>(a2, pr, c, n, lane, wid, V, sm);
+  if constexpr (CB0 + 1 < CB) tri_steps<NW, RA, CB, CB0 + 1>(a2, pr, n, lane, wid, V, sm);
 }
 
 template <int NW, int RA, int CB>
@@ -242,11 +269,15 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int SZ = NW * RA + 32;
   static_assert(SZ > 32 * CB, "shared vectors must cover every column index");
-  __shared__ float sx[2][SZ];
-  __shared__ __align__(16) float svp[SZ];
-  __shared__ __align__(16) float swp[SZ];
+  __shared__ float scol[2][SZ];
+  __shared__ __align__(16) float svp[2][SZ];
+  __shared__ __align__(16) float swp[2][SZ];
   __shared__ float sa[SZ], sb[SZ], stau[SZ];
-  for (int i = tid; i < SZ; i += blockDim.x) { sx[0][i] = 0.f; sx[1][i] = 0.f; svp[i] = 0.f; swp[i] = 0.f; }
+  for (int i = tid; i < SZ; i += blockDim.x) {
+    scol[0][i] = 0.f; scol[1][i] = 0.f;
+    svp[0][i] = 0.f; svp[1][i] = 0.f;
+    swp[0][i] = 0.f; swp[1][i] = 0.f;
+  }
   // the reflector block starts as zeros: entries above each reflector's leading 1 and the
   // columns n-2, n-1 (no reflector) then read as zero (the steps write rows c+1.. of column c)
   for (int L = tid; L < n * n; L += blockDim.x) V[L] = 0.f;
@@ -260,22 +291,23 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
                     (i1 < n && j < n) ? (float)G[(long long)i1 * n + j] : 0.f);
     }
   __syncthreads();
-  // column 0
+  // column 0 (step -1 is empty: v, p, tau start at zero)
   if (lane == 0) {
 #pragma unroll
-    for (int h = 0; h < RA / 2; ++h)
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int i = wid + NW * (2 * h + e);
-        const float val = e ? a2[h][0].y : a2[h][0].x;
-        if (i == 0) sa[0] = val;
-        else if (i < n) sx[0][i] = val;
-      }
+    for (int h = 0; h < RA / 2; ++h) {
+      scol[0][wid + NW * (2 * h)] = a2[h][0].x;
+      scol[0][wid + NW * (2 * h + 1)] = a2[h][0].y;
+    }
   }
   __syncthreads();
-  const TriSmem sm{sx[0], sx[1], svp, swp, sa, sb, stau};
-  tri_steps<NW, RA, CB, 0>(a2, n, lane, wid, V, sm);
-  // trailing entries: column n-2 is in buffer (n-2)&1; A(n-1, n-1) with its owner
+  const TriSmem sm{&scol[0][0], &svp[0][0], &swp[0][0], sa, sb, stau};
+  TriPrev<CB> pr;
+#pragma unroll
+  for (int b = 0; b < CB; ++b) pr.v[b] = 0.f;
+  pr.tau = 0.f;
+  tri_steps<NW, RA, CB, 0>(a2, pr, n, lane, wid, V, sm);
+  // trailing 2 x 2 block after step n-3, whose update was deferred: registers hold A after step
+  // n-4, scol[(n-2) & 1] column n-2 of it. A(n-1, n-1) goes through shared memory first.
   if (lane == ((n - 1) & 31) && wid == (n - 1) % NW) {
     const int a0 = (n - 1) / NW, b0 = (n - 1) >> 5;
     float v = 0.f;
@@ -288,9 +320,30 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
       }
     sa[n - 1] = v;
   }
-  if (tid == 0) {
-    if (n >= 2) { sb[n - 2] = sx[(n - 2) & 1][n - 1]; stau[n - 2] = 0.f; }
-    stau[n - 1] = 0.f;
+  __syncthreads();
+  if (wid == 0 && n >= 2) {
+    const int c = n - 2;
+    float wc[CB];
+    tri_w<NW, RA, CB, 0>(pr, swp[(c + 1) & 1], n, lane, wc);
+    // w_{n-3} and v_{n-3} at rows n-2 and n-1, by run-time block selection and shuffles
+    float w0 = 0.f, w1 = 0.f, v1 = 0.f;
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      w0 = sel_f32(b == (c >> 5), wc[b], w0);
+      w1 = sel_f32(b == ((c + 1) >> 5), wc[b], w1);
+      v1 = sel_f32(b == ((c + 1) >> 5), pr.v[b], v1);
+    }
+    w0 = __shfl_sync(0xffffffffu, w0, c & 31);
+    w1 = __shfl_sync(0xffffffffu, w1, (c + 1) & 31);
+    v1 = __shfl_sync(0xffffffffu, v1, (c + 1) & 31);
+    if (lane == 0) {
+      const float* col = scol[c & 1];
+      sa[c] = col[c] - 2.f * w0;
+      sb[c] = col[c + 1] - v1 * w0 - w1;
+      stau[c] = 0.f;
+      sa[c + 1] -= 2.f * v1 * w1;
+      stau[c + 1] = 0.f;
+    }
   }
   __syncthreads();
   for (int i = tid; i < n; i += blockDim.x) {
