@@ -349,9 +349,14 @@ namespace tk {
 //   MMA1  P[f, :] = X[f, :] U_k (K = n_k), 3xTF32, X tiles by TMA, U_k chunks (TF32 hi/lo)
 //         streamed with them; P accumulates in TMEM.
 //   epi-1 P -> global, column-major (F x r_k) (the next mode's input); P split in place into
-//         TF32 hi (TMEM cols 0..63) and lo (cols 64..127).
+//         TF32 hi (TMEM cols 0..63 of its buffer) and lo (cols 64..127).
 //   MMA2  (RESID) Rec = P U_k^T with A = P read from tensor memory, B = U_k rows resident in
-//         shared memory, 3xTF32; Rec in TMEM cols 128..128+n_k.
+//         shared memory, 3xTF32; Rec in TMEM cols 256..256+n_k.
+// P has two TMEM buffers (tile t in buffer t & 1, cols 128 (t & 1) ..): MMA1 of tile t+1 runs
+// while the epilogue reads P of tile t, and MMA2 of tile t is issued between the chunk MMAs of
+// tile t+1 as soon as the epilogue has stored P's split (the tensor pipe runs MMAs in issue
+// order). Barriers that complete once per tile and are waited for across a tile boundary
+// (d1full, pready, mma2done) have one instance per buffer, so a phase is never two ahead.
 //   epi-2 (RESID) E = X - Rec with X re-read (L2-resident), ||E||^2 (and ||Y||^2 for k = 0) as
 //         per-block partials; WRITE_ET: E^T (n_k x Fs, row stride Fs) for the residual Gram.
 // =============================================================================================
@@ -422,12 +427,12 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
   uint64_t* full = bars;
   uint64_t* conv = bars + TP_S;
   uint64_t* empty = bars + 2 * TP_S;
-  uint64_t* d1full = bars + 3 * TP_S;
-  uint64_t* pready = d1full + 1;
-  uint64_t* d2full = pready + 1;
+  uint64_t* d1full = bars + 3 * TP_S;              // [2] per P buffer
+  uint64_t* pready = d1full + 2;                   // [2]
+  uint64_t* d2full = pready + 2;
   uint64_t* d2free = d2full + 1;
-  uint64_t* mma2done = d2free + 1;
-  uint64_t* bload = mma2done + 1;
+  uint64_t* mma2done = d2free + 1;                 // [2]
+  uint64_t* bload = mma2done + 2;
   uint64_t* done = bload + 1;
   uint64_t* ybar = done + 1;                       // [2] Y chunk loaded (residual epilogue)
   uint64_t* yfree = ybar + 2;                      // [2] Y chunk consumed by the 4 epilogue warps
@@ -442,11 +447,13 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
       mbar_init(&conv[s], 32 * TP_SPLIT_WARPS);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(d1full, 1);
-    mbar_init(pready, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&d1full[b], 1);
+      mbar_init(&pready[b], 128);
+      mbar_init(&mma2done[b], 1);
+    }
     mbar_init(d2full, 1);
     mbar_init(d2free, 128);
-    mbar_init(mma2done, 1);
     mbar_init(bload, 1);
     mbar_init(done, 1);
     mbar_init(&ybar[0], 1);
@@ -464,7 +471,7 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tD1 = tmem, tDlo = tmem + 64, tD2 = tmem + 128;
+  const uint32_t tD2 = tmem + 256;   // P buffers at tmem + 128 b (hi) and + 64 (lo)
 
   if (warp == 0) {
     if (lane == 0) {
@@ -517,15 +524,40 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
       const uint32_t id1 = idesc_tf32(TC_M, Rp);
       const uint32_t id2 = idesc_tf32(TC_M, n1p);
       bool ok = RESID ? wait_bar(bload, 0, abort) : true;
+      // MMA2 of tile jt: Rec = P U_k^T into D2 once the epilogue has stored P's split and has
+      // read D2 of tile jt - 1 (it did so before it stored P of tile jt)
+      auto mma2 = [&](int jt) -> bool {
+        const uint32_t pb = (uint32_t)((jt >> 1) & 1);
+        if (!wait_bar(&pready[jt & 1], pb, abort)) return false;
+        if (!wait_bar(d2free, (uint32_t)((jt & 1) ^ 1), abort)) return false;
+        tc_fence_after();
+        const uint32_t tA = tmem + 128u * (uint32_t)(jt & 1);
+        for (int k8 = 0; k8 < Rp / 8; ++k8) {
+          const int kc = k8 >> 2;
+          const uint64_t o = (uint64_t)((k8 & 3) * 32) >> 4;
+          const uint64_t bhi = desc_sw128(B2hi + (size_t)kc * n1p * TC_KC) + o;
+          const uint64_t blo = desc_sw128(B2lo + (size_t)kc * n1p * TC_KC) + o;
+          mma_tf32_ts(tD2, tA + 8 * k8, bhi, id2, k8 ? 1u : 0u);
+          mma_tf32_ts(tD2, tA + 8 * k8, blo, id2, 1u);
+          mma_tf32_ts(tD2, tA + 64 + 8 * k8, bhi, id2, 1u);
+        }
+        tc_commit(d2full);
+        tc_commit(&mma2done[jt & 1]);
+        return true;
+      };
       long long q = 0;
       int it = 0;
+      int pend = -1;   // tile whose MMA2 is not issued yet (RESID)
       for (long long t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++it) {
-        // D1 may be overwritten once the previous tile's P was consumed
-        if (it > 0) {
-          if (RESID) ok = wait_bar(mma2done, (uint32_t)((it - 1) & 1), abort);
-          else ok = wait_bar(pready, (uint32_t)((it - 1) & 1), abort);
-          if (!ok) break;
-        }
+        const int b = it & 1;
+        const uint32_t tD1 = tmem + 128u * (uint32_t)b;
+        // P buffer b is free once tile it - 2 is done with it: its MMA2 completed (RESID,
+        // issued by the end of tile it - 1), else its epi-1 read it. First uses pass at once.
+        const uint32_t fpar = (uint32_t)(((it >> 1) & 1) ^ 1);
+        if (RESID) ok = wait_bar(&mma2done[b], fpar, abort);
+        else ok = wait_bar(&pready[b], fpar, abort);
+        if (!ok) break;
+        tc_fence_after();
         for (int kc = 0; kc < Kc1; ++kc, ++q) {
           const int s = (int)(q % TP_S);
           if (!wait_bar(&conv[s], (uint32_t)((q / TP_S) & 1), abort)) { ok = false; break; }
@@ -541,26 +573,20 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
             mma_tf32(tD1, alo + o, bhi + o, id1, 1u);
           }
           tc_commit(&empty[s]);
+          // the pending MMA2 goes in as soon as its P split is stored
+          if (RESID && pend >= 0 && mbar_try_wait(&pready[pend & 1], (uint32_t)((pend >> 1) & 1))) {
+            if (!mma2(pend)) { ok = false; break; }
+            pend = -1;
+          }
         }
         if (!ok) break;
-        tc_commit(d1full);
+        tc_commit(&d1full[b]);
         if (RESID) {
-          if (!wait_bar(pready, (uint32_t)(it & 1), abort)) break;
-          if (!wait_bar(d2free, (uint32_t)((it & 1) ^ 1), abort)) break;
-          tc_fence_after();
-          for (int k8 = 0; k8 < Rp / 8; ++k8) {
-            const int kc = k8 >> 2;
-            const uint64_t o = (uint64_t)((k8 & 3) * 32) >> 4;
-            const uint64_t bhi = desc_sw128(B2hi + (size_t)kc * n1p * TC_KC) + o;
-            const uint64_t blo = desc_sw128(B2lo + (size_t)kc * n1p * TC_KC) + o;
-            mma_tf32_ts(tD2, tD1 + 8 * k8, bhi, id2, k8 ? 1u : 0u);
-            mma_tf32_ts(tD2, tD1 + 8 * k8, blo, id2, 1u);
-            mma_tf32_ts(tD2, tDlo + 8 * k8, bhi, id2, 1u);
-          }
-          tc_commit(d2full);
-          tc_commit(mma2done);
+          if (pend >= 0 && !mma2(pend)) break;
+          pend = it;
         }
       }
+      if (RESID && ok && pend >= 0) mma2(pend);
       tc_commit(done);
       wait_bar(done, 0, abort);
     }
@@ -617,7 +643,8 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
         if (issue_y(t, 0, yq) && nck > 1) issue_y(t, 1, yq + 1);
       }
       __syncwarp();
-      bool okw = wait_bar(d1full, (uint32_t)(it & 1), abort);
+      const uint32_t tD1 = tmem + 128u * (uint32_t)(it & 1), tDlo = tD1 + 64;
+      bool okw = wait_bar(&d1full[it & 1], (uint32_t)((it >> 1) & 1), abort);
       okw = __all_sync(0xffffffffu, okw);
       if (!okw) break;
       tc_fence_after();
@@ -641,7 +668,7 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
         }
       }
       tc_fence_before();
-      mbar_arrive(pready);
+      mbar_arrive(&pready[it & 1]);
       if (RESID) {
         okw = wait_bar(d2full, (uint32_t)(it & 1), abort);
         okw = __all_sync(0xffffffffu, okw);
