@@ -370,10 +370,12 @@ template <bool RESID> struct TpCfg {
 };
 constexpr int TP_PF = 12;                           // X chunks prefetched into L2 ahead
 // warps: 0 TMA producer, 1 MMA issuer, 2 .. 2+TP_SPLIT_WARPS-1 TF32 splitters of the X chunks,
-// then 4 epilogue warps (TMEM lane quarter = warp % 4, so the first is a multiple of 4)
+// then 4 warps for epilogue 1 (P) and 4 for epilogue 2 (the residual), so that epilogue 1 of
+// tile t+1 runs while epilogue 2 of tile t waits for its reloaded X (TMEM lane quarter =
+// warp % 4, so each group starts at a multiple of 4)
 constexpr int TP_SPLIT_WARPS = 6;
 constexpr int TP_EPI_W0 = 2 + TP_SPLIT_WARPS;
-constexpr int TP_NT = 32 * (TP_EPI_W0 + 4);
+constexpr int TP_NT = 32 * (TP_EPI_W0 + 8);
 static_assert(TP_EPI_W0 % 4 == 0, "epilogue warps must start at a TMEM lane quarter boundary");
 
 struct TcProjArgs {
@@ -616,15 +618,48 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
       }
     }
   } else if (warp >= TP_EPI_W0 && warp < TP_EPI_W0 + 4) {
-    // ---------------- epilogue ----------------
+    // ---------------- epilogue 1: P ----------------
     const int wq = warp - TP_EPI_W0;   // TMEM lane quarter (warp % 4)
     const uint32_t lq = (uint32_t)(wq * 32) << 16;
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const uint32_t tD1 = tmem + 128u * (uint32_t)(it & 1), tDlo = tD1 + 64;
+      bool okw = wait_bar(&d1full[it & 1], (uint32_t)((it >> 1) & 1), abort);
+      okw = __all_sync(0xffffffffu, okw);
+      if (!okw) break;
+      tc_fence_after();
+      const long long f = t * TC_M + wq * 32 + lane;
+      const bool live = f < F;
+      for (int c0 = 0; c0 < Rp; c0 += 32) {
+        float v[32];
+        tmem_ld32(tD1 + lq + c0, v);
+        if (live && !WRITE_ET) {
+          // column-major (F x r): consecutive threads write consecutive addresses
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (c0 + i < r) P[f + F * (c0 + i)] = v[i];
+        }
+        if (RESID) {
+          float l[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) tf32_split(v[i], v[i], l[i]);
+          tmem_st32(tD1 + lq + c0, v);
+          tmem_st32(tDlo + lq + c0, l);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&pready[it & 1]);
+    }
+  } else if (RESID && warp >= TP_EPI_W0 + 4) {
+    // ---------------- epilogue 2: E = X - Rec, norms ----------------
+    const int wq = warp - TP_EPI_W0 - 4;   // TMEM lane quarter (warp % 4)
+    const uint32_t lq = (uint32_t)(wq * 32) << 16;
     double eacc = 0.0, yacc = 0.0;
-    // The residual needs the tile's Y again: when the resident U copy leaves 32 KB, the epilogue
-    // reloads Y by 32-column chunks (TMA, an L2 hit: the tile was streamed moments before) into
+    // The residual needs the tile's Y again: when the resident U copy leaves 32 KB, these warps
+    // reload Y by 32-column chunks (TMA, an L2 hit: the tile was streamed moments before) into
     // two swizzled buffers, instead of 128 strided row reads per chunk from global memory.
     const int nck = (n1 + TC_KC - 1) / TC_KC;
-    const bool ysm = RESID && (size_t)2 * Kc2 * n1p * TC_KC * 4 + 2 * TC_M * TC_KC * 4 <= 128 * 1024;
+    const bool ysm = (size_t)2 * Kc2 * n1p * TC_KC * 4 + 2 * TC_M * TC_KC * 4 <= 128 * 1024;
     float* ybuf = B2lo + (size_t)Kc2 * n1p * TC_KC;   // [2][TC_M][TC_KC], 1024-byte aligned
     const bool yleader = (wq == 0 && lane == 0);
     if (ysm && yleader && xb < 0 && a.mYg) tensormap_acquire(a.mYg);
@@ -643,90 +678,64 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
         if (issue_y(t, 0, yq) && nck > 1) issue_y(t, 1, yq + 1);
       }
       __syncwarp();
-      const uint32_t tD1 = tmem + 128u * (uint32_t)(it & 1), tDlo = tD1 + 64;
-      bool okw = wait_bar(&d1full[it & 1], (uint32_t)((it >> 1) & 1), abort);
+      bool okw = wait_bar(d2full, (uint32_t)(it & 1), abort);
       okw = __all_sync(0xffffffffu, okw);
       if (!okw) break;
       tc_fence_after();
       const long long f = t * TC_M + wq * 32 + lane;
       const bool live = f < F;
-      for (int c0 = 0; c0 < Rp; c0 += 32) {
+      const float* xrow = Xg + f * n1;
+      const int row = wq * 32 + lane;
+      for (int c0 = 0, ci = 0; c0 < n1p; c0 += 32, ++ci) {
         float v[32];
-        tmem_ld32(tD1 + lq + c0, v);
-        if (live && !WRITE_ET) {
-          // column-major (F x r): consecutive threads write consecutive addresses
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (c0 + i < r) P[f + F * (c0 + i)] = v[i];
+        tmem_ld32(tD2 + lq + c0, v);
+        const float4* ych = reinterpret_cast<const float4*>(ybuf + (size_t)(yq & 1) * TC_M * TC_KC) + row * 8;
+        if (ysm) {
+          okw = wait_bar(&ybar[yq & 1], (uint32_t)((yq >> 1) & 1), abort);
+          okw = __all_sync(0xffffffffu, okw);
         }
-        if (RESID) {
-          float h[32], l[32];
+        if (live && okw) {
+          // FP32 partial sums over 32 elements, flushed to FP64 per chunk
+          float es = 0.f, ys = 0.f;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) tf32_split(v[i], h[i], l[i]);
-          tmem_st32(tD1 + lq + c0, h);
-          tmem_st32(tDlo + lq + c0, l);
+          for (int i = 0; i < 32; i += 4) {
+            if (c0 + i < n1) {
+              // SWIZZLE_128B: 16-byte piece j of row `row` sits at piece j ^ (row & 7)
+              const float4 y = ysm ? ych[(i >> 2) ^ (row & 7)]
+                                   : *reinterpret_cast<const float4*>(xrow + c0 + i);
+              const float e0 = y.x - v[i], e1 = y.y - v[i + 1], e2 = y.z - v[i + 2], e3 = y.w - v[i + 3];
+              es = fmaf(e0, e0, es); es = fmaf(e1, e1, es); es = fmaf(e2, e2, es); es = fmaf(e3, e3, es);
+              ys = fmaf(y.x, y.x, ys); ys = fmaf(y.y, y.y, ys); ys = fmaf(y.z, y.z, ys); ys = fmaf(y.w, y.w, ys);
+              if (WRITE_ET) {
+                float* et = a.Et + f;
+                et[(long long)(c0 + i) * a.et_stride] = e0;
+                et[(long long)(c0 + i + 1) * a.et_stride] = e1;
+                et[(long long)(c0 + i + 2) * a.et_stride] = e2;
+                et[(long long)(c0 + i + 3) * a.et_stride] = e3;
+              }
+            }
+          }
+          eacc += (double)es;
+          yacc += (double)ys;
+        } else if (WRITE_ET && f < a.et_stride) {
+          // zero the padding fibers the Gram's last K chunk reads
+          for (int i = 0; i < 32; ++i)
+            if (c0 + i < n1) a.Et[(long long)(c0 + i) * a.et_stride + f] = 0.f;
+        }
+        if (ysm) {
+          // this warp is done with the buffer; it is refilled with chunk ci + 2 once all four
+          // warps of this group are
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&yfree[yq & 1]);
+          if (yleader && ci + 2 < nck) issue_y(t, ci + 2, yq + 2);
+          __syncwarp();   // the next tcgen05.ld is warp-collective: lane 0 may have waited
+          ++yq;
         }
       }
       tc_fence_before();
-      mbar_arrive(&pready[it & 1]);
-      if (RESID) {
-        okw = wait_bar(d2full, (uint32_t)(it & 1), abort);
-        okw = __all_sync(0xffffffffu, okw);
-        if (!okw) break;
-        tc_fence_after();
-        const float* xrow = Xg + f * n1;
-        const int row = wq * 32 + lane;
-        for (int c0 = 0, ci = 0; c0 < n1p; c0 += 32, ++ci) {
-          float v[32];
-          tmem_ld32(tD2 + lq + c0, v);
-          const float4* ych = reinterpret_cast<const float4*>(ybuf + (size_t)(yq & 1) * TC_M * TC_KC) + row * 8;
-          if (ysm) {
-            okw = wait_bar(&ybar[yq & 1], (uint32_t)((yq >> 1) & 1), abort);
-            okw = __all_sync(0xffffffffu, okw);
-          }
-          if (live && okw) {
-            // FP32 partial sums over 32 elements, flushed to FP64 per chunk
-            float es = 0.f, ys = 0.f;
-#pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-              if (c0 + i < n1) {
-                // SWIZZLE_128B: 16-byte piece j of row `row` sits at piece j ^ (row & 7)
-                const float4 y = ysm ? ych[(i >> 2) ^ (row & 7)]
-                                     : *reinterpret_cast<const float4*>(xrow + c0 + i);
-                const float e0 = y.x - v[i], e1 = y.y - v[i + 1], e2 = y.z - v[i + 2], e3 = y.w - v[i + 3];
-                es = fmaf(e0, e0, es); es = fmaf(e1, e1, es); es = fmaf(e2, e2, es); es = fmaf(e3, e3, es);
-                ys = fmaf(y.x, y.x, ys); ys = fmaf(y.y, y.y, ys); ys = fmaf(y.z, y.z, ys); ys = fmaf(y.w, y.w, ys);
-                if (WRITE_ET) {
-                  float* et = a.Et + f;
-                  et[(long long)(c0 + i) * a.et_stride] = e0;
-                  et[(long long)(c0 + i + 1) * a.et_stride] = e1;
-                  et[(long long)(c0 + i + 2) * a.et_stride] = e2;
-                  et[(long long)(c0 + i + 3) * a.et_stride] = e3;
-                }
-              }
-            }
-            eacc += (double)es;
-            yacc += (double)ys;
-          } else if (WRITE_ET && f < a.et_stride) {
-            // zero the padding fibers the Gram's last K chunk reads
-            for (int i = 0; i < 32; ++i)
-              if (c0 + i < n1) a.Et[(long long)(c0 + i) * a.et_stride + f] = 0.f;
-          }
-          if (ysm) {
-            // this warp is done with the buffer; it is refilled with chunk ci + 2 once all four
-            // epilogue warps are
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&yfree[yq & 1]);
-            if (yleader && ci + 2 < nck) issue_y(t, ci + 2, yq + 2);
-            __syncwarp();   // the next tcgen05.ld is warp-collective: lane 0 may have waited
-            ++yq;
-          }
-        }
-        tc_fence_before();
-        mbar_arrive(d2free);
-      }
+      mbar_arrive(d2free);
     }
-    if (RESID && !WRITE_ET) {
+    if (!WRITE_ET) {
       double se = warp_sum(eacc), sy = warp_sum(yacc);
       if (lane == 0) { red[wq] = se; red[4 + wq] = sy; }
       asm volatile("bar.sync 1, 128;" ::: "memory");
