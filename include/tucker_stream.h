@@ -211,6 +211,8 @@ typedef struct {
                                     pass, from the ranks in effect), summed */
   int64_t launches;              /* kernels launched by profiled updates */
   int64_t updates;               /* profiled updates */
+  double ms_slice_pass;          /* CUDA-event time of the launch that streams the slice (the
+                                    mode-1 projection + residual kernel alone), summed */
 } tucker_profile;
 
 /* on = 1: the following updates record CUDA events around each phase on their stream (adds

@@ -61,7 +61,8 @@ class StepInfo(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * NPHASES), ("bytes", ctypes.c_double * NPHASES),
-                ("launches", ctypes.c_int64), ("updates", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
+                ("ms_slice_pass", ctypes.c_double)]
 
 
 class TuckerError(RuntimeError):
@@ -238,7 +239,7 @@ def tucker_profile_read(h: int) -> dict:
     p = Profile()
     _check(load_library().tucker_profile_read(h, ctypes.byref(p)), h)
     return dict(ms=[p.ms[i] for i in range(NPHASES)], bytes=[p.bytes[i] for i in range(NPHASES)],
-                launches=int(p.launches), updates=int(p.updates))
+                launches=int(p.launches), updates=int(p.updates), ms_slice_pass=p.ms_slice_pass)
 
 
 # --- batched form -----------------------------------------------------------------------------

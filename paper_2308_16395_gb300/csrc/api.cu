@@ -378,8 +378,9 @@ struct PhaseMark {
   cudaStream_t st;
   int phase;
   size_t idx;
+  // ph < 0: no mark
   PhaseMark(tucker_state* s_, cudaStream_t st_, int ph) : s(s_), st(st_), phase(ph), idx(0) {
-    if (!s->prof) return;
+    if (!s->prof || ph < 0) return;
     while (s->ev.size() < s->ev_used + 2) {
       cudaEvent_t e;
       cudaEventCreate(&e);
@@ -391,7 +392,7 @@ struct PhaseMark {
     cudaEventRecord(s->ev[idx], st);
   }
   ~PhaseMark() {
-    if (s->prof) cudaEventRecord(s->ev[idx + 1], st);
+    if (s->prof && phase >= 0) cudaEventRecord(s->ev[idx + 1], st);
   }
 };
 
@@ -590,14 +591,17 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       // pass A: P_k = D*_{k-1} x_k U_k^T, ||E_k||^2 (and ||Y||^2 for k = 0); Alg. 4's branch
       PhaseMark pm(s, st, k == 0 ? TK_PH_PROJ1 : TK_PH_PROJN);
       if (tck) {
+        PhaseMark pk(s, st, k == 0 ? TK_PH_SLICE : -1);
         CK(launch_tc_proj(s->ctl, k, 1, 0, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
                           s->d_dbufs, 1, s->part_e2, k == 0 ? s->part_y2 : nullptr, s->grid_p,
                           nullptr, 0, s->grid_tc, st));
         launches += 1;
       }
-      if (k == 0)
+      if (k == 0) {
+        PhaseMark pk(s, st, tck ? -1 : TK_PH_SLICE);
         CK((launch_proj<TX, TW>(s->ctl, k, 1, 0, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], s->part_e2,
                                 s->part_y2, s->grid_p, st)));
+      }
       else
         CK((launch_proj<TW, TW>(s->ctl, k, 1, 0, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], s->part_e2,
                                 nullptr, s->grid_p, st)));
@@ -1248,7 +1252,8 @@ tucker_status tucker_profile_read(tucker_state* s, tucker_profile* out) {
   for (size_t i = 0; i < s->ev_phase.size(); ++i) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, s->ev[2 * i], s->ev[2 * i + 1]));
-    out->ms[s->ev_phase[i]] += ms;
+    if (s->ev_phase[i] == TK_PH_SLICE) out->ms_slice_pass += ms;
+    else out->ms[s->ev_phase[i]] += ms;
   }
   for (int i = 0; i < TK_NPH; ++i) out->bytes[i] = s->hctl->acc_bytes[i] - s->bytes0[i];
   out->launches = s->prof_launches;

@@ -77,6 +77,7 @@ struct Ctl {
 #define TK_PH_ISVD 3     // p = V^T d, e = d - V p, secular SVD of S'
 #define TK_PH_FACT 4     // U~_d and M
 #define TK_PH_CV 5       // core and V updates
+#define TK_PH_SLICE 6    // the mode-1 pass kernel alone (inside phase 0; timed, no bytes)
 #define TK_NPH 6
 
 // Mode-k view (A, n, B) of the operand of mode k, column-major: element (a, j, b) at

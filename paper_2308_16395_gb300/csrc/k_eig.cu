@@ -105,10 +105,12 @@ __device__ __forceinline__ int tri_perm(int i) { return (i % NW) * RA + i / NW; 
 // round-to-nearest in each half) per two entries.
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 
-// Loop-carried vectors of the previous step at the thread's columns.
+// Loop-carried vectors of the previous step at the thread's columns, and the shared-memory
+// offsets of those columns in the row-permuted vectors (tri_perm, -1 past n), fixed per lane.
 template <int CB> struct TriPrev {
   float v[CB];   // v_{c-1}
   float tau;     // tau_{c-1}
+  int po[CB];
 };
 
 // w_{c-1} = p_{c-1} - (tau_{c-1}/2)(p_{c-1}^T v_{c-1}) v_{c-1} at the thread's columns (blocks
@@ -122,7 +124,7 @@ __device__ __forceinline__ float tri_w(const TriPrev<CB>& pr, const float* pp, i
 #pragma unroll
   for (int b = B0; b < CB; ++b) {
     const int j = lane + 32 * b;
-    pc[b] = j < n ? pp[tri_perm<NW, RA>(j)] : 0.f;
+    pc[b] = pr.po[b] >= 0 ? pp[pr.po[b]] : 0.f;
     pv = fmaf(pc[b], pr.v[b], pv);
   }
   const float K = -0.5f * pr.tau * warp_sum(pv);
@@ -179,7 +181,7 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], TriPrev<CB>& 
     for (int b = 0; b < CB; ++b) {
       const int j = lane + 32 * b;
       if (b >= CB0 && j > c && j < n) V[(long long)c * n + j] = vc[b];
-      if (j < n) sm.svp[par + tri_perm<NW, RA>(j)] = b >= CB0 ? vc[b] : 0.f;
+      if (pr.po[b] >= 0) sm.svp[par + pr.po[b]] = b >= CB0 ? vc[b] : 0.f;
     }
   }
   // fused: A22 -= v_{c-1} w_{c-1}^T + w_{c-1} v_{c-1}^T, then p = A22 v_c
@@ -303,7 +305,11 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
   const TriSmem sm{&scol[0][0], &svp[0][0], &swp[0][0], sa, sb, stau};
   TriPrev<CB> pr;
 #pragma unroll
-  for (int b = 0; b < CB; ++b) pr.v[b] = 0.f;
+  for (int b = 0; b < CB; ++b) {
+    const int j = lane + 32 * b;
+    pr.v[b] = 0.f;
+    pr.po[b] = j < n ? tri_perm<NW, RA>(j) : -1;
+  }
   pr.tau = 0.f;
   tri_steps<NW, RA, CB, 0>(a2, pr, n, lane, wid, V, sm);
   // trailing 2 x 2 block after step n-3, whose update was deferred: registers hold A after step
