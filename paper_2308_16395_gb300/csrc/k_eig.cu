@@ -87,7 +87,7 @@ __device__ __forceinline__ float sel_f32(bool p, float x, float y) {
 // Two buffers of SZ floats each, buffer c & 1 for step c (base + (c & 1) SZ: a run-time index
 // into an array of pointers would put the array in local memory).
 struct TriSmem {
-  float* scol;   // column c of A after step c-2, natural row order
+  float* scol;   // column c of A after step c-2, row-permuted (see tri_perm)
   float* svp;    // v of step c, row-permuted (see tri_perm)
   float* swp;    // p = tau A22 v of step c, row-permuted
   float* sa;
@@ -95,10 +95,13 @@ struct TriSmem {
   float* stau;
 };
 
-// Row i of the register block (warp i % NW, block i / NW) stored at (i % NW) RA + i / NW, so a
-// warp's RA rows are contiguous and its row pairs load as float2.
+// Row i of the register block (warp i % NW, block i / NW) stored at (i % NW) RS + i / NW, so a
+// warp's RA rows are contiguous (row pairs load as float2, quads store as float4). RS pads the
+// stride between warps: a warp reading 32 consecutive rows then touches at most 2 rows per shared-
+// memory bank (6 with RS = RA = 16, 3 with RS = RA = 8).
+template <int RA> constexpr int tri_rs() { return RA == 16 ? 20 : RA == 8 ? 12 : RA; }
 template <int NW, int RA>
-__device__ __forceinline__ int tri_perm(int i) { return (i % NW) * RA + i / NW; }
+__device__ __forceinline__ int tri_perm(int i) { return (i % NW) * tri_rs<RA>() + i / NW; }
 
 // Packed FP32 pairs: rows 2h and 2h+1 of a thread's register block share one 64-bit register
 // pair, so the matrix-vector product and the rank-2 update issue one paired FMA (__ffma2_rn,
@@ -142,7 +145,8 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], TriPrev<CB>& 
   // updated and multiplied harmlessly, and its p entry is stored as zero)
   constexpr int A0 = 32 * CB0 >= NW - 1 ? (32 * CB0 - NW + 1) / NW + 1 : 0;
   constexpr int H0 = A0 / 2;
-  constexpr int SZ = NW * RA + 32;
+  constexpr int RS = tri_rs<RA>();
+  constexpr int SZ = NW * RS + 32;
   const int par = (c & 1) * SZ, prv = SZ - par;
   // w_{c-1} at the thread's columns (the barrier of step c-1 published p_{c-1})
   float wc[CB];
@@ -155,7 +159,7 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], TriPrev<CB>& 
 #pragma unroll
   for (int b = CB0; b < CB; ++b) {
     const int j = lane + 32 * b;
-    xc[b] = fmaf(-pr.v[b], wcc, col[j]) - wc[b];
+    xc[b] = fmaf(-pr.v[b], wcc, pr.po[b] >= 0 ? col[pr.po[b]] : 0.f) - wc[b];
     part += sel_f32(j >= c + 2 && j < n, xc[b] * xc[b], 0.f);
   }
   const float xn2 = warp_sum(part);
@@ -175,21 +179,26 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], TriPrev<CB>& 
     const int j = lane + 32 * b;
     vc[b] = sel_f32(j == c + 1, 1.f, sel_f32(j > c + 1 && j < n, xc[b] * scal, 0.f));
   }
-  if (wid == 0) {
-    if (lane == 0) { sm.stau[c] = tau; sm.sb[c] = beta; sm.sa[c] = col[c] - 2.f * wcc; }
+  if (wid == 0 && lane == 0) {
+    sm.stau[c] = tau;
+    sm.sb[c] = beta;
+    sm.sa[c] = col[tri_perm<NW, RA>(c)] - 2.f * wcc;
+  }
+  // reflector c to V and to the shared row vector: column block b by warp b and warp CB + b
+  // (one store per lane per warp instead of all of them in one warp)
+  static_assert(2 * CB <= NW, "a warp per column block for V and for the row vector");
 #pragma unroll
-    for (int b = 0; b < CB; ++b) {
-      const int j = lane + 32 * b;
-      if (b >= CB0 && j > c && j < n) V[(long long)c * n + j] = vc[b];
-      if (pr.po[b] >= 0) sm.svp[par + pr.po[b]] = b >= CB0 ? vc[b] : 0.f;
-    }
+  for (int b = 0; b < CB; ++b) {
+    const int j = lane + 32 * b;
+    if (wid == b && b >= CB0 && j > c && j < n) V[(long long)c * n + j] = vc[b];
+    if (wid == CB + b && pr.po[b] >= 0) sm.svp[par + pr.po[b]] = b >= CB0 ? vc[b] : 0.f;
   }
   // fused: A22 -= v_{c-1} w_{c-1}^T + w_{c-1} v_{c-1}^T, then p = A22 v_c
   float wn[CB], vn[CB], vv[CB];
 #pragma unroll
   for (int b = CB0; b < CB; ++b) { wn[b] = -wc[b]; vn[b] = -pr.v[b]; vv[b] = vc[b]; }
-  const float2* v2p = reinterpret_cast<const float2*>(sm.svp + prv + wid * RA);
-  const float2* p2p = reinterpret_cast<const float2*>(sm.swp + prv + wid * RA);
+  const float2* v2p = reinterpret_cast<const float2*>(sm.svp + prv + wid * RS);
+  const float2* p2p = reinterpret_cast<const float2*>(sm.swp + prv + wid * RS);
   const float2 K2 = f2(K, K);
   float acc[RA];
 #pragma unroll
@@ -227,21 +236,29 @@ __device__ __forceinline__ void tri_step(float2 (&a2)[RA / 2][CB], TriPrev<CB>& 
     const int my_a = lane >> (5 - LOGRA);
     const bool writer = (lane & ((1 << (5 - LOGRA)) - 1)) == 0;
     const int i = wid + NW * my_a;
-    if (writer && i < n) sm.swp[par + wid * RA + my_a] = (i > c) ? tau * acc[0] : 0.f;
+    if (writer && i < n) sm.swp[par + wid * RS + my_a] = (i > c) ? tau * acc[0] : 0.f;
   }
-  // publish column c+1 of A after step c-1 (rows >= c+1 all lie in live pairs; other rows of
-  // the buffer are never read)
+  // publish column c+1 of A after step c-1, row-permuted, so the warp's rows are contiguous and
+  // go out as 16-byte stores (rows >= c+1 all lie in live pairs; the other rows of the buffer,
+  // including a dead pair stored with its live neighbour, are never read)
   if (lane == ((c + 1) & 31)) {
-    float* nc = sm.scol + prv;
-#pragma unroll
-    for (int h = H0; h < RA / 2; ++h) {
+    float* nc = sm.scol + prv + wid * RS;
+    const bool hi = ((c + 1) >> 5) != CB0;
+    auto colv = [&](int h) -> float2 {
       float2 val = a2[h][CB0];
-      if constexpr (CB0 + 1 < CB) {
-        const bool hi = ((c + 1) >> 5) != CB0;
+      if constexpr (CB0 + 1 < CB)
         val = f2(sel_f32(hi, a2[h][CB0 + 1].x, val.x), sel_f32(hi, a2[h][CB0 + 1].y, val.y));
+      return val;
+    };
+    if constexpr (RA % 4 == 0) {
+#pragma unroll
+      for (int h = H0 & ~1; h < RA / 2; h += 2) {
+        const float2 v0 = colv(h), v1 = colv(h + 1);
+        *reinterpret_cast<float4*>(nc + 2 * h) = make_float4(v0.x, v0.y, v1.x, v1.y);
       }
-      nc[wid + NW * (2 * h)] = val.x;
-      nc[wid + NW * (2 * h + 1)] = val.y;
+    } else {
+#pragma unroll
+      for (int h = H0; h < RA / 2; ++h) *reinterpret_cast<float2*>(nc + 2 * h) = colv(h);
     }
   }
 #pragma unroll
@@ -269,9 +286,11 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
   const int d = ctl->d;
   const int n = (k == d - 1) ? ctl->init_nt : ctl->n[k];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int SZ = NW * RA + 32;
+  constexpr int RS = tri_rs<RA>();
+  constexpr int SZ = NW * RS + 32;
   static_assert(SZ > 32 * CB, "shared vectors must cover every column index");
-  __shared__ float scol[2][SZ];
+  static_assert(RS % 2 == 0 && (RA % 4 != 0 || RS % 4 == 0) && SZ % 4 == 0, "vector alignment");
+  __shared__ __align__(16) float scol[2][SZ];
   __shared__ __align__(16) float svp[2][SZ];
   __shared__ __align__(16) float swp[2][SZ];
   __shared__ float sa[SZ], sb[SZ], stau[SZ];
@@ -297,8 +316,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
   if (lane == 0) {
 #pragma unroll
     for (int h = 0; h < RA / 2; ++h) {
-      scol[0][wid + NW * (2 * h)] = a2[h][0].x;
-      scol[0][wid + NW * (2 * h + 1)] = a2[h][0].y;
+      scol[0][wid * RS + 2 * h] = a2[h][0].x;
+      scol[0][wid * RS + 2 * h + 1] = a2[h][0].y;
     }
   }
   __syncthreads();
@@ -344,8 +363,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
     v1 = __shfl_sync(0xffffffffu, v1, (c + 1) & 31);
     if (lane == 0) {
       const float* col = scol[c & 1];
-      sa[c] = col[c] - 2.f * w0;
-      sb[c] = col[c + 1] - v1 * w0 - w1;
+      sa[c] = col[tri_perm<NW, RA>(c)] - 2.f * w0;
+      sb[c] = col[tri_perm<NW, RA>(c + 1)] - v1 * w0 - w1;
       stau[c] = 0.f;
       sa[c + 1] -= 2.f * v1 * w1;
       stau[c + 1] = 0.f;
