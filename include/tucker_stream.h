@@ -176,10 +176,12 @@ tucker_status tucker_error_norm(tucker_state* s, double* err_bound_host, double*
 
 /* Asynchronous form of tucker_error_norm for pipelined callers: enqueues on `stream` a copy of
  * the squared running error bound and the squared data norm, as they stand after the work
- * enqueued so far, into out2_host[0] and out2_host[1] (host memory, preferably pinned). No
- * synchronization: the values are valid once `stream` has reached this point. A latched device
- * error is not reported here (the next synchronizing call reports it). Errors: EINVAL, ESTATE,
- * ECUDA. */
+ * enqueued so far, into out2_host[0] and out2_host[1] (host memory, preferably pinned). With
+ * pinned (mapped) or managed memory a one-thread kernel stores the values, so the read does not
+ * wait in a copy-engine queue behind host-to-device copies of other streams; other memory is
+ * copied by cudaMemcpyAsync. No synchronization: the values are valid once `stream` has reached
+ * this point. A latched device error is not reported here (the next synchronizing call reports
+ * it). Errors: EINVAL, ESTATE, ECUDA. */
 tucker_status tucker_error_norm_async(tucker_state* s, double* out2_host, void* stream);
 
 /* Current ranks r_1..r_d (d entries) and n_d. Synchronizes. */

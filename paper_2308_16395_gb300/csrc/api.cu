@@ -1091,8 +1091,23 @@ tucker_status tucker_error_norm_async(tucker_state* s, double* out2, void* strea
   if (!s || !out2) return TUCKER_EINVAL;
   if (!usable(s)) return TUCKER_ESTATE;
   static_assert(offsetof(Ctl, data2) == offsetof(Ctl, err2) + sizeof(double), "err2, data2 adjacent");
-  CK(cudaMemcpyAsync(out2, reinterpret_cast<unsigned char*>(s->ctl) + offsetof(Ctl, err2),
-                     2 * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  // Pinned (mapped) or managed destination: one GPU thread stores the two values over the host
+  // link. A copy-engine read would queue behind host-to-device slice copies that other streams
+  // have in flight, serializing a pipelined caller's copies with its updates.
+  cudaPointerAttributes pa{};
+  double* dptr = nullptr;
+  if (cudaPointerGetAttributes(&pa, out2) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeManaged)
+      dptr = static_cast<double*>(pa.devicePointer);
+  } else {
+    cudaGetLastError();   // unregistered memory on older runtimes: use the copy
+  }
+  if (dptr) {
+    CK(launch_read_err(s->ctl, dptr, (cudaStream_t)stream));
+  } else {
+    CK(cudaMemcpyAsync(out2, reinterpret_cast<unsigned char*>(s->ctl) + offsetof(Ctl, err2),
+                       2 * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  }
   return TUCKER_OK;
 }
 

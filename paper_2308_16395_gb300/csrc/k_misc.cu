@@ -119,6 +119,19 @@ cudaError_t launch_set_slot(Ctl* ctl, const SlotArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+__global__ void k_read_err(const Ctl* ctl, double* out2) {
+  if (threadIdx.x == 0) {
+    out2[0] = ctl->err2;
+    out2[1] = ctl->data2;
+    __threadfence_system();
+  }
+}
+
+cudaError_t launch_read_err(const Ctl* ctl, double* out2, cudaStream_t st) {
+  k_read_err<<<1, 32, 0, st>>>(ctl, out2);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_init_finish<float>(Ctl*, const void*, long long, int, const double*,
                                                const double*, int, void*, void*, double*, double*,
                                                int, cudaStream_t);

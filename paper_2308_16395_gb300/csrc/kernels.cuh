@@ -108,6 +108,9 @@ struct SlotArgs {
   const void* y;           // slice address
 };
 cudaError_t launch_set_slot(Ctl* ctl, const SlotArgs& a, cudaStream_t st);
+// (err^2, ||X||^2) of the control block stored by one GPU thread into memory the GPU can address
+// (mapped pinned host memory, managed or device memory): no copy engine involved.
+cudaError_t launch_read_err(const Ctl* ctl, double* out2, cudaStream_t st);
 template <typename TW>
 cudaError_t launch_init_finish(Ctl* ctl, const void* Ccol, long long R, int rd, const double* lam,
                                const double* Utmp, int nt, void* C, void* V, double* Ud, double* S,
