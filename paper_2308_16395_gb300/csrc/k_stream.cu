@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) k_isvd_p(Ctl* __restrict__ ctl, TW* const
                                                TW* const* vbufs, double* __restrict__ part,
                                                double* __restrict__ pout) {
   if (ctl->status) return;
-  if (rows_isvd_ok(ctl)) return;   // k_isvd_p_rows does this pass
+  if (rows_isvd_ok(ctl)) return;   // k_isvd_p_all does this pass (bulk tiles or a lane per row)
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
   const int ldc = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) k_isvd_e(Ctl* __restrict__ ctl, TW* const
                                                double* __restrict__ es, const double* __restrict__ S,
                                                SecWork w) {
   if (ctl->status) return;
-  if (rows_isvd_ok(ctl)) return;   // k_isvd_e_rows does this pass
+  if (rows_isvd_ok(ctl)) return;   // k_isvd_e_all does this pass (bulk tiles or a lane per row)
   const int d = ctl->d, m = d - 1;
   const int r = ctl->r[d - 1];
   const int ldc = tk_cv_stride(r, ctl->ldc, (int)sizeof(TW));
@@ -1206,8 +1206,8 @@ __device__ __forceinline__ void isvd_p_bulk(Ctl* __restrict__ ctl, TW* const* db
   (void)pout;
 }
 
-// e = d - V p (stored), ||e||^2 (compensated) and s = V^T e; the last block to finish then runs
-// the small ISVD step, as k_isvd_e_rows does.
+// e = d - V p (stored), ||e||^2 (compensated) and s = V^T e as per-block partials; k_col_reduce
+// sums them and its last block runs the small ISVD step (as for the lane-per-row body).
 template <int S4>
 __device__ __forceinline__ long long isvd_e_tiles(const BulkTiles& bt, const float* __restrict__ dv,
                                                   const float* pl, float* __restrict__ evec, int r,
