@@ -87,3 +87,40 @@ def test_ttm_workspace_query_is_host_only(lib):
     for n, r in [((8, 8), (9, 2)), ((8, 0), (2, 0)), ((), ())]:
         with pytest.raises(pkg.TuckerError):
             pkg.tucker_ttm_workspace_bytes(pkg.ttm_desc(n, r, "f64"))
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the C compiler's size and field offsets (the header
+    compiled as C by gcc; no GPU and no CUDA library needed)."""
+    import ctypes
+    import shutil
+
+    import paper_2308_16395_gb300 as pkg
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("tucker_config", pkg.TuckerConfig), ("tucker_step_info", pkg.StepInfo),
+             ("tucker_profile", pkg.Profile), ("tucker_launch_plan", pkg.LaunchPlan),
+             ("tucker_ttm_desc", pkg.TtmDesc)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tucker_stream.h"',
+             '#include "tucker_ttm.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, py in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
