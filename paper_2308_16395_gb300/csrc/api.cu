@@ -484,7 +484,7 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
     }
     if (k == 0) e = launch_proj<TX, TW>(s->ctl, k, 1, 0, X, d_ib, Uwk, nv, rk, nullptr, nullptr, kGridP, st);
     else e = launch_proj<TW, TW>(s->ctl, k, 1, 0, X, d_ib, Uwk, nv, rk, nullptr, nullptr, kGridP, st);
-    if (e == cudaSuccess) e = launch_mode_end(s->ctl, k, st);
+    if (e == cudaSuccess) e = launch_mode_end(s->ctl, k, 0, st);
     if (e != cudaSuccess) { set_err(s, "CUDA error (%s) in the projection of mode %lld", cudaGetErrorString(e), k + 1); rc = TUCKER_ECUDA; break; }
   }
   if (rc == TUCKER_OK) rc = sync_ctl(s);
@@ -649,11 +649,11 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       else
         CK((launch_proj<TW, TW>(s->ctl, k, 2, 1, Y, s->d_dbufs, s->Uw[k], n, s->cap[k], nullptr,
                                 nullptr, s->grid_p, st)));
+      CK(launch_mode_end(s->ctl, k, 1, st));
       if (s->gform) {
         CK(cond_end(s->body_st));
         s->body_open = false;
       }
-      CK(launch_mode_end(s->ctl, k, main_st));
     }
     launches += 8;
   }

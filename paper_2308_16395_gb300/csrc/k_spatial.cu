@@ -216,6 +216,9 @@ __global__ void k_decide(Ctl* ctl, int k, const double* part_e2, const double* p
     if (hcond) cudaGraphSetConditional(hcond, g ? 1u : 0u);
     ctl->e2[k] = se;
     ctl->grew[k] = g;
+    // no growth: D*_k is P_k, the next buffer in the rotation (the growth chain, which would have
+    // moved it two ahead, does not run; its kernels return before reading xbuf)
+    if (!g) ctl->xbuf = (ctl->xbuf + 1) % 3;
     ctl->radd[k] = 0;
     ctl->disc[k] = g ? 0.0 : se;
     if (k == 0) {
@@ -226,12 +229,16 @@ __global__ void k_decide(Ctl* ctl, int k, const double* part_e2, const double* p
 }
 
 // After mode k: the buffer holding D*_k becomes the input of mode k+1.
-// After the last spatial mode of an update, the new spatial core size must fit the C/V capacity.
-__global__ void k_mode_end(Ctl* ctl, int k) {
+// grown_only (updates): the last kernel of mode k's growth chain, a no-op when mode k did not
+// grow (k_decide advanced the buffer then). A growth changes the spatial core size, which must
+// still fit the C/V capacity; without growth the size is the one checked when it last changed.
+// Otherwise (initial ST-HOSVD): advance by one, as no mode grows there.
+__global__ void k_mode_end(Ctl* ctl, int k, int grown_only) {
   if (ctl->status) return;
+  if (grown_only && !ctl->grew[k]) return;
   const int xb = ctl->xbuf;
   ctl->xbuf = ctl->grew[k] ? (xb + 2 + 3) % 3 : (xb + 1 + 3) % 3;
-  if (ctl->init_nt == 0 && k == ctl->d - 2) {
+  if (grown_only) {
     long long R = 1;
     for (int i = 0; i < ctl->d - 1; ++i) R *= ctl->r[i];
     if (R > ctl->core_cap) ctl->status = TK_ECAPACITY;
@@ -474,8 +481,8 @@ cudaError_t launch_decide(Ctl* ctl, int k, const double* pe, const double* py, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_mode_end(Ctl* ctl, int k, cudaStream_t st) {
-  k_mode_end<<<1, 1, 0, st>>>(ctl, k);
+cudaError_t launch_mode_end(Ctl* ctl, int k, int grown_only, cudaStream_t st) {
+  k_mode_end<<<1, 1, 0, st>>>(ctl, k, grown_only);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ cudaError_t launch_resid_gram(const Ctl* ctl, int k, int n, const void* Xext, vo
                               int data_only, cudaStream_t st);
 cudaError_t launch_decide(Ctl* ctl, int k, const double* pe, const double* py, int nparts,
                           cudaGraphConditionalHandle hcond, cudaStream_t st);
-cudaError_t launch_mode_end(Ctl* ctl, int k, cudaStream_t st);
+cudaError_t launch_mode_end(Ctl* ctl, int k, int grown_only, cudaStream_t st);
 cudaError_t launch_gram_reduce(const Ctl* ctl, int k, const double* gpart, int pairs, int chunks,
                                double* G, int data_only, cudaStream_t st);
 template <typename TI, typename TW, typename TO>
