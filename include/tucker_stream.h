@@ -111,6 +111,16 @@ tucker_status tucker_init_sthosvd(const tucker_config* cfg, const void* X_dev, i
  * conditions are latched (see above). */
 tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* stream);
 
+/* Host-input form of tucker_stream_update, for slices that arrive in host memory: copies Y_host
+ * (same layout, preferably pinned) into one of two library-owned device staging buffers on an
+ * internal copy stream, then enqueues the update of Y on `stream` after that copy. Returns
+ * without waiting, so the next call's copy (into the other buffer) overlaps this update; a
+ * buffer is reused only once the update that read it has completed. The caller keeps Y_host
+ * unmodified until the copy has completed: at the latest when `stream` has reached this update.
+ * From pageable memory the copy is synchronous for the caller. The staging buffers (2 slices)
+ * are allocated on the first call. Errors: as tucker_stream_update; ENOMEM; ECUDA. */
+tucker_status tucker_stream_update_host(tucker_state* s, const void* Y_host, void* stream);
+
 /* Batched form: many independent streams, each updated by Alg. 5, advanced together by one
  * CUDA-graph launch per time step.
  *

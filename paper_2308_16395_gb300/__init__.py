@@ -29,7 +29,7 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint", "tucker_ttm_reconstruct_adjoint",
            "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy",
            "tucker_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
-           "tucker_get_launch_plan"]
+           "tucker_get_launch_plan", "tucker_stream_update_host"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -90,6 +90,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     lib.tucker_init_sthosvd.argtypes = [ctypes.POINTER(TuckerConfig), vp, i64, vp, ctypes.POINTER(vp)]
     lib.tucker_stream_update.argtypes = [vp, vp, vp]
+    lib.tucker_stream_update_host.argtypes = [vp, vp, vp]
     lib.tucker_reconstruct.argtypes = [vp, i64, i64, vp, vp]
     lib.tucker_reconstruct_noalloc.argtypes = [vp, i64, i64, vp, vp]
     lib.tucker_error_norm.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
@@ -131,7 +132,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     for name in ("tucker_ttm_project", "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint",
                  "tucker_ttm_reconstruct_adjoint"):
         getattr(lib, name).restype = ctypes.c_int
-    for name in ("tucker_profile_enable", "tucker_profile_read", "tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
+    for name in ("tucker_profile_enable", "tucker_profile_read", "tucker_init_sthosvd", "tucker_stream_update",
+                 "tucker_stream_update_host", "tucker_reconstruct",
                  "tucker_reconstruct_noalloc", "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
                  "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv"):
         getattr(lib, name).restype = ctypes.c_int
@@ -179,6 +181,10 @@ def tucker_init_sthosvd(cfg: TuckerConfig, X_ptr: int, n_init: int, stream: int 
 
 def tucker_stream_update(h: int, Y_ptr: int, stream: int = 0) -> None:
     _check(load_library().tucker_stream_update(h, ctypes.c_void_p(Y_ptr), ctypes.c_void_p(stream)), h)
+
+
+def tucker_stream_update_host(h: int, Y_host_ptr: int, stream: int = 0) -> None:
+    _check(load_library().tucker_stream_update_host(h, ctypes.c_void_p(Y_host_ptr), ctypes.c_void_p(stream)), h)
 
 
 def tucker_reconstruct(h: int, t0: int, t1: int, out_ptr: int, stream: int = 0) -> None:
@@ -432,6 +438,14 @@ class TuckerStream:
         if tuple(reversed(Y.shape)) != self.n or Y.dtype != self.dtype or not Y.is_contiguous():
             raise ValueError("slice shape/dtype/layout mismatch")
         tucker_stream_update(self.h, Y.data_ptr(), self._sp())
+
+    def update_host(self, Y) -> None:
+        """Update from a slice in host memory (a CPU tensor, pinned for overlap): the library
+        copies it into a staging buffer on its own copy stream and updates after the copy."""
+        if (Y.device.type != "cpu" or tuple(reversed(Y.shape)) != self.n or Y.dtype != self.dtype
+                or not Y.is_contiguous()):
+            raise ValueError("host slice shape/dtype/layout mismatch")
+        tucker_stream_update_host(self.h, Y.data_ptr(), self._sp())
 
     @property
     def ranks(self) -> tuple:

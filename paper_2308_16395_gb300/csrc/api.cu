@@ -113,6 +113,12 @@ struct tucker_state {
   bool graph_failed = false;          // capture or instantiation failed once: stay eager
   long long graph_kernels = 0;        // kernel nodes of the update graph (bodies included)
   std::vector<cudaGraph_t> bodies;    // IF bodies created by the last capture
+  // host-input updates (tucker_stream_update_host): two staging slices, a copy stream, and per
+  // buffer an event after its copy and one after the update that read it
+  void* hstage[2]{};
+  cudaStream_t hcs = nullptr;
+  cudaEvent_t hcopied[2]{}, hconsumed[2]{};
+  int hnext = 0;
 };
 
 namespace {
@@ -1048,6 +1054,40 @@ tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* str
   return update_dispatch(s, Y_dev, st);
 }
 
+tucker_status tucker_stream_update_host(tucker_state* s, const void* Y_host, void* stream) {
+  if (!s || !Y_host) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)s->N * (size_t)s->tx;
+  if (!s->hcs) {
+    for (int b = 0; b < 2; ++b) {
+      if (cudaMalloc(&s->hstage[b], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(s, "cannot allocate the host-input staging buffers%s (%lld bytes each)", "", (long long)bytes);
+        return TUCKER_ENOMEM;
+      }
+      s->allocs.push_back(s->hstage[b]);
+    }
+    CK(cudaStreamCreateWithFlags(&s->hcs, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      CK(cudaEventCreateWithFlags(&s->hcopied[b], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&s->hconsumed[b], cudaEventDisableTiming));
+      CK(cudaEventRecord(s->hconsumed[b], st));   // both buffers free
+    }
+  }
+  const int b = s->hnext;
+  s->hnext ^= 1;
+  // the copy into buffer b waits for the update that last read it; the update waits for the copy
+  CK(cudaStreamWaitEvent(s->hcs, s->hconsumed[b], 0));
+  CK(cudaMemcpyAsync(s->hstage[b], Y_host, bytes, cudaMemcpyHostToDevice, s->hcs));
+  CK(cudaEventRecord(s->hcopied[b], s->hcs));
+  CK(cudaStreamWaitEvent(st, s->hcopied[b], 0));
+  const tucker_status rc = tucker_stream_update(s, s->hstage[b], stream);
+  if (rc != TUCKER_OK) return rc;
+  CK(cudaEventRecord(s->hconsumed[b], st));
+  return TUCKER_OK;
+}
+
 tucker_status tucker_reconstruct(tucker_state* s, int64_t t_begin, int64_t t_end, void* out_dev,
                                  void* stream) {
   if (!s || !out_dev) return TUCKER_EINVAL;
@@ -1279,6 +1319,14 @@ tucker_status tucker_profile_read(tucker_state* s, tucker_profile* out) {
 void tucker_destroy(tucker_state* s) {
   if (!s) return;
   cudaStreamSynchronize(s->last_stream);
+  if (s->hcs) {
+    cudaStreamSynchronize(s->hcs);
+    cudaStreamDestroy(s->hcs);
+    for (int b = 0; b < 2; ++b) {
+      cudaEventDestroy(s->hcopied[b]);
+      cudaEventDestroy(s->hconsumed[b]);
+    }
+  }
   if (s->uexec) cudaGraphExecDestroy(s->uexec);
   if (s->ugraph) cudaGraphDestroy(s->ugraph);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);

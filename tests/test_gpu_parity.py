@@ -341,3 +341,27 @@ def test_async_error_norm_read(pkg):
     assert abs(float(out[5, 1]) - dn * dn) <= 1e-14 * dn * dn
     assert all(float(out[i + 1, 1]) > float(out[i, 1]) for i in range(5))   # data norm grows
     ts.close()
+
+
+def test_update_from_host_equals_device_update(pkg):
+    """tucker_stream_update_host (slices in pinned host memory, copied on the library's copy
+    stream into alternating staging buffers) gives the same state as updates from device slices."""
+    import torch
+
+    X = _growth_stream(n=(40, 28, 12))
+    Xg = to_device(X.astype(np.float32).astype(np.float64), torch.float32)
+    a = pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="mixed", steps_cap=24)
+    b = pkg.TuckerStream(Xg[:6].contiguous(), 1e-3, precision="mixed", steps_cap=24)
+    host = [Xg[t].cpu().pin_memory() for t in range(6, X.shape[-1])]
+    for i, t in enumerate(range(6, X.shape[-1])):
+        a.update(Xg[t].contiguous())
+        b.update_host(host[i])
+    assert a.ranks == b.ranks
+    assert a.ranks[:3] == (5, 5, 5)
+    assert a.error_norm() == b.error_norm()
+    Ra, Rb = a.reconstruct(0, a.n_d), b.reconstruct(0, b.n_d)
+    assert torch.equal(Ra, Rb)
+    with pytest.raises(ValueError):
+        b.update_host(Xg[6])          # a device tensor is not a host slice
+    a.close()
+    b.close()
