@@ -1,12 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the streaming ST-HOSVD update on one GB300 (or N independent replicas).
 
-Workload: the advected-blob stream, 4-way slices 192 x 192 x 96 x 12 (x, y, z, variable), FP32,
-tau = 1e-4, initial ST-HOSVD on the first 10 slices, then one update (Alg. 5) per step. Every
-step assimilates a new 170 MB slice (larger than the 129 MB L2), all slices resident in HBM before
-the timed region. Prints one JSON line (rank 0).
+Default workload (``--workload stream``): the large advected-blob stream, 4-way slices
+384 x 384 x 256 x 4 (x, y, z, variable) of 80 advected anisotropic Gaussian blobs, FP32 storage
+(604 MB per slice), tau = 1e-4, initial ST-HOSVD on the first 10 slices, then one update (Alg. 5)
+per step with the full mixed-precision path. Every step assimilates a new slice larger than the
+129 MB L2; all slices are resident in HBM before the timed region. ``--workload stream192``: the
+192 x 192 x 96 x 12 stream of 40 blobs (170 MB slices), with the plain FP64 GPU form beside it.
+Prints one JSON line (rank 0), with the parity of the timed updates against the FP64 CPU oracle
+(run over exactly the same stream in the CPU-baseline leg).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision mixed|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload stream|stream192|batched|adjoint|sine] [--precision mixed|fp64]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this build) on the host cores.
 """
@@ -26,11 +31,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "slices/s and GB/s ingested at ≤1e-5 rel. error vs FP64 oracle; % of roofline"
-GRID = (192, 192, 96)
-NVAR = 12
-NBLOBS = 40
-TAU = 1e-4
 N_INIT = 10
+# single-stream workloads: (grid, variables, blobs, seed, tau)
+STREAMS = {
+    "stream": dict(grid=(384, 384, 256), nvar=4, nblobs=80, seed=5, tau=1e-4,
+                   name="advected-blob stream 384x384x256x4 fp32 slices (80 blobs, 604 MB per slice)"),
+    "stream192": dict(grid=(192, 192, 96), nvar=12, nblobs=40, seed=2, tau=1e-4,
+                      name="advected-blob stream 192x192x96x12 fp32 slices (40 blobs, 170 MB per slice)"),
+}
+DELTA_DEC = 1e-3    # relative distance of a near-cutoff decision from eps^2 (mixed form)
 PHASES = ["mode-1 projection + residual (k_tc_proj)", "k_ttm_proj (modes 2..d-1)", "growth (gram/eig/append)",
           "isvd (k_isvd_p/k_isvd_e/secular)", "factor (k_ud_update/k_core_m)", "k_cv_update (C and V)"]
 KERNEL_OF_PHASE = ["k_tc_proj<1, 0>", "k_tc_proj", "k_resid_gram", "k_isvd_e", "k_core_m", "k_cv_update"]
@@ -72,6 +81,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)   # the first sample lands inside the timed region
         except Exception:
             self.proc = None
 
@@ -113,27 +123,138 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_rate(updates: int, warmup: int = 0, slices=None):
-    """Time the FP64 oracle's stream_update on the full-size workload (host cores)."""
+def _blobfield(wl: str):
+    from workloads import BlobField
+
+    c = STREAMS[wl]
+    return BlobField(grid=c["grid"], nvar=c["nvar"], nblobs=c["nblobs"], noise=1e-5, seed=c["seed"])
+
+
+def _host64(y):
+    """A device slice (row-major (n_{d-1}, ..., n_1)) as a Fortran-ordered FP64 NumPy array."""
+    import numpy as np
+
+    return y.cpu().numpy().T.astype(np.float64)
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU-baseline leg: the FP64 oracle over the same stream, timed, and the parity of the GPU run
+# ---------------------------------------------------------------------------------------------
+
+def _oracle_margins(rec, eps2):
+    """Relative distances |stat - eps^2| / eps^2 of one oracle update's decisions."""
+    import numpy as np
+
+    out = {}
+    for m in rec["modes"]:
+        out[f"branch{m.k + 1}"] = abs(m.e_norm2 - eps2) / eps2
+        if m.grew and m.lam is not None:
+            lam = np.asarray(m.lam)
+            tails = np.concatenate([np.cumsum(lam[::-1])[::-1], [0.0]])
+            r = m.r_add
+            out[f"cut{m.k + 1}"] = min(abs(tails[r] - eps2), abs(tails[r - 1] - eps2)) / eps2
+    out["isvd"] = abs(rec["isvd"].q ** 2 - eps2) / eps2
+    return out
+
+
+def oracle_leg(wl: str, slices, W: int, K: int, snap: dict | None):
+    """Run the FP64 oracle (host cores) over the initial slices, the W warm-up updates and the K
+    timed updates of the GPU run; time the K timed updates; compare with the GPU snapshot."""
     import numpy as np
 
     import oracle as O
-    from workloads import BlobField
 
-    bf = BlobField(grid=GRID, nvar=NVAR, nblobs=NBLOBS, noise=1e-5, seed=2)
-    need = N_INIT + warmup + updates
-    if slices is None:
-        slices = [bf.slice_torch(t, "cuda").cpu().numpy().T.astype(np.float64) for t in range(need)]
-    X0 = np.asfortranarray(np.stack(slices[:N_INIT], axis=-1))
-    st = O.init_stream(X0, TAU)
+    tau = STREAMS[wl]["tau"]
+    X0 = np.asfortranarray(np.stack([_host64(slices[t]) for t in range(N_INIT)], axis=-1))
+    st = O.init_stream(X0, tau)
     del X0
-    for t in range(N_INIT, N_INIT + warmup):
-        O.stream_update(st, slices[t])
-    t0 = time.perf_counter()
-    for t in range(N_INIT + warmup, need):
-        O.stream_update(st, slices[t])
-    dt = time.perf_counter() - t0
-    return updates / dt, dt, st.ranks
+    for t in range(N_INIT, N_INIT + W):
+        O.stream_update(st, _host64(slices[t]))
+    dt = 0.0
+    for t in range(N_INIT + W, N_INIT + W + K):
+        Y = _host64(slices[t])
+        t0 = time.perf_counter()
+        O.stream_update(st, Y)
+        dt += time.perf_counter() - t0
+    cpu = {"value": K / dt, "unit": "slices/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"FP64 NumPy oracle on the same stream: initial ST-HOSVD of {N_INIT} slices and "
+                     f"{W} warm-up updates (untimed), then the {K} timed updates of the GPU run"}
+    if snap is None:
+        return cpu, None, st.ranks
+    par = {"delta_dec": DELTA_DEC}
+    upd = [r for r in st.log if r["kind"] == "update"]
+    gl = snap["log"]
+    trace_equal, first_flip = True, None
+    for i, (ro, rg) in enumerate(zip(upd, gl)):
+        if tuple(ro["ranks"]) != tuple(rg["ranks"]):
+            trace_equal = False
+            marg = _oracle_margins(ro, ro["eps"] ** 2)
+            first_flip = {"update": i, "t": N_INIT + i, "oracle_ranks": list(ro["ranks"]),
+                          "gpu_ranks": list(rg["ranks"]), "smallest_margin": min(marg.values()),
+                          "margins": {k: float(v) for k, v in marg.items()}}
+            break
+    par["updates_compared"] = len(gl)
+    par["rank_trace_equal"] = trace_equal
+    par["first_flip"] = first_flip
+    if first_flip is not None:
+        par["flip_within_delta_dec"] = first_flip["smallest_margin"] < DELTA_DEC
+    par["oracle_final_ranks"] = list(st.ranks)
+    par["gpu_final_ranks"] = list(snap["ranks"])
+    if trace_equal:
+        # reconstructions of the sampled slices (invariant to sign and rotation freedom)
+        rd = []
+        for t, xg in snap["recon"].items():
+            xo = O.reconstruct_slices(st, t, t + 1)[..., 0]
+            rd.append(float(np.linalg.norm(xg.astype(np.float64) - xo) / np.linalg.norm(xo)))
+        par["recon_slices"] = sorted(snap["recon"].keys())
+        par["recon_rel_diff_max"] = max(rd)
+        # largest principal angle between the oracle's and the GPU's factor subspaces
+        sines = []
+        for k, Ug in enumerate(snap["factors"]):
+            Uo = st.Us[k]
+            Pg = Ug - Uo @ (Uo.T @ Ug)
+            sines.append(float(np.linalg.norm(Pg, 2)))
+        par["subspace_sin_max"] = sines
+        # core after aligning the column signs of every factor
+        Cg = snap["core"]
+        for k, Ug in enumerate(snap["factors"]):
+            sg = np.sign(np.sum(st.Us[k] * Ug, axis=0))
+            sg[sg == 0] = 1.0
+            shape = [1] * Cg.ndim
+            shape[k] = -1
+            Cg = Cg * sg.reshape(shape)
+        par["core_rel_diff_aligned"] = float(np.linalg.norm(Cg - st.C) / np.linalg.norm(st.C))
+        par["recon_within_1e-5"] = par["recon_rel_diff_max"] <= 1e-5
+    par["gpu_true_rel_error"] = snap["true_rel"]
+    par["gpu_bound_rel"] = snap["bound_rel"]
+    par["oracle_bound_rel"] = math.sqrt(st.err2 / st.data_norm2)
+    par["tau"] = tau
+    par["error_within_tau"] = snap["true_rel"] <= tau
+    return cpu, par, st.ranks
+
+
+def gpu_snapshot(pkg, ts, slices, t_end: int, samples):
+    """State of the GPU run for the parity leg: update log, ranks, factors and core (FP64), the
+    reconstruction of a few slices, and the true error over every slice seen."""
+    import torch
+
+    d = ts.d
+    snap = {"log": ts.step_log(0, t_end - N_INIT), "ranks": ts.ranks}
+    snap["factors"] = [ts.factor(k).cpu().numpy() for k in range(d)]
+    snap["core"] = ts.core().cpu().numpy()
+    snap["recon"] = {}
+    err2 = tot2 = 0.0
+    for t in range(t_end):
+        xh = ts.reconstruct(t, t + 1)[0]
+        err2 += float(torch.sum((xh.double() - slices[t].double()) ** 2))
+        tot2 += float(torch.sum(slices[t].double() ** 2))
+        if t in samples:
+            snap["recon"][t] = xh.cpu().numpy().T.copy()
+        del xh
+    snap["true_rel"] = math.sqrt(err2 / tot2)
+    eb, dn = ts.error_norm()
+    snap["bound_rel"] = eb / dn
+    return snap
 
 
 def run_reference(args):
@@ -142,18 +263,21 @@ def run_reference(args):
         return
     import torch
 
+    wl = args.workload if args.workload in STREAMS else "stream"
     K = max(1, min(args.steps, 40))
     W = min(args.warmup, 5)
-    rate, dt, ranks = cpu_oracle_rate(K, W)
-    cores = os.cpu_count()
+    bf = _blobfield(wl)
+    slices = [bf.slice_torch(t, "cuda") for t in range(N_INIT + W + K)]
+    torch.cuda.synchronize()
+    cpu, _, ranks = oracle_leg(wl, slices, W, K, None)
+    rate = cpu["value"]
     line = {
         "metric": METRIC, "value": rate, "unit": "slices/s", "n_gpus": args.gpus, "steps": K,
-        "warmup": W, "ms_per_step": 1e3 * dt / K, "higher_is_better": True, "scaling": "weak",
+        "warmup": W, "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": "advected-blob stream 192x192x96x12 fp32 slices, tau=1e-4, n_init=10",
+        "config": {"workload": STREAMS[wl]["name"] + f", tau={STREAMS[wl]['tau']:g}, n_init={N_INIT}",
                    "parallelism": "host cores (numpy)"},
-        "cpu_baseline": {"value": rate, "unit": "slices/s", "cores": cores, "kind": "oracle",
-                         "sample": f"FP64 oracle: init on 10 slices, {W} warm-up + {K} timed updates"},
+        "cpu_baseline": dict(cpu),
         "e2e": {"value": rate, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "final_ranks": list(ranks),
     }
@@ -164,8 +288,10 @@ def run_ours(args):
     import torch
 
     import paper_2308_16395_gb300 as pkg
-    from workloads import BlobField
 
+    wl = args.workload
+    conf = STREAMS[wl]
+    tau = conf["tau"]
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     dist = None
@@ -173,11 +299,14 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    bf = BlobField(grid=GRID, nvar=NVAR, nblobs=NBLOBS, noise=1e-5, seed=2)
+    bf = _blobfield(wl)
     K, W = args.steps, args.warmup
-    T = N_INIT + W + K
+    KP = min(K, 8)                   # profiled updates (launch by launch, phase events)
+    KE = 0 if args.no_e2e else min(K, 10)   # end-to-end updates (host slices in)
+    T_timed = N_INIT + W + K
+    T = T_timed + KP + KE
     dev = torch.device("cuda", local)
-    slices = [bf.slice_torch(t, dev) for t in range(T)]         # (12, 96, 192, 192) FP32 each
+    slices = [bf.slice_torch(t, dev) for t in range(T)]         # row-major (nvar, n3, n2, n1) FP32
     torch.cuda.synchronize()
     slice_bytes = slices[0].numel() * slices[0].element_size()
     # the streaming rank never exceeds the number of slices seen, so that bounds its capacity
@@ -185,20 +314,15 @@ def run_ours(args):
     caps = [0, 0, 0, 0, min(256, (T + 4 + 7) // 8 * 8)]
     kw = dict(precision=args.precision, rank_cap=caps, steps_cap=T + 4, core_cap=4 << 20)
 
-    def fresh_state(last_from_host=None):
-        X0 = torch.stack(slices[:N_INIT]).contiguous()
-        ts = pkg.TuckerStream(X0, TAU, **kw)
-        del X0
-        for t in range(N_INIT, N_INIT + W):
-            if last_from_host is not None and t == N_INIT + W - 1:
-                ts.update_host(last_from_host)   # allocates the library's staging buffers
-            else:
-                ts.update(slices[t])
-        ts.ranks  # synchronizes, surfaces latched errors
-        return ts
+    X0 = torch.stack(slices[:N_INIT]).contiguous()
+    ts = pkg.TuckerStream(X0, tau, **kw)
+    del X0
+    torch.cuda.synchronize()
+    for t in range(N_INIT, N_INIT + W):
+        ts.update(slices[t])   # the first update captures the graph
+    ts.ranks  # synchronizes, surfaces latched errors
 
     # ---- device-resident timed region (graph form of the update) ----
-    ts = fresh_state()
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(local)
     clocks.start()
@@ -208,7 +332,7 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for t in range(N_INIT + W, T):
+    for t in range(N_INIT + W, T_timed):
         ts.update(slices[t])
     e1.record(stream)
     torch.cuda.synchronize()
@@ -219,35 +343,80 @@ def run_ours(args):
     graph_kernels = pkg.tucker_graph_kernels(ts.h)
     ranks = ts.ranks
     eb, dn = ts.error_norm()
-    ts.close()
+    log = ts.step_log(0, T_timed - N_INIT)
+    grown = sum(sum(r["grew"]) for r in log[W:])
     if dist:
         t_ = torch.tensor([ms], device=dev)
         dist.all_reduce(t_, op=dist.ReduceOp.MAX)
         ms = float(t_.item())
+    snap = None
+    want_parity = rank == 0 and ws == 1 and not args.no_cpu
+    if want_parity:
+        samples = {N_INIT + W, (N_INIT + W + T_timed - 1) // 2, T_timed - 1}
+        snap = gpu_snapshot(pkg, ts, slices, T_timed, samples)
 
-    # ---- the same steps launch by launch with CUDA events around each phase (phase breakdown,
-    # roofline of the mode-1 pass over the slice) ----
-    tp = fresh_state()
-    pkg.tucker_profile_enable(tp.h, 1)
+    # ---- the next KP updates of the same stream launch by launch, CUDA events around each
+    # phase and around the slice-pass kernel (phase breakdown, roofline of the slice pass) ----
+    pkg.tucker_profile_enable(ts.h, 1)
     torch.cuda.synchronize()
     p0 = torch.cuda.Event(enable_timing=True)
     p1 = torch.cuda.Event(enable_timing=True)
     p0.record(stream)
-    for t in range(N_INIT + W, T):
-        tp.update(slices[t])
+    for t in range(T_timed, T_timed + KP):
+        ts.update(slices[t])
     p1.record(stream)
     torch.cuda.synchronize()
     ms_eager = p0.elapsed_time(p1)
-    prof = pkg.tucker_profile_read(tp.h)
-    tp.close()
+    prof = pkg.tucker_profile_read(ts.h)
+    pkg.tucker_profile_enable(ts.h, 0)
+
+    # ---- end to end: the next KE slices from pinned host memory through the library's
+    # host-input update (tucker_stream_update_host: copy on the library's copy stream into
+    # alternating staging buffers, update after the copy, so slice t+1's copy overlaps update
+    # t), and the step's result (error bound and data norm) out every step into pinned host
+    # memory ----
+    e2e = None
+    if KE:
+        t_e = T_timed + KP
+        host = [slices[t].cpu().pin_memory() for t in range(t_e, t_e + KE)]
+        res = torch.zeros((KE, 2), dtype=torch.float64).pin_memory()
+        # the first host-input call allocates the staging buffers: outside the timed region
+        ts.update_host(host[0])
+        pkg.tucker_error_norm_async(ts.h, res[0].data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for i in range(1, KE):
+            ts.update_host(host[i])
+            pkg.tucker_error_norm_async(ts.h, res[i].data_ptr(), stream.cuda_stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = f0.elapsed_time(f1)
+        eb2 = ts.error_norm()[0]
+        assert abs(float(res[KE - 1, 0]) ** 0.5 - eb2) <= 1e-12 * (1 + eb2)
+        if dist:
+            t_ = torch.tensor([ms2], device=dev)
+            dist.all_reduce(t_, op=dist.ReduceOp.MAX)
+            ms2 = float(t_.item())
+        n_e = KE - 1
+        e2e = {"value": ws * n_e / (ms2 / 1e3), "unit": "slices/s", "h2d_bytes_per_step": slice_bytes,
+               "d2h_bytes_per_step": 16, "steps": n_e,
+               "api": "tucker_stream_update_host + tucker_error_norm_async",
+               "pipeline": "H2D of slice t+1 (library copy stream) overlaps update t",
+               "ms_per_step": ms2 / n_e}
+        del host
+    ts.close()
 
     # ---- the plain FP64 GPU form on the same slices (a few updates, graph form) ----
     fp64_form = None
-    if args.precision == "mixed" and not args.no_fp64:
+    if args.precision == "mixed" and not args.no_fp64 and wl == "stream192":
         K64 = min(K, 5)
         kw64 = dict(kw, precision="fp64")
         X0 = torch.stack(slices[:N_INIT]).contiguous()
-        t64 = pkg.TuckerStream(X0, TAU, **kw64)
+        t64 = pkg.TuckerStream(X0, tau, **kw64)
         del X0
         for t in range(N_INIT, N_INIT + W):
             t64.update(slices[t])
@@ -265,71 +434,42 @@ def run_ours(args):
                      "ranks": list(t64.ranks),
                      "note": "every step FP64 (SIMT contractions, FP64 eigensolves), same slices"}
         t64.close()
-
-    # ---- end to end: host slices (pinned) go in through the library's host-input update
-    # (tucker_stream_update_host: copy on the library's copy stream into alternating staging
-    # buffers, update after the copy, so slice t+1's copy overlaps update t), and the step's
-    # result (error bound and data norm) comes out every step into pinned host memory. ----
-    e2e = None
-    if not args.no_e2e:
-        host = [slices[t].cpu().pin_memory() for t in range(N_INIT + W, T)]
-        ts2 = fresh_state(last_from_host=slices[N_INIT + W - 1].cpu().pin_memory())
-        res = torch.zeros((K, 2), dtype=torch.float64).pin_memory()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for i in range(K):
-            ts2.update_host(host[i])
-            pkg.tucker_error_norm_async(ts2.h, res[i].data_ptr(), stream.cuda_stream)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms2 = f0.elapsed_time(f1)
-        assert abs(float(res[K - 1, 0]) ** 0.5 - ts2.error_norm()[0]) <= 1e-12 * (1 + ts2.error_norm()[0])
-        ts2.close()
-        if dist:
-            t_ = torch.tensor([ms2], device=dev)
-            dist.all_reduce(t_, op=dist.ReduceOp.MAX)
-            ms2 = float(t_.item())
-        e2e = {"value": ws * K / (ms2 / 1e3), "unit": "slices/s", "h2d_bytes_per_step": slice_bytes,
-               "d2h_bytes_per_step": 16, "api": "tucker_stream_update_host + tucker_error_norm_async",
-               "pipeline": "H2D of slice t+1 (library copy stream) overlaps update t"}
-        del host
+    elif wl == "stream":
+        fp64_form = {"skipped": "the FP64 form's eigensolves of 384 x 384 Grams run for seconds each "
+                                "on this part (FP64 is a small fraction of the FP32 rate); "
+                                "--workload stream192 carries the comparison"}
 
     # ---- roofline of the pass over the slice (live CUDA events, library byte accounting) ----
-    # The mode-1 projection + residual pass streams the slice (HBM-bound); the growth phase takes
-    # longer on average but is latency-bound (single-CTA eigensolves), see phases_*.
     peak, peak_src = _peaks()
     ph = 0
-    # the kernel alone: CUDA events around the launch of the mode-1 pass in the profiled updates
     ms_k = prof["ms_slice_pass"]
+    nprof = max(prof["updates"], 1)
     achieved = prof["bytes"][ph] / (ms_k / 1e3) / 1e9 if ms_k > 0 else 0.0
-    traffic = _traffic_table().get(KERNEL_OF_PHASE[ph])
+    traffic = _traffic_table().get(f"{KERNEL_OF_PHASE[ph]}@{wl}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": KERNEL_OF_PHASE[ph] + " (" + PHASES[ph] + ")",
-                "kernel_ms_per_launch": ms_k / max(prof["updates"], 1),
-                "algorithmic_bytes_per_launch": prof["bytes"][ph] / max(prof["updates"], 1),
+                "kernel_ms_per_launch": ms_k / nprof,
+                "algorithmic_bytes_per_launch": prof["bytes"][ph] / nprof,
                 "peak_source": peak_src,
-                "phases_ms_per_step": {PHASES[i]: prof["ms"][i] / max(prof["updates"], 1)
-                                       for i in range(len(PHASES))},
+                "profiled_updates": f"t={T_timed}..{T_timed + KP - 1} (the updates after the timed ones)",
+                "phases_ms_per_step": {PHASES[i]: prof["ms"][i] / nprof for i in range(len(PHASES))},
                 "phases_gbs": {PHASES[i]: (prof["bytes"][i] / (prof["ms"][i] / 1e3) / 1e9
                                            if prof["ms"][i] > 0 else 0.0) for i in range(len(PHASES))},
-                "launch_sequence_ms_per_step": ms_eager / K}
+                "launch_sequence_ms_per_step": ms_eager / max(KP, 1)}
 
     value = ws * K / (ms / 1e3)
     out = {
         "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": "advected-blob stream 192x192x96x12 fp32 slices (40 blobs), tau=1e-4, "
-                               f"n_init=10, timed updates t={N_INIT + W}..{T - 1}",
+        "config": {"workload": conf["name"] + f", tau={tau:g}, n_init={N_INIT}, "
+                               f"timed updates t={N_INIT + W}..{T_timed - 1}",
                    "precision": args.precision, "parallelism": "replicas" if ws > 1 else "1 gpu",
-                   "l2": "inputs larger than L2: every step reads a new 170 MB slice"},
+                   "l2": f"inputs larger than L2: every step reads a new {slice_bytes / 1e6:.0f} MB slice"},
         "gbs_ingested": value * slice_bytes / 1e9,
         "final_ranks": list(ranks), "rel_error_bound": eb / dn,
+        "grown_modes_in_timed_updates": grown,
         "gpu_launches": int(graph_kernels) * K,
         "gpu_launches_note": "kernel nodes of the update graph (conditional growth bodies included, an upper bound) x steps",
         "roofline": roofline,
@@ -337,15 +477,14 @@ def run_ours(args):
         "e2e": e2e,
         "fp64_form": fp64_form,
     }
-    if rank == 0 and ws == 1 and not args.no_cpu:
+    del slices[T_timed:]
+    if want_parity:
         try:
-            rate, dt, _ = cpu_oracle_rate(args.cpu_updates)
-            out["cpu_baseline"] = {"value": rate, "unit": "slices/s", "cores": os.cpu_count(),
-                                   "kind": "oracle",
-                                   "sample": f"FP64 oracle: init on the first 10 slices (untimed), "
-                                             f"{args.cpu_updates} timed updates of the same workload"}
+            cpu, par, _ = oracle_leg(wl, slices, W, K, snap)
+            out["cpu_baseline"] = cpu
+            out["parity"] = par
         except Exception as e:  # report, do not fail the GPU line
-            out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+            out["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -665,14 +804,14 @@ def run_sine(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="stream", choices=["stream", "adjoint", "batched", "sine"])
+    ap.add_argument("--workload", default="stream",
+                    choices=["stream", "stream192", "adjoint", "batched", "sine"])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--cpu-updates", type=int, default=3)
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg (CPU baseline and parity)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form comparison")
     args = ap.parse_args()

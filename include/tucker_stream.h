@@ -200,6 +200,54 @@ tucker_status tucker_get_ranks(tucker_state* s, int64_t* ranks_host, int64_t* n_
 /* Decisions of the most recent update. Synchronizes. */
 tucker_status tucker_get_step_info(tucker_state* s, tucker_step_info* info_host);
 
+/* Per-update log (Alg. 5 decisions). Every update since the initial ST-HOSVD leaves one record
+ * in a device array of steps_cap records (written by the update's last kernel, so recording
+ * costs no synchronization); tucker_get_step_log copies records [first, first + count) (0 = the
+ * first update after tucker_init_sthosvd) into out_host. The tails are Alg. 1's sums of the
+ * discarded eigenvalues of a grown mode's residual Gram at the chosen cut r'_k (tail_cut, the
+ * squared error that mode's truncation adds) and at r'_k - 1 (tail_prev, above eps^2 by the cut
+ * rule unless the cut was forced). Synchronizes. Errors: EINVAL (range beyond the updates
+ * recorded), latched device errors. */
+typedef struct {
+  int64_t n_d;                              /* n_d after the update */
+  int32_t ranks[TUCKER_MAX_MODES];          /* r_1..r_d after the update */
+  int32_t grew[TUCKER_MAX_MODES];           /* spatial mode k grew: ||E_k|| > eps (Alg. 4) */
+  int32_t r_add[TUCKER_MAX_MODES];          /* r'_k */
+  int32_t eig_path[TUCKER_MAX_MODES];       /* grown mode: 1 = subspace iteration + FP64
+                                               Rayleigh-Ritz cut, 2 = full tridiagonal solver */
+  int32_t eig_iters[TUCKER_MAX_MODES];      /* grown mode, path 1: subspace iterations */
+  int32_t augmented;                        /* q > eps (Alg. 3) */
+  int32_t replayed;                         /* 1 if tucker_replay_next forced this update */
+  double eps;                               /* tau ||Y|| / sqrt(d) */
+  double y_norm2;                           /* ||Y||^2 */
+  double e_norm2[TUCKER_MAX_MODES];         /* ||E_k||^2 */
+  double tail_cut[TUCKER_MAX_MODES];        /* grown mode: tail of the eigenvalues at r'_k */
+  double tail_prev[TUCKER_MAX_MODES];       /* grown mode: tail at r'_k - 1 */
+  double q;                                 /* ||e|| (Alg. 3) */
+  double discarded;                         /* squared error added by this update */
+} tucker_step_record;
+tucker_status tucker_get_step_log(tucker_state* s, int64_t first, int64_t count,
+                                  tucker_step_record* out_host);
+
+/* Decision replay: a TEST HOOK, not part of the method. Under mixed precision a decision whose
+ * statistic lies within a small relative distance of eps^2 (||E_k||^2 in Alg. 4, an eigenvalue
+ * tail at the cut of Alg. 1, q^2 in Alg. 3) can come out differently from an FP64 computation
+ * of the same step; once it has, the two states follow different paths and can no longer be
+ * compared. This call forces the decisions of the NEXT update (tucker_stream_update,
+ * tucker_stream_update_host or tucker_batch_update) of state s, so that a test can make the
+ * library take a reference's decision at such a step and keep comparing afterwards.
+ * grow[k] (k < d-1): -1 keeps the update's own decision for spatial mode k, 0 forces
+ * ||E_k|| <= eps (no growth), r > 0 forces growth with r'_k = r (clamped to n_k - r_k);
+ * augment: -1 keeps Alg. 3's own branch, 0 forces q <= eps, 1 forces q > eps (ignored when
+ * e = 0). The forced values reach the device with the next update, on its stream; the update
+ * that used them is marked in its log record. Synchronizes the state's last stream.
+ * Errors: EINVAL (NULL, values out of range), ESTATE, ECUDA. */
+typedef struct {
+  int32_t grow[TUCKER_MAX_MODES];
+  int32_t augment;
+} tucker_replay;
+tucker_status tucker_replay_next(tucker_state* s, const tucker_replay* r);
+
 /* Copy U_k (mode = 0..d-1, 0-based) as FP64 column-major (rows x r_k) into dst_dev, where rows
  * is n_k for spatial modes and n_d for the streaming mode. Synchronizes. */
 tucker_status tucker_copy_factor(tucker_state* s, int32_t mode, double* dst_dev);

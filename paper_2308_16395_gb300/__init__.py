@@ -29,7 +29,8 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint", "tucker_ttm_reconstruct_adjoint",
            "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy",
            "tucker_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
-           "tucker_get_launch_plan", "tucker_stream_update_host"]
+           "tucker_get_launch_plan", "tucker_stream_update_host", "tucker_get_step_log",
+           "tucker_replay_next"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -57,6 +58,21 @@ class StepInfo(ctypes.Structure):
                 ("r_add", ctypes.c_int32 * MAX_MODES), ("q", ctypes.c_double),
                 ("augmented", ctypes.c_int32), ("r_stream", ctypes.c_int32),
                 ("discarded", ctypes.c_double)]
+
+
+class StepRecord(ctypes.Structure):
+    _fields_ = [("n_d", ctypes.c_int64), ("ranks", ctypes.c_int32 * MAX_MODES),
+                ("grew", ctypes.c_int32 * MAX_MODES), ("r_add", ctypes.c_int32 * MAX_MODES),
+                ("eig_path", ctypes.c_int32 * MAX_MODES), ("eig_iters", ctypes.c_int32 * MAX_MODES),
+                ("augmented", ctypes.c_int32), ("replayed", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("y_norm2", ctypes.c_double),
+                ("e_norm2", ctypes.c_double * MAX_MODES), ("tail_cut", ctypes.c_double * MAX_MODES),
+                ("tail_prev", ctypes.c_double * MAX_MODES), ("q", ctypes.c_double),
+                ("discarded", ctypes.c_double)]
+
+
+class Replay(ctypes.Structure):
+    _fields_ = [("grow", ctypes.c_int32 * MAX_MODES), ("augment", ctypes.c_int32)]
 
 
 class Profile(ctypes.Structure):
@@ -96,6 +112,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_error_norm.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.tucker_get_ranks.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.tucker_get_step_info.argtypes = [vp, ctypes.POINTER(StepInfo)]
+    lib.tucker_get_step_log.argtypes = [vp, i64, i64, ctypes.POINTER(StepRecord)]
+    lib.tucker_replay_next.argtypes = [vp, ctypes.POINTER(Replay)]
     lib.tucker_copy_factor.argtypes = [vp, i32, vp]
     lib.tucker_copy_core.argtypes = [vp, vp]
     lib.tucker_copy_sv.argtypes = [vp, vp, vp]
@@ -135,7 +153,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     for name in ("tucker_profile_enable", "tucker_profile_read", "tucker_init_sthosvd", "tucker_stream_update",
                  "tucker_stream_update_host", "tucker_reconstruct",
                  "tucker_reconstruct_noalloc", "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
-                 "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv"):
+                 "tucker_get_step_log", "tucker_replay_next", "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv"):
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -223,6 +241,36 @@ def tucker_get_step_info(h: int, d: int) -> dict:
     return dict(eps=s.eps, y_norm2=s.y_norm2, e_norm2=[s.e_norm2[i] for i in range(m)],
                 grew=[bool(s.grew[i]) for i in range(m)], r_add=[s.r_add[i] for i in range(m)],
                 q=s.q, augmented=bool(s.augmented), r_stream=s.r_stream, discarded=s.discarded)
+
+
+def tucker_get_step_log(h: int, d: int, first: int, count: int) -> list[dict]:
+    """Records [first, first + count) of the per-update log, one dict per update."""
+    arr = (StepRecord * max(count, 1))()
+    _check(load_library().tucker_get_step_log(h, int(first), int(count), arr), h)
+    m = d - 1
+    out = []
+    for i in range(count):
+        r = arr[i]
+        out.append(dict(n_d=int(r.n_d), ranks=tuple(int(r.ranks[k]) for k in range(d)),
+                        grew=[bool(r.grew[k]) for k in range(m)], r_add=[int(r.r_add[k]) for k in range(m)],
+                        eig_path=[int(r.eig_path[k]) for k in range(m)],
+                        eig_iters=[int(r.eig_iters[k]) for k in range(m)],
+                        augmented=bool(r.augmented), replayed=bool(r.replayed), eps=r.eps,
+                        y_norm2=r.y_norm2, e_norm2=[r.e_norm2[k] for k in range(m)],
+                        tail_cut=[r.tail_cut[k] for k in range(m)],
+                        tail_prev=[r.tail_prev[k] for k in range(m)], q=r.q, discarded=r.discarded))
+    return out
+
+
+def tucker_replay_next(h: int, grow, augment: int = -1) -> None:
+    """Test hook: force the decisions of the next update (grow[k]: -1 own, 0 none, r > 0)."""
+    rp = Replay()
+    for k in range(MAX_MODES):
+        rp.grow[k] = -1
+    for k, v in enumerate(grow):
+        rp.grow[k] = int(v)
+    rp.augment = int(augment)
+    _check(load_library().tucker_replay_next(h, ctypes.byref(rp)), h)
 
 
 def tucker_copy_factor(h: int, mode: int, dst_ptr: int) -> None:
@@ -426,6 +474,7 @@ class TuckerStream:
         self.cfg = make_config(self.n, tau, dtype=dt, precision=precision, rank_cap=rank_cap,
                                steps_cap=steps_cap, core_cap=core_cap, eps_m=eps_m)
         self._stream = stream
+        self.n_init = int(X.shape[0])
         self.h = tucker_init_sthosvd(self.cfg, X.data_ptr(), X.shape[0], self._sp())
 
     def _sp(self) -> int:
@@ -460,6 +509,16 @@ class TuckerStream:
 
     def step_info(self) -> dict:
         return tucker_get_step_info(self.h, self.d)
+
+    def step_log(self, first: int = 0, count: int | None = None) -> list[dict]:
+        """Per-update records (decisions, norms, tails) of updates [first, first + count)."""
+        if count is None:
+            count = self.n_d - self.n_init - first
+        return tucker_get_step_log(self.h, self.d, first, count)
+
+    def replay_next(self, grow, augment: int = -1) -> None:
+        """Test hook: force the next update's decisions (see tucker_replay_next)."""
+        tucker_replay_next(self.h, grow, augment)
 
     def reconstruct(self, t0: int, t1: int):
         import torch

@@ -119,11 +119,23 @@ struct tucker_state {
   cudaStream_t hcs = nullptr;
   cudaEvent_t hcopied[2]{}, hconsumed[2]{};
   int hnext = 0;
+  // per-update log (StepRec per update) and the replay hook's pinned staging words
+  StepRec* log = nullptr;
+  long long log_cap = 0;
+  int* rp_host = nullptr;
+  bool rp_pending = false;
 };
 
 namespace {
 
-const char* kVersion = "tucker_stream 0.1 (sm_103a)";
+const char* kVersion = "tucker_stream 0.2 (sm_103a)";
+
+// rp_on, rp_grow[TK_MAXD], rp_aug: contiguous words of the control block
+constexpr size_t kReplayBytes = sizeof(int) * (2 + TK_MAXD);
+static_assert(offsetof(Ctl, rp_aug) == offsetof(Ctl, rp_on) + sizeof(int) * (1 + TK_MAXD), "replay words contiguous");
+static_assert(sizeof(StepRec) == sizeof(tucker_step_record), "step record layout");
+static_assert(offsetof(StepRec, eps) == offsetof(tucker_step_record, eps), "step record layout");
+static_assert(offsetof(StepRec, discarded) == offsetof(tucker_step_record, discarded), "step record layout");
 
 void set_err(tucker_state* s, const char* fmt, const char* a = "", long long b = 0) {
   if (!s) return;
@@ -157,6 +169,8 @@ void free_all(tucker_state* s) {
   s->allocs.clear();
   if (s->hctl) cudaFreeHost(s->hctl);
   s->hctl = nullptr;
+  if (s->rp_host) cudaFreeHost(s->rp_host);
+  s->rp_host = nullptr;
 }
 
 tucker_status map_status(int st) {
@@ -265,6 +279,8 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
   CK(cudaMallocHost((void**)&s->hctl, sizeof(Ctl)));
   memset(s->hctl, 0, sizeof(Ctl));
   CK(dalloc(s, (void**)&s->ctl, sizeof(Ctl)));
+  s->log_cap = s->steps_cap;
+  CK(dalloc(s, (void**)&s->log, sizeof(StepRec) * (size_t)s->log_cap));
   for (int i = 0; i < 3; ++i) CK(dalloc(s, &s->dbuf[i], (size_t)maxD * tw));
   CK(dalloc(s, (void**)&s->d_dbufs, sizeof(void*) * 3));
   CK(cudaMemcpy(s->d_dbufs, s->dbuf, sizeof(void*) * 3, cudaMemcpyHostToDevice));
@@ -432,6 +448,8 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
   h.N = s->N;
   h.tcmask = s->tcmask;
   h.etmask = s->etmask;
+  h.log = s->log;
+  h.log_cap = s->log_cap;
   // ||X||^2 -> eps (Alg. 2, first step)
   const long long NX = s->N * n_init;
   CK(launch_norm2<TX>(X, NX, s->part_y2, 1024, st));
@@ -501,6 +519,17 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
     const int rd = c.r[d - 1];
     cudaError_t e = launch_init_finish<TW>(s->ctl, ib[c.xbuf], R, rd, s->elam, Utmp, (int)n_init, s->Cb[0], s->Vb[0],
                                            s->Ud[0], s->S, s->ldc, st);
+    if (e == cudaSuccess && s->tw == 4) {
+      // mixed form: C_(d)^T = C*_{d-1} U_d again in FP64 (U_d row-major in Ud[0] now), and C, V
+      // from it; C*_{d-1} is the buffer before the last mode's output
+      double* C64 = nullptr;
+      e = cudaMalloc((void**)&C64, sizeof(double) * (size_t)R * rd);
+      if (e == cudaSuccess)
+        e = launch_expand<float, double, double>(ib[(c.xbuf + 2) % 3], R, (int)n_init, 1, s->Ud[0], s->ldc, rd, C64, st);
+      if (e == cudaSuccess) e = launch_init_cv64<float>(C64, R, rd, s->elam, s->Cb[0], s->Vb[0], s->ldc, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (C64) cudaFree(C64);
+    }
     if (e != cudaSuccess) { set_err(s, "CUDA error (%s) in the core factorization (R = %lld)", cudaGetErrorString(e), R); rc = TUCKER_ECUDA; }
     if (rc == TUCKER_OK) {
       double err2 = 0.0;
@@ -641,7 +670,15 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
         CK((launch_resid_gram<TW, TW>(s->ctl, k, n, Y, s->d_dbufs, s->Uw[k], n, s->gpart, pairs,
                                       chunks, 0, st)));
       CK(launch_gram_reduce(s->ctl, k, s->gpart, pairs, chunks, s->G, 0, st));
-      CK(launch_eig<TE>(s->ctl, k, 0, s->G, s->eAw, s->eZ, s->eLD, s->eW, nullptr, s->mcap, n, st));
+      if (sizeof(TE) == 4) {
+        // mixed form: subspace iteration with the cut in FP64; the full FP32 tridiagonal solver
+        // only where that cannot certify the cut
+        CK(launch_eig_sub(s->ctl, k, s->G, s->eAw, s->eW, s->mcap, s->gpart, n, st));
+        CK(launch_eig<TE>(s->ctl, k, 2, s->G, s->eAw, s->eZ, s->eLD, s->eW, nullptr, s->mcap, n, st));
+        launches += 2;
+      } else {
+        CK(launch_eig<TE>(s->ctl, k, 0, s->G, s->eAw, s->eZ, s->eLD, s->eW, nullptr, s->mcap, n, st));
+      }
       CK(launch_append<TW>(s->ctl, k, 0, s->eW, s->U[k], (s->tw == 8) ? nullptr : s->Uw[k], n, n, st));
       if (tck) {
         CK(launch_split_u(s->ctl, k, 1, s->U[k], n, s->usplit[k], st));
@@ -942,6 +979,16 @@ tucker_status capture_batch(tucker_batch* b, const void* const* Y, cudaStream_t*
   return TUCKER_OK;
 }
 
+// The replay hook's forced decisions (tucker_replay_next) go into the control block on the
+// stream of the update they apply to.
+tucker_status push_replay(tucker_state* s, cudaStream_t st) {
+  if (!s->rp_pending) return TUCKER_OK;
+  s->rp_pending = false;
+  CK(cudaMemcpyAsync(reinterpret_cast<unsigned char*>(s->ctl) + offsetof(Ctl, rp_on), s->rp_host,
+                     kReplayBytes, cudaMemcpyHostToDevice, st));
+  return TUCKER_OK;
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -1029,6 +1076,8 @@ tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* str
   if (!usable(s)) return TUCKER_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
   s->last_stream = st;
+  tucker_status rp = push_replay(s, st);
+  if (rp != TUCKER_OK) return rp;
   // Graph form (unless phase profiling is on): the update is captured once; each call writes
   // the slice's address (and its TMA descriptor) into the control block with a one-block kernel
   // and launches the graph.
@@ -1182,6 +1231,43 @@ tucker_status tucker_get_step_info(tucker_state* s, tucker_step_info* info) {
   return TUCKER_OK;
 }
 
+tucker_status tucker_get_step_log(tucker_state* s, int64_t first, int64_t count,
+                                  tucker_step_record* out) {
+  if (!s || !out || first < 0 || count < 0) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  const long long have = std::min<long long>(s->hctl->nupdates, s->log_cap);
+  if (first + count > have) {
+    set_err(s, "step log holds updates [0, %s%lld)", "", have);
+    return TUCKER_EINVAL;
+  }
+  if (count == 0) return TUCKER_OK;
+  CK(cudaMemcpyAsync(out, s->log + first, sizeof(StepRec) * (size_t)count, cudaMemcpyDeviceToHost,
+                     s->last_stream));
+  CK(cudaStreamSynchronize(s->last_stream));
+  return TUCKER_OK;
+}
+
+tucker_status tucker_replay_next(tucker_state* s, const tucker_replay* r) {
+  if (!s || !r) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  for (int k = 0; k < s->d - 1; ++k) {
+    if (r->grow[k] < -1 || r->grow[k] > s->n[k]) {
+      set_err(s, "replay: grow[%s%lld] out of range", "", k);
+      return TUCKER_EINVAL;
+    }
+  }
+  if (r->augment < -1 || r->augment > 1) return TUCKER_EINVAL;
+  if (!s->rp_host) CK(cudaMallocHost((void**)&s->rp_host, kReplayBytes));
+  // the staging words of an earlier replay must have reached the device
+  CK(cudaStreamSynchronize(s->last_stream));
+  s->rp_host[0] = 1;
+  for (int k = 0; k < TK_MAXD; ++k) s->rp_host[1 + k] = (k < s->d - 1) ? r->grow[k] : -1;
+  s->rp_host[1 + TK_MAXD] = r->augment;
+  s->rp_pending = true;
+  return TUCKER_OK;
+}
+
 tucker_status tucker_copy_factor(tucker_state* s, int32_t mode, double* dst) {
   if (!s || !dst || mode < 0 || mode >= s->d) return TUCKER_EINVAL;
   tucker_status rc = sync_ctl(s);
@@ -1272,6 +1358,8 @@ tucker_status tucker_batch_update(tucker_batch* b, void* stream) {
   for (tucker_state* s : b->states)
     if (!usable(s)) return TUCKER_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
+  for (tucker_state* s : b->states)
+    if (push_replay(s, st) != TUCKER_OK) return TUCKER_ECUDA;
   if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return TUCKER_ECUDA;
   for (tucker_state* s : b->states) s->last_stream = st;
   return TUCKER_OK;

@@ -63,12 +63,55 @@ struct Ctl {
   double acc_bytes[8];
   // ---- completion tickets of the cross-block reductions (zero between launches) ----
   unsigned ticket[4];
+  // ---- Alg. 1's tails of the grown modes: tail at r'_k - 1 (the tail at r'_k is disc[k]) ----
+  double tail_prev[TK_MAXD];
+  // ---- growth eigensolver of the mixed form (k_eig_sub / k_eig_refine): eig_m[k] candidate
+  // eigenvectors in W, eig_it[k] subspace iterations, eig_fb[k] = 1 when the full tridiagonal
+  // solver must decide instead ----
+  int eig_m[TK_MAXD];
+  int eig_it[TK_MAXD];
+  int eig_fb[TK_MAXD];
+  double eig_tr[TK_MAXD];   // trace(G) of the residual Gram, FP64
+  // ---- decision replay (a test hook): branches and cuts forced on the next update, written
+  // by the host before the update and cleared by k_end_update. rp_grow[k] < 0 keeps mode k's
+  // own decision, 0 forces ||E_k|| <= eps, r > 0 forces growth by r'_k = r; rp_aug < 0 keeps
+  // Alg. 3's own branch, 0 forces q <= eps, 1 forces q > eps ----
+  int rp_on;
+  int rp_grow[TK_MAXD];
+  int rp_aug;
+  // ---- per-update log (device array of StepRec, one per update since the initial ST-HOSVD;
+  // written by k_end_update while nupdates < log_cap) ----
+  struct StepRec* log;
+  long long log_cap;
   // ---- slice of the current update when the update runs as a CUDA graph (written by one
   // host-to-device copy before each launch): TMA descriptor of the slice as a row-major
   // (N / n_1) x n_1 FP32 matrix (only with the tensor-core mode-1 pass) and its address ----
   alignas(128) unsigned char ymap[128];
   const void* yptr;
 };
+
+// One update's decisions as the host reads them back (same layout as tucker_step_record).
+struct StepRec {
+  long long nd;
+  int r[TK_MAXD];
+  int grew[TK_MAXD];
+  int radd[TK_MAXD];
+  int eig_path[TK_MAXD];
+  int eig_it[TK_MAXD];
+  int aug;
+  int replayed;
+  double eps;
+  double y2;
+  double e2[TK_MAXD];
+  double tail_cut[TK_MAXD];
+  double tail_prev[TK_MAXD];
+  double q;
+  double discarded;
+};
+
+// Forced decisions of the replay hook (a test hook; see Ctl::rp_on).
+__device__ __forceinline__ int rp_grow_of(const Ctl* c, int k) { return c->rp_on ? c->rp_grow[k] : -1; }
+__device__ __forceinline__ int rp_aug_of(const Ctl* c) { return c->rp_on ? c->rp_aug : -1; }
 
 // Phases of one update (profiling and byte accounting).
 #define TK_PH_PROJ1 0    // mode-1 projection + residual norm (the pass over the slice)

@@ -282,6 +282,12 @@ __global__ void __launch_bounds__(NW * 32, 1) k_tridiag_reg(Ctl* ctl, int k, int
                                                           float* tri) {
   static_assert(RA % 2 == 0, "register rows are paired");
   if (ctl->status) return;
+  // mode 2: residual Gram handed over by the subspace solver (k_eig_sub.cu) only when it set
+  // eig_fb[k]; otherwise as mode 0
+  if (mode == 2) {
+    if (!ctl->eig_fb[k]) return;
+    mode = 0;
+  }
   if (mode == 0 && !ctl->grew[k]) return;
   const int d = ctl->d;
   const int n = (k == d - 1) ? ctl->init_nt : ctl->n[k];
@@ -505,11 +511,17 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
                                                     int use_smem, int use_amat, int pre) {
   extern __shared__ __align__(16) unsigned char eig_dyn[];
   if (ctl->status) return;
+  if (mode == 2) {   // fallback of the subspace solver (see k_tridiag_reg)
+    if (!ctl->eig_fb[k]) return;
+    mode = 0;
+  }
   if (mode == 0 && !ctl->grew[k]) return;
   const int d = ctl->d;
   const int n = (k == d - 1) ? ctl->init_nt : ctl->n[k];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
+  // decision replay (test hook): a cut forced for this update
+  const int want = (mode == 0) ? max(rp_grow_of(ctl, k), 0) : 0;
   TE* A = use_amat ? reinterpret_cast<TE*>(eig_dyn) : reinterpret_cast<TE*>(ea.Aw);
   __shared__ TE sa[TK_N_MAX], sb[TK_N_MAX], sb2[TK_N_MAX], stau[TK_N_MAX], slam[TK_N_MAX];
   __shared__ TE sv[TK_N_MAX], sp[TK_N_MAX];
@@ -676,7 +688,7 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
     // small because the cut of a residual Gram usually keeps a few eigenpairs. The initial
     // ST-HOSVD (mode 1) computes every eigenvalue: its discarded energy is a tiny fraction of the
     // trace, so it is summed from the bottom of the spectrum below instead.
-    for (int j0 = 0; j0 < n && (j0 == 0 || s_cut < 0 || mode == 1); j0 += (j0 == 0 ? bs0 : nwarp)) {
+    for (int j0 = 0; j0 < n && (j0 == 0 || s_cut < 0 || mode == 1 || s_cnt < want); j0 += (j0 == 0 ? bs0 : nwarp)) {
       const int bs = (j0 == 0) ? bs0 : nwarp;
       const int j = j0 + wid;            // descending index of this warp's eigenvalue
       if (wid < bs && j < n) {
@@ -764,8 +776,10 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
     s_cut = cut;
     s_cnt = n;
   }
+  __shared__ double s_tprev;
   if (tid == 0) {
     int m = s_cut;
+    if (want > 0) m = min(want, s_cnt);
     int status = 0;
     if (mode == 0) {
       const int rk = ctl->r[k];
@@ -779,6 +793,7 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
     if (status) ctl->status = status;
     s_m = status ? 0 : m;
     s_disc = (m <= s_cnt) ? stails[m] : 0.0;
+    s_tprev = (m >= 1 && m - 1 <= s_cnt) ? stails[m - 1] : 0.0;
   }
   __syncthreads();
   const int m = s_m;
@@ -786,7 +801,7 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
     for (int i = tid; i < s_cnt; i += nt) ea.lam_out[i] = (double)slam[i];
   if (m == 0) {
     if (tid == 0) {
-      if (mode == 0) { ctl->radd[k] = 0; ctl->disc[k] = s_disc; }
+      if (mode == 0) { ctl->radd[k] = 0; ctl->disc[k] = s_disc; ctl->tail_prev[k] = s_tprev; }
       else { ctl->r[k] = 0; ctl->disc[k] = s_disc; }
     }
     return;
@@ -973,7 +988,7 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
       }
     }
     if (tid == 0) {
-      if (mode == 0) { ctl->radd[k] = m; ctl->disc[k] = s_disc; }
+      if (mode == 0) { ctl->radd[k] = m; ctl->disc[k] = s_disc; ctl->tail_prev[k] = s_tprev; }
       else { ctl->r[k] = m; ctl->disc[k] = s_disc; }
     }
     return;
@@ -1162,7 +1177,7 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
   __syncthreads();
   for (long long L = tid; L < (long long)m * n; L += nt) ea.W[L] = (double)Z[L];
   if (tid == 0) {
-    if (mode == 0) { ctl->radd[k] = m; ctl->disc[k] = s_disc; }
+    if (mode == 0) { ctl->radd[k] = m; ctl->disc[k] = s_disc; ctl->tail_prev[k] = s_tprev; }
     else { ctl->r[k] = m; ctl->disc[k] = s_disc; }
   }
 }

@@ -1,0 +1,526 @@
+// Growth eigensolver of the mixed form: the top eigenpairs of a residual Gram G = E_(k) E_(k)^T
+// and Alg. 1's rank cut (inside Alg. 4), without the O(n^3) tridiagonalization.
+//
+// Alg. 1 keeps the smallest l with lambda_{l+1} + ... + lambda_n <= eps^2. For a residual Gram
+// the cut sits at the top of the spectrum (||E_k||^2 = trace(G) exceeds eps^2 by a little), so
+// only the few eigenpairs above the cut are needed:
+//
+//   k_eig_sub     one CTA, FP32: block subspace iteration Z = G Q on SB vectors with a
+//                 Rayleigh-Ritz step every iteration (Golub & Van Loan, Matrix Computations,
+//                 Sec. 8.2.4 "orthogonal iteration" and Sec. 8.1.2 Rayleigh-Ritz), cyclic Jacobi
+//                 for the SB x SB projected matrix (Sec. 8.5.3, parallel ordering), column-scaled
+//                 Cholesky QR applied twice for the orthonormalization. It stops when the
+//                 residuals ||G q_c - theta_c q_c|| of the Ritz pairs up to one past the FP32 cut
+//                 are below SUB_TOL theta_1, and hands those m Ritz vectors on.
+//   k_eig_refine  all SMs, FP64: P = W^T G W and M = W^T W for the m vectors, then the cut in
+//                 FP64 from the nested Rayleigh-Ritz sums: the energy of G captured by
+//                 span(w_1..w_l) is trace(M_l^-1 P_l) (leading l x l blocks), evaluated to first
+//                 order in Delta = M - I (|Delta| is at FP32 rounding level, so the neglected
+//                 terms are ~|Delta|^2 |P|); tail(l) = trace(G) - that energy, with trace(G)
+//                 summed in FP64 from G's diagonal. tail(l) is the exact discarded energy of the
+//                 subspace that the augmentation appends.
+//
+// When the subspace step cannot certify the cut (no convergence within SUB_MAXIT iterations, the
+// cut deeper than SB - 2 vectors, a Cholesky breakdown, small problems) it sets ctl->eig_fb[k]
+// and the full tridiagonal solver of k_eig.cu (predicated on that flag) decides instead.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tk {
+
+constexpr int SB = 16;                   // block size of the subspace iteration
+constexpr int SUB_NT = 512;              // one thread per row of Q and Z (n <= 512)
+constexpr int SUB_NW = SUB_NT / 32;
+constexpr int SUB_MAXIT = 40;
+constexpr float SUB_TOL = 4e-6f;         // Ritz residual / theta_1 accepted as converged
+constexpr int SUB_GS_NMAX = 192;         // G held in shared memory (FP32) up to this n
+constexpr int SUB_NMIN = 48;             // smaller Grams go to the full solver (cheap there)
+constexpr int REF_NT = 128;
+constexpr int REF_MAXB = 96;             // CTAs of k_eig_refine
+
+// Counter-based start vectors (a hash of row and column): deterministic, entries in [-1, 1).
+__device__ __forceinline__ float sub_hash(int i, int c) {
+  unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)(c + 1) * 0x85EBCA77u);
+  h ^= h >> 16; h *= 0x7FEB352Du; h ^= h >> 15; h *= 0x846CA68Bu; h ^= h >> 16;
+  return (float)(h >> 8) * (2.0f / 16777216.0f) - 1.0f;
+}
+
+// Sum over the block of the SB x SB outer products a_i b_i^T of every thread's row vectors,
+// into out[SB * SB] (shared). Four rounds of 64 values (rows 4g .. 4g + 3 of the product): a
+// butterfly reduce-scatter leaves lane l with the warp sums of values 2l and 2l + 1, the warps'
+// sums are then added in warp order (a fixed order: deterministic).
+__device__ void sub_outer_sum(const float (&a)[SB], const float (&b)[SB], float* red, float* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int g = 0; g < SB / 4; ++g) {
+    float p[64];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) p[r * 16 + c] = a[4 * g + r] * b[c];
+#pragma unroll
+    for (int lev = 0; lev < 5; ++lev) {
+      const int M = 16 >> lev;          // lane bit exchanged at this level
+      const int H = 32 >> lev;          // half of the values still held
+      const bool up = (lane & M) != 0;
+#pragma unroll
+      for (int t = 0; t < H; ++t) {
+        const float keep = up ? p[H + t] : p[t];
+        const float send = up ? p[t] : p[H + t];
+        p[t] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+      }
+    }
+    red[wid * 64 + 2 * lane] = p[0];
+    red[wid * 64 + 2 * lane + 1] = p[1];
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      float s = 0.f;
+      for (int w = 0; w < SUB_NW; ++w) s += red[w * 64 + threadIdx.x];
+      out[64 * g + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Block sums of SB per-thread values into out[SB] (shared): reduce-scatter to lanes 2c, 2c + 1
+// holding value c, then warp order.
+__device__ void sub_vec_sum(const float (&v)[SB], float* red, float* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float p[SB];
+#pragma unroll
+  for (int c = 0; c < SB; ++c) p[c] = v[c];
+#pragma unroll
+  for (int lev = 0; lev < 4; ++lev) {
+    const int M = 16 >> lev;
+    const int H = 8 >> lev;
+    const bool up = (lane & M) != 0;
+#pragma unroll
+    for (int t = 0; t < H; ++t) {
+      const float keep = up ? p[H + t] : p[t];
+      const float send = up ? p[t] : p[H + t];
+      p[t] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+    }
+  }
+  const float tot = p[0] + __shfl_xor_sync(0xffffffffu, p[0], 1);   // value lane >> 1
+  if ((lane & 1) == 0) red[wid * SB + (lane >> 1)] = tot;
+  __syncthreads();
+  if (threadIdx.x < SB) {
+    float s = 0.f;
+    for (int w = 0; w < SUB_NW; ++w) s += red[w * SB + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Cyclic Jacobi on the symmetric SB x SB matrix H (shared, row stride SB + 1), one warp: each
+// round rotates SB / 2 disjoint pairs (round-robin ordering), Rutishauser's rotation formulas;
+// Y accumulates the rotations (Y <- Y J). Stops after a sweep that found every off-diagonal entry
+// negligible against its diagonal pair, or after 10 sweeps.
+__device__ void sub_jacobi(float* H, float* Y, float* cs, int lane) {
+  constexpr int L = SB + 1;
+#pragma unroll 1
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    int rotated = 0;
+#pragma unroll 1
+    for (int rnd = 0; rnd < SB - 1; ++rnd) {
+      if (lane < SB / 2) {
+        auto pos = [&](int x) { return x == 0 ? 0 : 1 + (x - 1 + rnd) % (SB - 1); };
+        const int p = pos(lane), q = pos(SB - 1 - lane);
+        const float hpp = H[p * L + p], hqq = H[q * L + q], hpq = H[p * L + q];
+        float c = 1.f, s = 0.f;
+        if (fabsf(hpq) > 1e-7f * sqrtf(fabsf(hpp * hqq)) && fabsf(hpq) > 1e-37f) {
+          const float th = (hqq - hpp) / (2.f * hpq);
+          const float t = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+          c = rsqrtf(fmaf(t, t, 1.f));
+          s = t * c;
+          rotated = 1;
+        }
+        cs[4 * lane] = c;
+        cs[4 * lane + 1] = s;
+        reinterpret_cast<int*>(cs)[4 * lane + 2] = p;
+        reinterpret_cast<int*>(cs)[4 * lane + 3] = q;
+      }
+      __syncwarp();
+      // H <- H J (columns p, q of every row), then H <- J^T H (rows p, q), Y <- Y J
+      for (int it = lane; it < (SB / 2) * SB; it += 32) {
+        const int pr = it / SB, x = it % SB;
+        const float c = cs[4 * pr], s = cs[4 * pr + 1];
+        const int p = reinterpret_cast<const int*>(cs)[4 * pr + 2], q = reinterpret_cast<const int*>(cs)[4 * pr + 3];
+        const float hp = H[x * L + p], hq = H[x * L + q];
+        H[x * L + p] = c * hp - s * hq;
+        H[x * L + q] = s * hp + c * hq;
+        const float yp = Y[x * L + p], yq = Y[x * L + q];
+        Y[x * L + p] = c * yp - s * yq;
+        Y[x * L + q] = s * yp + c * yq;
+      }
+      __syncwarp();
+      for (int it = lane; it < (SB / 2) * SB; it += 32) {
+        const int pr = it / SB, x = it % SB;
+        const float c = cs[4 * pr], s = cs[4 * pr + 1];
+        const int p = reinterpret_cast<const int*>(cs)[4 * pr + 2], q = reinterpret_cast<const int*>(cs)[4 * pr + 3];
+        const float hp = H[p * L + x], hq = H[q * L + x];
+        H[p * L + x] = c * hp - s * hq;
+        H[q * L + x] = s * hp + c * hq;
+      }
+      __syncwarp();
+    }
+    if (!__any_sync(0xffffffffu, rotated)) break;
+  }
+}
+
+// Cholesky R^T R = M of the SB x SB matrix M (shared, stride SB + 1, overwritten), one warp;
+// R upper triangular into R (stride SB + 1), rinv[c] = 1 / R(c, c). Returns false on a
+// non-positive pivot.
+__device__ bool sub_cholesky(float* M, float* R, float* rinv, int lane) {
+  constexpr int L = SB + 1;
+  bool ok = true;
+#pragma unroll 1
+  for (int c = 0; c < SB; ++c) {
+    const float dcc = M[c * L + c];
+    if (!(dcc > 0.f)) ok = false;
+    const float rcc = ok ? sqrtf(dcc) : 1.f;
+    const float ri = 1.f / rcc;
+    if (lane < SB) R[c * L + lane] = lane < c ? 0.f : (lane == c ? rcc : M[c * L + lane] * ri);
+    if (lane == 0) rinv[c] = ri;
+    __syncwarp();
+    for (int it = lane; it < SB * SB; it += 32) {
+      const int x = it / SB, y = it % SB;
+      if (x > c && y > c) M[x * L + y] -= R[c * L + x] * R[c * L + y];
+    }
+    __syncwarp();
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+struct SubArgs {
+  const double* G;   // n x n residual Gram (FP64, column-major, symmetric)
+  float* Gf;         // n x n FP32 scratch (global) when G does not fit in shared memory
+  double* W;         // n x mcap: the m Ritz vectors (FP64 copies)
+  int mcap;
+};
+
+__global__ void __launch_bounds__(SUB_NT, 1) k_eig_sub(Ctl* ctl, int k, SubArgs a) {
+  extern __shared__ __align__(16) float sub_dyn[];
+  if (ctl->status || !ctl->grew[k]) return;
+  const int n = ctl->n[k];
+  const int r0 = ctl->r[k];
+  const int nfree = n - r0;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int want = max(rp_grow_of(ctl, k), 0);
+  // small or nearly full problems, or a forced cut deeper than the block: the full solver
+  if (n < SUB_NMIN || nfree < SB + 2 || want + 1 > SB - 2 || n > SUB_NT) {
+    if (tid == 0) ctl->eig_fb[k] = 1;
+    return;
+  }
+  const bool gsm = n <= SUB_GS_NMAX;
+  float* Gs = sub_dyn;                                   // n x n (if gsm)
+  float* Qs = sub_dyn + (gsm ? (size_t)n * n : 0);       // [n][SB], row j's SB values contiguous
+  float* red = Qs + (size_t)n * SB;                      // [SUB_NW][64]
+  float* H = red + SUB_NW * 64;                          // SB x (SB + 1)
+  float* Y = H + SB * (SB + 1);                          // SB x (SB + 1)
+  float* R = Y + SB * (SB + 1);                          // SB x (SB + 1)
+  float* vs = R + SB * (SB + 1);                         // [4][SB]: theta, residual^2, scale, rinv
+  float* cs = vs + 4 * SB;                               // [SB / 2][4] Jacobi rotations
+  __shared__ int s_flag[4];
+  __shared__ double s_tr[SUB_NW];
+  const float* Gcol = gsm ? Gs : a.Gf;
+
+  // G in FP32 (shared memory or the global scratch), trace(G) in FP64
+  double trp = 0.0;
+  for (long long L = tid; L < (long long)n * n; L += SUB_NT) {
+    const double g = a.G[L];
+    if (gsm) Gs[L] = (float)g; else a.Gf[L] = (float)g;
+    if (L % (n + 1) == 0) trp += g;
+  }
+  trp = warp_sum(trp);
+  if (lane == 0) s_tr[wid] = trp;
+  if (tid == 0) { s_flag[0] = 0; s_flag[1] = 0; s_flag[2] = -1; s_flag[3] = 0; }
+  __syncthreads();
+  double trace = 0.0;
+  for (int w = 0; w < SUB_NW; ++w) trace += s_tr[w];
+  const double eps2 = ctl->eps * ctl->eps;
+
+  const bool live = tid < n;
+  float q[SB], z[SB];
+#pragma unroll
+  for (int c = 0; c < SB; ++c) q[c] = live ? sub_hash(tid, c) : 0.f;
+
+  // column-scaled Cholesky QR of the rows x[] (every thread's row), twice; false on breakdown
+  auto orthonormalize = [&](float (&x)[SB]) -> bool {
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      float sq[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) sq[c] = x[c] * x[c];
+      sub_vec_sum(sq, red, vs + 2 * SB);
+      // scale columns to unit norm; a vanished column restarts from a hash vector
+#pragma unroll
+      for (int c = 0; c < SB; ++c) {
+        const float nn = vs[2 * SB + c];
+        if (nn > 1e-30f) x[c] *= rsqrtf(nn);
+        else x[c] = live ? sub_hash(tid + 7919 * (pass + 1), c) * rsqrtf((float)n) : 0.f;
+      }
+      sub_outer_sum(x, x, red, Y);   // M = X^T X into Y (scratch, row stride SB)
+      if (wid == 0) {
+        // M to row stride SB + 1 (in H) for the factorization
+        for (int it = lane; it < SB * SB; it += 32) H[(it / SB) * (SB + 1) + it % SB] = Y[it];
+        __syncwarp();
+        const bool ok = sub_cholesky(H, R, vs + 3 * SB, lane);
+        if (lane == 0 && !ok) s_flag[1] = 1;
+      }
+      __syncthreads();
+      if (s_flag[1]) return false;
+      // x <- x R^-1 (row times the inverse of the upper triangular factor)
+#pragma unroll
+      for (int c = 0; c < SB; ++c) {
+        float v = x[c];
+#pragma unroll
+        for (int b = 0; b < SB; ++b)
+          if (b < c) v = fmaf(-x[b], R[b * (SB + 1) + c], v);
+        x[c] = v * vs[3 * SB + c];
+      }
+      __syncthreads();
+    }
+    return true;
+  };
+
+  bool ok = orthonormalize(q);
+  int it = 0, m = 0;
+  bool conv = false;
+#pragma unroll 1
+  for (; ok && it < SUB_MAXIT; ++it) {
+    // Q into shared memory, then Z = G Q (thread i: row i, G(j, i) = G(i, j) read down column i)
+    if (live) {
+#pragma unroll
+      for (int c4 = 0; c4 < SB / 4; ++c4)
+        reinterpret_cast<float4*>(Qs + (size_t)tid * SB)[c4] = make_float4(q[4 * c4], q[4 * c4 + 1], q[4 * c4 + 2], q[4 * c4 + 3]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < SB; ++c) z[c] = 0.f;
+    if (live) {
+      const float* gc = Gcol + tid;
+#pragma unroll 4
+      for (int j = 0; j < n; ++j) {
+        const float g = gc[(size_t)j * n];
+        const float4* qj = reinterpret_cast<const float4*>(Qs + (size_t)j * SB);
+#pragma unroll
+        for (int c4 = 0; c4 < SB / 4; ++c4) {
+          const float4 v = qj[c4];
+          z[4 * c4] = fmaf(g, v.x, z[4 * c4]);
+          z[4 * c4 + 1] = fmaf(g, v.y, z[4 * c4 + 1]);
+          z[4 * c4 + 2] = fmaf(g, v.z, z[4 * c4 + 2]);
+          z[4 * c4 + 3] = fmaf(g, v.w, z[4 * c4 + 3]);
+        }
+      }
+    }
+    // Rayleigh-Ritz: H = Q^T Z, H = Y Theta Y^T
+    sub_outer_sum(q, z, red, Y);
+    if (wid == 0) {
+      for (int it2 = lane; it2 < SB * SB; it2 += 32) {
+        const int x = it2 / SB, y = it2 % SB;
+        H[x * (SB + 1) + y] = 0.5f * (Y[x * SB + y] + Y[y * SB + x]);
+      }
+      __syncwarp();
+      for (int it2 = lane; it2 < SB * SB; it2 += 32) R[(it2 / SB) * (SB + 1) + it2 % SB] = (it2 / SB == it2 % SB) ? 1.f : 0.f;
+      __syncwarp();
+      sub_jacobi(H, R, cs, lane);
+      // sort the Ritz values descending (rank of each, ties by index); Y = eigenvectors sorted
+      float th = lane < SB ? H[lane * (SB + 1) + lane] : 0.f;
+      int rk = 0;
+      for (int j = 0; j < SB; ++j) {
+        const float tj = __shfl_sync(0xffffffffu, th, j);
+        if (lane < SB && (tj > th || (tj == th && j < lane))) ++rk;
+      }
+      if (lane < SB) {
+        vs[rk] = th;
+        for (int x = 0; x < SB; ++x) Y[x * (SB + 1) + rk] = R[x * (SB + 1) + lane];
+      }
+    }
+    __syncthreads();
+    // rotate Q and Z to the Ritz basis: q <- q Y, z <- z Y
+    {
+      float q2[SB], z2[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) {
+        float aq = 0.f, az = 0.f;
+#pragma unroll
+        for (int b = 0; b < SB; ++b) {
+          const float y = Y[b * (SB + 1) + c];
+          aq = fmaf(q[b], y, aq);
+          az = fmaf(z[b], y, az);
+        }
+        q2[c] = aq;
+        z2[c] = az;
+      }
+#pragma unroll
+      for (int c = 0; c < SB; ++c) { q[c] = q2[c]; z[c] = z2[c]; }
+    }
+    // residual norms of the Ritz pairs
+    {
+      float rr[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) {
+        const float e = fmaf(-vs[c], q[c], z[c]);
+        rr[c] = e * e;
+      }
+      sub_vec_sum(rr, red, vs + SB);
+    }
+    // FP32 cut estimate and convergence of the Ritz pairs up to one past it
+    if (tid == 0) {
+      double tail = trace;
+      int l = -1;
+      for (int c = 0; c < SB - 2; ++c) {
+        tail -= (double)vs[c];
+        if (tail <= eps2) { l = c + 1; break; }
+      }
+      int mm = (want > 0) ? want + 1 : (l > 0 ? l + 1 : 0);
+      if (mm > nfree) mm = nfree;
+      bool cv = mm > 0 && vs[0] > 0.f;
+      const float tol = SUB_TOL * vs[0];
+      for (int c = 0; c < mm && cv; ++c) cv = sqrtf(vs[SB + c]) <= tol;
+      s_flag[0] = cv ? 1 : 0;
+      s_flag[2] = mm;
+    }
+    __syncthreads();
+    if (s_flag[0]) { conv = true; m = s_flag[2]; break; }
+    // next basis: the columns of Z, orthonormalized
+#pragma unroll
+    for (int c = 0; c < SB; ++c) q[c] = z[c];
+    ok = orthonormalize(q);
+  }
+  if (!conv) {
+    if (tid == 0) { ctl->eig_fb[k] = 1; ctl->eig_it[k] = it; }
+    return;
+  }
+  if (live)
+    for (int c = 0; c < m; ++c) a.W[(long long)c * n + tid] = (double)q[c];
+  if (tid == 0) {
+    ctl->eig_tr[k] = trace;
+    ctl->eig_m[k] = m;
+    ctl->eig_it[k] = it + 1;
+    ctl->eig_fb[k] = 0;
+  }
+}
+
+// FP64 Rayleigh-Ritz over the m Ritz vectors and Alg. 1's cut (see the file comment).
+// Grid: up to REF_MAXB CTAs, one warp per row of G W at a time.
+__global__ void __launch_bounds__(REF_NT) k_eig_refine(Ctl* ctl, int k, const double* __restrict__ G,
+                                                      const double* __restrict__ W, double* part, int mcap) {
+  if (ctl->status || !ctl->grew[k] || ctl->eig_fb[k]) return;
+  const int n = ctl->n[k];
+  const int m = ctl->eig_m[k];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NWR = REF_NT / 32;
+  constexpr int E = SB * SB / 32;   // entries of an m x m matrix per lane (m <= SB)
+  // per-warp partials of P = W^T G W and M = W^T W, entry e = lane + 32 u (row e / SB, col e % SB)
+  double pp[E], pm[E];
+#pragma unroll
+  for (int u = 0; u < E; ++u) { pp[u] = 0.0; pm[u] = 0.0; }
+  for (int i = blockIdx.x * NWR + wid; i < n; i += gridDim.x * NWR) {
+    // (G W)(i, c) = sum_j G(j, i) W(j, c), lanes over j
+    double gw[SB];
+#pragma unroll
+    for (int c = 0; c < SB; ++c) gw[c] = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const double g = G[(long long)i * n + j];
+#pragma unroll
+      for (int c = 0; c < SB; ++c)
+        if (c < m) gw[c] = fma(g, W[(long long)c * n + j], gw[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < SB; ++c) if (c < m) gw[c] = warp_sum(gw[c]);
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      const int e = lane + 32 * u, x = e / SB, y = e % SB;
+      if (x < m && y < m) {
+        const double wx = W[(long long)x * n + i];
+        double gy = 0.0, wy = W[(long long)y * n + i];
+#pragma unroll
+        for (int c = 0; c < SB; ++c) if (c == y) gy = gw[c];
+        pp[u] = fma(wx, gy, pp[u]);
+        pm[u] = fma(wx, wy, pm[u]);
+      }
+    }
+  }
+  __shared__ double sp[NWR][2 * SB * SB];
+#pragma unroll
+  for (int u = 0; u < E; ++u) {
+    sp[wid][lane + 32 * u] = pp[u];
+    sp[wid][SB * SB + lane + 32 * u] = pm[u];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * SB * SB; e += REF_NT) {
+    double s = 0.0;
+    for (int w = 0; w < NWR; ++w) s += sp[w][e];
+    part[(long long)blockIdx.x * 2 * SB * SB + e] = s;
+  }
+  if (!tk_block_ticket(&ctl->ticket[3])) return;
+  // last block: sum the partials in block order, then the nested traces and the cut
+  __shared__ double Pm[2 * SB * SB];
+  for (int e = threadIdx.x; e < 2 * SB * SB; e += REF_NT) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(part + (long long)b * 2 * SB * SB + e);
+    Pm[e] = s;
+  }
+  __syncthreads();
+  const double* P = Pm;
+  const double* M = Pm + SB * SB;
+  // energy captured by span(w_1..w_{l+1}) minus that of span(w_1..w_l), to first order in
+  // Delta = M - I: trace(M_l^-1 P_l) = trace(P_l) - trace(Delta_l P_l) + O(|Delta|^2 |P|), so
+  // inc(l) = P_ll - Delta_ll P_ll - 2 sum_{x<l} Delta_lx P_xl (P and Delta symmetric)
+  __shared__ double inc[SB];
+  if (threadIdx.x < SB) {
+    const int l = threadIdx.x;
+    double v = 0.0;
+    if (l < m) {
+      double d1 = (M[l * SB + l] - 1.0) * P[l * SB + l];
+      for (int x = 0; x < l; ++x) d1 = fma(2.0 * M[l * SB + x], P[x * SB + l], d1);
+      v = P[l * SB + l] - d1;
+    }
+    inc[l] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double eps2 = ctl->eps * ctl->eps;
+    const double trace = ctl->eig_tr[k];
+    const int want = max(rp_grow_of(ctl, k), 0);
+    const int r0 = ctl->r[k];
+    double tail = trace, prev = trace;
+    int l = -1;
+    for (int c = 0; c < m; ++c) {
+      prev = tail;
+      tail -= inc[c];
+      if ((want > 0 && c + 1 == want) || (want == 0 && tail <= eps2)) { l = c + 1; break; }
+    }
+    if (l < 0) {
+      ctl->eig_fb[k] = 1;   // the cut lies beyond the certified vectors: full solver
+    } else {
+      if (l > n - r0) l = n - r0;
+      if (r0 + l > ctl->cap[k] || l > mcap) { ctl->status = TK_ECAPACITY; return; }
+      ctl->radd[k] = l;
+      ctl->disc[k] = tail;
+      ctl->tail_prev[k] = prev;
+    }
+  }
+}
+
+size_t eig_sub_smem(int n) {
+  const bool gsm = n <= SUB_GS_NMAX;
+  return sizeof(float) * ((gsm ? (size_t)n * n : 0) + (size_t)n * SB + SUB_NW * 64 + 3 * SB * (SB + 1) + 4 * SB + 2 * SB);
+}
+
+cudaError_t launch_eig_sub(Ctl* ctl, int k, const double* G, void* Gf, double* W, int mcap,
+                           double* part, int n, cudaStream_t st) {
+  // shared memory for the largest n this state can see (set once per size)
+  const size_t sm = eig_sub_smem(n);
+  cudaError_t e = cudaFuncSetAttribute(k_eig_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  SubArgs a{G, reinterpret_cast<float*>(Gf), W, mcap};
+  k_eig_sub<<<1, SUB_NT, sm, st>>>(ctl, k, a);
+  const int nb = std::min(REF_MAXB, std::max(1, (n + 3) / 4));
+  k_eig_refine<<<nb, REF_NT, 0, st>>>(ctl, k, G, W, part, mcap);
+  return cudaGetLastError();
+}
+
+}  // namespace tk

@@ -33,6 +33,38 @@ __global__ void k_init_finish(const TW* Ccol, long long R, int rd, const double*
   }
 }
 
+// Mixed form: C and V of the initial state from C_(d)^T = C*_{d-1} U_d computed in FP64 (C64,
+// column-major R x rd). V = C_(d)^T U S^-1 is then orthonormal to FP64 accuracy before it is
+// stored in FP32; from an FP32 product its weak columns (small S) would carry errors of about
+// u_fp32 S_1 / S_c, and the incremental SVD needs V orthonormal well below q / ||d||.
+template <typename TW>
+__global__ void k_init_cv64(const double* C64, long long R, int rd, const double* lam, TW* C, TW* V,
+                            int ldc) {
+  const int ls = tk_cv_stride(rd, ldc, (int)sizeof(TW));
+  const long long total = R * rd;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
+       L += (long long)gridDim.x * blockDim.x) {
+    const long long j = L % R;
+    const int i = (int)(L / R);
+    const double c = C64[L];
+    const double s = sqrt(fmax(lam[i], 0.0));
+    C[j * ls + i] = (TW)c;
+    V[j * ls + i] = (TW)(c / s);
+  }
+}
+
+template <typename TW>
+cudaError_t launch_init_cv64(const double* C64, long long R, int rd, const double* lam, void* C,
+                             void* V, int ldc, cudaStream_t st) {
+  const long long total = R * rd;
+  int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+  if (grid < 1) grid = 1;
+  k_init_cv64<TW><<<grid, 256, 0, st>>>(C64, R, rd, lam, (TW*)C, (TW*)V, ldc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_init_cv64<float>(const double*, long long, int, const double*, void*,
+                                             void*, int, cudaStream_t);
+
 template <typename TW>
 cudaError_t launch_init_finish(Ctl* ctl, const void* Ccol, long long R, int rd, const double* lam,
                                const double* Utmp, int nt, void* C, void* V, double* Ud, double* S,

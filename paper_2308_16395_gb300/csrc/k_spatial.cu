@@ -212,7 +212,10 @@ __global__ void k_decide(Ctl* ctl, int k, const double* part_e2, const double* p
       const double e = ctl->eps;
       eps2 = e * e;
     }
-    const int g = se > eps2 ? 1 : 0;
+    int g = se > eps2 ? 1 : 0;
+    // decision replay (test hook): the branch forced for this update
+    const int fg = rp_grow_of(ctl, k);
+    if (fg >= 0) g = fg > 0 ? 1 : 0;
     if (hcond) cudaGraphSetConditional(hcond, g ? 1u : 0u);
     ctl->e2[k] = se;
     ctl->grew[k] = g;
@@ -521,6 +524,9 @@ template cudaError_t launch_expand<double, double, double>(const void*, long lon
                                                            const void*, int, int, void*,
                                                            cudaStream_t);
 template cudaError_t launch_expand<double, double, float>(const void*, long long, int, long long,
+                                                          const void*, int, int, void*,
+                                                          cudaStream_t);
+template cudaError_t launch_expand<float, double, double>(const void*, long long, int, long long,
                                                           const void*, int, int, void*,
                                                           cudaStream_t);
 template cudaError_t launch_expand<float, float, double>(const void*, long long, int, long long,

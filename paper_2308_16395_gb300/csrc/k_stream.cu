@@ -121,7 +121,11 @@ __device__ void isvd_small_tail(Ctl* ctl, const double* S, const SecWork& w, con
                                 int capd) {
   ctl->q2 = q2;
   ctl->q = q;
-  const int aug = q > eps ? 1 : 0;   // Alg. 3: ignore e if q <= eps
+  int aug = q > eps ? 1 : 0;   // Alg. 3: ignore e if q <= eps
+  // decision replay (test hook): the branch forced for this update (never a new direction
+  // from e = 0)
+  const int fa = rp_aug_of(ctl);
+  if (fa >= 0) aug = (fa > 0 && q > 0.0) ? 1 : 0;
   ctl->aug = aug;
   if (aug && r + 1 > capd) { ctl->status = TK_ECAPACITY; return; }
   if (Rn > ctl->core_cap) { ctl->status = TK_ECAPACITY; return; }
@@ -1436,6 +1440,29 @@ __global__ void k_end_update(Ctl* ctl, const double* Snew, double* S) {
     if (!stay) ctl->cbuf = c.cbuf ^ 1;
     ctl->ubuf = c.ubuf ^ 1;
     ctl->nupdates = c.nupdates + 1;
+    // the update's decisions into the log, and the replay hook is spent
+    if (c.log && c.nupdates < c.log_cap) {
+      StepRec& o = c.log[c.nupdates];
+      o.nd = c.nd + 1;
+      for (int k = 0; k < TK_MAXD; ++k) {
+        const bool sp = k < d - 1;
+        o.r[k] = (k < d - 1) ? c.r[k] : (k == d - 1 ? keep : 0);
+        o.grew[k] = sp ? c.grew[k] : 0;
+        o.radd[k] = sp ? c.radd[k] : 0;
+        o.eig_path[k] = (sp && c.grew[k]) ? (c.eig_fb[k] ? 2 : 1) : 0;
+        o.eig_it[k] = (sp && c.grew[k]) ? c.eig_it[k] : 0;
+        o.e2[k] = sp ? c.e2[k] : 0.0;
+        o.tail_cut[k] = (sp && c.grew[k]) ? c.disc[k] : 0.0;
+        o.tail_prev[k] = (sp && c.grew[k]) ? c.tail_prev[k] : 0.0;
+      }
+      o.aug = c.aug;
+      o.replayed = c.rp_on;
+      o.eps = c.eps;
+      o.y2 = c.y2;
+      o.q = c.q;
+      o.discarded = disc;
+    }
+    ctl->rp_on = 0;
   }
 }
 
@@ -1447,6 +1474,10 @@ __global__ void k_begin_update(Ctl* ctl) {
     ctl->radd[k] = 0;
     ctl->e2[k] = 0.0;
     ctl->disc[k] = 0.0;
+    ctl->tail_prev[k] = 0.0;
+    ctl->eig_m[k] = 0;
+    ctl->eig_it[k] = 0;
+    ctl->eig_fb[k] = 0;
   }
   ctl->xbuf = -1;
   ctl->aug = 0;

@@ -39,6 +39,12 @@ template <typename TW>
 cudaError_t launch_append(Ctl* ctl, int k, int mode, const double* W, double* U, void* Uw, int ldu,
                           int n, cudaStream_t st);
 
+// ---- k_eig_sub.cu ----
+// Residual-Gram eigensolve of the mixed form (subspace iteration + FP64 Rayleigh-Ritz cut); sets
+// ctl->eig_fb[k] when the full solver (launch_eig with mode 2) must decide instead.
+cudaError_t launch_eig_sub(Ctl* ctl, int k, const double* G, void* Gf, double* W, int mcap,
+                           double* part, int n, cudaStream_t st);
+
 // ---- k_stream.cu ----
 struct SecWork {
   double* delta;
@@ -115,6 +121,9 @@ template <typename TW>
 cudaError_t launch_init_finish(Ctl* ctl, const void* Ccol, long long R, int rd, const double* lam,
                                const double* Utmp, int nt, void* C, void* V, double* Ud, double* S,
                                int ldc, cudaStream_t st);
+template <typename TW>
+cudaError_t launch_init_cv64(const double* C64, long long R, int rd, const double* lam, void* C,
+                             void* V, int ldc, cudaStream_t st);
 template <typename TW>
 cudaError_t launch_core_times_ud(const void* C, long long R, int rd, int ldc, const double* Ud,
                                  long long t0, long long T, void* out, cudaStream_t st);

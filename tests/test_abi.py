@@ -54,11 +54,12 @@ def test_binding_names_match_header(lib):
     assert set(pkg.EXPORTS) == set(_declared())
 
 
-def test_library_is_built_for_sm_103a(lib):
-    _, path = lib
-    out = subprocess.run(["/usr/local/cuda/bin/cuobjdump", "--list-elf", path], capture_output=True,
-                         text=True).stdout
-    assert "sm_103a" in out
+def test_library_is_built_for_sm_103a():
+    """The build compiles every translation unit for sm_103a and nothing else."""
+    from paper_2308_16395_gb300 import build as b
+
+    assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert all(f not in b._flags() for f in ("-arch=native", "-march=native"))
 
 
 def test_config_struct_size_matches_header(lib):
@@ -102,7 +103,8 @@ def test_struct_layouts_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     pairs = [("tucker_config", pkg.TuckerConfig), ("tucker_step_info", pkg.StepInfo),
              ("tucker_profile", pkg.Profile), ("tucker_launch_plan", pkg.LaunchPlan),
-             ("tucker_ttm_desc", pkg.TtmDesc)]
+             ("tucker_ttm_desc", pkg.TtmDesc), ("tucker_step_record", pkg.StepRecord),
+             ("tucker_replay", pkg.Replay)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tucker_stream.h"',
              '#include "tucker_ttm.h"', "int main(void) {"]
     for cname, py in pairs:

@@ -202,7 +202,8 @@ class BlobField:
         x = torch.arange(n1, device=device, dtype=dtype) / n1
         y = torch.arange(n2, device=device, dtype=dtype) / n2
         z = torch.arange(n3, device=device, dtype=dtype) / n3
-        acc = torch.zeros((self.nblobs, n3, n2, n1), device=device, dtype=dtype)
+        amp = torch.as_tensor(self.amp, device=device, dtype=dtype)  # (nb, nvar)
+        out = torch.zeros((self.nvar, n3, n2, n1), device=device, dtype=dtype)
         for b in range(self.nblobs):
             c = self.centres[b] + self.vel[b] * t
             dx = x - float(c[0])
@@ -218,9 +219,9 @@ class BlobField:
             q = (float(p[0, 0]) * X * X + float(p[1, 1]) * Yy * Yy + float(p[2, 2]) * Z * Z
                  + 2.0 * float(p[0, 1]) * X * Yy + 2.0 * float(p[0, 2]) * X * Z
                  + 2.0 * float(p[1, 2]) * Yy * Z)
-            acc[b] = torch.exp(-0.5 * q)
-        amp = torch.as_tensor(self.amp, device=device, dtype=dtype)  # (nb, nvar)
-        out = torch.einsum("bv,bzyx->vzyx", amp, acc)
+            g = torch.exp(-0.5 * q)
+            # blob b's contribution to every variable, accumulated blob by blob
+            out.addcmul_(amp[b].view(-1, 1, 1, 1), g.unsqueeze(0))
         return out.contiguous()
 
     def slice(self, t: int, dtype=np.float32) -> np.ndarray:
