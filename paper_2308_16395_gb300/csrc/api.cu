@@ -309,8 +309,13 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
     int dev0 = 0, nsm0 = 152;
     CK(cudaGetDevice(&dev0));
     CK(cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0));
-    // SIMT residual Gram tiles, or the tensor-core split-K blocks (<= nsm x 128 x 256)
-    const size_t g1 = (size_t)(kGramBlocks + 64) * 4096, g2 = (size_t)nsm0 * 128 * 256;
+    // SIMT residual Gram tiles, or the tensor-core split-K partial Grams (nsm planes of
+    // n1p x n1p FP32, n_k <= 384; counted here in doubles)
+    int ntc = 16;
+    for (int k = 0; k < d - 1; ++k)
+      if (s->n[k] <= 384) ntc = std::max(ntc, (s->n[k] + 15) / 16 * 16);
+    const size_t g1 = (size_t)(kGramBlocks + 64) * 4096;
+    const size_t g2 = std::max((size_t)nsm0 * 128 * 256, ((size_t)nsm0 * ntc * ntc + 1) / 2);
     CK(dalloc(s, (void**)&s->gpart, sizeof(double) * std::max(g1, g2)));
   }
   CK(dalloc(s, (void**)&s->G, sizeof(double) * (size_t)s->nmax * s->nmax));
@@ -372,7 +377,7 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
     CK(dalloc(s, (void**)&s->et, sizeof(float) * et_elems));
     for (int k = 0; k < d - 1; ++k) {
       const int nk = s->n[k];
-      if (nk % 4 != 0 || nk > 256 || (k == 0 && s->tx != 4)) continue;
+      if (nk % 4 != 0 || nk > 512 || (k == 0 && s->tx != 4)) continue;
       for (int i = 0; i < 2; ++i) CK(dalloc(s, (void**)&s->usplit[k][i], sizeof(float) * nk * s->cap[k]));
       for (int i = 2; i < 4; ++i) CK(dalloc(s, (void**)&s->usplit[k][i], sizeof(float) * nk * 64));
       TcProjMaps& m = s->pmaps[k];
@@ -387,7 +392,8 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
       s->tcmask |= 1 << k;
       const long long fs = (s->dbuf_elems / nk + 32 + 3) / 4 * 4;
       s->et_stride[k] = fs;
-      bool oke = make_map_2d_f32(&m.eta, s->et, nk, fs, fs, 32, 128);
+      // the tensor-core residual Gram takes n_k <= 384 (three 128-row blocks)
+      bool oke = nk <= 384 && make_map_2d_f32(&m.eta, s->et, nk, fs, fs, 32, 128);
       if (oke) s->etmask |= 1 << k;
     }
   }

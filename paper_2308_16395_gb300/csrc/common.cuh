@@ -384,16 +384,18 @@ __device__ __forceinline__ bool spatial_grew(const Ctl* ctl) {
 
 // Spatial mode k on the tensor cores: mixed form, streaming update (rotating layout), the host
 // built the tensor maps for this mode (bit k of tcmask), FP32 input (the slice for k = 0),
-// n_k a multiple of 4 (TMA row stride) and <= 256, padded rank <= 64.
+// n_k a multiple of 4 (TMA row stride) and <= 512 (above 256 the residual product runs in
+// column blocks), padded rank <= 64.
 __device__ __forceinline__ bool tc_proj_ok(const Ctl* c, int k, int r) {
   if (c->tw != 4 || c->init_nt != 0) return false;
   if (!((c->tcmask >> k) & 1)) return false;
   if (k == 0 && c->tx != 4) return false;
   const int nk = c->n[k];
-  if (nk % 4 != 0 || nk > 256 || r < 1) return false;
+  if (nk % 4 != 0 || nk > 512 || r < 1) return false;
   return (r + 15) / 16 * 16 <= TP_RMAX;
 }
-// Residual Gram of mode k on the tensor cores (needs the E^T maps, bit k of etmask).
+// Residual Gram of mode k on the tensor cores (needs the E^T maps, bit k of etmask, which the
+// host sets only for n_k <= 384).
 __device__ __forceinline__ bool tc_gram_ok(const Ctl* c, int k) {
-  return c->grew[k] && ((c->etmask >> k) & 1) && tc_proj_ok(c, k, c->rold[k]);
+  return c->grew[k] && ((c->etmask >> k) & 1) && c->n[k] <= 384 && tc_proj_ok(c, k, c->rold[k]);
 }

@@ -1256,7 +1256,13 @@ cudaError_t launch_eig(Ctl* ctl, int k, int mode, const double* G, void* Aw, voi
   const int use_vec = (vec <= std::min<size_t>(150 * 1024, lim)) ? 1 : 0;
   const int use_amat = (use_vec && mat + vec <= lim) ? 1 : 0;
   const size_t sm = (use_amat ? mat : 0) + (use_vec ? vec : 0);
-  if (sm) cudaFuncSetAttribute(k_eig_topk<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  // raised to the largest size seen so far, never lowered (see launch_eig_sub)
+  static size_t attr_set[2] = {0, 0};
+  size_t& aset = attr_set[sizeof(TE) == 8 ? 1 : 0];
+  if (sm > aset) {
+    cudaFuncSetAttribute(k_eig_topk<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    aset = sm;
+  }
   // FP32 Grams up to 192 x 192 are tridiagonalized by the register kernel first; the reflectors
   // (n x n floats) and the tridiagonal (3n floats) fit in Aw, which holds n x n doubles
   int pre = 0;

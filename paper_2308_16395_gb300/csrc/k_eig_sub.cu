@@ -512,10 +512,17 @@ size_t eig_sub_smem(int n) {
 
 cudaError_t launch_eig_sub(Ctl* ctl, int k, const double* G, void* Gf, double* W, int mcap,
                            double* part, int n, cudaStream_t st) {
-  // shared memory for the largest n this state can see (set once per size)
+  // the attribute is raised to the largest size any n needs (n = SUB_GS_NMAX, G in shared
+  // memory) once, and never lowered: launches captured into a graph for one n must stay valid
+  // after launches for another
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_eig_sub, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)eig_sub_smem(SUB_GS_NMAX));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   const size_t sm = eig_sub_smem(n);
-  cudaError_t e = cudaFuncSetAttribute(k_eig_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   SubArgs a{G, reinterpret_cast<float*>(Gf), W, mcap};
   k_eig_sub<<<1, SUB_NT, sm, st>>>(ctl, k, a);
   const int nb = std::min(REF_MAXB, std::max(1, (n + 3) / 4));

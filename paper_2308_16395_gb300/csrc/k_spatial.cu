@@ -423,19 +423,30 @@ size_t proj_smem_bytes(int r, int tw_size) {
   return (size_t)tw_size * ((size_t)JC * FT + (size_t)JC * ucols + (size_t)r * FT);
 }
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never lowering it: launches
+// of one kernel with different sizes are captured into the same update graph, and each must stay
+// within the limit in force when the graph runs. `seen` is the kernel's own high-water mark.
+static inline void raise_smem_limit(const void* kern, size_t bytes, size_t* seen) {
+  if (bytes > *seen) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    *seen = bytes;
+  }
+}
+
 template <typename TX, typename TW>
 cudaError_t launch_proj(const Ctl* ctl, int k, int out_off, int pred, const void* Xext,
                         void* const* dbufs, const void* U, int ldu, int rmax, double* part_e2,
                         double* part_y2, int grid, cudaStream_t st) {
   const size_t sm = proj_smem_bytes(rmax, sizeof(TW));
+  static size_t seen[2] = {0, 0};
   if (part_e2) {
     auto kern = k_ttm_proj<TX, TW, true>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)kern, sm, &seen[0]);
     kern<<<grid, NT, sm, st>>>(ctl, k, out_off, pred, (const TX*)Xext, (TW* const*)dbufs,
                                (const TW*)U, ldu, part_e2, part_y2);
   } else {
     auto kern = k_ttm_proj<TX, TW, false>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)kern, sm, &seen[1]);
     kern<<<grid, NT, sm, st>>>(ctl, k, out_off, pred, (const TX*)Xext, (TW* const*)dbufs,
                                (const TW*)U, ldu, nullptr, part_y2);
   }
@@ -472,7 +483,8 @@ cudaError_t launch_resid_gram(const Ctl* ctl, int k, int n, const void* Xext, vo
   const size_t sm = sizeof(TW) * ((size_t)2 * GT * (GF + 1) + (size_t)2 * GT * (GC + 1) +
                                   (size_t)GC * (GF + 1));
   auto kern = k_resid_gram<TX, TW>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static size_t seen = 0;
+  raise_smem_limit((const void*)kern, sm, &seen);
   kern<<<grid, NT, sm, st>>>(ctl, k, (const TX*)Xext, (TW* const*)dbufs, (const TW*)U, ldu, gpart,
                              data_only);
   return cudaGetLastError();

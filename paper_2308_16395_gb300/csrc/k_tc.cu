@@ -348,7 +348,8 @@ namespace tk {
 // output in the rotating layout).
 //   MMA1  P[f, :] = X[f, :] U_k (K = n_k), 3xTF32, X tiles by TMA, U_k chunks (TF32 hi/lo)
 //         streamed with them; P accumulates in TMEM.
-//   epi-1 P -> global, column-major (F x r_k) (the next mode's input); P split in place into
+//   epi-1 P = (hi x hi part, TMEM cols 0..63 of its buffer) + (correction part, cols 64..127)
+//         -> global, column-major (F x r_k) (the next mode's input); P split in place into
 //         TF32 hi (TMEM cols 0..63 of its buffer) and lo (cols 64..127).
 //   MMA2  (RESID) Rec = P U_k^T with A = P read from tensor memory, B = U_k rows resident in
 //         shared memory, 3xTF32; Rec in TMEM cols 256..256+n_k.
@@ -359,6 +360,13 @@ namespace tk {
 // (d1full, pready, mma2done) have one instance per buffer, so a phase is never two ahead.
 //   epi-2 (RESID) E = X - Rec with X re-read (L2-resident), ||E||^2 (and ||Y||^2 for k = 0) as
 //         per-block partials; WRITE_ET: E^T (n_k x Fs, row stride Fs) for the residual Gram.
+// Blocked form (n_k > 256: Rec no longer fits 256 TMEM columns, nor U_k's rows in shared memory):
+// MMA2 runs in column blocks of TP_NB = 128. Block g of the CTA's sequence (tile g / NB, columns
+// TP_NB (g % NB) ..) accumulates into D2 buffer g & 1 (TMEM cols 256 + 128 (g & 1)), with B =
+// rows TP_NB (g % NB) .. of U_k (TF32 hi/lo) in one shared buffer. The residual epilogue's
+// leader loads B2 block g + 1 as soon as block g's MMA2 has completed (its d2full), and the MMA
+// issuer issues block g once the tile's P split is stored, B2 block g has landed and D2 buffer
+// g & 1 has been read (d2free, block g - 2), between the chunk MMAs of the next tile.
 // =============================================================================================
 constexpr int TP_STAGE = 48 * 1024;                // X hi | X lo | U chunk hi | U chunk lo
 // stages: 2 when the residual runs (the resident U rows for MMA2 and the Y buffers take 128 KB),
@@ -366,8 +374,9 @@ constexpr int TP_STAGE = 48 * 1024;                // X hi | X lo | U chunk hi |
 template <bool RESID> struct TpCfg {
   static constexpr int S = RESID ? 2 : 4;
   static constexpr size_t B2 = RESID ? 128 * 1024 : 0;
-  static constexpr size_t SMEM = (size_t)S * TP_STAGE + B2 + 1024 + 256;
+  static constexpr size_t SMEM = (size_t)S * TP_STAGE + B2 + 1024 + 512;
 };
+constexpr int TP_NB = 128;                          // columns of an MMA2 block (blocked form)
 constexpr int TP_PF = 12;                           // X chunks prefetched into L2 ahead
 // warps: 0 TMA producer, 1 MMA issuer, 2 .. 2+TP_SPLIT_WARPS-1 TF32 splitters of the X chunks,
 // then 4 warps for epilogue 1 (P) and 4 for epilogue 2 (the residual), so that epilogue 1 of
@@ -414,6 +423,9 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
   const int Kc1 = (n1 + TC_KC - 1) / TC_KC;
   const int Kc2 = (Rp + TC_KC - 1) / TC_KC;
   const long long ntiles = (F + TC_M - 1) / TC_M;
+  // blocked MMA2 (n_k > 256): NB column blocks per tile
+  const bool blocked = RESID && n1p > 256;
+  const int NB = blocked ? (n1p + TP_NB - 1) / TP_NB : 1;
   const int xb = ctl->xbuf;
   const CUtensorMap* mX = xb < 0 ? (a.mYg ? a.mYg : &mY) : (xb == 0 ? &mD0 : (xb == 1 ? &mD1 : &mD2));
   const float* Xg = xb < 0 ? (a.Y ? a.Y : reinterpret_cast<const float*>(ctl->yptr)) : a.dbufs[xb];
@@ -423,18 +435,21 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(psm_raw) + 1023) & ~uintptr_t(1023));
   constexpr int TP_S = TpCfg<RESID>::S;
-  float* B2hi = reinterpret_cast<float*>(base + TP_S * TP_STAGE);   // [Kc2][n1p][32] (RESID)
-  float* B2lo = B2hi + (size_t)Kc2 * n1p * TC_KC;
+  // RESID: U_k rows for MMA2, [Kc2][n1p][32] hi then lo (resident), or [Kc2][TP_NB][32] hi then
+  // lo (one column block, blocked form)
+  const int b2rows = blocked ? TP_NB : n1p;
+  float* B2hi = reinterpret_cast<float*>(base + TP_S * TP_STAGE);
+  float* B2lo = B2hi + (size_t)Kc2 * b2rows * TC_KC;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + TP_S * TP_STAGE + TpCfg<RESID>::B2);
   uint64_t* full = bars;
   uint64_t* conv = bars + TP_S;
   uint64_t* empty = bars + 2 * TP_S;
   uint64_t* d1full = bars + 3 * TP_S;              // [2] per P buffer
   uint64_t* pready = d1full + 2;                   // [2]
-  uint64_t* d2full = pready + 2;
-  uint64_t* d2free = d2full + 1;
-  uint64_t* mma2done = d2free + 1;                 // [2]
-  uint64_t* bload = mma2done + 2;
+  uint64_t* d2full = pready + 2;                   // [2] per D2 buffer (blocked form; else [0])
+  uint64_t* d2free = d2full + 2;                   // [2]
+  uint64_t* mma2done = d2free + 2;                 // [2]
+  uint64_t* bload = mma2done + 2;                  // resident B2 (one load) or B2 block g (phase g)
   uint64_t* done = bload + 1;
   uint64_t* ybar = done + 1;                       // [2] Y chunk loaded (residual epilogue)
   uint64_t* yfree = ybar + 2;                      // [2] Y chunk consumed by the 4 epilogue warps
@@ -454,8 +469,10 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
       mbar_init(&pready[b], 128);
       mbar_init(&mma2done[b], 1);
     }
-    mbar_init(d2full, 1);
-    mbar_init(d2free, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&d2full[b], 1);
+      mbar_init(&d2free[b], 128);
+    }
     mbar_init(bload, 1);
     mbar_init(done, 1);
     mbar_init(&ybar[0], 1);
@@ -485,6 +502,8 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
       if (RESID) {
         tma_prefetch(&mUrhi);
         tma_prefetch(&mUrlo);
+      }
+      if (RESID && !blocked) {
         mbar_arrive_expect_tx(bload, (uint32_t)Kc2 * n1p * TC_KC * 4 * 2);
         for (int kc = 0; kc < Kc2; ++kc)
           for (int n0 = 0; n0 < n1p; n0 += 16) {
@@ -524,14 +543,14 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t id1 = idesc_tf32(TC_M, Rp);
-      const uint32_t id2 = idesc_tf32(TC_M, n1p);
-      bool ok = RESID ? wait_bar(bload, 0, abort) : true;
+      const uint32_t id2 = idesc_tf32(TC_M, blocked ? TP_NB : n1p);
+      bool ok = (RESID && !blocked) ? wait_bar(bload, 0, abort) : true;
       // MMA2 of tile jt: Rec = P U_k^T into D2 once the epilogue has stored P's split and has
       // read D2 of tile jt - 1 (it did so before it stored P of tile jt)
       auto mma2 = [&](int jt) -> bool {
         const uint32_t pb = (uint32_t)((jt >> 1) & 1);
         if (!wait_bar(&pready[jt & 1], pb, abort)) return false;
-        if (!wait_bar(d2free, (uint32_t)((jt & 1) ^ 1), abort)) return false;
+        if (!wait_bar(&d2free[0], (uint32_t)((jt & 1) ^ 1), abort)) return false;
         tc_fence_after();
         const uint32_t tA = tmem + 128u * (uint32_t)(jt & 1);
         for (int k8 = 0; k8 < Rp / 8; ++k8) {
@@ -543,9 +562,49 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
           mma_tf32_ts(tD2, tA + 8 * k8, blo, id2, 1u);
           mma_tf32_ts(tD2, tA + 64 + 8 * k8, bhi, id2, 1u);
         }
-        tc_commit(d2full);
+        tc_commit(&d2full[0]);
         tc_commit(&mma2done[jt & 1]);
         return true;
+      };
+      // blocked form: the next MMA2 block to issue is block b_nb of tile b_tile (-1: none), the
+      // CTA's g2-th block; returns 1 once issued, 0 if not ready (non-blocking), -1 on abort
+      long long g2 = 0;
+      int b_tile = -1, b_nb = 0;
+      auto mma2_block = [&](bool blocking) -> int {
+        const uint32_t pb = (uint32_t)((b_tile >> 1) & 1);
+        const int bb = (int)(g2 & 1);
+        const uint32_t lpar = (uint32_t)(g2 & 1), fpar2 = (uint32_t)(((g2 >> 1) & 1) ^ 1);
+        if (blocking) {
+          if (b_nb == 0 && !wait_bar(&pready[b_tile & 1], pb, abort)) return -1;
+          if (!wait_bar(bload, lpar, abort)) return -1;
+          if (!wait_bar(&d2free[bb], fpar2, abort)) return -1;
+        } else {
+          if (b_nb == 0 && !mbar_try_wait(&pready[b_tile & 1], pb)) return 0;
+          if (!mbar_try_wait(bload, lpar)) return 0;
+          if (!mbar_try_wait(&d2free[bb], fpar2)) return 0;
+        }
+        tc_fence_after();
+        const int ncol = min(TP_NB, n1p - TP_NB * b_nb);
+        const uint32_t idb = idesc_tf32(TC_M, ncol);
+        const uint32_t tA = tmem + 128u * (uint32_t)(b_tile & 1);
+        const uint32_t tDb = tD2 + 128u * (uint32_t)bb;
+        for (int k8 = 0; k8 < Rp / 8; ++k8) {
+          const int kc = k8 >> 2;
+          const uint64_t o = (uint64_t)((k8 & 3) * 32) >> 4;
+          const uint64_t bhi = desc_sw128(B2hi + (size_t)kc * TP_NB * TC_KC) + o;
+          const uint64_t blo = desc_sw128(B2lo + (size_t)kc * TP_NB * TC_KC) + o;
+          mma_tf32_ts(tDb, tA + 8 * k8, bhi, idb, k8 ? 1u : 0u);
+          mma_tf32_ts(tDb, tA + 8 * k8, blo, idb, 1u);
+          mma_tf32_ts(tDb, tA + 64 + 8 * k8, bhi, idb, 1u);
+        }
+        tc_commit(&d2full[bb]);
+        ++g2;
+        if (++b_nb == NB) {
+          tc_commit(&mma2done[b_tile & 1]);
+          b_tile = -1;
+          b_nb = 0;
+        }
+        return 1;
       };
       long long q = 0;
       int it = 0;
@@ -567,28 +626,47 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
           unsigned char* st = base + (size_t)s * TP_STAGE;
           const uint64_t ahi = desc_sw128(st), alo = desc_sw128(st + 16 * 1024);
           const uint64_t bhi = desc_sw128(st + 32 * 1024), blo = desc_sw128(st + 40 * 1024);
+          // hi x hi into the accumulator at cols 0.. of the P buffer, the two correction
+          // products into a second one at cols 64..: the FP32 accumulation error of a chain grows
+          // with its number of steps and is mostly toward zero, so P's large part is summed over
+          // n_k / 8 steps rather than 3 n_k / 8 (an error of P lies in span(U_k) and adds its
+          // square to ||E_k||^2); epilogue 1 adds the two
 #pragma unroll
           for (int k4 = 0; k4 < TC_KC / 8; ++k4) {
             const uint64_t o = (uint64_t)(k4 * 32) >> 4;
             mma_tf32(tD1, ahi + o, bhi + o, id1, (kc | k4) ? 1u : 0u);
-            mma_tf32(tD1, ahi + o, blo + o, id1, 1u);
-            mma_tf32(tD1, alo + o, bhi + o, id1, 1u);
+            mma_tf32(tD1 + 64, ahi + o, blo + o, id1, (kc | k4) ? 1u : 0u);
+            mma_tf32(tD1 + 64, alo + o, bhi + o, id1, 1u);
           }
           tc_commit(&empty[s]);
-          // the pending MMA2 goes in as soon as its P split is stored
-          if (RESID && pend >= 0 && mbar_try_wait(&pready[pend & 1], (uint32_t)((pend >> 1) & 1))) {
+          if (blocked) {
+            // pending MMA2 blocks of the previous tile go in as soon as they are ready
+            int rc = 1;
+            while (b_tile >= 0 && (rc = mma2_block(false)) > 0) {}
+            if (rc < 0) { ok = false; break; }
+          } else if (RESID && pend >= 0 && mbar_try_wait(&pready[pend & 1], (uint32_t)((pend >> 1) & 1))) {
+            // the pending MMA2 goes in as soon as its P split is stored
             if (!mma2(pend)) { ok = false; break; }
             pend = -1;
           }
         }
         if (!ok) break;
         tc_commit(&d1full[b]);
-        if (RESID) {
+        if (blocked) {
+          while (ok && b_tile >= 0) ok = mma2_block(true) > 0;
+          if (!ok) break;
+          b_tile = it;
+          b_nb = 0;
+        } else if (RESID) {
           if (pend >= 0 && !mma2(pend)) break;
           pend = it;
         }
       }
-      if (RESID && ok && pend >= 0) mma2(pend);
+      if (blocked) {
+        while (ok && b_tile >= 0) ok = mma2_block(true) > 0;
+      } else if (RESID && ok && pend >= 0) {
+        mma2(pend);
+      }
       tc_commit(done);
       wait_bar(done, 0, abort);
     }
@@ -631,8 +709,11 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
       const long long f = t * TC_M + wq * 32 + lane;
       const bool live = f < F;
       for (int c0 = 0; c0 < Rp; c0 += 32) {
-        float v[32];
+        float v[32], w[32];
         tmem_ld32(tD1 + lq + c0, v);
+        tmem_ld32(tDlo + lq + c0, w);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += w[i];
         if (live && !WRITE_ET) {
           // column-major (F x r): consecutive threads write consecutive addresses
 #pragma unroll
@@ -659,8 +740,8 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
     // reload Y by 32-column chunks (TMA, an L2 hit: the tile was streamed moments before) into
     // two swizzled buffers, instead of 128 strided row reads per chunk from global memory.
     const int nck = (n1 + TC_KC - 1) / TC_KC;
-    const bool ysm = (size_t)2 * Kc2 * n1p * TC_KC * 4 + 2 * TC_M * TC_KC * 4 <= 128 * 1024;
-    float* ybuf = B2lo + (size_t)Kc2 * n1p * TC_KC;   // [2][TC_M][TC_KC], 1024-byte aligned
+    const bool ysm = blocked || (size_t)2 * Kc2 * n1p * TC_KC * 4 + 2 * TC_M * TC_KC * 4 <= 128 * 1024;
+    float* ybuf = B2lo + (size_t)Kc2 * b2rows * TC_KC;   // [2][TC_M][TC_KC], 1024-byte aligned
     const bool yleader = (wq == 0 && lane == 0);
     if (ysm && yleader && xb < 0 && a.mYg) tensormap_acquire(a.mYg);
     long long yq = 0;                                 // Y chunks consumed so far
@@ -672,23 +753,52 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
       tma_load_2d(mX, &ybar[seq & 1], ybuf + (size_t)(seq & 1) * TC_M * TC_KC, ci * TC_KC, (int)(t_ * TC_M));
       return true;
     };
+    // blocked form: B2 block gg (rows TP_NB (gg % NB) .. of U_k) into the B2 buffer, issued by
+    // the leader once block gg - 1's MMA2 has completed
+    const long long myt = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const long long nblk = myt * NB;
+    auto issue_b2 = [&](long long gg) {
+      const int nb = (int)(gg % NB);
+      mbar_arrive_expect_tx(bload, (uint32_t)Kc2 * TP_NB * TC_KC * 4 * 2);
+      for (int kc = 0; kc < Kc2; ++kc)
+        for (int n0 = 0; n0 < TP_NB; n0 += 16) {
+          tma_load_2d(&mUrhi, bload, B2hi + ((size_t)kc * TP_NB + n0) * TC_KC, kc * TC_KC, TP_NB * nb + n0);
+          tma_load_2d(&mUrlo, bload, B2lo + ((size_t)kc * TP_NB + n0) * TC_KC, kc * TC_KC, TP_NB * nb + n0);
+        }
+    };
+    if (blocked && yleader && nblk > 0) issue_b2(0);
+    long long g = 0;    // MMA2 blocks consumed (blocked form)
+    bool okall = true;
     int it = 0;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    for (long long t = blockIdx.x; okall && t < ntiles; t += gridDim.x, ++it) {
       if (ysm && yleader) {
         if (issue_y(t, 0, yq) && nck > 1) issue_y(t, 1, yq + 1);
       }
       __syncwarp();
-      bool okw = wait_bar(d2full, (uint32_t)(it & 1), abort);
-      okw = __all_sync(0xffffffffu, okw);
-      if (!okw) break;
-      tc_fence_after();
+      bool okw = true;
+      if (!blocked) {
+        okw = wait_bar(&d2full[0], (uint32_t)(it & 1), abort);
+        okw = __all_sync(0xffffffffu, okw);
+        if (!okw) break;
+        tc_fence_after();
+      }
       const long long f = t * TC_M + wq * 32 + lane;
       const bool live = f < F;
       const float* xrow = Xg + f * n1;
       const int row = wq * 32 + lane;
       for (int c0 = 0, ci = 0; c0 < n1p; c0 += 32, ++ci) {
+        if (blocked && c0 % TP_NB == 0) {
+          // start of column block g: wait for its MMA2, then refill the B2 buffer with block g + 1
+          okw = wait_bar(&d2full[g & 1], (uint32_t)((g >> 1) & 1), abort);
+          okw = __all_sync(0xffffffffu, okw);
+          if (!okw) { okall = false; break; }
+          tc_fence_after();
+          if (yleader && g + 1 < nblk) issue_b2(g + 1);
+          __syncwarp();
+        }
+        const uint32_t tcol = blocked ? tD2 + 128u * (uint32_t)(g & 1) + (uint32_t)(c0 % TP_NB) : tD2 + (uint32_t)c0;
         float v[32];
-        tmem_ld32(tD2 + lq + c0, v);
+        tmem_ld32(tcol + lq, v);
         const float4* ych = reinterpret_cast<const float4*>(ybuf + (size_t)(yq & 1) * TC_M * TC_KC) + row * 8;
         if (ysm) {
           okw = wait_bar(&ybar[yq & 1], (uint32_t)((yq >> 1) & 1), abort);
@@ -731,9 +841,18 @@ __global__ void __launch_bounds__(TP_NT, 1) k_tc_proj(const Ctl* __restrict__ ct
           __syncwarp();   // the next tcgen05.ld is warp-collective: lane 0 may have waited
           ++yq;
         }
+        if (blocked && ((c0 + 32) % TP_NB == 0 || c0 + 32 >= n1p)) {
+          // end of column block g: its D2 buffer may be reused by block g + 2
+          tc_fence_before();
+          mbar_arrive(&d2free[g & 1]);
+          ++g;
+        }
       }
-      tc_fence_before();
-      mbar_arrive(d2free);
+      if (!okall) break;
+      if (!blocked) {
+        tc_fence_before();
+        mbar_arrive(&d2free[0]);
+      }
     }
     if (!WRITE_ET) {
       double se = warp_sum(eacc), sy = warp_sum(yacc);
@@ -816,30 +935,61 @@ cudaError_t launch_tc_proj(const Ctl* ctl, int k, int mode, int pred, const floa
 
 // =============================================================================================
 // k_tc_syrk: partial Gram G = E^T E of the mode-k residual unfolding (Alg. 1's Gram of E_(k)),
-// split over the fibers (K). One CTA per K split computes every block of G it needs from one
-// stream of E^T chunks: a chunk is the n_k rows x 32 fibers of E^T (TMA, 128-row boxes, rows past
-// n_k zero-filled), split on chip into TF32 hi/lo (3xTF32); the MMA operands are row ranges of
-// that one buffer: block 0 = rows 0..127 x columns 0..n_k, block 1 (n_k > 128) = rows 128..255 x
-// columns 128..n_k (the block below it is the transpose of block 0's right part). FP32 partial
-// blocks per split are summed in FP64 by k_syrk_reduce, in a fixed split order.
+// split over the fibers (K). A chunk is the n_k rows x 32 fibers of E^T (TMA, 128-row boxes,
+// rows past n_k zero-filled), split on chip into TF32 hi/lo (3xTF32); the MMA operands are row
+// ranges of that one buffer. Only the blocks on and right of the diagonal of 128-row blocks are
+// formed (the rest of G is their transpose): row block a covers rows 128a .. 128a + 127 and
+// columns 128a .. n_k. Up to 256 rows (ROWS = 256) one CTA per K split forms both row blocks
+// (TMEM cols 0.. and 256..); up to 384 rows (ROWS = 384) the three row blocks do not fit 512
+// TMEM columns together, so the splits run twice (blockIdx.y): group 0 forms row block 0 (two
+// MMAs, columns 0..255 and 256..), group 1 row blocks 1 and 2, each group streaming the same
+// chunks. FP32 partial blocks per split are summed in FP64 by k_syrk_reduce, in a fixed order.
 // Warps: 0 TMA producer, 1 MMA issuer, 2..11 splitters; 4..7 also read the accumulators out.
 // =============================================================================================
-constexpr int TS_ROWS = 256;                          // E^T rows per stage (n_k <= 256)
-constexpr int TS_STAGE = 2 * TS_ROWS * TC_KC * 4;     // hi | lo: 64 KB
-constexpr int TS_S = 3;
 constexpr int TS_SPLIT_W = 10;
 constexpr int TS_NT = 32 * (2 + TS_SPLIT_W);
-constexpr size_t TS_SMEM = (size_t)TS_S * TS_STAGE + 1024 + 256;
+template <int ROWS> struct TsCfg {
+  static constexpr int STAGE = 2 * ROWS * TC_KC * 4;     // hi | lo: 64 KB (256 rows), 96 KB (384)
+  static constexpr int S = ROWS <= 256 ? 3 : 2;
+  static constexpr size_t SMEM = (size_t)S * STAGE + 1024 + 256;
+};
+constexpr int TS_NMAX = 384;                          // largest n_k of the tensor-core Gram
 
+// One MMA target of a CTA: D (TMEM cols tm ..) += rows [128 a, 128 a + 128) x rows [cs, cs + N)
+// of the chunk.
+struct TsTarget { int a, cs, N, tm; };
+__device__ __forceinline__ int ts_targets(int n1p, int group, TsTarget (&t)[2]) {
+  if (n1p <= 256) {
+    t[0] = {0, 0, n1p, 0};
+    if (n1p <= TC_M) return 1;
+    t[1] = {1, TC_M, n1p - TC_M, 256};
+    return 2;
+  }
+  if (group == 0) {
+    t[0] = {0, 0, 256, 0};
+    t[1] = {0, 256, n1p - 256, 256};
+  } else {
+    t[0] = {1, TC_M, n1p - TC_M, 0};
+    t[1] = {2, 256, n1p - 256, 256};
+  }
+  return 2;
+}
+
+template <int ROWS>
 __global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ctl, int k,
                                                      const __grid_constant__ CUtensorMap mEa,
                                                      float* __restrict__ gpart) {
+  constexpr int TS_S = TsCfg<ROWS>::S;
+  constexpr int TS_STAGE = TsCfg<ROWS>::STAGE;
   if (ctl->status) return;
   if (!tc_gram_ok(ctl, k)) return;
   const int n1 = ctl->n[k];
   const long long F = view_B(ctl, k);
   const int n1p = (n1 + 15) / 16 * 16;
-  const int MT = (n1p + TC_M - 1) / TC_M;             // 1 or 2 row blocks
+  if (n1p > ROWS || (ROWS > 256 && n1p <= 256)) return;   // the other instance takes this size
+  const int MT = (n1p + TC_M - 1) / TC_M;             // row blocks loaded per chunk
+  TsTarget tg[2];
+  const int ntg = ts_targets(n1p, blockIdx.y, tg);
   const int S = gridDim.x, sp = blockIdx.x;
   const long long KC = (F + TC_KC - 1) / TC_KC;
   const long long per = (KC + S - 1) / S;
@@ -877,8 +1027,7 @@ __global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ct
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t t0 = tmem, t1 = tmem + 256;          // block 0 (<= 256 cols), block 1 (<= 128)
-  // stage layout: hi rows [0, 256) x 128 B, then lo rows [0, 256) x 128 B
+  // stage layout: hi rows [0, ROWS) x 128 B, then lo rows [0, ROWS) x 128 B
   if (warp == 0) {
     if (lane == 0) {
       tma_prefetch(&mEa);
@@ -897,27 +1046,27 @@ __global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ct
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id0 = idesc_tf32(TC_M, n1p);
-      const uint32_t id1 = idesc_tf32(TC_M, MT > 1 ? n1p - TC_M : 16);
+      uint32_t id[2];
+      for (int g = 0; g < ntg; ++g) id[g] = idesc_tf32(TC_M, tg[g].N);
       bool ok = true;
       for (int c = 0; c < nchunks; ++c) {
         const int s = c % TS_S;
         if (!wait_bar(&conv[s], (uint32_t)((c / TS_S) & 1), abort)) { ok = false; break; }
         tc_fence_after();
         unsigned char* st = base + (size_t)s * TS_STAGE;
-        const uint64_t h0 = desc_sw128(st), l0 = desc_sw128(st + TS_ROWS * 128);
-        const uint64_t h1 = desc_sw128(st + TC_M * 128), l1 = desc_sw128(st + TS_ROWS * 128 + TC_M * 128);
+        for (int g = 0; g < ntg; ++g) {
+          const uint64_t ha = desc_sw128(st + (size_t)tg[g].a * TC_M * 128);
+          const uint64_t la = desc_sw128(st + (size_t)ROWS * 128 + (size_t)tg[g].a * TC_M * 128);
+          const uint64_t hb = desc_sw128(st + (size_t)tg[g].cs * 128);
+          const uint64_t lb = desc_sw128(st + (size_t)ROWS * 128 + (size_t)tg[g].cs * 128);
+          const uint32_t td = tmem + (uint32_t)tg[g].tm;
 #pragma unroll
-        for (int k4 = 0; k4 < TC_KC / 8; ++k4) {
-          const uint64_t o = (uint64_t)(k4 * 32) >> 4;
-          const uint32_t acc = (c | k4) ? 1u : 0u;
-          mma_tf32(t0, h0 + o, h0 + o, id0, acc);
-          mma_tf32(t0, h0 + o, l0 + o, id0, 1u);
-          mma_tf32(t0, l0 + o, h0 + o, id0, 1u);
-          if (MT > 1) {
-            mma_tf32(t1, h1 + o, h1 + o, id1, acc);
-            mma_tf32(t1, h1 + o, l1 + o, id1, 1u);
-            mma_tf32(t1, l1 + o, h1 + o, id1, 1u);
+          for (int k4 = 0; k4 < TC_KC / 8; ++k4) {
+            const uint64_t o = (uint64_t)(k4 * 32) >> 4;
+            const uint32_t acc = (c | k4) ? 1u : 0u;
+            mma_tf32(td, ha + o, hb + o, id[g], acc);
+            mma_tf32(td, ha + o, lb + o, id[g], 1u);
+            mma_tf32(td, la + o, hb + o, id[g], 1u);
           }
         }
         tc_commit(&empty[s]);
@@ -937,7 +1086,7 @@ __global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ct
       if (!wait_bar(&full[s], (uint32_t)((c / TS_S) & 1), abort)) break;
       unsigned char* st = base + (size_t)s * TS_STAGE;
       float4* hi = reinterpret_cast<float4*>(st);
-      float4* lo = reinterpret_cast<float4*>(st + TS_ROWS * 128);
+      float4* lo = reinterpret_cast<float4*>(st + (size_t)ROWS * 128);
       for (int i = ct; i < nv4; i += 32 * TS_SPLIT_W) {
         float4 v = hi[i], h, l;
         tf32_split(v.x, h.x, l.x); tf32_split(v.y, h.y, l.y);
@@ -948,17 +1097,17 @@ __global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ct
       mbar_arrive(&conv[s]);
     }
     if (warp >= 4 && warp < 8) {
-      // partial blocks out: gpart[sp][row][col] (row-major, n1p x n1p FP32); block 0 rows
-      // 0..127 every column, block 1 rows 128.. columns 128..
+      // partial blocks out: gpart[sp][row][col] (row-major, n1p x n1p FP32); row block a holds
+      // columns 128 a ..
       const int wq = warp - 4;
       bool okw = nchunks > 0 ? wait_bar(accfull, 0, abort) : false;
       okw = __all_sync(0xffffffffu, okw);
       float* outp = gpart + (long long)sp * n1p * n1p;
-      for (int mt = 0; mt < MT; ++mt) {
-        const int row = mt * TC_M + wq * 32 + lane;
-        const int cb = mt * TC_M;                    // first column of the block
-        const uint32_t tb = (mt ? t1 : t0) + ((uint32_t)(wq * 32) << 16);
-        for (int c0 = 0; c0 < n1p - cb; c0 += 32) {
+      for (int g = 0; g < ntg; ++g) {
+        const int row = tg[g].a * TC_M + wq * 32 + lane;
+        const int cb = tg[g].cs;                     // first column of the target
+        const uint32_t tb = tmem + (uint32_t)tg[g].tm + ((uint32_t)(wq * 32) << 16);
+        for (int c0 = 0; c0 < tg[g].N; c0 += 32) {
           float v[32];
           if (okw) {
             tc_fence_after();
@@ -971,7 +1120,7 @@ __global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ct
             float* o = outp + (long long)row * n1p + cb + c0;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (cb + c0 + i < n1p) o[i] = v[i];
+              if (c0 + i < tg[g].N && cb + c0 + i < n1p) o[i] = v[i];
           }
         }
       }
@@ -987,8 +1136,8 @@ __global__ void __launch_bounds__(TS_NT, 1) k_tc_syrk(const Ctl* __restrict__ ct
 // G (n_k x n_k, FP64, column-major) = sum over the K splits of the partial blocks. Block: 32
 // consecutive entries of G (lanes) x 8 warps; warp w sums the splits w, w + 8, ... in FP64 and
 // the 8 warp sums are added in warp order (a fixed summation order). Entry (i, j) is read as
-// partial (j, i) (consecutive lanes, consecutive i: contiguous) except in the block rows < 128,
-// columns >= 128 of G's lower-left mirror, which only block 0 holds (as (i, j)).
+// partial (j, i) (consecutive lanes, consecutive i: contiguous) when the 128-row block of i is
+// not left of that of j, else as partial (i, j) (the mirror, held by the row block of i).
 constexpr int SR_W = 8;
 constexpr int SR_SMAX = 160;   // K splits (grid of k_tc_syrk) at most
 __global__ void __launch_bounds__(32 * SR_W) k_syrk_reduce(const Ctl* ctl, int k, const float* gpart,
@@ -1006,7 +1155,7 @@ __global__ void __launch_bounds__(32 * SR_W) k_syrk_reduce(const Ctl* ctl, int k
   long long off = 0;
   if (live) {
     const int i = (int)(L % n1), j = (int)(L / n1);
-    const bool direct = (j < TC_M) || (i >= TC_M);
+    const bool direct = (i / TC_M) >= (j / TC_M);
     off = direct ? (long long)j * n1p + i : (long long)i * n1p + j;
     // every partial of this warp's splits is loaded before the first add (one round of L2
     // latency rather than one per split)
@@ -1037,9 +1186,15 @@ cudaError_t launch_tc_gram(const Ctl* ctl, int k, const TcProjMaps& m, int n1, d
                            double* G, int nsm, cudaStream_t st) {
   const int S = nsm > 0 ? (nsm < SR_SMAX ? nsm : SR_SMAX) : 1;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k_tc_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM); attr = true; }
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_syrk<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TsCfg<256>::SMEM);
+    cudaFuncSetAttribute(k_tc_syrk<TS_NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TsCfg<TS_NMAX>::SMEM);
+    attr = true;
+  }
   float* gp = reinterpret_cast<float*>(gpart);
-  k_tc_syrk<<<S, TS_NT, TS_SMEM, st>>>(ctl, k, m.eta, gp);
+  const int n1p = (n1 + 15) / 16 * 16;
+  if (n1p <= 256) k_tc_syrk<256><<<S, TS_NT, TsCfg<256>::SMEM, st>>>(ctl, k, m.eta, gp);
+  else k_tc_syrk<TS_NMAX><<<dim3(S, 2), TS_NT, TsCfg<TS_NMAX>::SMEM, st>>>(ctl, k, m.eta, gp);
   k_syrk_reduce<<<(n1 * n1 + 31) / 32, 32 * SR_W, 0, st>>>(ctl, k, gp, S, G);
   return cudaGetLastError();
 }
