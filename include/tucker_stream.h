@@ -168,9 +168,10 @@ tucker_status tucker_reconstruct(tucker_state* s, int64_t t_begin, int64_t t_end
  * half of it. A call whose largest temporary, C x_d U_d(t_begin:t_end, :) or a partial expansion
  * C x_d U_d x_1 U_1 ... x_k U_k (k < d-1), needs more than half returns TUCKER_EINVAL before
  * any device work. Reconstruct fewer slices per call in that case. The call allocates nothing:
- * no cudaMalloc, no cudaFree, no pool or library allocation. The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress) with that device current, so make that
- * first call outside any stream capture. Every call, on every state, shares the one array and
+ * no cudaMalloc, no cudaFree, no pool or library allocation. Every call looks up the array's
+ * device address in the current device's context (cudaGetSymbolAddress, which allocates
+ * nothing); the first lookup in a context also loads the library's device symbols, so make the
+ * first call on each device outside any stream capture. Every call, on every state, shares the one array and
  * keeps its last contents. Nothing in it needs to start at zero, because each call writes every
  * element it reads. Calls whose device work overlaps (on different streams or host threads)
  * race on the array and must be serialised by the caller. Synchronizes `stream` once before

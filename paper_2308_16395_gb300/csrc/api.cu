@@ -681,7 +681,8 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
         // only where that cannot certify the cut
         CK(launch_eig_sub(s->ctl, k, s->G, s->eAw, s->eW, s->mcap, s->gpart, n, st));
         CK(launch_eig<TE>(s->ctl, k, 2, s->G, s->eAw, s->eZ, s->eLD, s->eW, nullptr, s->mcap, n, st));
-        launches += 2;
+        CK(launch_eig_refine_post(s->ctl, k, s->G, s->eW, s->mcap, s->gpart, n, st));
+        launches += 3;
       } else {
         CK(launch_eig<TE>(s->ctl, k, 0, s->G, s->eAw, s->eZ, s->eLD, s->eW, nullptr, s->mcap, n, st));
       }
@@ -785,10 +786,6 @@ bool usable(tucker_state* s) { return s && !s->latched; }
 // allocation-free reconstruction: the two ping-pong temporaries live in one fixed device array
 // ---------------------------------------------------------------------------------------------
 constexpr size_t kNoallocScratchBytes = (size_t)TUCKER_NOALLOC_SCRATCH_BYTES;
-constexpr int kNoallocMaxDevices = 64;
-
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kNoallocMaxDevices] = {};
 
 }  // namespace
 
@@ -798,22 +795,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[TUCKER_NOALLOC_
 
 namespace {
 
-// Device address of g_noalloc_scratch on the current device, looked up once per device.
+// Device address of g_noalloc_scratch in the current device's context. Looked up on every call
+// (the lookup allocates nothing): a cached address would dangle once the context is recreated
+// (after cudaDeviceReset, for instance). The first lookup in a context loads the module's
+// device symbols, which is why the first call on a device belongs outside any stream capture.
 tucker_status noalloc_scratch(tucker_state* s, void** out) {
   *out = nullptr;
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kNoallocMaxDevices) {
-    set_err(s, "allocation-free reconstruction supports device ordinals below %s%lld", "", kNoallocMaxDevices);
-    return TUCKER_EINVAL;
-  }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  *out = p;
   return TUCKER_OK;
 }
 
@@ -1115,20 +1105,37 @@ tucker_status tucker_stream_update_host(tucker_state* s, const void* Y_host, voi
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)s->N * (size_t)s->tx;
   if (!s->hcs) {
-    for (int b = 0; b < 2; ++b) {
-      if (cudaMalloc(&s->hstage[b], bytes) != cudaSuccess) {
-        cudaGetLastError();
-        set_err(s, "cannot allocate the host-input staging buffers%s (%lld bytes each)", "", (long long)bytes);
-        return TUCKER_ENOMEM;
+    // created into locals and committed to the state only when every step succeeded, so that a
+    // failure leaves nothing half made (the next call starts over)
+    void* stage[2] = {nullptr, nullptr};
+    cudaStream_t cs = nullptr;
+    cudaEvent_t cp[2] = {nullptr, nullptr}, cn[2] = {nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&stage[b], bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaEventCreateWithFlags(&cp[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&cn[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(cn[b], st);   // both buffers free
+    }
+    if (e != cudaSuccess) {
+      for (int b = 0; b < 2; ++b) {
+        if (stage[b]) cudaFree(stage[b]);
+        if (cp[b]) cudaEventDestroy(cp[b]);
+        if (cn[b]) cudaEventDestroy(cn[b]);
       }
-      s->allocs.push_back(s->hstage[b]);
+      if (cs) cudaStreamDestroy(cs);
+      cudaGetLastError();
+      set_err(s, "cannot set up the host-input staging buffers%s (%lld bytes each)", "", (long long)bytes);
+      return e == cudaErrorMemoryAllocation ? TUCKER_ENOMEM : TUCKER_ECUDA;
     }
-    CK(cudaStreamCreateWithFlags(&s->hcs, cudaStreamNonBlocking));
     for (int b = 0; b < 2; ++b) {
-      CK(cudaEventCreateWithFlags(&s->hcopied[b], cudaEventDisableTiming));
-      CK(cudaEventCreateWithFlags(&s->hconsumed[b], cudaEventDisableTiming));
-      CK(cudaEventRecord(s->hconsumed[b], st));   // both buffers free
+      s->hstage[b] = stage[b];
+      s->allocs.push_back(stage[b]);
+      s->hcopied[b] = cp[b];
+      s->hconsumed[b] = cn[b];
     }
+    s->hcs = cs;
   }
   const int b = s->hnext;
   s->hnext ^= 1;

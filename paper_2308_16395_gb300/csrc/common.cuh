@@ -71,7 +71,6 @@ struct Ctl {
   int eig_m[TK_MAXD];
   int eig_it[TK_MAXD];
   int eig_fb[TK_MAXD];
-  double eig_tr[TK_MAXD];   // trace(G) of the residual Gram, FP64
   // ---- decision replay (a test hook): branches and cuts forced on the next update, written
   // by the host before the update and cleared by k_end_update. rp_grow[k] < 0 keeps mode k's
   // own decision, 0 forces ||E_k|| <= eps, r > 0 forces growth by r'_k = r; rp_aug < 0 keeps

@@ -522,6 +522,9 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
   const int lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
   // decision replay (test hook): a cut forced for this update
   const int want = (mode == 0) ? max(rp_grow_of(ctl, k), 0) : 0;
+  // FP32 residual Grams: one eigenvector past the cut is formed as well, for the FP64
+  // Rayleigh-Ritz cut that follows (k_eig_refine)
+  const bool xtra = mode == 0 && sizeof(TE) == 4;
   TE* A = use_amat ? reinterpret_cast<TE*>(eig_dyn) : reinterpret_cast<TE*>(ea.Aw);
   __shared__ TE sa[TK_N_MAX], sb[TK_N_MAX], sb2[TK_N_MAX], stau[TK_N_MAX], slam[TK_N_MAX];
   __shared__ TE sv[TK_N_MAX], sp[TK_N_MAX];
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
     // small because the cut of a residual Gram usually keeps a few eigenpairs. The initial
     // ST-HOSVD (mode 1) computes every eigenvalue: its discarded energy is a tiny fraction of the
     // trace, so it is summed from the bottom of the spectrum below instead.
-    for (int j0 = 0; j0 < n && (j0 == 0 || s_cut < 0 || mode == 1 || s_cnt < want); j0 += (j0 == 0 ? bs0 : nwarp)) {
+    for (int j0 = 0; j0 < n && (j0 == 0 || s_cut < 0 || mode == 1 || s_cnt < want || (xtra && s_cnt <= s_cut)); j0 += (j0 == 0 ? bs0 : nwarp)) {
       const int bs = (j0 == 0) ? bs0 : nwarp;
       const int j = j0 + wid;            // descending index of this warp's eigenvalue
       if (wid < bs && j < n) {
@@ -777,6 +780,7 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
     s_cnt = n;
   }
   __shared__ double s_tprev;
+  __shared__ int s_mv;
   if (tid == 0) {
     int m = s_cut;
     if (want > 0) m = min(want, s_cnt);
@@ -792,11 +796,17 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
     if (m > ea.mcap) status = TK_ECAPACITY;
     if (status) ctl->status = status;
     s_m = status ? 0 : m;
-    s_disc = (m <= s_cnt) ? stails[m] : 0.0;
-    s_tprev = (m >= 1 && m - 1 <= s_cnt) ? stails[m - 1] : 0.0;
+    // (a top-down tail below the eigenvalues' resolution is rounding noise of either sign; a
+    // discarded energy is not negative)
+    s_disc = (m <= s_cnt) ? fmax(stails[m], 0.0) : 0.0;
+    s_tprev = (m >= 1 && m - 1 <= s_cnt) ? fmax(stails[m - 1], 0.0) : 0.0;
+    int mv = s_m;
+    if (xtra && s_m > 0) mv = min(min(s_m + 1, s_cnt), min(n - ctl->r[k], ea.mcap));
+    s_mv = mv;
   }
   __syncthreads();
-  const int m = s_m;
+  const int mcut = s_m;   // the cut (Alg. 1)
+  const int m = s_mv;     // eigenvectors formed
   if (ea.lam_out)
     for (int i = tid; i < s_cnt; i += nt) ea.lam_out[i] = (double)slam[i];
   if (m == 0) {
@@ -988,8 +998,8 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
       }
     }
     if (tid == 0) {
-      if (mode == 0) { ctl->radd[k] = m; ctl->disc[k] = s_disc; ctl->tail_prev[k] = s_tprev; }
-      else { ctl->r[k] = m; ctl->disc[k] = s_disc; }
+      if (mode == 0) { ctl->radd[k] = mcut; ctl->disc[k] = s_disc; ctl->tail_prev[k] = s_tprev; ctl->eig_m[k] = m; }
+      else { ctl->r[k] = mcut; ctl->disc[k] = s_disc; }
     }
     return;
   }
@@ -1177,8 +1187,8 @@ __global__ void __launch_bounds__(sizeof(TE) == 4 ? EIG_NT_F32 : EIG_NT) k_eig_t
   __syncthreads();
   for (long long L = tid; L < (long long)m * n; L += nt) ea.W[L] = (double)Z[L];
   if (tid == 0) {
-    if (mode == 0) { ctl->radd[k] = m; ctl->disc[k] = s_disc; ctl->tail_prev[k] = s_tprev; }
-    else { ctl->r[k] = m; ctl->disc[k] = s_disc; }
+    if (mode == 0) { ctl->radd[k] = mcut; ctl->disc[k] = s_disc; ctl->tail_prev[k] = s_tprev; ctl->eig_m[k] = m; }
+    else { ctl->r[k] = mcut; ctl->disc[k] = s_disc; }
   }
 }
 

@@ -38,6 +38,12 @@ constexpr int SUB_NMIN = 48;             // smaller Grams go to the full solver 
 constexpr int REF_NT = 128;
 constexpr int REF_MAXB = 96;             // CTAs of k_eig_refine
 
+// Floats of the shared-memory copy of G, rounded up to a multiple of 4 so that the region after
+// it starts on a 16-byte boundary (n odd gives an odd n^2).
+__host__ __device__ __forceinline__ size_t sub_gs_floats(int n) {
+  return ((size_t)n * n + 3) / 4 * 4;
+}
+
 // Counter-based start vectors (a hash of row and column): deterministic, entries in [-1, 1).
 __device__ __forceinline__ float sub_hash(int i, int c) {
   unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)(c + 1) * 0x85EBCA77u);
@@ -214,7 +220,8 @@ __global__ void __launch_bounds__(SUB_NT, 1) k_eig_sub(Ctl* ctl, int k, SubArgs 
   }
   const bool gsm = n <= SUB_GS_NMAX;
   float* Gs = sub_dyn;                                   // n x n (if gsm)
-  float* Qs = sub_dyn + (gsm ? (size_t)n * n : 0);       // [n][SB], row j's SB values contiguous
+  // Q's rows are read and written as float4: its offset is rounded up to 4 floats (16 bytes)
+  float* Qs = sub_dyn + (gsm ? sub_gs_floats(n) : 0);   // [n][SB], row j's SB values contiguous
   float* red = Qs + (size_t)n * SB;                      // [SUB_NW][64]
   float* H = red + SUB_NW * 64;                          // SB x (SB + 1)
   float* Y = H + SB * (SB + 1);                          // SB x (SB + 1)
@@ -396,7 +403,6 @@ __global__ void __launch_bounds__(SUB_NT, 1) k_eig_sub(Ctl* ctl, int k, SubArgs 
   if (live)
     for (int c = 0; c < m; ++c) a.W[(long long)c * n + tid] = (double)q[c];
   if (tid == 0) {
-    ctl->eig_tr[k] = trace;
     ctl->eig_m[k] = m;
     ctl->eig_it[k] = it + 1;
     ctl->eig_fb[k] = 0;
@@ -404,12 +410,19 @@ __global__ void __launch_bounds__(SUB_NT, 1) k_eig_sub(Ctl* ctl, int k, SubArgs 
 }
 
 // FP64 Rayleigh-Ritz over the m Ritz vectors and Alg. 1's cut (see the file comment).
-// Grid: up to REF_MAXB CTAs, one warp per row of G W at a time.
+// Grid: up to REF_MAXB CTAs, one warp per row of G W at a time. post = 0: the vectors of
+// k_eig_sub (skipped when it handed the mode to the full solver); post = 1: after the full FP32
+// solver (only then), over the eigenvectors it formed (its cut and one more): the cut and its
+// tails in FP64 again, the FP32 cut kept if the FP64 one lies past those vectors.
 __global__ void __launch_bounds__(REF_NT) k_eig_refine(Ctl* ctl, int k, const double* __restrict__ G,
-                                                      const double* __restrict__ W, double* part, int mcap) {
-  if (ctl->status || !ctl->grew[k] || ctl->eig_fb[k]) return;
+                                                      const double* __restrict__ W, double* part, int mcap,
+                                                      int post) {
+  if (ctl->status || !ctl->grew[k]) return;
+  if (post ? !ctl->eig_fb[k] : ctl->eig_fb[k]) return;
   const int n = ctl->n[k];
   const int m = ctl->eig_m[k];
+  // (after the full solver the vectors may exceed the block: its FP32 cut then stands)
+  if (m < 1 || m > SB) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int NWR = REF_NT / 32;
   constexpr int E = SB * SB / 32;   // entries of an m x m matrix per lane (m <= SB)
@@ -480,10 +493,18 @@ __global__ void __launch_bounds__(REF_NT) k_eig_refine(Ctl* ctl, int k, const do
     }
     inc[l] = v;
   }
+  // trace(G) in FP64, one warp over the diagonal
+  __shared__ double s_trace;
+  if (threadIdx.x < 32) {
+    double tr = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) tr += G[(long long)i * n + i];
+    tr = warp_sum(tr);
+    if (threadIdx.x == 0) s_trace = tr;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     const double eps2 = ctl->eps * ctl->eps;
-    const double trace = ctl->eig_tr[k];
+    const double trace = s_trace;
     const int want = max(rp_grow_of(ctl, k), 0);
     const int r0 = ctl->r[k];
     double tail = trace, prev = trace;
@@ -493,21 +514,34 @@ __global__ void __launch_bounds__(REF_NT) k_eig_refine(Ctl* ctl, int k, const do
       tail -= inc[c];
       if ((want > 0 && c + 1 == want) || (want == 0 && tail <= eps2)) { l = c + 1; break; }
     }
-    if (l < 0) {
+    if (l < 0 && post) {
+      // past the vectors formed: the full solver's cut stands, its tails recomputed in FP64
+      l = min(ctl->radd[k], m);
+      if (l >= 1) {
+        double tt = trace;
+        for (int c = 0; c < l; ++c) { prev = tt; tt -= inc[c]; }
+        tail = tt;
+      } else {
+        l = -2;   // nothing to refine
+      }
+    }
+    if (l == -1) {
       ctl->eig_fb[k] = 1;   // the cut lies beyond the certified vectors: full solver
-    } else {
+    } else if (l >= 1) {
       if (l > n - r0) l = n - r0;
       if (r0 + l > ctl->cap[k] || l > mcap) { ctl->status = TK_ECAPACITY; return; }
+      // a discarded energy is not negative: below the Gram's own resolution (its FP32
+      // accumulation, ~u_fp32 trace(G)) the computed tail is rounding noise of either sign
       ctl->radd[k] = l;
-      ctl->disc[k] = tail;
-      ctl->tail_prev[k] = prev;
+      ctl->disc[k] = fmax(tail, 0.0);
+      ctl->tail_prev[k] = fmax(prev, 0.0);
     }
   }
 }
 
 size_t eig_sub_smem(int n) {
   const bool gsm = n <= SUB_GS_NMAX;
-  return sizeof(float) * ((gsm ? (size_t)n * n : 0) + (size_t)n * SB + SUB_NW * 64 + 3 * SB * (SB + 1) + 4 * SB + 2 * SB);
+  return sizeof(float) * ((gsm ? sub_gs_floats(n) : 0) + (size_t)n * SB + SUB_NW * 64 + 3 * SB * (SB + 1) + 4 * SB + 2 * SB);
 }
 
 cudaError_t launch_eig_sub(Ctl* ctl, int k, const double* G, void* Gf, double* W, int mcap,
@@ -526,7 +560,14 @@ cudaError_t launch_eig_sub(Ctl* ctl, int k, const double* G, void* Gf, double* W
   SubArgs a{G, reinterpret_cast<float*>(Gf), W, mcap};
   k_eig_sub<<<1, SUB_NT, sm, st>>>(ctl, k, a);
   const int nb = std::min(REF_MAXB, std::max(1, (n + 3) / 4));
-  k_eig_refine<<<nb, REF_NT, 0, st>>>(ctl, k, G, W, part, mcap);
+  k_eig_refine<<<nb, REF_NT, 0, st>>>(ctl, k, G, W, part, mcap, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eig_refine_post(Ctl* ctl, int k, const double* G, double* W, int mcap,
+                                   double* part, int n, cudaStream_t st) {
+  const int nb = std::min(REF_MAXB, std::max(1, (n + 3) / 4));
+  k_eig_refine<<<nb, REF_NT, 0, st>>>(ctl, k, G, W, part, mcap, 1);
   return cudaGetLastError();
 }
 

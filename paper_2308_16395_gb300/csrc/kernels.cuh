@@ -44,6 +44,9 @@ cudaError_t launch_append(Ctl* ctl, int k, int mode, const double* W, double* U,
 // ctl->eig_fb[k] when the full solver (launch_eig with mode 2) must decide instead.
 cudaError_t launch_eig_sub(Ctl* ctl, int k, const double* G, void* Gf, double* W, int mcap,
                            double* part, int n, cudaStream_t st);
+// FP64 Rayleigh-Ritz cut over the eigenvectors of the full FP32 solver (runs when it ran).
+cudaError_t launch_eig_refine_post(Ctl* ctl, int k, const double* G, double* W, int mcap,
+                                   double* part, int n, cudaStream_t st);
 
 // ---- k_stream.cu ----
 struct SecWork {

@@ -62,3 +62,40 @@ def gpu_state_numpy(ts):
     C = ts.core().cpu().numpy()
     Us = [ts.factor(k).cpu().numpy() for k in range(ts.d)]
     return C, Us
+
+
+def oracle_tails(m) -> np.ndarray:
+    """Alg. 1's tails lambda_{l+1} + ... + lambda_n (l = 0..n) of a grown mode's residual Gram."""
+    lam = np.asarray(m.lam)
+    return np.concatenate([np.cumsum(lam[::-1])[::-1], [0.0]])
+
+
+def replay_for(log: dict, delta: float, delta_q: float | None = None):
+    """The oracle's decisions of one update whose statistic lies within `delta` (relative) of
+    eps^2 (`delta_q` for Alg. 3's q^2, default `delta`), as (grow, augment) arguments of
+    tucker_replay_next; None when no decision is near.
+
+    grow[k] is -1 (the library decides), 0 (no growth) or the oracle's r'_k; augment is -1 or the
+    oracle's branch of Alg. 3 (reading of the paper on near-cutoff decisions under mixed
+    precision: such a decision may come out either way, and the library is then made to take the
+    oracle's so that the two stay comparable)."""
+    eps2 = log["eps"] ** 2
+    if eps2 == 0.0:
+        return None
+    near = False
+    grow = []
+    for m in log["modes"]:
+        g = -1
+        if abs(m.e_norm2 - eps2) / eps2 < delta:
+            g = m.r_add if m.grew else 0
+        elif m.grew and m.lam is not None:
+            t = oracle_tails(m)
+            if min(abs(t[m.r_add] - eps2), abs(t[m.r_add - 1] - eps2)) / eps2 < delta:
+                g = m.r_add
+        near |= g >= 0
+        grow.append(g)
+    aug = -1
+    if abs(log["isvd"].q ** 2 - eps2) / eps2 < (delta if delta_q is None else delta_q):
+        aug = int(log["isvd"].augmented)
+        near = True
+    return (grow, aug) if near else None
