@@ -151,6 +151,20 @@ int64_t tucker_batch_kernels(const tucker_batch* b);
 /* Release the graph (the states are not touched). */
 void tucker_batch_destroy(tucker_batch* b);
 
+/* One update (Alg. 5) of each of `count` independent states, state i from the slice Y_dev[i]
+ * (device pointer; layout and type of that state's config), as one CUDA-graph launch on
+ * `stream`. The first call for a given list of states captures the batch graph once (as
+ * tucker_batch_create does; the call synchronizes the states' last streams then); later calls
+ * with the same list, in the same order, write each state's slice address into its control
+ * block (one small kernel per state on `stream`) and launch that graph. Slice pointers may
+ * differ from call to call. A state appears at most once per list; destroying a state drops
+ * the graphs that hold it. Calls with different lists keep separate graphs. The caller keeps
+ * each slice unmodified until `stream` has passed this call. Device-side errors latch in the
+ * state that met them. Errors: EINVAL (NULL, count outside 1..4096, a repeated state, a slice
+ * unusable for TMA), ESTATE, ECUDA. */
+tucker_status tucker_stream_update_batched(tucker_state* const* states, const void* const* Y_dev,
+                                           int32_t count, void* stream);
+
 /* Reconstruction X^(:, ..., t) = C x_1 U_1 ... x_{d-1} U_{d-1} x_d U_d(t, :) for slices
  * t in [t_begin, t_end) (0-based) into out_dev (n_1 x ... x n_{d-1} x (t_end - t_begin),
  * column-major, element type cfg->dtype). Enqueued on `stream`. Errors: EINVAL, ESTATE. */

@@ -30,7 +30,7 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy",
            "tucker_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
            "tucker_get_launch_plan", "tucker_stream_update_host", "tucker_get_step_log",
-           "tucker_replay_next"]
+           "tucker_replay_next", "tucker_stream_update_batched"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -127,6 +127,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_batch_create.argtypes = [vp, vp, i32, ctypes.POINTER(vp)]
     lib.tucker_batch_create.restype = ctypes.c_int
     lib.tucker_batch_update.argtypes = [vp, vp]
+    lib.tucker_stream_update_batched.argtypes = [vp, vp, i32, vp]
+    lib.tucker_stream_update_batched.restype = ctypes.c_int
     lib.tucker_batch_update.restype = ctypes.c_int
     lib.tucker_set_launch_plan.argtypes = [vp, ctypes.POINTER(LaunchPlan)]
     lib.tucker_set_launch_plan.restype = ctypes.c_int
@@ -309,6 +311,14 @@ def tucker_batch_create(handles, slot_ptrs) -> int:
 
 def tucker_batch_update(b: int, stream: int = 0) -> None:
     _check(load_library().tucker_batch_update(b, ctypes.c_void_p(stream)))
+
+
+def tucker_stream_update_batched(handles, slice_ptrs, stream: int = 0) -> None:
+    """One update of each state from its own device slice, one graph launch (cached per list)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*handles)
+    ys = (ctypes.c_void_p * n)(*slice_ptrs)
+    _check(load_library().tucker_stream_update_batched(hs, ys, n, ctypes.c_void_p(stream)))
 
 
 def tucker_batch_kernels(b: int) -> int:

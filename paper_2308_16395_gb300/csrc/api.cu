@@ -985,6 +985,33 @@ tucker_status push_replay(tucker_state* s, cudaStream_t st) {
   return TUCKER_OK;
 }
 
+// Graph-form slice slot: the slice's address (and, for the tensor-core mode-1 pass, its TMA
+// descriptor) written into the control block by a one-block kernel on `st`.
+tucker_status write_slot(tucker_state* s, const void* Y_dev, cudaStream_t st) {
+  SlotArgs sa{};
+  if ((s->tcmask & 1) && s->tx == 4) {
+    CUtensorMap m;
+    if (!make_map_2d_f32(&m, Y_dev, s->N / s->n[0], s->n[0], s->n[0], 32, 128)) {
+      set_err(s, "slice address unusable for TMA (16-byte alignment)%s%lld", "", 0);
+      return TUCKER_EINVAL;
+    }
+    static_assert(sizeof(m) == sizeof(sa.map), "descriptor size");
+    memcpy(sa.map, &m, sizeof(m));
+  }
+  sa.y = Y_dev;
+  CK(launch_set_slot(s->ctl, sa, st));
+  return TUCKER_OK;
+}
+
+// Batches of tucker_stream_update_batched, one per set of states (in call order), captured with
+// the slice read from each state's control block; a state's destruction drops every batch
+// holding it.
+std::mutex g_auto_mu;
+std::vector<tucker_batch*> g_auto_batches;
+
+tucker_status batch_create(tucker_state* const* states, const void* const* Y_slots_dev,
+                           int32_t count, tucker_batch** out);
+
 }  // namespace
 
 // =============================================================================================
@@ -1080,18 +1107,8 @@ tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* str
   if (!s->prof && !s->graph_failed) {
     if (!s->uexec && capture_update(s) != TUCKER_OK) s->graph_failed = true;
     if (s->uexec) {
-      SlotArgs sa{};
-      if ((s->tcmask & 1) && s->tx == 4) {
-        CUtensorMap m;
-        if (!make_map_2d_f32(&m, Y_dev, s->N / s->n[0], s->n[0], s->n[0], 32, 128)) {
-          set_err(s, "slice address unusable for TMA (16-byte alignment)%s%lld", "", 0);
-          return TUCKER_EINVAL;
-        }
-        static_assert(sizeof(m) == sizeof(sa.map), "descriptor size");
-        memcpy(sa.map, &m, sizeof(m));
-      }
-      sa.y = Y_dev;
-      CK(launch_set_slot(s->ctl, sa, st));
+      tucker_status rs = write_slot(s, Y_dev, st);
+      if (rs != TUCKER_OK) return rs;
       CK(cudaGraphLaunch(s->uexec, st));
       return TUCKER_OK;
     }
@@ -1330,11 +1347,24 @@ tucker_status tucker_copy_sv(tucker_state* s, double* S_dev, double* V_dev) {
 
 tucker_status tucker_batch_create(tucker_state* const* states, const void* const* Y_slots_dev,
                                   int32_t count, tucker_batch** out) {
+  if (!Y_slots_dev || count < 1) return TUCKER_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!Y_slots_dev[i]) return TUCKER_EINVAL;
+  return batch_create(states, Y_slots_dev, count, out);
+}
+
+}  // extern "C"
+
+namespace {
+// tucker_batch_create without the slot check: a NULL slot makes that state's branch read its slice
+// from the state's control block (tucker_stream_update_batched writes it before each launch).
+tucker_status batch_create(tucker_state* const* states, const void* const* Y_slots_dev,
+                           int32_t count, tucker_batch** out) {
   if (!out) return TUCKER_EINVAL;
   *out = nullptr;
   if (!states || !Y_slots_dev || count < 1 || count > 4096) return TUCKER_EINVAL;
   for (int i = 0; i < count; ++i) {
-    if (!states[i] || !Y_slots_dev[i]) return TUCKER_EINVAL;
+    if (!states[i]) return TUCKER_EINVAL;
     if (!usable(states[i])) return TUCKER_ESTATE;
     for (int j = 0; j < i; ++j)
       if (states[j] == states[i]) return TUCKER_EINVAL;   // a state updates once per launch
@@ -1365,6 +1395,9 @@ tucker_status tucker_batch_create(tucker_state* const* states, const void* const
   *out = b;
   return TUCKER_OK;
 }
+}  // namespace
+
+extern "C" {
 
 tucker_status tucker_batch_update(tucker_batch* b, void* stream) {
   if (!b || !b->exec) return TUCKER_EINVAL;
@@ -1379,6 +1412,33 @@ tucker_status tucker_batch_update(tucker_batch* b, void* stream) {
 }
 
 int64_t tucker_batch_kernels(const tucker_batch* b) { return b ? b->launches : -1; }
+
+tucker_status tucker_stream_update_batched(tucker_state* const* states, const void* const* Y_dev,
+                                           int32_t count, void* stream) {
+  if (!states || !Y_dev || count < 1 || count > 4096) return TUCKER_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!states[i] || !Y_dev[i]) return TUCKER_EINVAL;
+    if (!usable(states[i])) return TUCKER_ESTATE;
+  }
+  std::lock_guard<std::mutex> lock(g_auto_mu);
+  tucker_batch* b = nullptr;
+  for (tucker_batch* c : g_auto_batches)
+    if ((int)c->states.size() == count && std::equal(c->states.begin(), c->states.end(), states)) b = c;
+  if (!b) {
+    // first call for this set of states: one graph, each branch reading its state's slice from
+    // the control block (written below by the slot kernels)
+    std::vector<const void*> none(count, nullptr);
+    tucker_status rc = batch_create(states, none.data(), count, &b);
+    if (rc != TUCKER_OK) return rc;
+    g_auto_batches.push_back(b);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < count; ++i) {
+    tucker_status rc = write_slot(states[i], Y_dev[i], st);
+    if (rc != TUCKER_OK) return rc;
+  }
+  return tucker_batch_update(b, stream);
+}
 
 void tucker_batch_destroy(tucker_batch* b) {
   if (!b) return;
@@ -1419,6 +1479,19 @@ tucker_status tucker_profile_read(tucker_state* s, tucker_profile* out) {
 
 void tucker_destroy(tucker_state* s) {
   if (!s) return;
+  {
+    // batches of tucker_stream_update_batched that hold this state go with it
+    std::lock_guard<std::mutex> lock(g_auto_mu);
+    for (size_t i = 0; i < g_auto_batches.size();) {
+      tucker_batch* b = g_auto_batches[i];
+      if (std::find(b->states.begin(), b->states.end(), s) != b->states.end()) {
+        tucker_batch_destroy(b);
+        g_auto_batches.erase(g_auto_batches.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+  }
   cudaStreamSynchronize(s->last_stream);
   if (s->hcs) {
     cudaStreamSynchronize(s->hcs);

@@ -152,3 +152,37 @@ def test_launch_plan_changes_no_result(pkg):
     assert float(torch.linalg.norm(Ra - Rb) / torch.linalg.norm(Ra)) <= 1e-6
     a.close()
     b.close()
+
+
+def test_stream_update_batched_equals_single_updates(pkg):
+    """tucker_stream_update_batched (each state's slice by pointer, one graph launch per call,
+    the graph cached per list of states) gives the same states as one tucker_stream_update per
+    state; the slice buffers change from call to call."""
+    import torch
+
+    n_init, T = 5, 12
+    entries = []
+    for s, tau, prec, dt in _small_streams()[:3]:
+        X = s.tensor(0, T).astype(np.float32).astype(np.float64)
+        Xg = to_device(X, torch.float32)
+        a = pkg.TuckerStream(Xg[:n_init].contiguous(), tau, precision="mixed", steps_cap=T + 4)
+        b = pkg.TuckerStream(Xg[:n_init].contiguous(), tau, precision="mixed", steps_cap=T + 4)
+        entries.append((a, b, Xg))
+    st = torch.cuda.current_stream().cuda_stream
+    for t in range(n_init, T):
+        ys = [e[2][t].clone() for e in entries]          # fresh buffers every step
+        pkg.tucker_stream_update_batched([e[0].h for e in entries], [y.data_ptr() for y in ys], st)
+        for e in entries:
+            e[1].update(e[2][t].contiguous())
+        torch.cuda.synchronize()
+    for a, b, _ in entries:
+        assert a.ranks == b.ranks
+        Ra, Rb = a.reconstruct(0, T).double(), b.reconstruct(0, T).double()
+        assert float(torch.linalg.norm(Ra - Rb) / torch.linalg.norm(Rb)) <= 1e-12
+        assert a.error_norm() == b.error_norm()
+    with pytest.raises(pkg.TuckerError):
+        pkg.tucker_stream_update_batched([entries[0][0].h, entries[0][0].h],
+                                         [entries[0][2][0].data_ptr()] * 2, st)
+    for a, b, _ in entries:
+        a.close()
+        b.close()
