@@ -348,3 +348,45 @@ def reconstruct_slices(st: StreamState, t0: int, t1: int) -> np.ndarray:
     """X^(:, ..., t) for t in [t0, t1): C x_1 U_1 ... x_{d-1} U_{d-1} x_d U_d(t0:t1, :)."""
     Us = list(st.Us[:-1]) + [st.Us[-1][t0:t1, :]]
     return reconstruct(st.C, Us)
+
+
+# ---------------------------------------------------------------------------------------------
+# Re-compression of a streaming state (batch ST-HOSVD of the current Tucker representation)
+# ---------------------------------------------------------------------------------------------
+
+def recompress(st: StreamState, tau_total: float) -> StreamState:
+    """Re-truncate the Tucker representation of the state by the batch ST-HOSVD (Alg. 2), in place.
+
+    The streaming ranks are over-estimates of what the data needs (Sec. 5, Tables 1-2); running
+    Alg. 2 on the current representation X^ = C x_1 U_1 ... x_d U_d lowers them again. With every
+    U_k orthonormal, the ST-HOSVD of X^ is the ST-HOSVD of the core C with the factors multiplied
+    in: the mode-k Gram of X^'s partially projected unfolding is U_k G_k U_k^T for the
+    corresponding Gram G_k of C's, so its eigenvectors are U_k Q_k with Q_k those of G_k. The
+    budget: the running bound b (Prop. 1, Prop. 2) may grow to tau_total ||X||, and since
+    ||X - X^'|| <= ||X - X^|| + ||X^ - X^'|| the re-compression may discard (tau_total ||X|| - b)^2
+    in all, eps' = (tau_total ||X|| - b) / sqrt(d) per mode (Alg. 2's rule). The new bound is
+    b + ||X^ - X^'||. The state keeps Assumption 1: S and V from the last mode's truncated SVD.
+    """
+    d = st.d
+    b = math.sqrt(max(st.err2, 0.0))
+    budget = tau_total * math.sqrt(st.data_norm2) - b
+    if budget <= 0.0:
+        raise ValueError("tau_total leaves no error budget beyond the running bound")
+    eps = budget / math.sqrt(d)
+    C = st.C
+    Qs = []
+    disc = 0.0
+    last = None
+    for k in range(d):
+        res = truncated_svd(unfold(C, k), eps, min_rank=1)
+        Qs.append(res.U)
+        disc += res.discarded
+        C = ttm(C, res.U.T, k)
+        last = res
+    st.Us = [U @ Q for U, Q in zip(st.Us, Qs)]
+    st.C = C
+    st.S = last.s.copy()
+    st.V = fold(unfold(C, d - 1) / st.S[:, None], d - 1, C.shape)
+    st.err2 = (b + math.sqrt(disc)) ** 2
+    st.log.append(dict(kind="recompress", ranks=st.ranks, eps=eps, discarded=disc))
+    return st
