@@ -263,6 +263,31 @@ typedef struct {
 } tucker_replay;
 tucker_status tucker_replay_next(tucker_state* s, const tucker_replay* r);
 
+/* Re-compression of the streamed decomposition: the batch ST-HOSVD (Alg. 2) run again on the
+ * current Tucker representation X^ = C x_1 U_1 ... x_d U_d, so that ranks the per-slice updates
+ * over-estimated come down. Since the factors are orthonormal, Alg. 2 on X^ equals Alg. 2 on the
+ * core C (r_1 x ... x r_d, the streaming mode's r_d entries taken as its slices) followed by
+ * U_k <- U_k Q_k, with Q_k the factors of the core's decomposition; the new core, S and V come
+ * from that decomposition's last mode (C' = V' x_d S', Assumption 1(c)).
+ * Budget: with b the running bound (sqrt of the accumulated discarded energy) and ||X|| the
+ * norm of the data seen so far, the core's decomposition takes the per-mode tolerance
+ * eps' = (tau_total ||X|| - b) / sqrt(d), so that its discarded energy e' <= (tau_total ||X|| -
+ * b)^2; the new bound is (b + sqrt(e'))^2 (triangle inequality), hence ||X - X^'|| <=
+ * tau_total ||X||. Streaming continues from the new state with the configured tau.
+ * tau_total must exceed b / ||X||. The core's decomposition runs in FP64 on the device
+ * (spatial ranks <= 256); temporary device memory is allocated and freed. Synchronizes.
+ * info (host, may be NULL) receives the new ranks, the core decomposition's discarded energy e'
+ * and the new bound.
+ * Errors: EINVAL (NULL, tau_total <= b / ||X||, a spatial rank above 256), ENOMEM, ESTATE,
+ * ECUDA, and the errors of tucker_init_sthosvd. */
+typedef struct {
+  int64_t ranks[TUCKER_MAX_MODES];  /* r'_1..r'_d; entries >= d are 0 */
+  double discarded;                 /* e' (energy the core's truncation dropped) */
+  double err_bound;                 /* b + sqrt(e'), the new running bound */
+} tucker_recompress_info;
+tucker_status tucker_recompress(tucker_state* s, double tau_total, void* stream,
+                                tucker_recompress_info* info);
+
 /* Copy U_k (mode = 0..d-1, 0-based) as FP64 column-major (rows x r_k) into dst_dev, where rows
  * is n_k for spatial modes and n_d for the streaming mode. Synchronizes. */
 tucker_status tucker_copy_factor(tucker_state* s, int32_t mode, double* dst_dev);

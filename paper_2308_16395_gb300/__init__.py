@@ -30,7 +30,7 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy",
            "tucker_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
            "tucker_get_launch_plan", "tucker_stream_update_host", "tucker_get_step_log",
-           "tucker_replay_next", "tucker_stream_update_batched"]
+           "tucker_replay_next", "tucker_stream_update_batched", "tucker_recompress"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -75,6 +75,11 @@ class Replay(ctypes.Structure):
     _fields_ = [("grow", ctypes.c_int32 * MAX_MODES), ("augment", ctypes.c_int32)]
 
 
+class RecompressInfo(ctypes.Structure):
+    _fields_ = [("ranks", ctypes.c_int64 * MAX_MODES), ("discarded", ctypes.c_double),
+                ("err_bound", ctypes.c_double)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * NPHASES), ("bytes", ctypes.c_double * NPHASES),
                 ("launches", ctypes.c_int64), ("updates", ctypes.c_int64),
@@ -117,6 +122,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_copy_factor.argtypes = [vp, i32, vp]
     lib.tucker_copy_core.argtypes = [vp, vp]
     lib.tucker_copy_sv.argtypes = [vp, vp, vp]
+    lib.tucker_recompress.argtypes = [vp, ctypes.c_double, vp, ctypes.POINTER(RecompressInfo)]
     lib.tucker_last_error.argtypes = [vp]
     lib.tucker_last_error.restype = ctypes.c_char_p
     lib.tucker_destroy.argtypes = [vp]
@@ -155,7 +161,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     for name in ("tucker_profile_enable", "tucker_profile_read", "tucker_init_sthosvd", "tucker_stream_update",
                  "tucker_stream_update_host", "tucker_reconstruct",
                  "tucker_reconstruct_noalloc", "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
-                 "tucker_get_step_log", "tucker_replay_next", "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv"):
+                 "tucker_get_step_log", "tucker_replay_next", "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv",
+                 "tucker_recompress"):
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -285,6 +292,15 @@ def tucker_copy_core(h: int, dst_ptr: int) -> None:
 
 def tucker_copy_sv(h: int, S_ptr: int, V_ptr: int) -> None:
     _check(load_library().tucker_copy_sv(h, ctypes.c_void_p(S_ptr), ctypes.c_void_p(V_ptr)), h)
+
+
+def tucker_recompress(h: int, d: int, tau_total: float, stream: int = 0) -> dict:
+    """Batch ST-HOSVD (Alg. 2) of the current representation within tau_total ||X||."""
+    info = RecompressInfo()
+    _check(load_library().tucker_recompress(h, float(tau_total), ctypes.c_void_p(stream),
+                                            ctypes.byref(info)), h)
+    return {"ranks": tuple(int(info.ranks[k]) for k in range(d)), "discarded": info.discarded,
+            "err_bound": info.err_bound}
 
 
 def tucker_profile_enable(h: int, on: int = 1) -> None:
@@ -529,6 +545,10 @@ class TuckerStream:
     def replay_next(self, grow, augment: int = -1) -> None:
         """Test hook: force the next update's decisions (see tucker_replay_next)."""
         tucker_replay_next(self.h, grow, augment)
+
+    def recompress(self, tau_total: float) -> dict:
+        """Re-compress within tau_total ||X|| (see tucker_recompress)."""
+        return tucker_recompress(self.h, self.d, tau_total, self._sp())
 
     def reconstruct(self, t0: int, t1: int):
         import torch

@@ -1298,6 +1298,127 @@ tucker_status tucker_replay_next(tucker_state* s, const tucker_replay* r) {
   return TUCKER_OK;
 }
 
+tucker_status tucker_recompress(tucker_state* s, double tau_total, void* stream,
+                                tucker_recompress_info* info) {
+  if (!s || !(tau_total > 0.0)) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  const int d = s->d;
+  Ctl c = *s->hctl;
+  long long R = 1;
+  for (int k = 0; k < d - 1; ++k) R *= c.r[k];
+  const int rd = c.r[d - 1];
+  const double b = std::sqrt(std::max(c.err2, 0.0));
+  const double budget = tau_total * std::sqrt(c.data2) - b;
+  if (!(budget > 0.0)) {
+    set_err(s, "tucker_recompress: tau_total leaves no error budget beyond the running bound");
+    return TUCKER_EINVAL;
+  }
+  // the core as the data of a batch ST-HOSVD (an FP64 state of sizes r_1 x ... x r_{d-1} with
+  // r_d "slices"): its factors Q_k, core C', S', V' and discarded energy
+  std::vector<void*> tmpbufs;
+  auto dmalloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    tmpbufs.push_back(p);
+    return p;
+  };
+  auto cleanup = [&]() { for (void* p : tmpbufs) cudaFree(p); };
+  double* C64 = (double*)dmalloc(sizeof(double) * (size_t)R * rd);
+  double* part = (double*)dmalloc(sizeof(double) * 1024);
+  if (!C64 || !part) { cleanup(); return TUCKER_ENOMEM; }
+  rc = tucker_copy_core(s, C64);
+  if (rc != TUCKER_OK) { cleanup(); return rc; }
+  std::vector<double> parts(1024);
+  cudaError_t e = launch_norm2<double>(C64, R * rd, part, 1024, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(parts.data(), part, sizeof(double) * 1024, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { cleanup(); CK(e); }
+  double c2 = 0.0;
+  for (double v : parts) c2 += v;
+  tucker_config tc{};
+  tc.ndim = d;
+  tc.dtype = TUCKER_F64;
+  tc.precision = TUCKER_PREC_FP64;
+  for (int k = 0; k < d - 1; ++k) tc.n[k] = c.r[k];
+  tc.rank_cap[d - 1] = rd;
+  tc.steps_cap = rd + 1;
+  tc.core_cap = R;
+  tc.eps_m = s->cfg.eps_m;
+  // eps' = tau' ||C|| / sqrt(d) = budget / sqrt(d) (||C|| = ||X^||, orthonormal factors)
+  tc.tau = budget / std::sqrt(std::max(c2, 1e-300));
+  tucker_state* t = nullptr;
+  rc = tucker_init_sthosvd(&tc, C64, rd, stream, &t);
+  if (rc != TUCKER_OK) { cleanup(); set_err(s, "tucker_recompress: ST-HOSVD of the core failed%s%lld", "", rc); return rc; }
+  rc = sync_ctl(t);
+  if (rc != TUCKER_OK) { tucker_destroy(t); cleanup(); return rc; }
+  const Ctl ct = *t->hctl;
+  long long Rn = 1;
+  for (int k = 0; k < d - 1; ++k) Rn *= ct.r[k];
+  const int rdn = ct.r[d - 1];
+  double* Q = (double*)dmalloc(sizeof(double) * (size_t)TK_N_MAX * TK_N_MAX);
+  double* Ck = (double*)dmalloc(sizeof(double) * (size_t)Rn * rdn);
+  double* Vk = (double*)dmalloc(sizeof(double) * (size_t)Rn * rdn);
+  const size_t un_elems = (size_t)std::max(TK_N_MAX, s->steps_cap) * TK_N_MAX;
+  double* Un = (double*)dmalloc(sizeof(double) * un_elems);
+  if (!Q || !Ck || !Vk || !Un) { tucker_destroy(t); cleanup(); return TUCKER_ENOMEM; }
+  rc = tucker_copy_core(t, Ck);
+  if (rc == TUCKER_OK) rc = tucker_copy_sv(t, s->S, Vk);
+  // spatial factors U_k <- U_k Q_k (FP64 master and the work copy), streaming U_d <- U_d Q_d
+  for (int k = 0; k < d && rc == TUCKER_OK; ++k) {
+    rc = tucker_copy_factor(t, k, Q);   // r_k x r'_k, column-major
+    if (rc != TUCKER_OK) break;
+    if (k < d - 1) {
+      // n_k x r'_k, column-major with leading dimension n_k (FP64 master, FP32 work copy)
+      const int nk = s->n[k];
+      float* uw = (s->tw == 4) ? static_cast<float*>(s->Uw[k]) : nullptr;
+      e = launch_small_gemm(s->U[k], 1, nk, nk, c.r[k], Q, c.r[k], ct.r[k], Un, 1, nk, uw, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->U[k], Un, sizeof(double) * nk * ct.r[k], cudaMemcpyDeviceToDevice, st);
+    } else {
+      // n_d x r'_d rows of stride ldc; the columns past r'_d stay zero
+      e = cudaMemsetAsync(Un, 0, sizeof(double) * (size_t)c.nd * s->ldc, st);
+      if (e == cudaSuccess)
+        e = launch_small_gemm(s->Ud[c.ubuf], s->ldc, 1, c.nd, rd, Q, rd, rdn, Un, s->ldc, 1, nullptr, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->Ud[c.ubuf], Un, sizeof(double) * (size_t)c.nd * s->ldc,
+                            cudaMemcpyDeviceToDevice, st);
+    }
+    if (e != cudaSuccess) { rc = TUCKER_ECUDA; set_err(s, "tucker_recompress: %s", cudaGetErrorString(e), k); }
+  }
+  if (rc == TUCKER_OK) {
+    const int ls = tk_cv_stride(rdn, s->ldc, s->tw);
+    e = (s->tw == 4) ? launch_set_cv<float>(Ck, Vk, Rn, rdn, s->Cb[c.cbuf], s->Vb[c.cbuf], ls, st)
+                     : launch_set_cv<double>(Ck, Vk, Rn, rdn, s->Cb[c.cbuf], s->Vb[c.cbuf], ls, st);
+    if (e != cudaSuccess) { rc = TUCKER_ECUDA; set_err(s, "tucker_recompress: %s", cudaGetErrorString(e), 0); }
+  }
+  const double disc = std::max(ct.err2, 0.0);
+  tucker_destroy(t);
+  if (rc == TUCKER_OK) {
+    Ctl& h = *s->hctl;
+    for (int k = 0; k < d; ++k) { h.r[k] = ct.r[k]; h.rold[k] = ct.r[k]; }
+    h.err2 = (b + std::sqrt(disc)) * (b + std::sqrt(disc));
+    h.xbuf = -1;
+    e = cudaMemcpyAsync(s->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st);
+    // TF32 hi/lo splits of the new spatial factors for the tensor-core passes (they read the
+    // ranks from the control block just written)
+    for (int k = 0; k < d - 1 && e == cudaSuccess; ++k)
+      if ((s->tcmask >> k) & 1) e = launch_split_u(s->ctl, k, 0, s->U[k], s->n[k], s->usplit[k], st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { rc = TUCKER_ECUDA; set_err(s, "tucker_recompress: %s", cudaGetErrorString(e), 0); }
+  }
+  cleanup();
+  if (rc == TUCKER_OK && info) {
+    info->discarded = disc;
+    info->err_bound = b + std::sqrt(disc);
+    for (int k = 0; k < TUCKER_MAX_MODES; ++k) info->ranks[k] = k < d ? ct.r[k] : 0;
+  }
+  return rc;
+}
+
 tucker_status tucker_copy_factor(tucker_state* s, int32_t mode, double* dst) {
   if (!s || !dst || mode < 0 || mode >= s->d) return TUCKER_EINVAL;
   tucker_status rc = sync_ctl(s);

@@ -180,3 +180,64 @@ template cudaError_t launch_state_to_colmajor<double>(const void*, long long, in
                                                       cudaStream_t);
 
 }  // namespace tk
+
+namespace tk {
+
+// out(i, c) = sum_j A(i, j) B(j, c) in FP64 for the small products of the re-compression
+// (U_k Q_k and U_d Q_d): A(i, j) at A[i * as_i + j * as_j], B column-major (ldb), out(i, c) at
+// out[i * os_i + c * os_c]; outw (may be NULL) receives the same values in FP32. One thread per
+// entry (rows x cols is at most n_k x r_k).
+__global__ void k_small_gemm(const double* __restrict__ A, long long as_i, long long as_j,
+                             int rows, int inner, const double* __restrict__ B, int ldb, int cols,
+                             double* __restrict__ out, long long os_i, long long os_c,
+                             float* __restrict__ outw) {
+  const long long total = (long long)rows * cols;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(L % rows), c = (int)(L / rows);
+    double s = 0.0;
+    for (int j = 0; j < inner; ++j) s = fma(A[i * as_i + j * as_j], B[(long long)c * ldb + j], s);
+    out[i * os_i + c * os_c] = s;
+    if (outw) outw[i * os_i + c * os_c] = (float)s;
+  }
+}
+
+cudaError_t launch_small_gemm(const double* A, long long as_i, long long as_j, int rows, int inner,
+                              const double* B, int ldb, int cols, double* out, long long os_i,
+                              long long os_c, float* outw, cudaStream_t st) {
+  const long long total = (long long)rows * cols;
+  int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 4);
+  if (grid < 1) grid = 1;
+  k_small_gemm<<<grid, 256, 0, st>>>(A, as_i, as_j, rows, inner, B, ldb, cols, out, os_i, os_c, outw);
+  return cudaGetLastError();
+}
+
+// C and V state rows (stride ld, type TW) from FP64 column-major R x rd arrays.
+template <typename TW>
+__global__ void k_set_cv(const double* C64, const double* V64, long long R, int rd, TW* C, TW* V,
+                         int ld) {
+  const long long total = R * rd;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
+       L += (long long)gridDim.x * blockDim.x) {
+    const long long j = L % R;
+    const int i = (int)(L / R);
+    C[j * ld + i] = (TW)C64[L];
+    V[j * ld + i] = (TW)V64[L];
+  }
+}
+
+template <typename TW>
+cudaError_t launch_set_cv(const double* C64, const double* V64, long long R, int rd, void* C,
+                          void* V, int ld, cudaStream_t st) {
+  const long long total = R * rd;
+  int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+  if (grid < 1) grid = 1;
+  k_set_cv<TW><<<grid, 256, 0, st>>>(C64, V64, R, rd, (TW*)C, (TW*)V, ld);
+  return cudaGetLastError();
+}
+template cudaError_t launch_set_cv<float>(const double*, const double*, long long, int, void*,
+                                          void*, int, cudaStream_t);
+template cudaError_t launch_set_cv<double>(const double*, const double*, long long, int, void*,
+                                           void*, int, cudaStream_t);
+
+}  // namespace tk

@@ -127,6 +127,12 @@ cudaError_t launch_init_finish(Ctl* ctl, const void* Ccol, long long R, int rd, 
 template <typename TW>
 cudaError_t launch_init_cv64(const double* C64, long long R, int rd, const double* lam, void* C,
                              void* V, int ldc, cudaStream_t st);
+cudaError_t launch_small_gemm(const double* A, long long as_i, long long as_j, int rows, int inner,
+                              const double* B, int ldb, int cols, double* out, long long os_i,
+                              long long os_c, float* outw, cudaStream_t st);
+template <typename TW>
+cudaError_t launch_set_cv(const double* C64, const double* V64, long long R, int rd, void* C,
+                          void* V, int ld, cudaStream_t st);
 template <typename TW>
 cudaError_t launch_core_times_ud(const void* C, long long R, int rd, int ldc, const double* Ud,
                                  long long t0, long long T, void* out, cudaStream_t st);

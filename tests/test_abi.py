@@ -104,7 +104,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     pairs = [("tucker_config", pkg.TuckerConfig), ("tucker_step_info", pkg.StepInfo),
              ("tucker_profile", pkg.Profile), ("tucker_launch_plan", pkg.LaunchPlan),
              ("tucker_ttm_desc", pkg.TtmDesc), ("tucker_step_record", pkg.StepRecord),
-             ("tucker_replay", pkg.Replay)]
+             ("tucker_replay", pkg.Replay), ("tucker_recompress_info", pkg.RecompressInfo)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tucker_stream.h"',
              '#include "tucker_ttm.h"', "int main(void) {"]
     for cname, py in pairs:
