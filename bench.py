@@ -40,9 +40,9 @@ STREAMS = {
                       name="advected-blob stream 192x192x96x12 fp32 slices (40 blobs, 170 MB per slice)"),
 }
 DELTA_DEC = 3e-2    # relative distance of a near-cutoff decision from eps^2 (mixed form)
-PHASES = ["mode-1 projection + residual (k_tc_proj)", "k_ttm_proj (modes 2..d-1)", "growth (gram/eig/append)",
+PHASES = ["mode-1 projection + residual (k_tc_pass16)", "k_ttm_proj (modes 2..d-1)", "growth (gram/eig/append)",
           "isvd (k_isvd_p/k_isvd_e/secular)", "factor (k_ud_update/k_core_m)", "k_cv_update (C and V)"]
-KERNEL_OF_PHASE = ["k_tc_proj<1, 0>", "k_tc_proj", "k_resid_gram", "k_isvd_e", "k_core_m", "k_cv_update"]
+KERNEL_OF_PHASE = ["k_tc_pass16<1, 0>", "k_tc_pass16", "k_resid_gram", "k_isvd_e", "k_core_m", "k_cv_update"]
 
 
 def _peaks():

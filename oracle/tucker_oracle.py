@@ -15,7 +15,7 @@ Conventions
 * Everything is float64. Library primitives used as single steps: ``@`` (matmul),
   ``np.linalg.eigh`` (the eig of Alg. 1), ``np.linalg.qr`` (the QR of Alg. 3).
 
-Readings of the paper where it is silent, garbled or ambiguous (each is also listed in the design doc):
+Readings of the paper where it is silent, garbled or ambiguous:
   R1 eigenvalues sorted descending, ties broken by the smaller index (Alg. 1);
   R2 ST-HOSVD keeps at least rank 1 per mode; Alg. 4's r'_k is clamped to n_k - r_k;
   R3 Alg. 1 returns singular values sqrt(lambda) (negative round-off eigenvalues clamped at 0

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtucker_stream.so")
 
-SOURCES = ["api.cu", "k_spatial.cu", "k_eig.cu", "k_eig_sub.cu", "k_stream.cu", "k_misc.cu", "k_tc.cu",
+SOURCES = ["api.cu", "k_spatial.cu", "k_eig.cu", "k_eig_sub.cu", "k_stream.cu", "k_misc.cu", "k_tc.cu", "k_tc16.cu",
            "k_ttm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

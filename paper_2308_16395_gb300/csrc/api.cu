@@ -81,6 +81,9 @@ struct tucker_state {
   float* usplit[TK_MAXD][4]{};   // U_k TF32 hi/lo copies for the tensor-core spatial passes
   TcProjMaps pmaps[TK_MAXD]{};
   int tcmask = 0;                 // bit k: tensor-core projection of spatial mode k available
+  void* u16[TK_MAXD][4]{};        // FP16 hi/lo parts of 2^14 U_k (U1 hi, U1 lo, U2 hi, U2 lo)
+  int ld16[TK_MAXD]{};            // row stride of U1 (n_k rounded up to 64)
+  int h16mask = 0;                // bit k: the FP16 pass (input tile in TMEM) runs mode k
   int etmask = 0;                 // bit k: tensor-core residual Gram of spatial mode k available
   float* et = nullptr;            // E^T of the growing mode (n_k x Fs_k) for the Gram
   long long et_stride[TK_MAXD]{};
@@ -390,6 +393,17 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
       for (int i = 0; i < 3; ++i) ok &= make_map_2d_f32(&m.d[i], s->dbuf[i], rows, nk, nk, 32, 128);
       if (!ok) continue;
       s->tcmask |= 1 << k;
+      if (nk <= TK_H16_NMAX) {
+        const int ld1 = (nk + 63) / 64 * 64;
+        s->ld16[k] = ld1;
+        for (int i = 0; i < 2; ++i) CK(dalloc(s, &s->u16[k][i], 2 * (size_t)TP_RMAX * ld1));
+        for (int i = 2; i < 4; ++i) CK(dalloc(s, &s->u16[k][i], 2 * (size_t)nk * TP_RMAX));
+        bool okh = make_map_2d_f16(&m.h1hi, s->u16[k][0], TP_RMAX, nk, ld1, 64, 16);
+        okh &= make_map_2d_f16(&m.h1lo, s->u16[k][1], TP_RMAX, nk, ld1, 64, 16);
+        okh &= make_map_2d_f16(&m.h2hi, s->u16[k][2], nk, TP_RMAX, TP_RMAX, 64, 64);
+        okh &= make_map_2d_f16(&m.h2lo, s->u16[k][3], nk, TP_RMAX, TP_RMAX, 64, 64);
+        if (okh) s->h16mask |= 1 << k;
+      }
       const long long fs = (s->dbuf_elems / nk + 32 + 3) / 4 * 4;
       s->et_stride[k] = fs;
       // the tensor-core residual Gram takes n_k <= 384 (three 128-row blocks)
@@ -433,6 +447,31 @@ int gram_chunks(int n) { return std::max(1, kGramBlocks / gram_pairs(n)); }
 // ---------------------------------------------------------------------------------------------
 // batch ST-HOSVD (Alg. 2) on the device
 // ---------------------------------------------------------------------------------------------
+// Tensor-core copies of U_k after it changed (pred: only if mode k grew in this update).
+cudaError_t split_u(tucker_state* s, int k, int pred, cudaStream_t st) {
+  if ((s->h16mask >> k) & 1)
+    return launch_split_u16(s->ctl, k, pred, s->U[k], s->n[k], s->ld16[k], s->u16[k], st);
+  return launch_split_u(s->ctl, k, pred, s->U[k], s->n[k], s->usplit[k], st);
+}
+
+// Mode k's tensor-core pass (mode 0 projection, 1 projection + residual norms, 2 residual E^T):
+// the FP16 form where it applies, else the 3xTF32 form. rerun = 1: the second launch of the FP16
+// form's pass A, which runs the pass again only if its input left the FP16 scale window (nothing
+// to launch for the 3xTF32 form).
+cudaError_t tc_pass(tucker_state* s, int k, int mode, int pred, int rerun, const void* Y,
+                    int out_off, double* part_e2, double* part_y2, float* Et, long long et_stride,
+                    cudaStream_t st) {
+  const long long F0 = s->N / s->n[0];
+  if ((s->h16mask >> k) & 1)
+    return launch_tc_pass16(s->ctl, k, mode, pred, rerun, (const float*)Y, F0, s->n[0],
+                            s->pmaps[k], s->d_dbufs, out_off, part_e2, part_y2, s->grid_p, Et,
+                            et_stride, s->grid_tc, st);
+  if (rerun) return cudaSuccess;
+  return launch_tc_proj(s->ctl, k, mode, pred, (const float*)Y, F0, s->n[0], s->pmaps[k],
+                        s->d_dbufs, out_off, part_e2, part_y2, s->grid_p, Et, et_stride,
+                        s->grid_tc, st);
+}
+
 template <typename TX, typename TW, typename TE>
 tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream_t st) {
   const int d = s->d;
@@ -468,6 +507,13 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
   if (x2 == 0.0) { set_err(s, "initial data is all zero (Assumption 1(c) needs S > 0)"); return TUCKER_EINVAL; }
   h.eps = s->cfg.tau * std::sqrt(x2) / std::sqrt((double)d);
   h.data2 = x2;
+  {
+    // first FP16 scale of every mode's input: from the norm of an average initial slice (an
+    // upper bound of its entries; the first update re-scales a mode whose input lies far below)
+    int e2 = 0;
+    std::frexp(std::sqrt(x2 / (double)n_init), &e2);
+    for (int k = 0; k < TK_MAXD; ++k) h.x16e[k] = x16_sigma_for(e2 - 1);
+  }
   h.y2 = x2;
   CK(cudaMemcpyAsync(s->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
   // temporary partial-core buffers (the initial slices are larger than one slice)
@@ -500,8 +546,7 @@ tucker_status do_init(tucker_state* s, const void* X, int64_t n_init, cudaStream
     double* Uk = (k == d - 1) ? Utmp : s->U[k];
     void* Uwk = (k == d - 1) ? (s->tw == 8 ? (void*)Utmp : Uwtmp) : s->Uw[k];
     if (e == cudaSuccess) e = launch_append<TW>(s->ctl, k, 1, s->eW, Uk, (s->tw == 8) ? nullptr : Uwk, nv, nv, st);
-    if (e == cudaSuccess && k < d - 1 && ((s->tcmask >> k) & 1))
-      e = launch_split_u(s->ctl, k, 0, s->U[k], s->n[k], s->usplit[k], st);
+    if (e == cudaSuccess && k < d - 1 && ((s->tcmask >> k) & 1)) e = split_u(s, k, 0, st);
     if (e != cudaSuccess) { set_err(s, "CUDA error (%s) in the Gram/eig/append step of mode %lld", cudaGetErrorString(e), k + 1); rc = TUCKER_ECUDA; break; }
     s->last_stream = st;
     rc = sync_ctl(s);
@@ -632,11 +677,12 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       // pass A: P_k = D*_{k-1} x_k U_k^T, ||E_k||^2 (and ||Y||^2 for k = 0); Alg. 4's branch
       PhaseMark pm(s, st, k == 0 ? TK_PH_PROJ1 : TK_PH_PROJN);
       if (tck) {
-        PhaseMark pk(s, st, k == 0 ? TK_PH_SLICE : -1);
-        CK(launch_tc_proj(s->ctl, k, 1, 0, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
-                          s->d_dbufs, 1, s->part_e2, k == 0 ? s->part_y2 : nullptr, s->grid_p,
-                          nullptr, 0, s->grid_tc, st));
-        launches += 1;
+        {
+          PhaseMark pk(s, st, k == 0 ? TK_PH_SLICE : -1);
+          CK(tc_pass(s, k, 1, 0, 0, Y, 1, s->part_e2, k == 0 ? s->part_y2 : nullptr, nullptr, 0, st));
+        }
+        CK(tc_pass(s, k, 1, 0, 1, Y, 1, s->part_e2, k == 0 ? s->part_y2 : nullptr, nullptr, 0, st));
+        launches += ((s->h16mask >> k) & 1) ? 2 : 1;
       }
       if (k == 0) {
         PhaseMark pk(s, st, tck ? -1 : TK_PH_SLICE);
@@ -663,9 +709,7 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       PhaseMark pm(s, st, TK_PH_GROW);
       if ((s->etmask >> k) & 1) {
         // residual E^T of mode k, then its Gram on the tensor cores (only if mode k grew)
-        CK(launch_tc_proj(s->ctl, k, 2, 1, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
-                          s->d_dbufs, 1, nullptr, nullptr, s->grid_p, s->et, s->et_stride[k],
-                          s->grid_tc, st));
+        CK(tc_pass(s, k, 2, 1, 0, Y, 1, nullptr, nullptr, s->et, s->et_stride[k], st));
         CK(launch_tc_gram(s->ctl, k, s->pmaps[k], n, s->gpart, s->G, s->grid_tc, st));
         launches += 3;
       }
@@ -688,9 +732,8 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
       }
       CK(launch_append<TW>(s->ctl, k, 0, s->eW, s->U[k], (s->tw == 8) ? nullptr : s->Uw[k], n, n, st));
       if (tck) {
-        CK(launch_split_u(s->ctl, k, 1, s->U[k], n, s->usplit[k], st));
-        CK(launch_tc_proj(s->ctl, k, 0, 1, (const float*)Y, s->N / s->n[0], s->n[0], s->pmaps[k],
-                          s->d_dbufs, 2, nullptr, nullptr, s->grid_p, nullptr, 0, s->grid_tc, st));
+        CK(split_u(s, k, 1, st));
+        CK(tc_pass(s, k, 0, 1, 0, Y, 2, nullptr, nullptr, nullptr, 0, st));
         launches += 2;
       }
       if (k == 0)
@@ -1406,7 +1449,7 @@ tucker_status tucker_recompress(tucker_state* s, double tau_total, void* stream,
     // TF32 hi/lo splits of the new spatial factors for the tensor-core passes (they read the
     // ranks from the control block just written)
     for (int k = 0; k < d - 1 && e == cudaSuccess; ++k)
-      if ((s->tcmask >> k) & 1) e = launch_split_u(s->ctl, k, 0, s->U[k], s->n[k], s->usplit[k], st);
+      if ((s->tcmask >> k) & 1) e = split_u(s, k, 0, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { rc = TUCKER_ECUDA; set_err(s, "tucker_recompress: %s", cudaGetErrorString(e), 0); }
   }

@@ -87,7 +87,26 @@ struct Ctl {
   // (N / n_1) x n_1 FP32 matrix (only with the tensor-core mode-1 pass) and its address ----
   alignas(128) unsigned char ymap[128];
   const void* yptr;
+  // ---- FP16-split tensor-core passes: x16e[k] is the exponent sigma of the power of two that
+  // scales mode k's input before its FP16 split; xmax[k] the largest |x| of that input seen by
+  // the update's pass A (float bits, atomicMax; reset by k_begin_update) ----
+  int x16e[TK_MAXD];
+  unsigned xmax[TK_MAXD];
 };
+
+// FP16 scale window: a pass's input scaled by 2^sigma must have its largest |x| in
+// [2^1, 2^15) (FP16's largest finite value is 65504). sigma for a largest |x| of exponent e puts
+// it at 2^8.
+__host__ __device__ __forceinline__ int x16_sigma_for(int e) {
+  const int s = 8 - e;
+  return s < -100 ? -100 : (s > 100 ? 100 : s);
+}
+__host__ __device__ __forceinline__ bool x16_in_window(int e, int sigma) {
+  const int s = e + sigma;
+  return s >= 1 && s <= 14;
+}
+// Exponent floor(log2 x) of a positive float given by its bits (subnormals count as -127).
+__host__ __device__ __forceinline__ int x16_exp_of_bits(unsigned b) { return (int)((b >> 23) & 255u) - 127; }
 
 // One update's decisions as the host reads them back (same layout as tucker_step_record).
 struct StepRec {
@@ -379,6 +398,7 @@ __device__ __forceinline__ bool spatial_grew(const Ctl* ctl) {
 }
 
 // ---- tensor-core path of the spatial-mode projections (mixed form) ----
+#define TK_H16_NMAX 384                 // largest n_k of the FP16 tensor-core pass (input tile in TMEM)
 #define TP_RMAX 64                      // largest padded r_k handled on the tensor cores
 
 // Spatial mode k on the tensor cores: mixed form, streaming update (rotating layout), the host

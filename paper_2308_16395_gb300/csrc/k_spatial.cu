@@ -228,6 +228,10 @@ __global__ void k_decide(Ctl* ctl, int k, const double* part_e2, const double* p
       ctl->y2 = sy;
       ctl->eps = ctl->tau * sqrt(sy) / sqrt((double)ctl->d);
     }
+    // FP16 scale of mode k's input for this update's later passes and the next update's pass A,
+    // from the largest |x| of this input
+    const unsigned mb = ctl->xmax[k];
+    if (mb != 0u && mb < 0x7f800000u) ctl->x16e[k] = x16_sigma_for(x16_exp_of_bits(mb));
   }
 }
 

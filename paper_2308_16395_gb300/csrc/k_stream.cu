@@ -1478,6 +1478,7 @@ __global__ void k_begin_update(Ctl* ctl) {
     ctl->eig_m[k] = 0;
     ctl->eig_it[k] = 0;
     ctl->eig_fb[k] = 0;
+    ctl->xmax[k] = 0u;
   }
   ctl->xbuf = -1;
   ctl->aug = 0;

@@ -1,0 +1,535 @@
+// FP16-split tensor-core pass of a spatial mode (Alg. 4: projection P_k, residual E_k and its
+// norm), with the input tile held in tensor memory so that the residual needs no second read of
+// the input.
+//
+// The mode-k input X (row-major F x n_k, the mode-k fibers as rows) streams through shared memory
+// by TMA in chunks of 128 fibers x 64 columns (two 32-column boxes, 128-byte swizzle). Eight
+// splitter warps convert each chunk in place into the FP16 high and low parts of 2^sigma X
+// (2^sigma x = hi + lo up to 2^-23 |2^sigma x| + 2^-25) and, in the residual passes, store the
+// FP32 values 2^(sigma+9) X into tensor memory (lane = fiber, one column per element).
+//   MMA1  P_s = (2^sigma X)(2^14 U_k) on kind::f16, three products per K step of 16 (hi*hi into
+//         one accumulator, hi*lo + lo*hi into a second; FP16 products are exact in FP32),
+//         U_k's FP16 parts streamed with the chunks.
+//   epi-1 P = 2^-(sigma+14) P_s -> global, column-major (F x r_k, the next mode's input);
+//         -2^-19 P_s split into FP16 hi/lo in shared memory (MMA2's A operand).
+//   MMA2  accumulated onto the stored tile: 2^(sigma+9) X + (-2^-19 P_s)(2^14 U_k)^T =
+//         2^(sigma+9) (X - P U_k^T) = 2^(sigma+9) E, three products per K step, U_k^T's FP16 parts
+//         resident in shared memory, in 128-column blocks.
+//   epi-2 ||E||^2 per CTA (FP32 over 32 elements, then FP64), and E^T for the residual Gram when
+//         the mode grew.
+// Block b of the tensor-memory tile is released to the next tile's chunks as soon as epi-2 has
+// read it, so the next tile streams in while MMA2 and epi-2 finish. The ring of input stages is
+// fed from L2, into which the producer prefetches chunks ahead of their loads.
+//
+// Scale: sigma_k (Ctl::x16e) puts the input's largest |x| near 2^8, far from the FP16 limits
+// (|2^sigma x| <= 2^15 keeps hi finite; the low end loses only an absolute 2^-25). Pass A records
+// max |x| (Ctl::xmax); a second launch of pass A right after it returns at once unless the
+// scaled maximum left [2^1, 2^15), and then runs the pass again with sigma from that maximum.
+// With |2^sigma x| < 2^15, |U| <= 1 and |p| <= sqrt(n_k) max|x| (orthonormal U_k), every FP16
+// operand stays below 2^15 for n_k <= 384.
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_common.cuh"
+
+namespace tk {
+
+using namespace tc;
+
+constexpr int H_M = 128;                         // fibers per tile
+constexpr int H_KC = 64;                         // input columns per chunk
+constexpr int H_XB = H_M * H_KC * 4;             // 32 KB: raw FP32 chunk, then FP16 hi | lo
+constexpr int H_UB = TP_RMAX * 128;              // 8 KB: U chunk (hi or lo), <= 64 rows x 128 B
+constexpr int H_STAGE = H_XB + 2 * H_UB;         // 48 KB
+constexpr int H_U2 = TK_H16_NMAX * 128;          // 48 KB: U_k rows (hi or lo), n_k x 64 FP16
+constexpr int H_P16 = H_M * 128;                 // 16 KB: MMA2's A operand (hi or lo)
+constexpr int H_PF = 6;                          // chunks prefetched into L2 ahead of the loads
+constexpr int H_SPLIT_W = 8;                     // splitter warps 4..11
+constexpr int H_EPI_W0 = 12;                     // epilogue warps 12..15
+constexpr int H_NT = 32 * 16;
+constexpr int H_TP = TK_H16_NMAX;                // TMEM column of the P accumulators
+constexpr uint32_t H_TMEM_COLS = 512;
+static_assert(H_TP + 2 * TP_RMAX <= (int)H_TMEM_COLS, "input tile and P accumulators fit TMEM");
+
+template <bool RESID> struct HCfg {
+  static constexpr int S = RESID ? 2 : 4;
+  static constexpr size_t EXTRA = RESID ? (size_t)2 * H_U2 + 2 * H_P16 : 0;
+  static constexpr size_t SMEM = (size_t)S * H_STAGE + EXTRA + 1024 + 1024;
+};
+static_assert(HCfg<true>::SMEM <= 232448, "shared memory of the residual pass");
+static_assert(HCfg<false>::SMEM <= 232448, "shared memory of the projection pass");
+
+// Bounded wait (1 s of wall time); sets *abort on timeout, returns false once aborted.
+__device__ __forceinline__ unsigned long long h_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool h_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = h_timer();
+  for (long long i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63) {
+      if (*abort) return false;
+      if (h_timer() - t0 > 1000000000ull) { *abort = 1; return false; }
+    }
+  }
+}
+// Wait (0.2 s at most, whatever *abort says) for copies or MMAs this CTA has in flight, before
+// its shared and tensor memory go away.
+__device__ __forceinline__ void h_drain(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return;
+  const unsigned long long t0 = h_timer();
+  while (!mbar_try_wait(bar, parity))
+    if (h_timer() - t0 > 200000000ull) return;
+}
+
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// FP16 hi/lo of a pair: a = hi + lo up to the rounding of lo.
+__device__ __forceinline__ void split_h2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a0, a1);
+  const float2 hf = __half22float2(h);
+  hi = h2_bits(h);
+  lo = h2_bits(__floats2half2_rn(a0 - hf.x, a1 - hf.y));
+}
+
+struct TcPass16Args {
+  const CUtensorMap* mYg;   // slice descriptor in the control block (graph form), else NULL
+  float* const* dbufs;
+  int out_off;
+  double* part_e2;
+  double* part_y2;
+  int nparts;
+  const float* Y;
+  float* Et;
+  long long et_stride;
+  int k;
+  int rerun;                // the second launch of pass A (runs only outside the scale window)
+  int track;                // record max |x| (pass A)
+};
+
+template <bool RESID, bool WRITE_ET>
+__global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, int pred,
+                                                     const __grid_constant__ CUtensorMap mY,
+                                                     const __grid_constant__ CUtensorMap mD0,
+                                                     const __grid_constant__ CUtensorMap mD1,
+                                                     const __grid_constant__ CUtensorMap mD2,
+                                                     const __grid_constant__ CUtensorMap mU1hi,
+                                                     const __grid_constant__ CUtensorMap mU1lo,
+                                                     const __grid_constant__ CUtensorMap mU2hi,
+                                                     const __grid_constant__ CUtensorMap mU2lo,
+                                                     TcPass16Args a) {
+  if (ctl->status) return;
+  const int k = a.k;
+  if (pred && !ctl->grew[k]) return;
+  const int r = ctl->r[k];
+  if (!tc_proj_ok(ctl, k, r)) return;
+  const int n1 = ctl->n[k];
+  if (n1 > TK_H16_NMAX) return;
+  int sigma = ctl->x16e[k];
+  if (a.rerun) {
+    const unsigned mb = ctl->xmax[k];
+    if (mb == 0u || mb >= 0x7f800000u) return;
+    const int em = x16_exp_of_bits(mb);
+    if (x16_in_window(em, sigma)) return;
+    sigma = x16_sigma_for(em);
+  }
+  const long long F = view_B(ctl, k);
+  const int Rp = (r + 15) / 16 * 16;
+  const int n1p = (n1 + 15) / 16 * 16;
+  const int Kc = (n1 + H_KC - 1) / H_KC;
+  const int nblk = (n1p + 127) / 128;
+  const long long ntiles = (F + H_M - 1) / H_M;
+  const int xb = ctl->xbuf;
+  const CUtensorMap* mX = xb < 0 ? (a.mYg ? a.mYg : &mY) : (xb == 0 ? &mD0 : (xb == 1 ? &mD1 : &mD2));
+  float* P = a.dbufs[(xb + a.out_off + 3) % 3];
+
+  extern __shared__ __align__(1024) unsigned char hsm_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(hsm_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int S = HCfg<RESID>::S;
+  unsigned char* U2hi = base + (size_t)S * H_STAGE;
+  unsigned char* U2lo = U2hi + H_U2;
+  unsigned char* P16hi = U2lo + H_U2;
+  unsigned char* P16lo = P16hi + H_P16;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)S * H_STAGE + HCfg<RESID>::EXTRA);
+  uint64_t* full = bars;                 // [S] chunk landed
+  uint64_t* conv = bars + S;             // [S] chunk split (and stored to TMEM)
+  uint64_t* empty = bars + 2 * S;        // [S] chunk's MMAs done
+  uint64_t* d1full = bars + 3 * S;       // P accumulators complete
+  uint64_t* pready = d1full + 1;         // P read out (and MMA2's A operand stored)
+  uint64_t* efull = pready + 1;          // [3] E block b complete
+  uint64_t* xfree = efull + 3;           // [3] E block b read out
+  uint64_t* bload = xfree + 3;           // resident U rows landed
+  uint64_t* done = bload + 1;            // every MMA complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* red = reinterpret_cast<double*>(tmem_slot + 4);        // [16] per-warp sums
+  unsigned* redm = reinterpret_cast<unsigned*>(red + 16);        // [16] per-warp max |x|
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 32 * H_SPLIT_W);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(d1full, 1);
+    mbar_init(pready, 128);
+    for (int b = 0; b < 3; ++b) {
+      mbar_init(&efull[b], 1);
+      mbar_init(&xfree[b], 128);
+    }
+    mbar_init(bload, 1);
+    mbar_init(done, 1);
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (threadIdx.x < 16) {
+    red[threadIdx.x] = 0.0;
+    redm[threadIdx.x] = 0u;
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, H_TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const long long myt = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      if (xb < 0 && a.mYg) tensormap_acquire(a.mYg);
+      tma_prefetch(mX);
+      tma_prefetch(&mU1hi);
+      tma_prefetch(&mU1lo);
+      const int u2rows = (n1p + 63) / 64 * 64;
+      if (RESID) {
+        tma_prefetch(&mU2hi);
+        tma_prefetch(&mU2lo);
+        mbar_arrive_expect_tx(bload, (uint32_t)u2rows * 128u * 2u);
+        for (int r0 = 0; r0 < u2rows; r0 += 64) {
+          tma_load_2d(&mU2hi, bload, U2hi + (size_t)r0 * 128, 0, r0);
+          tma_load_2d(&mU2lo, bload, U2lo + (size_t)r0 * 128, 0, r0);
+        }
+      }
+      const long long nq = myt * Kc;
+      auto prefetch_chunk = [&](long long qq) {
+        if (qq >= nq) return;
+        const long long tt = blockIdx.x + (qq / Kc) * (long long)gridDim.x;
+        const int x0 = (int)(qq % Kc) * H_KC;
+        tma_prefetch_l2_2d(mX, x0, (int)(tt * H_M));
+        if (x0 + 32 < n1) tma_prefetch_l2_2d(mX, x0 + 32, (int)(tt * H_M));
+      };
+      for (long long qq = 0; qq < H_PF; ++qq) prefetch_chunk(qq);
+      long long q = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+        for (int c = 0; c < Kc; ++c, ++q) {
+          const int s = (int)(q % S);
+          prefetch_chunk(q + H_PF);
+          if (!h_wait(&empty[s], (uint32_t)(((q / S) & 1) ^ 1), abort)) { ok = false; break; }
+          unsigned char* st = base + (size_t)s * H_STAGE;
+          mbar_arrive_expect_tx(&full[s], (uint32_t)(H_XB + Rp * 128 * 2));
+          // the second box may lie wholly past n_k: TMA writes zeros there
+          tma_load_2d(mX, &full[s], st, c * H_KC, (int)(t * H_M));
+          tma_load_2d(mX, &full[s], st + H_XB / 2, c * H_KC + 32, (int)(t * H_M));
+          for (int n0 = 0; n0 < Rp; n0 += 16) {
+            tma_load_2d(&mU1hi, &full[s], st + H_XB + n0 * 128, c * H_KC, n0);
+            tma_load_2d(&mU1lo, &full[s], st + H_XB + H_UB + n0 * 128, c * H_KC, n0);
+          }
+        }
+      }
+      // every load issued has landed before the CTA's shared memory goes away
+      for (long long j = (q > S ? q - S : 0); j < q; ++j) h_drain(&full[j % S], (uint32_t)((j / S) & 1));
+      if (RESID) h_drain(bload, 0);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t id1 = idesc_f16(H_M, Rp);
+      const uint32_t tP = tmem + H_TP, tC = tmem + H_TP + TP_RMAX;
+      bool ok = RESID ? h_wait(bload, 0, abort) : true;
+      long long q = 0;
+      int it = 0;
+      for (long long t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++it) {
+        // the P accumulators are free once epilogue 1 of the previous tile has read them
+        if (it > 0 && !h_wait(pready, (uint32_t)((it - 1) & 1), abort)) { ok = false; break; }
+        tc_fence_after();
+        for (int c = 0; c < Kc; ++c, ++q) {
+          const int s = (int)(q % S);
+          if (!h_wait(&conv[s], (uint32_t)((q / S) & 1), abort)) { ok = false; break; }
+          tc_fence_after();
+          unsigned char* st = base + (size_t)s * H_STAGE;
+          const uint64_t ahi = desc_sw128(st), alo = desc_sw128(st + H_XB / 2);
+          const uint64_t bhi = desc_sw128(st + H_XB), blo = desc_sw128(st + H_XB + H_UB);
+#pragma unroll
+          for (int k4 = 0; k4 < H_KC / 16; ++k4) {
+            const uint64_t o = (uint64_t)(k4 * 32) >> 4;
+            const uint32_t acc = (c | k4) ? 1u : 0u;
+            mma_f16(tP, ahi + o, bhi + o, id1, acc);
+            mma_f16(tC, ahi + o, blo + o, id1, acc);
+            mma_f16(tC, alo + o, bhi + o, id1, 1u);
+          }
+          tc_commit(&empty[s]);
+        }
+        if (!ok) break;
+        tc_commit(d1full);
+        if (RESID) {
+          // E = X - P U^T onto the stored tile, once P's FP16 parts are in shared memory
+          if (!h_wait(pready, (uint32_t)(it & 1), abort)) { ok = false; break; }
+          tc_fence_after();
+          const uint64_t phi = desc_sw128(P16hi), plo = desc_sw128(P16lo);
+          for (int b = 0; b < nblk; ++b) {
+            const int c0 = 128 * b;
+            const int nc = min(128, n1p - c0);
+            const uint32_t idb = idesc_f16(H_M, nc);
+            const uint64_t uhi = desc_sw128(U2hi + (size_t)c0 * 128), ulo = desc_sw128(U2lo + (size_t)c0 * 128);
+            for (int ks = 0; ks < Rp / 16; ++ks) {
+              const uint64_t o = (uint64_t)(ks * 32) >> 4;
+              mma_f16(tmem + c0, phi + o, uhi + o, idb, 1u);
+              mma_f16(tmem + c0, phi + o, ulo + o, idb, 1u);
+              mma_f16(tmem + c0, plo + o, uhi + o, idb, 1u);
+            }
+            tc_commit(&efull[b]);
+          }
+        }
+      }
+      tc_commit(done);
+      h_drain(done, 0);
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 4 + H_SPLIT_W) {
+    // ---------------- splitters ----------------
+    const int q4 = warp & 3, h = (warp - 4) >> 2;
+    const int row = q4 * 32 + lane;
+    const uint32_t lq = (uint32_t)(q4 * 32) << 16;
+    const float sc = pow2f(sigma), sct = pow2f(sigma + 9);
+    float xm = 0.f;
+    double yacc = 0.0;
+    long long q = 0;
+    int it = 0;
+    bool stop = false;
+    for (long long t = blockIdx.x; !stop && t < ntiles; t += gridDim.x, ++it) {
+      for (int c = 0; c < Kc; ++c, ++q) {
+        const int s = (int)(q % S);
+        bool ok = h_wait(&full[s], (uint32_t)((q / S) & 1), abort);
+        // block c / 2 of the tensor-memory tile must have been read out for the previous tile
+        if (RESID && ok && it > 0 && (c & 1) == 0) ok = h_wait(&xfree[c >> 1], (uint32_t)((it - 1) & 1), abort);
+        unsigned char* st = base + (size_t)s * H_STAGE;
+        float x[32];
+        const float4* src = reinterpret_cast<const float4*>(st + h * (H_XB / 2) + row * 128);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float4 v = src[u ^ (row & 7)];
+          x[4 * u] = v.x; x[4 * u + 1] = v.y; x[4 * u + 2] = v.z; x[4 * u + 3] = v.w;
+        }
+        // every splitter has read the stage before any writes its FP16 parts over it
+        if (bar_any(1, 32 * H_SPLIT_W, !ok)) { stop = true; break; }
+        float ys = 0.f;
+        uint32_t hp[16], lp[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float a0 = x[2 * i], a1 = x[2 * i + 1];
+          ys = fmaf(a0, a0, ys);
+          ys = fmaf(a1, a1, ys);
+          xm = fmaxf(xm, fmaxf(fabsf(a0), fabsf(a1)));
+          split_h2(a0 * sc, a1 * sc, hp[i], lp[i]);
+        }
+        yacc += (double)ys;
+        // hi row `row`: FP16 columns 32 h .. 32 h + 31 are 16-byte pieces 4 h .. 4 h + 3
+        uint4* dh = reinterpret_cast<uint4*>(st + row * 128);
+        uint4* dl = reinterpret_cast<uint4*>(st + H_XB / 2 + row * 128);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int u = (4 * h + j) ^ (row & 7);
+          dh[u] = make_uint4(hp[4 * j], hp[4 * j + 1], hp[4 * j + 2], hp[4 * j + 3]);
+          dl[u] = make_uint4(lp[4 * j], lp[4 * j + 1], lp[4 * j + 2], lp[4 * j + 3]);
+        }
+        if (RESID) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) x[i] *= sct;
+          tc_fence_after();   // after the wait on xfree: the block's reads are done
+          tmem_st32(tmem + lq + (uint32_t)(c * H_KC + 32 * h), x);
+          tc_fence_before();
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(&conv[s]);
+      }
+    }
+    const double sy = warp_sum(yacc);
+    float m = xm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+      red[warp] = sy;
+      redm[warp] = __float_as_uint(m);
+    }
+  } else if (warp >= H_EPI_W0) {
+    // ---------------- epilogue: P (epi-1), then E (epi-2) ----------------
+    const int q4 = warp & 3;
+    const int row = q4 * 32 + lane;
+    const uint32_t lq = (uint32_t)(q4 * 32) << 16;
+    const float pun = pow2f(-(sigma + 14)), pneg = -pow2f(-19), eun = pow2f(-(sigma + 9));
+    double eacc = 0.0;
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      bool okw = h_wait(d1full, (uint32_t)(it & 1), abort);
+      okw = __all_sync(0xffffffffu, okw);
+      if (!okw) break;
+      tc_fence_after();
+      const long long f = t * H_M + row;
+      const bool live = f < F;
+      for (int c0 = 0; c0 < Rp; c0 += 32) {
+        float v[32], w[32];
+        tmem_ld32(tmem + lq + H_TP + c0, v);
+        tmem_ld32(tmem + lq + H_TP + TP_RMAX + c0, w);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += w[i];
+        if (live && !WRITE_ET) {
+          // column-major (F x r): consecutive threads write consecutive addresses
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (c0 + i < r) P[f + F * (c0 + i)] = v[i] * pun;
+        }
+        if (RESID) {
+          uint32_t hp[16], lp[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) split_h2(v[2 * i] * pneg, v[2 * i + 1] * pneg, hp[i], lp[i]);
+          uint4* dh = reinterpret_cast<uint4*>(P16hi + row * 128);
+          uint4* dl = reinterpret_cast<uint4*>(P16lo + row * 128);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int u = ((c0 >> 3) + j) ^ (row & 7);
+            dh[u] = make_uint4(hp[4 * j], hp[4 * j + 1], hp[4 * j + 2], hp[4 * j + 3]);
+            dl[u] = make_uint4(lp[4 * j], lp[4 * j + 1], lp[4 * j + 2], lp[4 * j + 3]);
+          }
+        }
+      }
+      if (RESID) fence_proxy_async_smem();
+      tc_fence_before();
+      mbar_arrive(pready);
+      if (RESID) {
+        for (int b = 0; okw && b < nblk; ++b) {
+          okw = h_wait(&efull[b], (uint32_t)(it & 1), abort);
+          okw = __all_sync(0xffffffffu, okw);
+          if (!okw) break;
+          tc_fence_after();
+          const int cend = min(128 * (b + 1), n1p);
+          for (int c0 = 128 * b; c0 < cend; c0 += 32) {
+            float e[32];
+            tmem_ld32(tmem + lq + (uint32_t)c0, e);
+            float es = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const float ev = e[i] * eun;
+              if (c0 + i < n1) es = fmaf(ev, ev, es);
+              if (WRITE_ET) {
+                if (c0 + i < n1) {
+                  if (live) a.Et[(long long)(c0 + i) * a.et_stride + f] = ev;
+                  else if (f < a.et_stride) a.Et[(long long)(c0 + i) * a.et_stride + f] = 0.f;
+                }
+              }
+            }
+            if (live) eacc += (double)es;
+          }
+          tc_fence_before();
+          mbar_arrive(&xfree[b]);
+        }
+        if (!okw) break;
+      }
+    }
+    const double se = warp_sum(eacc);
+    if (lane == 0) red[warp] = se;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, H_TMEM_COLS);
+  if (threadIdx.x == 0) {
+    if (*abort) ctl->status = TK_ETIMEOUT;
+    double te = 0.0, ty = 0.0;
+    unsigned mb = 0u;
+    for (int w = 4; w < 4 + H_SPLIT_W; ++w) {
+      ty += red[w];
+      mb = max(mb, redm[w]);
+    }
+    for (int w = H_EPI_W0; w < H_EPI_W0 + 4; ++w) te += red[w];
+    if (RESID && !WRITE_ET) {
+      for (int j = blockIdx.x; j < a.nparts; j += gridDim.x) {
+        a.part_e2[j] = (j == (int)blockIdx.x) ? te : 0.0;
+        if (a.part_y2) a.part_y2[j] = (j == (int)blockIdx.x) ? ty : 0.0;
+      }
+    }
+    if (a.track) atomicMax(&ctl->xmax[k], mb);
+  }
+}
+
+// FP16 hi/lo parts of 2^14 U_k for the FP16 passes (after the initial ST-HOSVD and after
+// growth): U1 (64 rows x ld1: row i = column i of U_k, zero past r_k; MMA1's B) and U2 (n_k rows x
+// 64: row j = row j of U_k, zero past r_k; MMA2's B).
+__global__ void k_split_u16(const Ctl* ctl, int k, int pred, const double* U, int ldu, int ld1,
+                            __half* u1hi, __half* u1lo, __half* u2hi, __half* u2lo) {
+  if (ctl->status) return;
+  if (pred && !ctl->grew[k]) return;
+  const int n1 = ctl->n[k];
+  const int r = ctl->r[k];
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < (long long)TP_RMAX * n1;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(L % n1), i = (int)(L / n1);
+    const float v = (i < r) ? (float)U[(long long)i * ldu + j] * 16384.f : 0.f;
+    const __half hv = __float2half_rn(v);
+    const __half lv = __float2half_rn(v - __half2float(hv));
+    u1hi[(long long)i * ld1 + j] = hv;
+    u1lo[(long long)i * ld1 + j] = lv;
+    u2hi[(long long)j * TP_RMAX + i] = hv;
+    u2lo[(long long)j * TP_RMAX + i] = lv;
+  }
+}
+
+cudaError_t launch_split_u16(const Ctl* ctl, int k, int pred, const double* U, int ldu, int ld1,
+                             void* const* u16, cudaStream_t st) {
+  k_split_u16<<<64, 256, 0, st>>>(ctl, k, pred, U, ldu, ld1, (__half*)u16[0], (__half*)u16[1],
+                                  (__half*)u16[2], (__half*)u16[3]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_pass16(Ctl* ctl, int k, int mode, int pred, int rerun, const float* Y,
+                             long long F0, int n0, const TcProjMaps& m, void* const* dbufs,
+                             int out_off, double* part_e2, double* part_y2, int nparts, float* Et,
+                             long long et_stride, int grid, cudaStream_t st) {
+  CUtensorMap mY;
+  const CUtensorMap* mYg = nullptr;
+  if (k == 0 && Y) {
+    if (!make_map_2d_f32(&mY, Y, F0, n0, n0, 32, 128)) return cudaErrorInvalidValue;
+  } else {
+    mY = m.d[0];   // unused for k >= 1 (the input is a D buffer)
+    // graph form (Y == NULL): the slice descriptor is read from the control block
+    if (k == 0) mYg = reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const unsigned char*>(ctl) + offsetof(Ctl, ymap));
+  }
+  TcPass16Args a{mYg, (float* const*)dbufs, out_off, part_e2, part_y2, nparts, Y, Et, et_stride, k,
+                 rerun, mode == 1 ? 1 : 0};
+  static bool attr[3] = {false, false, false};
+  if (mode == 0) {
+    if (!attr[0]) { cudaFuncSetAttribute(k_tc_pass16<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HCfg<false>::SMEM); attr[0] = true; }
+    k_tc_pass16<false, false><<<grid, H_NT, HCfg<false>::SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.h1hi, m.h1lo, m.h2hi, m.h2lo, a);
+  } else if (mode == 1) {
+    if (!attr[1]) { cudaFuncSetAttribute(k_tc_pass16<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HCfg<true>::SMEM); attr[1] = true; }
+    k_tc_pass16<true, false><<<grid, H_NT, HCfg<true>::SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.h1hi, m.h1lo, m.h2hi, m.h2lo, a);
+  } else {
+    if (!attr[2]) { cudaFuncSetAttribute(k_tc_pass16<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HCfg<true>::SMEM); attr[2] = true; }
+    k_tc_pass16<true, true><<<grid, H_NT, HCfg<true>::SMEM, st>>>(ctl, pred, mY, m.d[0], m.d[1], m.d[2], m.h1hi, m.h1lo, m.h2hi, m.h2lo, a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tk

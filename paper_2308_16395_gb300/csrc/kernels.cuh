@@ -99,6 +99,8 @@ struct TcProjMaps {
   CUtensorMap urhi, urlo;   // U_k TF32 splits, row-major n_k x 64
   CUtensorMap d[3];         // the D* buffers viewed as row-major (rows x n_k), box 32 x 128
   CUtensorMap eta;          // E^T (n_k x Fs), box 32 x 128
+  CUtensorMap h1hi, h1lo;   // FP16 parts of 2^14 U_k, 64 x n_k (row i = column i of U_k), box 64 x 16
+  CUtensorMap h2hi, h2lo;   // FP16 parts of 2^14 U_k, n_k x 64 (row-major), box 64 x 64
 };
 cudaError_t launch_split_u(const Ctl* ctl, int k, int pred, const double* U, int ldu,
                            float* const* sp, cudaStream_t st);
@@ -108,6 +110,17 @@ cudaError_t launch_tc_proj(const Ctl* ctl, int k, int mode, int pred, const floa
                            long long F0, int n0, const TcProjMaps& m, void* const* dbufs,
                            int out_off, double* part_e2, double* part_y2, int nparts, float* Et,
                            long long et_stride, int grid, cudaStream_t st);
+// FP16-split pass of mode k (n_k <= TK_H16_NMAX), same modes and outputs as launch_tc_proj;
+// rerun = 1: the second launch of pass A, which runs only when the first one's input fell outside
+// the FP16 scale window.
+cudaError_t launch_tc_pass16(Ctl* ctl, int k, int mode, int pred, int rerun, const float* Y,
+                             long long F0, int n0, const TcProjMaps& m, void* const* dbufs,
+                             int out_off, double* part_e2, double* part_y2, int nparts, float* Et,
+                             long long et_stride, int grid, cudaStream_t st);
+cudaError_t launch_split_u16(const Ctl* ctl, int k, int pred, const double* U, int ldu, int ld1,
+                             void* const* u16, cudaStream_t st);
+bool make_map_2d_f16(CUtensorMap* map, const void* base, long long rows, long long cols,
+                     long long ld, int box_cols, int box_rows);
 cudaError_t launch_tc_gram(const Ctl* ctl, int k, const TcProjMaps& m, int n1, double* gpart,
                            double* G, int nsm, cudaStream_t st);
 

@@ -221,6 +221,49 @@ __host__ __device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
   return d;
 }
 
+// Instruction descriptor, kind::f16: D FP32, A and B FP16 (format code 0), both K-major, M x N.
+__host__ __device__ __forceinline__ uint32_t idesc_f16(int M, int N) {
+  uint32_t d = 0;
+  d |= 1u << 4;                            // D format: F32
+  d |= (uint32_t)(N >> 3) << 17;           // N / 8
+  d |= (uint32_t)(M >> 4) << 24;           // M / 16
+  return d;
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (A and B both FP16), FP32 accumulation, K = 16 per
+// instruction (32 bytes of a 128-byte swizzled row).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Named barrier over `count` threads that returns the OR of every participant's predicate (a
+// uniform decision for all of them).
+__device__ __forceinline__ bool bar_any(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "barrier.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
+// Exact power of two 2^e as a float (e in [-126, 127]).
+__host__ __device__ __forceinline__ float pow2f(int e) {
+  union { uint32_t u; float f; } v;
+  v.u = (uint32_t)(127 + e) << 23;
+  return v.f;
+}
+
 // Split x = hi + lo with hi rounded to the nearest TF32 value (10 explicit mantissa bits, low 13
 // bits zero) and lo = x - hi exact (|lo| <= 2^-11 |x|, at most 12 significant bits). Both parts
 // are then taken by the tensor core with an error of at most one dropped bit of lo (<= 2^-23 |x|),

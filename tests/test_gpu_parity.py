@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
-Bars (written here; the design doc gives their derivation):
+Bars (each derived from the arithmetic of the form it checks):
   FP64 form  -- identical ranks every step; reconstruction, subspaces and aligned core within
                 1e-9 relative; error bookkeeping within 1e-8 relative.
   mixed form -- identical ranks at every step; a decision whose oracle statistic lies within
