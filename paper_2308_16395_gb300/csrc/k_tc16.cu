@@ -4,29 +4,31 @@
 //
 // The mode-k input X (row-major F x n_k, the mode-k fibers as rows) streams through shared memory
 // by TMA in chunks of 128 fibers x 64 columns (two 32-column boxes, 128-byte swizzle). Eight
-// splitter warps convert each chunk in place into the FP16 high and low parts of 2^sigma X
-// (2^sigma x = hi + lo up to 2^-23 |2^sigma x| + 2^-25) and, in the residual passes, store the
-// FP32 values 2^(sigma+9) X into tensor memory (lane = fiber, one column per element).
-//   MMA1  P_s = (2^sigma X)(2^14 U_k) on kind::f16, three products per K step of 16 (hi*hi into
-//         one accumulator, hi*lo + lo*hi into a second; FP16 products are exact in FP32),
-//         U_k's FP16 parts streamed with the chunks.
-//   epi-1 P = 2^-(sigma+14) P_s -> global, column-major (F x r_k, the next mode's input);
-//         -2^-19 P_s split into FP16 hi/lo in shared memory (MMA2's A operand).
-//   MMA2  accumulated onto the stored tile: 2^(sigma+9) X + (-2^-19 P_s)(2^14 U_k)^T =
-//         2^(sigma+9) (X - P U_k^T) = 2^(sigma+9) E, three products per K step, U_k^T's FP16 parts
-//         resident in shared memory, in 128-column blocks.
-//   epi-2 ||E||^2 per CTA (FP32 over 32 elements, then FP64), and E^T for the residual Gram when
-//         the mode grew.
+// splitter warps convert each chunk in place into the FP16 high and low parts of X_s = 2^sigma X
+// (x_s = hi + lo up to 2^-23 |x_s| + 2^-25) for MMA1 and, in the residual passes, then store the
+// FP32 values X_s into tensor memory (lane = fiber, one column per element).
+//   MMA1  P_s = X_s (2^14 U_k) on kind::f16, three products per K step of 16 (hi*hi into one
+//         accumulator, hi*lo + lo*hi into a second; FP16 products are exact in FP32), U_k's FP16
+//         parts streamed with the chunks.
+//   epi-1 P = 2^-(sigma+14) P_s into a shared staging tile; -2^-19 P_s split into FP16 hi/lo in
+//         tensor memory over the accumulators just read (MMA2's A operand).
+//   MMA2  accumulated onto the stored tile: X_s + (-2^-19 P_s)(2^5 U_k)^T = 2^sigma (X - P U_k^T)
+//         = 2^sigma E, three products per K step, U_k^T's FP16 parts resident in shared memory,
+//         in 128-column blocks.
+//   epi-2 ||E||^2 per CTA (FP32 over a fiber's block, then FP64), E^T for the residual Gram when
+//         the mode grew; then the staged P to global memory, column-major (F x r_k, the next
+//         mode's input).
 // Block b of the tensor-memory tile is released to the next tile's chunks as soon as epi-2 has
-// read it, so the next tile streams in while MMA2 and epi-2 finish. The ring of input stages is
-// fed from L2, into which the producer prefetches chunks ahead of their loads.
+// read it; the splitters hand each chunk's FP16 parts to MMA1 before they wait for that release,
+// so the next tile's MMA1 follows MMA2 on the tensor pipe without waiting for the epilogue. The
+// ring of input stages is fed from L2, into which the producer prefetches chunks ahead.
 //
 // Scale: sigma_k (Ctl::x16e) puts the input's largest |x| near 2^8, far from the FP16 limits
-// (|2^sigma x| <= 2^15 keeps hi finite; the low end loses only an absolute 2^-25). Pass A records
-// max |x| (Ctl::xmax); a second launch of pass A right after it returns at once unless the
-// scaled maximum left [2^1, 2^15), and then runs the pass again with sigma from that maximum.
-// With |2^sigma x| < 2^15, |U| <= 1 and |p| <= sqrt(n_k) max|x| (orthonormal U_k), every FP16
-// operand stays below 2^15 for n_k <= 384.
+// (|x_s| <= 2^15 keeps hi finite; the low end loses only an absolute 2^-25). Pass A records
+// max |x| (Ctl::xmax); a second launch of pass A right after it returns at once unless the scaled
+// maximum left [2^1, 2^15), and then runs the pass again with sigma from that maximum. With
+// |x_s| < 2^15, |U| <= 1 and |p| <= sqrt(n_k) max|x| (orthonormal U_k), every FP16 operand
+// stays below 2^15 for n_k <= 384 (|2^-19 P_s| <= 2^-5 sqrt(n_k) max|x_s|).
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -43,7 +45,7 @@ constexpr int H_XB = H_M * H_KC * 4;             // 32 KB: raw FP32 chunk, then 
 constexpr int H_UB = TP_RMAX * 128;              // 8 KB: U chunk (hi or lo), <= 64 rows x 128 B
 constexpr int H_STAGE = H_XB + 2 * H_UB;         // 48 KB
 constexpr int H_U2 = TK_H16_NMAX * 128;          // 48 KB: U_k rows (hi or lo), n_k x 64 FP16
-constexpr int H_P16 = H_M * 128;                 // 16 KB: MMA2's A operand (hi or lo)
+constexpr int H_PST = TP_RMAX * H_M * 4;         // 32 KB: staged P tile, [column][fiber] FP32
 constexpr int H_PF = 6;                          // chunks prefetched into L2 ahead of the loads
 constexpr int H_SPLIT_W = 8;                     // splitter warps 4..11
 constexpr int H_EPI_W0 = 12;                     // epilogue warps 12..15
@@ -51,10 +53,17 @@ constexpr int H_NT = 32 * 16;
 constexpr int H_TP = TK_H16_NMAX;                // TMEM column of the P accumulators
 constexpr uint32_t H_TMEM_COLS = 512;
 static_assert(H_TP + 2 * TP_RMAX <= (int)H_TMEM_COLS, "input tile and P accumulators fit TMEM");
+// MMA2's A operand over the accumulators: K columns 0..31 (packed two per TMEM column) of the
+// high part at H_TP, of the low part at H_TP + 16 (both over P columns 0..31 of the hi*hi
+// accumulator, read first); K columns 32..63 at H_TP + 64 and H_TP + 80 (over P columns 0..31
+// of the correction accumulator, also read first)
+__device__ __forceinline__ uint32_t a16_col(int ks, int lo) {
+  return (uint32_t)(H_TP + (ks < 2 ? 0 : TP_RMAX) + 16 * lo + 8 * (ks & 1));
+}
 
 template <bool RESID> struct HCfg {
   static constexpr int S = RESID ? 2 : 4;
-  static constexpr size_t EXTRA = RESID ? (size_t)2 * H_U2 + 2 * H_P16 : 0;
+  static constexpr size_t EXTRA = (RESID ? (size_t)2 * H_U2 : 0) + H_PST;
   static constexpr size_t SMEM = (size_t)S * H_STAGE + EXTRA + 1024 + 1024;
 };
 static_assert(HCfg<true>::SMEM <= 232448, "shared memory of the residual pass");
@@ -155,17 +164,17 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
   constexpr int S = HCfg<RESID>::S;
   unsigned char* U2hi = base + (size_t)S * H_STAGE;
   unsigned char* U2lo = U2hi + H_U2;
-  unsigned char* P16hi = U2lo + H_U2;
-  unsigned char* P16lo = P16hi + H_P16;
+  float* Pst = reinterpret_cast<float*>(base + (size_t)S * H_STAGE + (RESID ? (size_t)2 * H_U2 : 0));
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)S * H_STAGE + HCfg<RESID>::EXTRA);
   uint64_t* full = bars;                 // [S] chunk landed
-  uint64_t* conv = bars + S;             // [S] chunk split (and stored to TMEM)
+  uint64_t* conv = bars + S;             // [S] chunk's FP16 parts in shared memory
   uint64_t* empty = bars + 2 * S;        // [S] chunk's MMAs done
   uint64_t* d1full = bars + 3 * S;       // P accumulators complete
-  uint64_t* pready = d1full + 1;         // P read out (and MMA2's A operand stored)
+  uint64_t* pready = d1full + 1;         // P read out (MMA2's A operand stored over it)
   uint64_t* efull = pready + 1;          // [3] E block b complete
   uint64_t* xfree = efull + 3;           // [3] E block b read out
-  uint64_t* bload = xfree + 3;           // resident U rows landed
+  uint64_t* xst = xfree + 3;             // the tile's input stored in tensor memory
+  uint64_t* bload = xst + 1;             // resident U rows landed
   uint64_t* done = bload + 1;            // every MMA complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -185,6 +194,7 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
       mbar_init(&efull[b], 1);
       mbar_init(&xfree[b], 128);
     }
+    mbar_init(xst, 32 * H_SPLIT_W);
     mbar_init(bload, 1);
     mbar_init(done, 1);
     *abort = 0;
@@ -262,8 +272,9 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
       long long q = 0;
       int it = 0;
       for (long long t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++it) {
-        // the P accumulators are free once epilogue 1 of the previous tile has read them
-        if (it > 0 && !h_wait(pready, (uint32_t)((it - 1) & 1), abort)) { ok = false; break; }
+        // projection form: the P accumulators are free once the epilogue has read the previous
+        // tile's (in the residual form MMA2 of the previous tile, issued before, waited for that)
+        if (!RESID && it > 0 && !h_wait(pready, (uint32_t)((it - 1) & 1), abort)) { ok = false; break; }
         tc_fence_after();
         for (int c = 0; c < Kc; ++c, ++q) {
           const int s = (int)(q % S);
@@ -285,10 +296,11 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
         if (!ok) break;
         tc_commit(d1full);
         if (RESID) {
-          // E = X - P U^T onto the stored tile, once P's FP16 parts are in shared memory
+          // E = X - P U^T onto the stored tile, once P's FP16 parts are in tensor memory and the
+          // tile's input is stored
           if (!h_wait(pready, (uint32_t)(it & 1), abort)) { ok = false; break; }
+          if (!h_wait(xst, (uint32_t)(it & 1), abort)) { ok = false; break; }
           tc_fence_after();
-          const uint64_t phi = desc_sw128(P16hi), plo = desc_sw128(P16lo);
           for (int b = 0; b < nblk; ++b) {
             const int c0 = 128 * b;
             const int nc = min(128, n1p - c0);
@@ -296,9 +308,9 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
             const uint64_t uhi = desc_sw128(U2hi + (size_t)c0 * 128), ulo = desc_sw128(U2lo + (size_t)c0 * 128);
             for (int ks = 0; ks < Rp / 16; ++ks) {
               const uint64_t o = (uint64_t)(ks * 32) >> 4;
-              mma_f16(tmem + c0, phi + o, uhi + o, idb, 1u);
-              mma_f16(tmem + c0, phi + o, ulo + o, idb, 1u);
-              mma_f16(tmem + c0, plo + o, uhi + o, idb, 1u);
+              mma_f16_ts(tmem + c0, tmem + a16_col(ks, 0), uhi + o, idb, 1u);
+              mma_f16_ts(tmem + c0, tmem + a16_col(ks, 0), ulo + o, idb, 1u);
+              mma_f16_ts(tmem + c0, tmem + a16_col(ks, 1), uhi + o, idb, 1u);
             }
             tc_commit(&efull[b]);
           }
@@ -313,18 +325,17 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
     const int q4 = warp & 3, h = (warp - 4) >> 2;
     const int row = q4 * 32 + lane;
     const uint32_t lq = (uint32_t)(q4 * 32) << 16;
-    const float sc = pow2f(sigma), sct = pow2f(sigma + 9);
+    const float sc = pow2f(sigma);
     float xm = 0.f;
     double yacc = 0.0;
     long long q = 0;
     int it = 0;
-    bool stop = false;
+    bool stop = false, okx = true;
     for (long long t = blockIdx.x; !stop && t < ntiles; t += gridDim.x, ++it) {
+      float yt = 0.f;   // FP32 over the tile's chunks (<= 6 sums of 32 terms), FP64 per tile
       for (int c = 0; c < Kc; ++c, ++q) {
         const int s = (int)(q % S);
-        bool ok = h_wait(&full[s], (uint32_t)((q / S) & 1), abort);
-        // block c / 2 of the tensor-memory tile must have been read out for the previous tile
-        if (RESID && ok && it > 0 && (c & 1) == 0) ok = h_wait(&xfree[c >> 1], (uint32_t)((it - 1) & 1), abort);
+        const bool ok = h_wait(&full[s], (uint32_t)((q / S) & 1), abort);
         unsigned char* st = base + (size_t)s * H_STAGE;
         float x[32];
         const float4* src = reinterpret_cast<const float4*>(st + h * (H_XB / 2) + row * 128);
@@ -333,8 +344,9 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
           const float4 v = src[u ^ (row & 7)];
           x[4 * u] = v.x; x[4 * u + 1] = v.y; x[4 * u + 2] = v.z; x[4 * u + 3] = v.w;
         }
-        // every splitter has read the stage before any writes its FP16 parts over it
-        if (bar_any(1, 32 * H_SPLIT_W, !ok)) { stop = true; break; }
+        // every splitter has read the stage before any writes its FP16 parts over it (and a
+        // wait that gave up, here or on the previous chunk's block, stops all of them)
+        if (bar_any(1, 32 * H_SPLIT_W, !(ok && okx))) { stop = true; break; }
         float ys = 0.f;
         uint32_t hp[16], lp[16];
 #pragma unroll
@@ -343,9 +355,11 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
           ys = fmaf(a0, a0, ys);
           ys = fmaf(a1, a1, ys);
           xm = fmaxf(xm, fmaxf(fabsf(a0), fabsf(a1)));
-          split_h2(a0 * sc, a1 * sc, hp[i], lp[i]);
+          x[2 * i] = a0 * sc;
+          x[2 * i + 1] = a1 * sc;
+          split_h2(x[2 * i], x[2 * i + 1], hp[i], lp[i]);
         }
-        yacc += (double)ys;
+        yt += ys;
         // hi row `row`: FP16 columns 32 h .. 32 h + 31 are 16-byte pieces 4 h .. 4 h + 3
         uint4* dh = reinterpret_cast<uint4*>(st + row * 128);
         uint4* dl = reinterpret_cast<uint4*>(st + H_XB / 2 + row * 128);
@@ -355,16 +369,23 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
           dh[u] = make_uint4(hp[4 * j], hp[4 * j + 1], hp[4 * j + 2], hp[4 * j + 3]);
           dl[u] = make_uint4(lp[4 * j], lp[4 * j + 1], lp[4 * j + 2], lp[4 * j + 3]);
         }
-        if (RESID) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) x[i] *= sct;
-          tc_fence_after();   // after the wait on xfree: the block's reads are done
-          tmem_st32(tmem + lq + (uint32_t)(c * H_KC + 32 * h), x);
-          tc_fence_before();
-        }
         fence_proxy_async_smem();
         mbar_arrive(&conv[s]);
+        if (RESID) {
+          // the FP32 values into tensor memory once block c / 2 of the previous tile has been read
+          if (it > 0 && (c & 1) == 0) okx = h_wait(&xfree[c >> 1], (uint32_t)((it - 1) & 1), abort);
+          okx = __all_sync(0xffffffffu, okx);
+          if (okx) {
+            tc_fence_after();
+            tmem_st32(tmem + lq + (uint32_t)(c * H_KC + 32 * h), x);
+            if (c == Kc - 1) {
+              tc_fence_before();
+              mbar_arrive(xst);
+            }
+          }
+        }
       }
+      yacc += (double)yt;
     }
     const double sy = warp_sum(yacc);
     float m = xm;
@@ -375,77 +396,100 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
       redm[warp] = __float_as_uint(m);
     }
   } else if (warp >= H_EPI_W0) {
-    // ---------------- epilogue: P (epi-1), then E (epi-2) ----------------
+    // ---------------- epilogue: P (epi-1), E (epi-2), then the staged P out ----------------
     const int q4 = warp & 3;
     const int row = q4 * 32 + lane;
     const uint32_t lq = (uint32_t)(q4 * 32) << 16;
-    const float pun = pow2f(-(sigma + 14)), pneg = -pow2f(-19), eun = pow2f(-(sigma + 9));
+    const float pun = pow2f(-(sigma + 14)), pneg = -pow2f(-19), eun = pow2f(-sigma);
+    constexpr bool OUT = !WRITE_ET;   // this pass writes P
     double eacc = 0.0;
     int it = 0;
+    // every give-up below is decided for the four warps together (named barrier 2 also orders
+    // the staging tile between them, so none of them may leave the loop alone)
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       bool okw = h_wait(d1full, (uint32_t)(it & 1), abort);
-      okw = __all_sync(0xffffffffu, okw);
-      if (!okw) break;
+      if (bar_any(2, 128, !okw)) break;
       tc_fence_after();
       const long long f = t * H_M + row;
       const bool live = f < F;
+      // P = sum of the two accumulators, 32 columns at a time; the staging tile was emptied by
+      // these threads at the end of the previous tile
       for (int c0 = 0; c0 < Rp; c0 += 32) {
-        float v[32], w[32];
-        tmem_ld32(tmem + lq + H_TP + c0, v);
-        tmem_ld32(tmem + lq + H_TP + TP_RMAX + c0, w);
+        float v[32];
+        {
+          uint32_t a0[32], a1[32];
+          tmem_ld32_nw(tmem + lq + H_TP + c0, a0);
+          tmem_ld32_nw(tmem + lq + H_TP + TP_RMAX + c0, a1);
+          tmem_ld_wait();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] += w[i];
-        if (live && !WRITE_ET) {
-          // column-major (F x r): consecutive threads write consecutive addresses
+          for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
+        }
+        if (OUT) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (c0 + i < r) P[f + F * (c0 + i)] = v[i] * pun;
+          for (int i = 0; i < 32; ++i) Pst[(c0 + i) * H_M + row] = v[i] * pun;
         }
         if (RESID) {
+          // MMA2's A operand over accumulator columns read already (see a16_col)
           uint32_t hp[16], lp[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) split_h2(v[2 * i] * pneg, v[2 * i + 1] * pneg, hp[i], lp[i]);
-          uint4* dh = reinterpret_cast<uint4*>(P16hi + row * 128);
-          uint4* dl = reinterpret_cast<uint4*>(P16lo + row * 128);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int u = ((c0 >> 3) + j) ^ (row & 7);
-            dh[u] = make_uint4(hp[4 * j], hp[4 * j + 1], hp[4 * j + 2], hp[4 * j + 3]);
-            dl[u] = make_uint4(lp[4 * j], lp[4 * j + 1], lp[4 * j + 2], lp[4 * j + 3]);
-          }
+          tmem_st16_nw(tmem + lq + a16_col(c0 >> 4, 0), hp);
+          tmem_st16_nw(tmem + lq + a16_col(c0 >> 4, 1), lp);
         }
       }
-      if (RESID) fence_proxy_async_smem();
+      if (RESID) tmem_st_wait();
       tc_fence_before();
       mbar_arrive(pready);
       if (RESID) {
         for (int b = 0; okw && b < nblk; ++b) {
           okw = h_wait(&efull[b], (uint32_t)(it & 1), abort);
-          okw = __all_sync(0xffffffffu, okw);
+          okw = !bar_any(2, 128, !okw);
           if (!okw) break;
           tc_fence_after();
           const int cend = min(128 * (b + 1), n1p);
-          for (int c0 = 128 * b; c0 < cend; c0 += 32) {
-            float e[32];
-            tmem_ld32(tmem + lq + (uint32_t)c0, e);
-            float es = 0.f;
+          float eb = 0.f;   // FP32 over the block's (at most 128) elements of this fiber
+          for (int c0 = 128 * b; c0 < cend; c0 += 64) {
+            // two 32-column loads before one wait
+            uint32_t e0[32], e1[32];
+            tmem_ld32_nw(tmem + lq + (uint32_t)c0, e0);
+            if (c0 + 32 < cend) tmem_ld32_nw(tmem + lq + (uint32_t)(c0 + 32), e1);
+            tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float ev = e[i] * eun;
-              if (c0 + i < n1) es = fmaf(ev, ev, es);
-              if (WRITE_ET) {
-                if (c0 + i < n1) {
-                  if (live) a.Et[(long long)(c0 + i) * a.et_stride + f] = ev;
-                  else if (f < a.et_stride) a.Et[(long long)(c0 + i) * a.et_stride + f] = 0.f;
+            for (int hh = 0; hh < 2; ++hh) {
+              const int cb = c0 + 32 * hh;
+              if (cb >= cend) break;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                const float ev = __uint_as_float(hh ? e1[i] : e0[i]) * eun;
+                if (cb + i < n1) eb = fmaf(ev, ev, eb);
+                if (WRITE_ET) {
+                  if (cb + i < n1) {
+                    if (live) a.Et[(long long)(cb + i) * a.et_stride + f] = ev;
+                    else if (f < a.et_stride) a.Et[(long long)(cb + i) * a.et_stride + f] = 0.f;
+                  }
                 }
               }
             }
-            if (live) eacc += (double)es;
           }
           tc_fence_before();
           mbar_arrive(&xfree[b]);
+          if (live) eacc += (double)eb;
         }
         if (!okw) break;
+      }
+      if (OUT) {
+        // staged P out, column-major (F x r): a warp writes 32 consecutive fibers of a column
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        const long long f0 = t * H_M;
+        for (int c = q4; c < r; c += 4) {
+          const float* src = Pst + c * H_M;
+          float* dst = P + F * c + f0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (f0 + 32 * j + lane < F) dst[32 * j + lane] = src[32 * j + lane];
+        }
+        // the staging tile is free again for the next tile's epi-1
+        asm volatile("bar.sync 2, 128;" ::: "memory");
       }
     }
     const double se = warp_sum(eacc);
@@ -474,9 +518,9 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
   }
 }
 
-// FP16 hi/lo parts of 2^14 U_k for the FP16 passes (after the initial ST-HOSVD and after
-// growth): U1 (64 rows x ld1: row i = column i of U_k, zero past r_k; MMA1's B) and U2 (n_k rows x
-// 64: row j = row j of U_k, zero past r_k; MMA2's B).
+// FP16 hi/lo parts of U_k for the FP16 passes (after the initial ST-HOSVD and after growth):
+// U1 = 2^14 U_k as 64 rows x ld1 (row i = column i of U_k, zero past r_k; MMA1's B) and
+// U2 = 2^5 U_k as n_k rows x 64 (row j = row j of U_k, zero past r_k; MMA2's B).
 __global__ void k_split_u16(const Ctl* ctl, int k, int pred, const double* U, int ldu, int ld1,
                             __half* u1hi, __half* u1lo, __half* u2hi, __half* u2lo) {
   if (ctl->status) return;
@@ -486,13 +530,13 @@ __global__ void k_split_u16(const Ctl* ctl, int k, int pred, const double* U, in
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < (long long)TP_RMAX * n1;
        L += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(L % n1), i = (int)(L / n1);
-    const float v = (i < r) ? (float)U[(long long)i * ldu + j] * 16384.f : 0.f;
-    const __half hv = __float2half_rn(v);
-    const __half lv = __float2half_rn(v - __half2float(hv));
-    u1hi[(long long)i * ld1 + j] = hv;
-    u1lo[(long long)i * ld1 + j] = lv;
-    u2hi[(long long)j * TP_RMAX + i] = hv;
-    u2lo[(long long)j * TP_RMAX + i] = lv;
+    const float u = (i < r) ? (float)U[(long long)i * ldu + j] : 0.f;
+    const float v1 = u * 16384.f, v2 = u * 32.f;
+    const __half h1 = __float2half_rn(v1), h2 = __float2half_rn(v2);
+    u1hi[(long long)i * ld1 + j] = h1;
+    u1lo[(long long)i * ld1 + j] = __float2half_rn(v1 - __half2float(h1));
+    u2hi[(long long)j * TP_RMAX + i] = h2;
+    u2lo[(long long)j * TP_RMAX + i] = __float2half_rn(v2 - __half2float(h2));
   }
 }
 

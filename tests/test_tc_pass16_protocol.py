@@ -1,17 +1,18 @@
 """Model check of the barrier protocol of the FP16 tensor-core pass (k_tc_pass16, residual form):
-TMA producer, splitters (FP16 parts to shared memory, the FP32 tile to tensor memory), MMA
-issuer, epilogue (P, then E block by block), over a ring of input stages, one tile of the input
-in tensor memory released block by block, one pair of P accumulators and one shared buffer for
-MMA2's A operand.
+TMA producer, splitters (FP16 parts to shared memory, then the FP32 tile to tensor memory),
+MMA issuer, epilogue (P, then E block by block, then the staged P out), over a ring of input
+stages, one tile of the input in tensor memory released block by block, and one pair of P
+accumulators over which the epilogue writes MMA2's A operand.
 
 Each role is a coroutine issuing the waits and arrivals the kernel issues, in the same order;
 tensor-core work runs in issue order on one pipe; durations are random. Two kinds of check:
 no wait starts on a barrier that has already completed the phase after the one it names (its
 parity would read as pending for ever), every role finishes; and no data hazard: a stage is
 refilled only after its MMAs ran, a tensor-memory block is overwritten by the next tile only
-after the epilogue read its E, MMA2 reads a block only once the tile's chunks are stored, the P
-accumulators are overwritten only after the epilogue read them, and MMA2's A operand is
-rewritten only after the MMA2s reading it ran. Planted bugs (a missing wait) must be caught.
+after the epilogue read its E, MMA2 reads a block only once the tile's chunks are stored and
+reads the A operand of its own tile, the P accumulators are overwritten only after the
+epilogue read them and after the MMA2 that read the A operand stored over them. Planted bugs
+(a missing wait) must be caught.
 """
 
 import heapq
@@ -38,7 +39,7 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
     full = [_Bar("full%d" % s) for s in range(stages)]
     conv = [_Bar("conv%d" % s) for s in range(stages)]
     empty = [_Bar("empty%d" % s) for s in range(stages)]
-    d1full, pready = _Bar("d1full"), _Bar("pready")
+    d1full, pready, xst = _Bar("d1full"), _Bar("pready"), _Bar("xst")
     efull = [_Bar("efull%d" % b) for b in range(nblk)]
     xfree = [_Bar("xfree%d" % b) for b in range(nblk)]
     pipe_free = [0.0]
@@ -85,21 +86,25 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
             for c in range(nchunks):
                 s = q % stages
                 yield wait(full[s], q // stages)
-                if resid and it > 0 and c % 2 == 0 and bug != "no_xfree_wait":
-                    yield wait(xfree[c // 2], it - 1)
                 yield ("delay", rng.uniform(0.1, 0.4))
+                conv[s].done += 1            # FP16 parts in shared memory: MMA1 may run
                 if resid:
                     b = c // 2
+                    if it > 0 and c % 2 == 0 and bug != "no_xfree_wait":
+                        yield wait(xfree[b], it - 1)
+                    # the store into tensor memory, now and then late
+                    yield ("delay", rng.uniform(2.0, 6.0) if rng.random() < 0.1 else rng.uniform(0.02, 0.1))
                     if blk_read[b] < it - 1:
                         errors.append("tile %d overwrote TMEM block %d before E of tile %d was read" % (it, b, it - 1))
                     blk_stored[b][c % 2] = it
-                conv[s].done += 1
+                    if c == nchunks - 1:
+                        xst.done += 1
                 q += 1
 
     def issuer():
         q = 0
         for it in range(ntiles):
-            if it > 0 and bug != "no_pacc_wait":
+            if not resid and it > 0 and bug != "no_pacc_wait":
                 yield wait(pready, it - 1)
             for c in range(nchunks):
                 s = q % stages
@@ -111,6 +116,8 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
                     if c == 0:
                         if pacc_read[0] < it - 1:
                             errors.append("MMA1 of tile %d overwrote P before it was read" % it)
+                        if resid and mma2_done_tile[0] < it - 1:
+                            errors.append("MMA1 of tile %d overwrote the A operand of tile %d" % (it, it - 1))
                         pacc_tile[0] = it
 
                 def fin(s=s):
@@ -121,6 +128,8 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
             tensor(0.0, lambda: None, lambda: setattr(d1full, "done", d1full.done + 1))
             if resid:
                 yield wait(pready, it)
+                if bug != "no_xst_wait":
+                    yield wait(xst, it)
                 for b in range(nblk):
                     def start2(b=b, it=it):
                         if blk_stored[b][0] != it or (2 * b + 1 < nchunks and blk_stored[b][1] != it):
@@ -150,11 +159,13 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
                 for b in range(nblk):
                     if bug != "no_efull_wait":
                         yield wait(efull[b], it)
-                    yield ("delay", rng.uniform(0.1, 0.6))
+                    # now and then a slow read-out, so that the next tile runs far ahead of it
+                    yield ("delay", rng.uniform(3.0, 8.0) if rng.random() < 0.1 else rng.uniform(0.1, 0.6))
                     if efull[b].done <= it:
                         errors.append("E block %d of tile %d read before MMA2 wrote it" % (b, it))
                     blk_read[b] = it
                     xfree[b].done += 1
+            yield ("delay", rng.uniform(0.3, 2.0))    # the staged P out
 
     roles = [producer(), splitters(), issuer(), epilogue()]
     pending, finished = {}, set()
@@ -203,10 +214,11 @@ def test_fp16_pass_protocol_has_no_deadlock_aliasing_or_hazard(resid, stages):
         assert all_done, (ntiles, nchunks)
 
 
-# (in the residual form the wait on the P read-out before a tile's MMA1 is implied by the one
-# before the previous tile's MMA2, so its removal is planted in the projection form)
+# (the wait on the P read-out before a tile's MMA1 exists in the projection form only: in the
+# residual form that MMA1 follows, on the same in-order pipe, the previous tile's MMA2, which
+# waited for the read-out)
 @pytest.mark.parametrize("bug,resid", [("no_xfree_wait", True), ("no_pacc_wait", False),
-                                       ("no_efull_wait", True)])
+                                       ("no_xst_wait", True), ("no_efull_wait", True)])
 def test_the_check_catches_a_missing_wait(bug, resid):
     rng = random.Random(5)
     caught = 0
