@@ -7,9 +7,11 @@
 //
 //   k_eig_sub     one CTA, FP32: block subspace iteration Z = G Q on SB vectors with a
 //                 Rayleigh-Ritz step every iteration (Golub & Van Loan, Matrix Computations,
-//                 Sec. 8.2.4 "orthogonal iteration" and Sec. 8.1.2 Rayleigh-Ritz), cyclic Jacobi
-//                 for the SB x SB projected matrix (Sec. 8.5.3, parallel ordering), column-scaled
-//                 Cholesky QR applied twice for the orthonormalization. It stops when the
+//                 Sec. 8.2.4 "orthogonal iteration" and Sec. 8.1.2 Rayleigh-Ritz; rotating the
+//                 basis to the Ritz vectors every iteration keeps the next G Q well conditioned
+//                 for the Cholesky QR), one-sided Jacobi for the SB x SB projected matrix
+//                 (Sec. 8.6.3, round-robin ordering), column-scaled Cholesky QR applied twice for
+//                 the orthonormalization. It stops when the
 //                 residuals ||G q_c - theta_c q_c|| of the Ritz pairs up to one past the FP32 cut
 //                 are below SUB_TOL theta_1, and hands those m Ritz vectors on.
 //   k_eig_refine  all SMs, FP64: P = W^T G W and M = W^T W for the m vectors, then the cut in
@@ -32,6 +34,7 @@ constexpr int SB = 16;                   // block size of the subspace iteration
 constexpr int SUB_NT = 512;              // one thread per row of Q and Z (n <= 512)
 constexpr int SUB_NW = SUB_NT / 32;
 constexpr int SUB_MAXIT = 40;
+
 constexpr float SUB_TOL = 4e-6f;         // Ritz residual / theta_1 accepted as converged
 constexpr int SUB_GS_NMAX = 192;         // G held in shared memory (FP32) up to this n
 constexpr int SUB_NMIN = 48;             // smaller Grams go to the full solver (cheap there)
@@ -118,83 +121,115 @@ __device__ void sub_vec_sum(const float (&v)[SB], float* red, float* out) {
   __syncthreads();
 }
 
-// Cyclic Jacobi on the symmetric SB x SB matrix H (shared, row stride SB + 1), one warp: each
-// round rotates SB / 2 disjoint pairs (round-robin ordering), Rutishauser's rotation formulas;
-// Y accumulates the rotations (Y <- Y J). Stops after a sweep that found every off-diagonal entry
-// negligible against its diagonal pair, or after 10 sweeps.
-__device__ void sub_jacobi(float* H, float* Y, float* cs, int lane) {
+// Eigenpairs of the symmetric positive semidefinite SB x SB matrix H (shared, row stride SB + 1)
+// by one-sided (Hestenes) Jacobi, one warp in registers: lane i (and its mirror i + 16) holds
+// column i of W (initially H) and of V (initially I); each round of the round-robin ordering
+// pairs every column with one partner, whose columns come by shuffle, and rotates the pair so
+// that the two columns of W V become orthogonal (Golub & Van Loan, Matrix Computations,
+// Sec. 8.6.3, one-sided Jacobi). At convergence H V = W has orthogonal columns, so V holds the
+// eigenvectors and the column norms of W are the eigenvalues (for H positive semidefinite its
+// singular values). A pair counts as orthogonal once |w_p . w_q| <= 4e-6 |w_p| |w_q| (the FP32
+// rounding of a 16-term dot product is ~1e-6 of that bound's scale, so tighter tests only stir
+// noise; the cut and the captured energy are recomputed in FP64 afterwards). Stops after a
+// sweep that rotated nothing, or after max_sweeps. Writes the
+// eigenvectors as the columns of Y (stride SB + 1) and the eigenvalues over the diagonal of H.
+__device__ void sub_jacobi(float* H, float* Y, int lane, int max_sweeps) {
   constexpr int L = SB + 1;
+  const int i = lane & (SB - 1);
+  const int half = lane & SB;   // lanes 16..31 repeat the work of lanes 0..15
+  float w[SB], v[SB];
+#pragma unroll
+  for (int x = 0; x < SB; ++x) {
+    w[x] = H[x * L + i];
+    v[x] = x == i ? 1.f : 0.f;
+  }
+  __syncwarp();
 #pragma unroll 1
-  for (int sweep = 0; sweep < 10; ++sweep) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int rotated = 0;
 #pragma unroll 1
     for (int rnd = 0; rnd < SB - 1; ++rnd) {
-      if (lane < SB / 2) {
-        auto pos = [&](int x) { return x == 0 ? 0 : 1 + (x - 1 + rnd) % (SB - 1); };
-        const int p = pos(lane), q = pos(SB - 1 - lane);
-        const float hpp = H[p * L + p], hqq = H[q * L + q], hpq = H[p * L + q];
-        float c = 1.f, s = 0.f;
-        if (fabsf(hpq) > 1e-7f * sqrtf(fabsf(hpp * hqq)) && fabsf(hpq) > 1e-37f) {
-          const float th = (hqq - hpp) / (2.f * hpq);
-          const float t = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
-          c = rsqrtf(fmaf(t, t, 1.f));
-          s = t * c;
-          rotated = 1;
+      // position of column i in this round, and its partner (positions x and SB - 1 - x pair up)
+      const int xi = i == 0 ? 0 : 1 + (i - 1 - rnd + 2 * (SB - 1)) % (SB - 1);
+      const int xp = SB - 1 - xi;
+      const int j = xp == 0 ? 0 : 1 + (xp - 1 + rnd) % (SB - 1);
+      const int src = half | j;
+      float wo[SB], vo[SB];
+#pragma unroll
+      for (int x = 0; x < SB; ++x) {
+        wo[x] = __shfl_sync(0xffffffffu, w[x], src);
+        vo[x] = __shfl_sync(0xffffffffu, v[x], src);
+      }
+      // the same sums on both lanes of the pair (products commute, same order)
+      float nown = 0.f, noth = 0.f, dot = 0.f;
+#pragma unroll
+      for (int x = 0; x < SB; ++x) {
+        nown = fmaf(w[x], w[x], nown);
+        noth = fmaf(wo[x], wo[x], noth);
+        dot = fmaf(w[x], wo[x], dot);
+      }
+      const bool isp = i < j;
+      const float al = isp ? nown : noth, be = isp ? noth : nown;
+      if (fabsf(dot) > 4e-6f * sqrtf(al * be) && fabsf(dot) > 1e-30f) {
+        const float ze = (be - al) / (2.f * dot);
+        const float t = copysignf(1.f, ze) / (fabsf(ze) + sqrtf(fmaf(ze, ze, 1.f)));
+        const float c = rsqrtf(fmaf(t, t, 1.f));
+        const float sn = c * t;
+        // p <- c p - s q, q <- s p + c q
+#pragma unroll
+        for (int x = 0; x < SB; ++x) {
+          w[x] = isp ? fmaf(c, w[x], -sn * wo[x]) : fmaf(sn, wo[x], c * w[x]);
+          v[x] = isp ? fmaf(c, v[x], -sn * vo[x]) : fmaf(sn, vo[x], c * v[x]);
         }
-        cs[4 * lane] = c;
-        cs[4 * lane + 1] = s;
-        reinterpret_cast<int*>(cs)[4 * lane + 2] = p;
-        reinterpret_cast<int*>(cs)[4 * lane + 3] = q;
+        rotated = 1;
       }
-      __syncwarp();
-      // H <- H J (columns p, q of every row), then H <- J^T H (rows p, q), Y <- Y J
-      for (int it = lane; it < (SB / 2) * SB; it += 32) {
-        const int pr = it / SB, x = it % SB;
-        const float c = cs[4 * pr], s = cs[4 * pr + 1];
-        const int p = reinterpret_cast<const int*>(cs)[4 * pr + 2], q = reinterpret_cast<const int*>(cs)[4 * pr + 3];
-        const float hp = H[x * L + p], hq = H[x * L + q];
-        H[x * L + p] = c * hp - s * hq;
-        H[x * L + q] = s * hp + c * hq;
-        const float yp = Y[x * L + p], yq = Y[x * L + q];
-        Y[x * L + p] = c * yp - s * yq;
-        Y[x * L + q] = s * yp + c * yq;
-      }
-      __syncwarp();
-      for (int it = lane; it < (SB / 2) * SB; it += 32) {
-        const int pr = it / SB, x = it % SB;
-        const float c = cs[4 * pr], s = cs[4 * pr + 1];
-        const int p = reinterpret_cast<const int*>(cs)[4 * pr + 2], q = reinterpret_cast<const int*>(cs)[4 * pr + 3];
-        const float hp = H[p * L + x], hq = H[q * L + x];
-        H[p * L + x] = c * hp - s * hq;
-        H[q * L + x] = s * hp + c * hq;
-      }
-      __syncwarp();
     }
     if (!__any_sync(0xffffffffu, rotated)) break;
   }
+  float nn = 0.f;
+#pragma unroll
+  for (int x = 0; x < SB; ++x) nn = fmaf(w[x], w[x], nn);
+  if (lane < SB) {
+#pragma unroll
+    for (int x = 0; x < SB; ++x) Y[x * L + i] = v[x];
+    H[i * L + i] = sqrtf(nn);
+  }
+  __syncwarp();
 }
 
-// Cholesky R^T R = M of the SB x SB matrix M (shared, stride SB + 1, overwritten), one warp;
-// R upper triangular into R (stride SB + 1), rinv[c] = 1 / R(c, c). Returns false on a
-// non-positive pivot.
-__device__ bool sub_cholesky(float* M, float* R, float* rinv, int lane) {
+// Cholesky R^T R = M of the SB x SB matrix M (shared, stride SB + 1; read only), one warp in
+// registers: lane j (< SB) holds column j of the shrinking Schur complement, the pivot row of
+// each step is shuffled from its owner. R upper triangular into R (stride SB + 1),
+// rinv[c] = 1 / R(c, c). Returns false on a non-positive pivot.
+__device__ bool sub_cholesky(const float* M, float* R, float* rinv, int lane) {
   constexpr int L = SB + 1;
+  const int j = lane < SB ? lane : SB - 1;
+  float col[SB];
+#pragma unroll
+  for (int x = 0; x < SB; ++x) col[x] = M[x * L + j];
   bool ok = true;
-#pragma unroll 1
+  float rrow[SB];   // rrow[c] = R(c, j)
+#pragma unroll
   for (int c = 0; c < SB; ++c) {
-    const float dcc = M[c * L + c];
+    const float dcc = __shfl_sync(0xffffffffu, col[c], c);
     if (!(dcc > 0.f)) ok = false;
     const float rcc = ok ? sqrtf(dcc) : 1.f;
     const float ri = 1.f / rcc;
-    if (lane < SB) R[c * L + lane] = lane < c ? 0.f : (lane == c ? rcc : M[c * L + lane] * ri);
+    const float rcj = j < c ? 0.f : (j == c ? rcc : col[c] * ri);
+    rrow[c] = rcj;
     if (lane == 0) rinv[c] = ri;
-    __syncwarp();
-    for (int it = lane; it < SB * SB; it += 32) {
-      const int x = it / SB, y = it % SB;
-      if (x > c && y > c) M[x * L + y] -= R[c * L + x] * R[c * L + y];
+    // Schur complement: col[x] -= R(c, x) R(c, j) for x > c (R(c, x) from lane x)
+#pragma unroll
+    for (int x = c + 1; x < SB; ++x) {
+      const float rcx = __shfl_sync(0xffffffffu, rcj, x);
+      col[x] = fmaf(-rcx, rcj, col[x]);
     }
-    __syncwarp();
   }
+  if (lane < SB) {
+#pragma unroll
+    for (int c = 0; c < SB; ++c) R[c * L + lane] = rrow[c];
+  }
+  __syncwarp();
   return __all_sync(0xffffffffu, ok);
 }
 
@@ -227,18 +262,19 @@ __global__ void __launch_bounds__(SUB_NT, 1) k_eig_sub(Ctl* ctl, int k, SubArgs 
   float* Y = H + SB * (SB + 1);                          // SB x (SB + 1)
   float* R = Y + SB * (SB + 1);                          // SB x (SB + 1)
   float* vs = R + SB * (SB + 1);                         // [4][SB]: theta, residual^2, scale, rinv
-  float* cs = vs + 4 * SB;                               // [SB / 2][4] Jacobi rotations
   __shared__ int s_flag[4];
   __shared__ double s_tr[SUB_NW];
   const float* Gcol = gsm ? Gs : a.Gf;
 
-  // G in FP32 (shared memory or the global scratch), trace(G) in FP64
-  double trp = 0.0;
-  for (long long L = tid; L < (long long)n * n; L += SUB_NT) {
-    const double g = a.G[L];
-    if (gsm) Gs[L] = (float)g; else a.Gf[L] = (float)g;
-    if (L % (n + 1) == 0) trp += g;
+  // G in FP32 (k_gram_f32 wrote it to the global scratch; small ones are copied into shared
+  // memory), trace(G) in FP64 from its diagonal
+  const int nn = n * n;
+  if (gsm) {
+    const float4* g4 = reinterpret_cast<const float4*>(a.Gf);
+    for (int L = tid; L < nn / 4; L += SUB_NT) reinterpret_cast<float4*>(Gs)[L] = g4[L];
+    for (int L = nn / 4 * 4 + tid; L < nn; L += SUB_NT) Gs[L] = a.Gf[L];
   }
+  double trp = tid < n ? a.G[(size_t)tid * (n + 1)] : 0.0;
   trp = warp_sum(trp);
   if (lane == 0) s_tr[wid] = trp;
   if (tid == 0) { s_flag[0] = 0; s_flag[1] = 0; s_flag[2] = -1; s_flag[3] = 0; }
@@ -306,9 +342,29 @@ __global__ void __launch_bounds__(SUB_NT, 1) k_eig_sub(Ctl* ctl, int k, SubArgs 
 #pragma unroll
     for (int c = 0; c < SB; ++c) z[c] = 0.f;
     if (live) {
+      // G's column tid in groups of 16 entries, all loaded before their FMAs (G comes from L2
+      // when it does not fit in shared memory: its latency is hidden by the loads in flight)
       const float* gc = Gcol + tid;
-#pragma unroll 4
-      for (int j = 0; j < n; ++j) {
+      int j = 0;
+#pragma unroll 1
+      for (; j + 16 <= n; j += 16) {
+        float g[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) g[u] = gc[(size_t)(j + u) * n];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const float4* qj = reinterpret_cast<const float4*>(Qs + (size_t)(j + u) * SB);
+#pragma unroll
+          for (int c4 = 0; c4 < SB / 4; ++c4) {
+            const float4 v = qj[c4];
+            z[4 * c4] = fmaf(g[u], v.x, z[4 * c4]);
+            z[4 * c4 + 1] = fmaf(g[u], v.y, z[4 * c4 + 1]);
+            z[4 * c4 + 2] = fmaf(g[u], v.z, z[4 * c4 + 2]);
+            z[4 * c4 + 3] = fmaf(g[u], v.w, z[4 * c4 + 3]);
+          }
+        }
+      }
+      for (; j < n; ++j) {
         const float g = gc[(size_t)j * n];
         const float4* qj = reinterpret_cast<const float4*>(Qs + (size_t)j * SB);
 #pragma unroll
@@ -329,9 +385,9 @@ __global__ void __launch_bounds__(SUB_NT, 1) k_eig_sub(Ctl* ctl, int k, SubArgs 
         H[x * (SB + 1) + y] = 0.5f * (Y[x * SB + y] + Y[y * SB + x]);
       }
       __syncwarp();
-      for (int it2 = lane; it2 < SB * SB; it2 += 32) R[(it2 / SB) * (SB + 1) + it2 % SB] = (it2 / SB == it2 % SB) ? 1.f : 0.f;
-      __syncwarp();
-      sub_jacobi(H, R, cs, lane);
+      // (from the second iteration on the basis holds the previous Ritz vectors: H is nearly
+      // diagonal and the sweeps stop early)
+      sub_jacobi(H, R, lane, 10);
       // sort the Ritz values descending (rank of each, ties by index); Y = eigenvectors sorted
       float th = lane < SB ? H[lane * (SB + 1) + lane] : 0.f;
       int rk = 0;
@@ -544,6 +600,15 @@ size_t eig_sub_smem(int n) {
   return sizeof(float) * ((gsm ? sub_gs_floats(n) : 0) + (size_t)n * SB + SUB_NW * 64 + 3 * SB * (SB + 1) + 4 * SB + 2 * SB);
 }
 
+// G (FP64) -> Gf (FP32) over all SMs for the subspace iteration (only when mode k grew).
+__global__ void k_gram_f32(const Ctl* ctl, int k, const double* __restrict__ G, float* __restrict__ Gf) {
+  if (ctl->status || !ctl->grew[k]) return;
+  const int n = ctl->n[k];
+  const int nn = n * n;
+  for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < nn; L += gridDim.x * blockDim.x)
+    Gf[L] = (float)G[L];
+}
+
 cudaError_t launch_eig_sub(Ctl* ctl, int k, const double* G, void* Gf, double* W, int mcap,
                            double* part, int n, cudaStream_t st) {
   // the attribute is raised to the largest size any n needs (n = SUB_GS_NMAX, G in shared
@@ -558,6 +623,7 @@ cudaError_t launch_eig_sub(Ctl* ctl, int k, const double* G, void* Gf, double* W
   }
   const size_t sm = eig_sub_smem(n);
   SubArgs a{G, reinterpret_cast<float*>(Gf), W, mcap};
+  k_gram_f32<<<std::min(152, std::max(1, (n * n + 1023) / 1024)), 256, 0, st>>>(ctl, k, G, a.Gf);
   k_eig_sub<<<1, SUB_NT, sm, st>>>(ctl, k, a);
   const int nb = std::min(REF_MAXB, std::max(1, (n + 3) / 4));
   k_eig_refine<<<nb, REF_NT, 0, st>>>(ctl, k, G, W, part, mcap, 0);
