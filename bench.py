@@ -38,6 +38,10 @@ STREAMS = {
                    name="advected-blob stream 384x384x256x4 fp32 slices (80 blobs, 604 MB per slice)"),
     "stream192": dict(grid=(192, 192, 96), nvar=12, nblobs=40, seed=2, tau=1e-4,
                       name="advected-blob stream 192x192x96x12 fp32 slices (40 blobs, 170 MB per slice)"),
+    # the 384 x 384 x 256 x 4 stream cut to 64 planes: the small case the kernel captures run on
+    # (151 MB slices, above L2, a few GB on the device)
+    "stream64": dict(grid=(384, 384, 64), nvar=4, nblobs=80, seed=5, tau=1e-4,
+                     name="advected-blob stream 384x384x64x4 fp32 slices (80 blobs, 151 MB per slice)"),
 }
 DELTA_DEC = 3e-2    # relative distance of a near-cutoff decision from eps^2 (mixed form)
 PHASES = ["mode-1 projection + residual (k_tc_pass16)", "k_ttm_proj (modes 2..d-1)", "growth (gram/eig/append)",
@@ -805,7 +809,7 @@ def run_sine(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="stream",
-                    choices=["stream", "stream192", "adjoint", "batched", "sine"])
+                    choices=["stream", "stream192", "stream64", "adjoint", "batched", "sine"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
