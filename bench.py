@@ -383,6 +383,15 @@ def run_ours(args):
     if KE:
         t_e = T_timed + KP
         host = [slices[t].cpu().pin_memory() for t in range(t_e, t_e + KE)]
+        # each pinned buffer goes to the device once before the timed region: the first
+        # device access to freshly pinned pages on this host runs at about half the link's rate
+        # (the pages are mapped for the GPU on first use), which a streaming application's reused
+        # ring of pinned buffers pays once
+        scratch = torch.empty_like(slices[0])
+        for h in host:
+            scratch.copy_(h, non_blocking=True)
+        torch.cuda.synchronize()
+        del scratch
         res = torch.zeros((KE, 2), dtype=torch.float64).pin_memory()
         # the first host-input call allocates the staging buffers: outside the timed region
         ts.update_host(host[0])
@@ -410,6 +419,7 @@ def run_ours(args):
                "d2h_bytes_per_step": 16, "steps": n_e,
                "api": "tucker_stream_update_host + tucker_error_norm_async",
                "pipeline": "H2D of slice t+1 (library copy stream) overlaps update t",
+               "host_buffers": "one pinned buffer per timed slice, each copied to the device once before the timed region (first-use page mapping, as a reused ring pays once)",
                "ms_per_step": ms2 / n_e}
         del host
     ts.close()

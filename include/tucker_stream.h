@@ -263,6 +263,15 @@ typedef struct {
 } tucker_replay;
 tucker_status tucker_replay_next(tucker_state* s, const tucker_replay* r);
 
+/* Test hook of the bounded waits: the next update's mode-1 tensor-core pass (mixed form, FP32
+ * slices, n_1 <= 384) withholds its loads, so every wait of the kernel's consumers gives up after
+ * its time limit (1 s of wall time). The kernel then latches TUCKER_ETIMEOUT and ends normally:
+ * the update's later kernels return at once, the next synchronizing call returns ETIMEOUT, the
+ * state is unusable afterwards (ESTATE) and the CUDA context stays usable. No fault, trap or
+ * unbounded wait is involved. Synchronizes the state's last stream.
+ * Errors: EINVAL (NULL), ESTATE, ECUDA. */
+tucker_status tucker_test_stall_next(tucker_state* s);
+
 /* Re-compression of the streamed decomposition: the batch ST-HOSVD (Alg. 2) run again on the
  * current Tucker representation X^ = C x_1 U_1 ... x_d U_d, so that ranks the per-slice updates
  * over-estimated come down. Since the factors are orthonormal, Alg. 2 on X^ equals Alg. 2 on the

@@ -30,7 +30,8 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy",
            "tucker_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
            "tucker_get_launch_plan", "tucker_stream_update_host", "tucker_get_step_log",
-           "tucker_replay_next", "tucker_stream_update_batched", "tucker_recompress"]
+           "tucker_replay_next", "tucker_stream_update_batched", "tucker_recompress",
+           "tucker_test_stall_next"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -123,6 +124,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_copy_core.argtypes = [vp, vp]
     lib.tucker_copy_sv.argtypes = [vp, vp, vp]
     lib.tucker_recompress.argtypes = [vp, ctypes.c_double, vp, ctypes.POINTER(RecompressInfo)]
+    lib.tucker_test_stall_next.argtypes = [vp]
     lib.tucker_last_error.argtypes = [vp]
     lib.tucker_last_error.restype = ctypes.c_char_p
     lib.tucker_destroy.argtypes = [vp]
@@ -162,7 +164,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                  "tucker_stream_update_host", "tucker_reconstruct",
                  "tucker_reconstruct_noalloc", "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
                  "tucker_get_step_log", "tucker_replay_next", "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv",
-                 "tucker_recompress"):
+                 "tucker_recompress", "tucker_test_stall_next"):
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -292,6 +294,12 @@ def tucker_copy_core(h: int, dst_ptr: int) -> None:
 
 def tucker_copy_sv(h: int, S_ptr: int, V_ptr: int) -> None:
     _check(load_library().tucker_copy_sv(h, ctypes.c_void_p(S_ptr), ctypes.c_void_p(V_ptr)), h)
+
+
+def tucker_test_stall_next(h: int) -> None:
+    """Test hook: the next update's mode-1 tensor-core pass withholds its loads (its waits run
+    out, TUCKER_ETIMEOUT latches)."""
+    _check(load_library().tucker_test_stall_next(h), h)
 
 
 def tucker_recompress(h: int, d: int, tau_total: float, stream: int = 0) -> dict:

@@ -1341,6 +1341,16 @@ tucker_status tucker_replay_next(tucker_state* s, const tucker_replay* r) {
   return TUCKER_OK;
 }
 
+tucker_status tucker_test_stall_next(tucker_state* s) {
+  if (!s) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  const int one = 1;
+  CK(cudaMemcpyAsync(reinterpret_cast<unsigned char*>(s->ctl) + offsetof(Ctl, test_stall), &one,
+                     sizeof(int), cudaMemcpyHostToDevice, s->last_stream));
+  CK(cudaStreamSynchronize(s->last_stream));
+  return TUCKER_OK;
+}
+
 tucker_status tucker_recompress(tucker_state* s, double tau_total, void* stream,
                                 tucker_recompress_info* info) {
   if (!s || !(tau_total > 0.0)) return TUCKER_EINVAL;

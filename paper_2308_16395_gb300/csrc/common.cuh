@@ -92,6 +92,9 @@ struct Ctl {
   // the update's pass A (float bits, atomicMax; reset by k_begin_update) ----
   int x16e[TK_MAXD];
   unsigned xmax[TK_MAXD];
+  // ---- test hook: nonzero makes the next mode-1 tensor-core pass A withhold its loads, so that
+  // every wait of its consumers runs out (the bounded-wait path; see tucker_test_stall_next) ----
+  int test_stall;
 };
 
 // FP16 scale window: a pass's input scaled by 2^sigma must have its largest |x| in

@@ -214,8 +214,11 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
   const uint32_t tmem = *tmem_slot;
   const long long myt = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
+  // test hook: the producer issues nothing, so the consumers' waits run out (1 s), the CTA
+  // latches TUCKER_ETIMEOUT and ends normally
+  const bool stall = a.track && k == 0 && ctl->test_stall != 0;
   if (warp == 0) {
-    if (lane == 0) {
+    if (lane == 0 && !stall) {
       // ---------------- TMA producer ----------------
       if (xb < 0 && a.mYg) tensormap_acquire(a.mYg);
       tma_prefetch(mX);
