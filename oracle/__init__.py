@@ -18,6 +18,8 @@ from .tucker_oracle import (  # noqa: F401
     init_stream,
     stream_update,
     recompress,
+    orthogonality_error,
+    restore_orthogonality,
     reconstruct,
     reconstruct_slices,
 )

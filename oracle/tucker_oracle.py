@@ -390,3 +390,32 @@ def recompress(st: StreamState, tau_total: float) -> StreamState:
     st.err2 = (b + math.sqrt(disc)) ** 2
     st.log.append(dict(kind="recompress", ranks=st.ranks, eps=eps, discarded=disc))
     return st
+
+
+# ---------------------------------------------------------------------------------------------
+# Orthogonality of the streaming factor (the loss the paper flags in the incremental SVD)
+# ---------------------------------------------------------------------------------------------
+
+def orthogonality_error(U: np.ndarray) -> float:
+    """||U^T U - I||_F: how far a factor's columns are from orthonormal. Sec. 3.1 remarks that
+    forming the new left singular vectors as a product U' U'' (Alg. 3) may lose orthogonality over
+    many incremental updates."""
+    r = U.shape[1]
+    return float(np.linalg.norm(U.T @ U - np.eye(r)))
+
+
+def restore_orthogonality(st: StreamState) -> float:
+    """Replace the streaming factor U_d by its nearest matrix with orthonormal columns (the polar
+    factor W Z^T of U_d = W Sigma Z^T, from numpy's SVD), in place, keeping C, S, V (Assumption 1
+    is untouched). The reconstruction changes by (U_d' - U_d) C_(d), of norm ||(U_d' - U_d) S||_F
+    since V_(d) is row-orthonormal; that amount is added to the running bound (triangle
+    inequality). Returns it."""
+    U = st.Us[-1]
+    W, _, Zt = np.linalg.svd(U, full_matrices=False)
+    Un = W @ Zt
+    change = float(np.linalg.norm((Un - U) * st.S[None, :]))
+    st.Us[-1] = Un
+    b = math.sqrt(max(st.err2, 0.0))
+    st.err2 = (b + change) ** 2
+    st.log.append(dict(kind="restore_orthogonality", change=change))
+    return change
