@@ -263,6 +263,23 @@ typedef struct {
 } tucker_replay;
 tucker_status tucker_replay_next(tucker_state* s, const tucker_replay* r);
 
+/* Orthogonality of the factors: out_host[k] = ||U_k^T U_k - I||_F for k = 0..d-1 (U_d the
+ * streaming factor, n_d x r_d), computed in FP64 on the device. Sec. 3.1 remarks that forming the
+ * new left singular vectors of the incremental SVD (Alg. 3) as a product U' U'' may lose
+ * orthogonality over many updates; this measures it. Synchronizes.
+ * Errors: EINVAL (NULL), ENOMEM, ESTATE, ECUDA. */
+tucker_status tucker_orthogonality_error(tucker_state* s, double* out_host);
+
+/* Restores the orthonormality of the streaming factor: U_d is replaced by its polar factor (the
+ * nearest matrix with orthonormal columns), computed by two Newton-Schulz steps
+ * U <- U (3 I - U^T U) / 2 in FP64 on the device. C, S and V are kept (Assumption 1 is
+ * untouched); the reconstruction moves by (U_d' - U_d) C_(d), whose norm ||(U_d' - U_d) S||_F
+ * is added to the running error bound (triangle inequality) and returned in *change_host (may be
+ * NULL). Meant for long streams, every few thousand updates or when tucker_orthogonality_error
+ * reports a deviation well above rounding. Allocates and frees temporary device memory.
+ * Synchronizes. Errors: EINVAL (NULL), ENOMEM, ESTATE, ECUDA. */
+tucker_status tucker_restore_orthogonality(tucker_state* s, void* stream, double* change_host);
+
 /* Test hook of the bounded waits: the next update's mode-1 tensor-core pass (mixed form, FP32
  * slices, n_1 <= 384) withholds its loads, so every wait of the kernel's consumers gives up after
  * its time limit (1 s of wall time). The kernel then latches TUCKER_ETIMEOUT and ends normally:

@@ -31,7 +31,7 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
            "tucker_get_launch_plan", "tucker_stream_update_host", "tucker_get_step_log",
            "tucker_replay_next", "tucker_stream_update_batched", "tucker_recompress",
-           "tucker_test_stall_next"]
+           "tucker_test_stall_next", "tucker_orthogonality_error", "tucker_restore_orthogonality"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
@@ -125,6 +125,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_copy_sv.argtypes = [vp, vp, vp]
     lib.tucker_recompress.argtypes = [vp, ctypes.c_double, vp, ctypes.POINTER(RecompressInfo)]
     lib.tucker_test_stall_next.argtypes = [vp]
+    lib.tucker_orthogonality_error.argtypes = [vp, vp]
+    lib.tucker_restore_orthogonality.argtypes = [vp, vp, vp]
     lib.tucker_last_error.argtypes = [vp]
     lib.tucker_last_error.restype = ctypes.c_char_p
     lib.tucker_destroy.argtypes = [vp]
@@ -164,7 +166,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                  "tucker_stream_update_host", "tucker_reconstruct",
                  "tucker_reconstruct_noalloc", "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
                  "tucker_get_step_log", "tucker_replay_next", "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv",
-                 "tucker_recompress", "tucker_test_stall_next"):
+                 "tucker_recompress", "tucker_test_stall_next", "tucker_orthogonality_error",
+                 "tucker_restore_orthogonality"):
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -294,6 +297,20 @@ def tucker_copy_core(h: int, dst_ptr: int) -> None:
 
 def tucker_copy_sv(h: int, S_ptr: int, V_ptr: int) -> None:
     _check(load_library().tucker_copy_sv(h, ctypes.c_void_p(S_ptr), ctypes.c_void_p(V_ptr)), h)
+
+
+def tucker_orthogonality_error(h: int, d: int) -> list:
+    """||U_k^T U_k - I||_F for every factor (FP64, on the device)."""
+    out = (ctypes.c_double * d)()
+    _check(load_library().tucker_orthogonality_error(h, out), h)
+    return [float(v) for v in out]
+
+
+def tucker_restore_orthogonality(h: int, stream: int = 0) -> float:
+    """Replace U_d by its polar factor; returns the reconstruction change added to the bound."""
+    ch = ctypes.c_double()
+    _check(load_library().tucker_restore_orthogonality(h, ctypes.c_void_p(stream), ctypes.byref(ch)), h)
+    return ch.value
 
 
 def tucker_test_stall_next(h: int) -> None:
@@ -553,6 +570,14 @@ class TuckerStream:
     def replay_next(self, grow, augment: int = -1) -> None:
         """Test hook: force the next update's decisions (see tucker_replay_next)."""
         tucker_replay_next(self.h, grow, augment)
+
+    def orthogonality_error(self) -> list:
+        """||U_k^T U_k - I||_F for every factor (see tucker_orthogonality_error)."""
+        return tucker_orthogonality_error(self.h, self.d)
+
+    def restore_orthogonality(self) -> float:
+        """Polar factor of U_d (see tucker_restore_orthogonality)."""
+        return tucker_restore_orthogonality(self.h, self._sp())
 
     def recompress(self, tau_total: float) -> dict:
         """Re-compress within tau_total ||X|| (see tucker_recompress)."""

@@ -1341,6 +1341,92 @@ tucker_status tucker_replay_next(tucker_state* s, const tucker_replay* r) {
   return TUCKER_OK;
 }
 
+// ||G - I||_F of G = U^T U for a factor whose element (t, c) sits at U[t ut + c uc].
+static tucker_status gram_dev(tucker_state* s, const double* U, long long ut, long long uc, int rows,
+                              int r, double* G, double* part, double* out, cudaStream_t st) {
+  CK(launch_gemm64(U, uc, ut, r, rows, U, ut, uc, r, G, 1, r, nullptr, st));
+  CK(launch_frob_minus_i(G, r, part, 64, st));
+  double hp[64];
+  CK(cudaMemcpyAsync(hp, part, sizeof(hp), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double a = 0.0;
+  for (double v : hp) a += v;
+  *out = std::sqrt(a);
+  return TUCKER_OK;
+}
+
+tucker_status tucker_orthogonality_error(tucker_state* s, double* out) {
+  if (!s || !out) return TUCKER_EINVAL;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  const Ctl& c = *s->hctl;
+  const cudaStream_t st = s->last_stream;
+  int rmax = 1;
+  for (int k = 0; k < s->d; ++k) rmax = std::max(rmax, c.r[k]);
+  double *G = nullptr, *part = nullptr;
+  if (cudaMalloc(&G, sizeof(double) * (size_t)rmax * rmax) != cudaSuccess) return TUCKER_ENOMEM;
+  if (cudaMalloc(&part, sizeof(double) * 64) != cudaSuccess) { cudaFree(G); return TUCKER_ENOMEM; }
+  for (int k = 0; k < s->d && rc == TUCKER_OK; ++k) {
+    if (k < s->d - 1) rc = gram_dev(s, s->U[k], 1, s->n[k], s->n[k], c.r[k], G, part, &out[k], st);
+    else rc = gram_dev(s, s->Ud[c.ubuf], s->ldc, 1, c.nd, c.r[k], G, part, &out[k], st);
+  }
+  cudaFree(G);
+  cudaFree(part);
+  return rc;
+}
+
+tucker_status tucker_restore_orthogonality(tucker_state* s, void* stream, double* change) {
+  if (!s) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  tucker_status rc = sync_ctl(s);
+  if (rc != TUCKER_OK) return rc;
+  Ctl& h = *s->hctl;
+  const int rd = h.r[s->d - 1], nd = h.nd, ld = s->ldc;
+  double* Ud = s->Ud[h.ubuf];
+  const size_t ubytes = sizeof(double) * (size_t)nd * ld;
+  double *U0 = nullptr, *Un = nullptr, *G = nullptr, *T = nullptr, *part = nullptr;
+  auto cleanup = [&]() { cudaFree(U0); cudaFree(Un); cudaFree(G); cudaFree(T); cudaFree(part); };
+  if (cudaMalloc(&U0, ubytes) != cudaSuccess || cudaMalloc(&Un, ubytes) != cudaSuccess ||
+      cudaMalloc(&G, sizeof(double) * rd * rd) != cudaSuccess ||
+      cudaMalloc(&T, sizeof(double) * rd * rd) != cudaSuccess ||
+      cudaMalloc(&part, sizeof(double) * 64) != cudaSuccess) {
+    cleanup();
+    return TUCKER_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(U0, Ud, ubytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Un, Ud, ubytes, cudaMemcpyDeviceToDevice, st);
+  // two Newton-Schulz steps U <- U (3 I - U^T U) / 2 towards the polar factor (quadratic once
+  // ||U^T U - I|| < 1; the streaming factor's deviation is at rounding level)
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+    e = launch_gemm64(Ud, 1, ld, rd, nd, Ud, ld, 1, rd, G, 1, rd, nullptr, st);
+    if (e == cudaSuccess) e = launch_ns_matrix(G, rd, T, st);
+    if (e == cudaSuccess) e = launch_gemm64(Ud, ld, 1, nd, rd, T, 1, rd, rd, Un, ld, 1, nullptr, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Ud, Un, ubytes, cudaMemcpyDeviceToDevice, st);
+  }
+  double hp[64];
+  if (e == cudaSuccess) e = launch_change_norm(Ud, U0, nd, rd, ld, s->S, part, 64, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hp, part, sizeof(hp), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cleanup();
+    set_err(s, "tucker_restore_orthogonality: %s", cudaGetErrorString(e), 0);
+    return TUCKER_ECUDA;
+  }
+  double c2 = 0.0;
+  for (double v : hp) c2 += v;
+  const double dchange = std::sqrt(c2);
+  const double b = std::sqrt(std::max(h.err2, 0.0));
+  h.err2 = (b + dchange) * (b + dchange);
+  e = cudaMemcpyAsync(s->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) CK(e);
+  if (change) *change = dchange;
+  return TUCKER_OK;
+}
+
 tucker_status tucker_test_stall_next(tucker_state* s) {
   if (!s) return TUCKER_EINVAL;
   if (!usable(s)) return TUCKER_ESTATE;

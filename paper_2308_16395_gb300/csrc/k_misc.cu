@@ -188,15 +188,15 @@ namespace tk {
 // out[i * os_i + c * os_c]; outw (may be NULL) receives the same values in FP32. One thread per
 // entry (rows x cols is at most n_k x r_k).
 __global__ void k_small_gemm(const double* __restrict__ A, long long as_i, long long as_j,
-                             int rows, int inner, const double* __restrict__ B, int ldb, int cols,
-                             double* __restrict__ out, long long os_i, long long os_c,
-                             float* __restrict__ outw) {
+                             int rows, int inner, const double* __restrict__ B, long long bs_j,
+                             long long bs_c, int cols, double* __restrict__ out, long long os_i,
+                             long long os_c, float* __restrict__ outw) {
   const long long total = (long long)rows * cols;
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
        L += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(L % rows), c = (int)(L / rows);
     double s = 0.0;
-    for (int j = 0; j < inner; ++j) s = fma(A[i * as_i + j * as_j], B[(long long)c * ldb + j], s);
+    for (int j = 0; j < inner; ++j) s = fma(A[i * as_i + j * as_j], B[c * bs_c + j * bs_j], s);
     out[i * os_i + c * os_c] = s;
     if (outw) outw[i * os_i + c * os_c] = (float)s;
   }
@@ -205,10 +205,66 @@ __global__ void k_small_gemm(const double* __restrict__ A, long long as_i, long 
 cudaError_t launch_small_gemm(const double* A, long long as_i, long long as_j, int rows, int inner,
                               const double* B, int ldb, int cols, double* out, long long os_i,
                               long long os_c, float* outw, cudaStream_t st) {
+  return launch_gemm64(A, as_i, as_j, rows, inner, B, 1, ldb, cols, out, os_i, os_c, outw, st);
+}
+
+cudaError_t launch_gemm64(const double* A, long long as_i, long long as_j, int rows, int inner,
+                          const double* B, long long bs_j, long long bs_c, int cols, double* out,
+                          long long os_i, long long os_c, float* outw, cudaStream_t st) {
   const long long total = (long long)rows * cols;
   int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 4);
   if (grid < 1) grid = 1;
-  k_small_gemm<<<grid, 256, 0, st>>>(A, as_i, as_j, rows, inner, B, ldb, cols, out, os_i, os_c, outw);
+  k_small_gemm<<<grid, 256, 0, st>>>(A, as_i, as_j, rows, inner, B, bs_j, bs_c, cols, out, os_i,
+                                     os_c, outw);
+  return cudaGetLastError();
+}
+
+// T = (3 I - G) / 2 (r x r, column-major): one Newton-Schulz step towards the polar factor.
+__global__ void k_ns_matrix(const double* __restrict__ G, int r, double* __restrict__ T) {
+  for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < r * r; L += gridDim.x * blockDim.x)
+    T[L] = (L % (r + 1) == 0 ? 1.5 : 0.0) - 0.5 * G[L];
+}
+
+// part[b]: block b's share of ||G - I||_F^2 (G r x r column-major).
+__global__ void k_frob_minus_i(const double* __restrict__ G, int r, double* __restrict__ part) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < r * r; L += gridDim.x * blockDim.x) {
+    const double v = G[L] - (L % (r + 1) == 0 ? 1.0 : 0.0);
+    a = fma(v, v, a);
+  }
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+// part[b]: block b's share of sum_t sum_c ((U1 - U0)(t, c) S(c))^2, U row-major rows x ld.
+__global__ void k_change_norm(const double* __restrict__ U1, const double* __restrict__ U0,
+                              int rows, int r, int ld, const double* __restrict__ S,
+                              double* __restrict__ part) {
+  __shared__ double red[32];
+  double a = 0.0;
+  const long long total = (long long)rows * r;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < total;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(L / r), c = (int)(L % r);
+    const double v = (U1[(long long)t * ld + c] - U0[(long long)t * ld + c]) * S[c];
+    a = fma(v, v, a);
+  }
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+cudaError_t launch_ns_matrix(const double* G, int r, double* T, cudaStream_t st) {
+  k_ns_matrix<<<std::max(1, std::min(256, (r * r + 255) / 256)), 256, 0, st>>>(G, r, T);
+  return cudaGetLastError();
+}
+cudaError_t launch_frob_minus_i(const double* G, int r, double* part, int nparts, cudaStream_t st) {
+  k_frob_minus_i<<<nparts, 256, 0, st>>>(G, r, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_change_norm(const double* U1, const double* U0, int rows, int r, int ld,
+                               const double* S, double* part, int nparts, cudaStream_t st) {
+  k_change_norm<<<nparts, 256, 0, st>>>(U1, U0, rows, r, ld, S, part);
   return cudaGetLastError();
 }
 

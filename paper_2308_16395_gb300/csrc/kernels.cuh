@@ -140,6 +140,15 @@ cudaError_t launch_init_finish(Ctl* ctl, const void* Ccol, long long R, int rd, 
 template <typename TW>
 cudaError_t launch_init_cv64(const double* C64, long long R, int rd, const double* lam, void* C,
                              void* V, int ldc, cudaStream_t st);
+// out(i, c) = sum_j A[i as_i + j as_j] B[j bs_j + c bs_c] (FP64), written at i os_i + c os_c, and
+// in FP32 to outw at the same offsets when outw is not NULL.
+cudaError_t launch_gemm64(const double* A, long long as_i, long long as_j, int rows, int inner,
+                          const double* B, long long bs_j, long long bs_c, int cols, double* out,
+                          long long os_i, long long os_c, float* outw, cudaStream_t st);
+cudaError_t launch_ns_matrix(const double* G, int r, double* T, cudaStream_t st);
+cudaError_t launch_frob_minus_i(const double* G, int r, double* part, int nparts, cudaStream_t st);
+cudaError_t launch_change_norm(const double* U1, const double* U0, int rows, int r, int ld,
+                               const double* S, double* part, int nparts, cudaStream_t st);
 cudaError_t launch_small_gemm(const double* A, long long as_i, long long as_j, int rows, int inner,
                               const double* B, int ldb, int cols, double* out, long long os_i,
                               long long os_c, float* outw, cudaStream_t st);
