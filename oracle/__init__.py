@@ -17,6 +17,7 @@ from .tucker_oracle import (  # noqa: F401
     StreamState,
     init_stream,
     stream_update,
+    block_update,
     recompress,
     orthogonality_error,
     restore_orthogonality,

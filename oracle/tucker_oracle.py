@@ -419,3 +419,59 @@ def restore_orthogonality(st: StreamState) -> float:
     st.err2 = (b + change) ** 2
     st.log.append(dict(kind="restore_orthogonality", change=change))
     return change
+
+
+# ---------------------------------------------------------------------------------------------
+# Several slices at once (the block update the Conclusions name as future work)
+# ---------------------------------------------------------------------------------------------
+
+def block_update(st: StreamState, Yb: np.ndarray) -> StreamState:
+    """Assimilate B slices Yb (n_1 x ... x n_{d-1} x B) at once, in place.
+
+    The spatial modes see the block as one tensor with a trailing mode of size B: Alg. 4 for each
+    k with eps = tau ||Yb|| / sqrt(d) (Alg. 5's rule applied to the block), so a mode's residual
+    Gram, rank cut and augmentation cover all B slices together. The streaming mode then takes
+    the B projected slices as B new rows, one incremental SVD step (Alg. 3) each, in slice order,
+    with the streaming share of the block's budget split evenly: eps_r = eps / sqrt(B) per row.
+    The block's added squared error is then at most (d - 1) eps^2 + B eps_r^2 = tau^2 ||Yb||^2,
+    Alg. 5's guarantee for the block (reading of the future-work sentence; B = 1 is Alg. 5).
+    """
+    d = st.d
+    B = Yb.shape[-1]
+    y2 = float(np.sum(Yb * Yb))
+    eps = st.tau * math.sqrt(y2) / math.sqrt(d)
+    C = st.C
+    D = Yb                                        # D*_0: the block, n_1 x ... x n_{d-1} x B
+    V = st.V
+    Us = list(st.Us)
+    modes = []
+    for k in range(d - 1):
+        Us[k], C, D, V, info = non_streaming_update(k, Us[k], C, D, V, eps)
+        modes.append(info)
+    eps_r = eps / math.sqrt(B)
+    spatial = C.shape[:-1]
+    S = st.S
+    err = sum(m.discarded for m in modes)
+    rows = []
+    for b in range(B):
+        dvec = D[..., b].reshape(-1, order="F")  # slice b of D*_{d-1}
+        rd = C.shape[-1]
+        Vmat = V.reshape(-1, rd, order="F")
+        Ud = Us[-1]
+        nd = Ud.shape[0]
+        Ut, St, Vt, info = isvd(Ud, S, Vmat, dvec, eps_r, st.eps_m)
+        rt = St.shape[0]
+        M = Ut[:nd, :].T @ Ud                     # U~_d(1:n_d,:)^T U_d            (R7)
+        Cd = M @ unfold(C, d - 1) + np.outer(Ut[nd, :], dvec)
+        C = fold(Cd, d - 1, spatial + (rt,))
+        Us[-1] = Ut
+        S = St
+        V = Vt.reshape(spatial + (rt,), order="F")
+        err += (0.0 if info.augmented else info.q ** 2) + info.dropped
+        rows.append(info)
+    st.C, st.Us, st.S, st.V = C, Us, S, V
+    st.err2 += err
+    st.data_norm2 += y2
+    st.log.append(dict(kind="block", eps=eps, eps_row=eps_r, y2=y2, modes=modes, rows=rows,
+                       ranks=st.ranks, added=err))
+    return st
