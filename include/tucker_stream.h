@@ -71,7 +71,8 @@ typedef struct {
   int32_t ndim;                         /* d, 2..8 (spatial modes + the streaming mode) */
   int32_t dtype;                        /* TUCKER_F32 or TUCKER_F64: element type of slices */
   int32_t precision;                    /* TUCKER_PREC_FP64 or TUCKER_PREC_MIXED */
-  int32_t reserved0;
+  int32_t block_cap;                    /* most slices one tucker_stream_update_block call takes
+                                           (0 = 1); the slice buffers scale with it */
   int64_t n[TUCKER_MAX_MODES];          /* n_1..n_{d-1}; entries >= d-1 ignored */
   int64_t rank_cap[TUCKER_MAX_MODES];   /* capacity of r_1..r_d (0 = default: n_k for spatial
                                            modes, 256 for the streaming mode); r_d cap <= 512,
@@ -279,6 +280,23 @@ tucker_status tucker_orthogonality_error(tucker_state* s, double* out_host);
  * reports a deviation well above rounding. Allocates and frees temporary device memory.
  * Synchronizes. Errors: EINVAL (NULL), ENOMEM, ESTATE, ECUDA. */
 tucker_status tucker_restore_orthogonality(tucker_state* s, void* stream, double* change_host);
+
+/* Block update: assimilate nslices slices at once (Y_dev: nslices slices, each n_1 x ... x n_{d-1}
+ * column-major, stored one after the other; device memory, caller-owned, read during the call's
+ * kernels). The paper names processing several slices at once as future work (Conclusions).
+ * The spatial modes take the block as one tensor with a trailing mode of size nslices: Alg. 4
+ * for each mode with eps = tau ||Y_block|| / sqrt(d), so one residual pass, one Gram and one
+ * rank cut per mode cover the whole block. The streaming mode then takes the nslices projected
+ * slices as new rows, one incremental-SVD step (Alg. 3) each in slice order, with the tolerance
+ * eps / sqrt(nslices) per row: the block adds at most (d - 1) eps^2 + nslices eps^2 / nslices =
+ * tau^2 ||Y_block||^2 to the squared error, Alg. 5's guarantee for the block. nslices = 1 is
+ * tucker_stream_update. n_d grows by nslices; the step log gets one record per slice (the
+ * block's spatial decisions and norm in the first). Runs launch by launch. nslices must not
+ * exceed the configuration's block_cap.
+ * Errors: EINVAL (NULL, nslices < 1 or above block_cap), ESTATE, ECUDA; device errors
+ * (ECAPACITY, ENUMERIC, ETIMEOUT) latch and surface at the next synchronizing call. */
+tucker_status tucker_stream_update_block(tucker_state* s, const void* Y_dev, int32_t nslices,
+                                         void* stream);
 
 /* Test hook of the bounded waits: the next update's mode-1 tensor-core pass (mixed form, FP32
  * slices, n_1 <= 384) withholds its loads, so every wait of the kernel's consumers gives up after

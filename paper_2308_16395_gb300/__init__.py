@@ -31,14 +31,15 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
            "tucker_get_launch_plan", "tucker_stream_update_host", "tucker_get_step_log",
            "tucker_replay_next", "tucker_stream_update_batched", "tucker_recompress",
-           "tucker_test_stall_next", "tucker_orthogonality_error", "tucker_restore_orthogonality"]
+           "tucker_test_stall_next", "tucker_orthogonality_error", "tucker_restore_orthogonality",
+           "tucker_stream_update_block"]
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024   # TUCKER_NOALLOC_SCRATCH_BYTES
 NPHASES = 6
 
 
 class TuckerConfig(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int32), ("dtype", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("n", ctypes.c_int64 * MAX_MODES),
+                ("block_cap", ctypes.c_int32), ("n", ctypes.c_int64 * MAX_MODES),
                 ("rank_cap", ctypes.c_int64 * MAX_MODES), ("steps_cap", ctypes.c_int64),
                 ("core_cap", ctypes.c_int64), ("tau", ctypes.c_double), ("eps_m", ctypes.c_double)]
 
@@ -113,6 +114,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_init_sthosvd.argtypes = [ctypes.POINTER(TuckerConfig), vp, i64, vp, ctypes.POINTER(vp)]
     lib.tucker_stream_update.argtypes = [vp, vp, vp]
     lib.tucker_stream_update_host.argtypes = [vp, vp, vp]
+    lib.tucker_stream_update_block.argtypes = [vp, vp, ctypes.c_int32, vp]
     lib.tucker_reconstruct.argtypes = [vp, i64, i64, vp, vp]
     lib.tucker_reconstruct_noalloc.argtypes = [vp, i64, i64, vp, vp]
     lib.tucker_error_norm.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
@@ -167,7 +169,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                  "tucker_reconstruct_noalloc", "tucker_error_norm", "tucker_get_ranks", "tucker_get_step_info",
                  "tucker_get_step_log", "tucker_replay_next", "tucker_copy_factor", "tucker_copy_core", "tucker_copy_sv",
                  "tucker_recompress", "tucker_test_stall_next", "tucker_orthogonality_error",
-                 "tucker_restore_orthogonality"):
+                 "tucker_restore_orthogonality", "tucker_stream_update_block"):
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -183,9 +185,10 @@ def _check(code: int, handle=None):
 
 
 def make_config(n, tau, *, dtype="f32", precision="mixed", rank_cap=None, steps_cap=0,
-                core_cap=0, eps_m=0.0) -> TuckerConfig:
+                core_cap=0, eps_m=0.0, block_cap=0) -> TuckerConfig:
     """n: spatial sizes n_1..n_{d-1}; rank_cap: d entries (0 = default)."""
     c = TuckerConfig()
+    c.block_cap = int(block_cap)
     c.ndim = len(n) + 1
     c.dtype = TUCKER_F32 if dtype in ("f32", "float32") else TUCKER_F64
     c.precision = TUCKER_PREC_MIXED if precision == "mixed" else TUCKER_PREC_FP64
@@ -213,6 +216,12 @@ def tucker_init_sthosvd(cfg: TuckerConfig, X_ptr: int, n_init: int, stream: int 
 
 def tucker_stream_update(h: int, Y_ptr: int, stream: int = 0) -> None:
     _check(load_library().tucker_stream_update(h, ctypes.c_void_p(Y_ptr), ctypes.c_void_p(stream)), h)
+
+
+def tucker_stream_update_block(h: int, Y_ptr: int, nslices: int, stream: int = 0) -> None:
+    """B slices at once (contiguous, slice after slice): the block update."""
+    _check(load_library().tucker_stream_update_block(h, ctypes.c_void_p(Y_ptr), int(nslices),
+                                                     ctypes.c_void_p(stream)), h)
 
 
 def tucker_stream_update_host(h: int, Y_host_ptr: int, stream: int = 0) -> None:
@@ -512,7 +521,7 @@ class TuckerStream:
     """
 
     def __init__(self, X, tau, *, precision="mixed", rank_cap=None, steps_cap=0, core_cap=0,
-                 eps_m=0.0, stream=None):
+                 eps_m=0.0, block_cap=0, stream=None):
         import torch
 
         if not X.is_cuda:
@@ -523,7 +532,8 @@ class TuckerStream:
         self.dtype = X.dtype
         dt = "f32" if X.dtype == torch.float32 else "f64"
         self.cfg = make_config(self.n, tau, dtype=dt, precision=precision, rank_cap=rank_cap,
-                               steps_cap=steps_cap, core_cap=core_cap, eps_m=eps_m)
+                               steps_cap=steps_cap, core_cap=core_cap, eps_m=eps_m,
+                               block_cap=block_cap)
         self._stream = stream
         self.n_init = int(X.shape[0])
         self.h = tucker_init_sthosvd(self.cfg, X.data_ptr(), X.shape[0], self._sp())
@@ -538,6 +548,12 @@ class TuckerStream:
         if tuple(reversed(Y.shape)) != self.n or Y.dtype != self.dtype or not Y.is_contiguous():
             raise ValueError("slice shape/dtype/layout mismatch")
         tucker_stream_update(self.h, Y.data_ptr(), self._sp())
+
+    def update_block(self, Yb) -> None:
+        """B slices at once: Yb row-major (B, n_{d-1}, ..., n_1), contiguous on the device."""
+        if tuple(reversed(Yb.shape[1:])) != self.n or Yb.dtype != self.dtype or not Yb.is_contiguous():
+            raise ValueError("block shape/dtype/layout mismatch")
+        tucker_stream_update_block(self.h, Yb.data_ptr(), int(Yb.shape[0]), self._sp())
 
     def update_host(self, Y) -> None:
         """Update from a slice in host memory (a CPU tensor, pinned for overlap): the library

@@ -84,6 +84,9 @@ struct tucker_state {
   void* u16[TK_MAXD][4]{};        // FP16 hi/lo parts of 2^14 U_k (U1 hi, U1 lo, U2 hi, U2 lo)
   int ld16[TK_MAXD]{};            // row stride of U1 (n_k rounded up to 64)
   int h16mask = 0;                // bit k: the FP16 pass (input tile in TMEM) runs mode k
+  int blk = 1;                    // slices of the update being launched (block update)
+  int block_cap = 1;              // most slices per block update (buffers sized for it)
+  void* Dt = nullptr;             // block update: the projected slices as rows (R x block_cap)
   int etmask = 0;                 // bit k: tensor-core residual Gram of spatial mode k available
   float* et = nullptr;            // E^T of the growing mode (n_k x Fs_k) for the Gram
   long long et_stride[TK_MAXD]{};
@@ -238,6 +241,7 @@ bool validate(const tucker_config* c, int64_t n_init, char* msg, size_t msz) {
     snprintf(msg, msz, "steps_cap must be >= n_init"); return false;
   }
   if (c->core_cap < 0) { snprintf(msg, msz, "core_cap must be >= 0"); return false; }
+  if (c->block_cap < 0 || c->block_cap > 64) { snprintf(msg, msz, "block_cap must be in 0..64"); return false; }
   return true;
 }
 
@@ -278,13 +282,15 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
     maxD = std::max(maxD, sz);
   }
   maxD = std::max(maxD, s->core_cap);
-  s->dbuf_elems = maxD;
+  // a block update holds block_cap slices in flight through the spatial modes
+  s->block_cap = std::max(1, (int)c.block_cap);
+  s->dbuf_elems = maxD * s->block_cap;
   CK(cudaMallocHost((void**)&s->hctl, sizeof(Ctl)));
   memset(s->hctl, 0, sizeof(Ctl));
   CK(dalloc(s, (void**)&s->ctl, sizeof(Ctl)));
   s->log_cap = s->steps_cap;
   CK(dalloc(s, (void**)&s->log, sizeof(StepRec) * (size_t)s->log_cap));
-  for (int i = 0; i < 3; ++i) CK(dalloc(s, &s->dbuf[i], (size_t)maxD * tw));
+  for (int i = 0; i < 3; ++i) CK(dalloc(s, &s->dbuf[i], (size_t)s->dbuf_elems * tw));
   CK(dalloc(s, (void**)&s->d_dbufs, sizeof(void*) * 3));
   CK(cudaMemcpy(s->d_dbufs, s->dbuf, sizeof(void*) * 3, cudaMemcpyHostToDevice));
   for (int k = 0; k < d - 1; ++k) {
@@ -304,6 +310,7 @@ tucker_status allocate(tucker_state* s, int64_t n_init) {
   CK(cudaMemcpy(s->d_cbufs, s->Cb, sizeof(void*) * 2, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_vbufs, s->Vb, sizeof(void*) * 2, cudaMemcpyHostToDevice));
   CK(dalloc(s, &s->evec, (size_t)tw * s->core_cap));
+  if (s->block_cap > 1) CK(dalloc(s, &s->Dt, (size_t)tw * s->core_cap * s->block_cap));
   CK(dalloc(s, (void**)&s->S, sizeof(double) * kSecMax));
   CK(dalloc(s, (void**)&s->Snew, sizeof(double) * kSecMax));
   CK(dalloc(s, (void**)&s->part_e2, sizeof(double) * 4096));
@@ -461,7 +468,7 @@ cudaError_t split_u(tucker_state* s, int k, int pred, cudaStream_t st) {
 cudaError_t tc_pass(tucker_state* s, int k, int mode, int pred, int rerun, const void* Y,
                     int out_off, double* part_e2, double* part_y2, float* Et, long long et_stride,
                     cudaStream_t st) {
-  const long long F0 = s->N / s->n[0];
+  const long long F0 = s->N / s->n[0] * s->blk;
   if ((s->h16mask >> k) & 1)
     return launch_tc_pass16(s->ctl, k, mode, pred, rerun, (const float*)Y, F0, s->n[0],
                             s->pmaps[k], s->d_dbufs, out_off, part_e2, part_y2, s->grid_p, Et,
@@ -667,7 +674,7 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
   long long launches = 0;
   // (an IF node costs more than the empty launch of a predicated kernel on this GPU, so only the
   // 11-kernel growth chains below are conditional nodes)
-  CK(launch_begin(s->ctl, st));
+  CK(launch_begin(s->ctl, st, s->blk));
   launches += 1;
   for (int k = 0; k < d - 1; ++k) {
     const int n = s->n[k];
@@ -750,34 +757,46 @@ tucker_status do_update(tucker_state* s, const void* Y, cudaStream_t st) {
     }
     launches += 8;
   }
-  {
-    // streaming mode: incremental SVD (Alg. 3)
-    PhaseMark pm(s, st, TK_PH_ISVD);
-    CK(launch_isvd<TW>(s->ctl, s->d_dbufs, s->d_vbufs, s->part_p, s->part_e, s->pvec, s->esvec,
-                       s->evec, s->S, s->sw, s->grid_i, st));
-    CK(launch_secular_vectors(s->ctl, s->S, s->sw, s->Snew, st));
-    launches += 6;
+  // block update: the projected slices become rows, one incremental-SVD step each
+  const int nrows = s->blk;
+  if (nrows > 1) {
+    CK(launch_block_rows<TW>(s->ctl, s->d_dbufs, s->Dt, st));
+    launches += 1;
   }
-  {
-    PhaseMark pm(s, st, TK_PH_FACT);
-    CK(launch_factor<TW>(s->ctl, s->d_udbufs, s->sw, s->esvec, s->Bc, s->cu, s->Bv, s->wv, s->ldc,
-                         s->tc ? s->d_bsplit : nullptr, 152 * 2, st));
-    launches += 2;
-  }
-  {
-    // core update (Alg. 5, last step) and V~ = V' V''
-    PhaseMark pm(s, st, TK_PH_CV);
-    if (s->tc) {
-      CK(launch_tc_cv(s->ctl, s->sw, s->maps, s->Cb, s->Vb, s->d_cbufs, s->d_vbufs, s->cu, s->wv,
-                      s->evec, s->d_dbufs, s->ldc, s->grid_tc, st));
-      launches += 3;
+  for (int row = 0; row < nrows; ++row) {
+    if (nrows > 1) {
+      CK(launch_row_begin<TW>(s->ctl, row, s->d_dbufs, s->Dt, st));
+      launches += 1;
     }
-    CK(launch_cv<TW>(s->ctl, s->d_dbufs, s->d_cbufs, s->d_vbufs, s->sw, s->Bc, s->cu, s->Bv, s->wv,
-                     s->ldc, s->evec, s->grid_cv, st));
-    launches += 2;
+    {
+      // streaming mode: incremental SVD (Alg. 3)
+      PhaseMark pm(s, st, TK_PH_ISVD);
+      CK(launch_isvd<TW>(s->ctl, s->d_dbufs, s->d_vbufs, s->part_p, s->part_e, s->pvec, s->esvec,
+                         s->evec, s->S, s->sw, s->grid_i, st));
+      CK(launch_secular_vectors(s->ctl, s->S, s->sw, s->Snew, st));
+      launches += 6;
+    }
+    {
+      PhaseMark pm(s, st, TK_PH_FACT);
+      CK(launch_factor<TW>(s->ctl, s->d_udbufs, s->sw, s->esvec, s->Bc, s->cu, s->Bv, s->wv, s->ldc,
+                           s->tc ? s->d_bsplit : nullptr, 152 * 2, st));
+      launches += 2;
+    }
+    {
+      // core update (Alg. 5, last step) and V~ = V' V''
+      PhaseMark pm(s, st, TK_PH_CV);
+      if (s->tc) {
+        CK(launch_tc_cv(s->ctl, s->sw, s->maps, s->Cb, s->Vb, s->d_cbufs, s->d_vbufs, s->cu, s->wv,
+                        s->evec, s->d_dbufs, s->ldc, s->grid_tc, st));
+        launches += 3;
+      }
+      CK(launch_cv<TW>(s->ctl, s->d_dbufs, s->d_cbufs, s->d_vbufs, s->sw, s->Bc, s->cu, s->Bv, s->wv,
+                       s->ldc, s->evec, s->grid_cv, st));
+      launches += 2;
+    }
+    CK(launch_end(s->ctl, s->Snew, s->S, st));
+    launches += 1;
   }
-  CK(launch_end(s->ctl, s->Snew, s->S, st));
-  launches += 1;
   if (s->prof) {
     s->prof_launches += launches;
     s->prof_updates += 1;
@@ -1157,6 +1176,27 @@ tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* str
     }
   }
   return update_dispatch(s, Y_dev, st);
+}
+
+tucker_status tucker_stream_update_block(tucker_state* s, const void* Y_dev, int32_t nslices,
+                                         void* stream) {
+  if (!s || !Y_dev || nslices < 1) return TUCKER_EINVAL;
+  if (!usable(s)) return TUCKER_ESTATE;
+  if (nslices > s->block_cap) {
+    set_err(s, "tucker_stream_update_block: %s%lld slices above the state's block_cap", "", nslices);
+    return TUCKER_EINVAL;
+  }
+  if (nslices == 1) return tucker_stream_update(s, Y_dev, stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  s->last_stream = st;
+  tucker_status rp = push_replay(s, st);
+  if (rp != TUCKER_OK) return rp;
+  // launch by launch (the graph form is captured for one slice); the spatial modes see the
+  // block as one tensor with a trailing mode of size nslices
+  s->blk = nslices;
+  const tucker_status rc = update_dispatch(s, Y_dev, st);
+  s->blk = 1;
+  return rc;
 }
 
 tucker_status tucker_stream_update_host(tucker_state* s, const void* Y_host, void* stream) {

@@ -95,6 +95,11 @@ struct Ctl {
   // ---- test hook: nonzero makes the next mode-1 tensor-core pass A withhold its loads, so that
   // every wait of its consumers runs out (the bounded-wait path; see tucker_test_stall_next) ----
   int test_stall;
+  // ---- block update: blk slices in the current update (1 for a single slice; the spatial modes
+  // take them as one tensor with a trailing mode of size blk), and the row of the block whose
+  // incremental-SVD step runs ----
+  int blk;
+  int row;
 };
 
 // FP16 scale window: a pass's input scaled by 2^sigma must have its largest |x| in
@@ -171,6 +176,7 @@ __device__ __forceinline__ long long view_B(const Ctl* c, int k) {
   for (int i = k + 1; i < c->d - 1; ++i) b *= c->n[i];
   if (c->init_nt == 0) {
     for (int i = 0; i < k; ++i) b *= c->r[i];
+    if (k < c->d - 1 && c->blk > 1) b *= c->blk;   // the block's trailing mode
   } else if (k < c->d - 1) {
     b *= c->init_nt;
   }

@@ -1419,9 +1419,11 @@ __global__ void k_end_update(Ctl* ctl, const double* Snew, double* S) {
       A *= c.r[k];
     }
     const long long nd = c.nd;
-    ctl->acc_bytes[TK_PH_PROJ1] = c.acc_bytes[TK_PH_PROJ1] + (double)bp1;
-    ctl->acc_bytes[TK_PH_PROJN] = c.acc_bytes[TK_PH_PROJN] + (double)bpn;
-    ctl->acc_bytes[TK_PH_GROW] = c.acc_bytes[TK_PH_GROW] + (double)bgr;
+    // a block update's spatial passes covered blk slices, once (its row 0)
+    const long long bm = c.row == 0 ? (c.blk > 1 ? c.blk : 1) : 0;
+    ctl->acc_bytes[TK_PH_PROJ1] = c.acc_bytes[TK_PH_PROJ1] + (double)(bm * bp1);
+    ctl->acc_bytes[TK_PH_PROJN] = c.acc_bytes[TK_PH_PROJN] + (double)(bm * bpn);
+    ctl->acc_bytes[TK_PH_GROW] = c.acc_bytes[TK_PH_GROW] + (double)(bm * bgr);
     ctl->acc_bytes[TK_PH_ISVD] = c.acc_bytes[TK_PH_ISVD] + (double)(tw * (2 * Ro * r + 3 * Rn));
     ctl->acc_bytes[TK_PH_FACT] = c.acc_bytes[TK_PH_FACT] + (double)(16 * (nd * r + (nd + 1) * keep));
     ctl->acc_bytes[TK_PH_CV] = c.acc_bytes[TK_PH_CV] + (double)(tw * (2 * Ro * r + 2 * Rn * keep + 2 * Rn));
@@ -1466,8 +1468,10 @@ __global__ void k_end_update(Ctl* ctl, const double* Snew, double* S) {
   }
 }
 
-__global__ void k_begin_update(Ctl* ctl) {
+__global__ void k_begin_update(Ctl* ctl, int blk) {
   if (ctl->status) return;
+  ctl->blk = blk;
+  ctl->row = 0;
   for (int k = 0; k < TK_MAXD; ++k) {
     ctl->rold[k] = ctl->r[k];
     ctl->grew[k] = 0;
@@ -1485,7 +1489,63 @@ __global__ void k_begin_update(Ctl* ctl) {
   ctl->q = 0.0;
   ctl->q2 = 0.0;
   ctl->dropped = 0.0;
-  if (ctl->nd + 1 > ctl->steps_cap) ctl->status = TK_ECAPACITY;
+  if (ctl->nd + blk > ctl->steps_cap) ctl->status = TK_ECAPACITY;
+}
+
+// Block update, after the spatial modes: D*_{d-1} holds the blk projected slices with the slice
+// index fastest (blk x R, the rotating layout's order); Dt gets them as blk contiguous vectors of
+// R entries (R x blk), and the streaming mode's tolerance becomes eps / sqrt(blk) per row (the
+// block's streaming share split evenly; see tucker_stream_update_block).
+template <typename TW>
+__global__ void k_block_rows(Ctl* ctl, TW* const* dbufs, TW* __restrict__ Dt) {
+  if (ctl->status) return;
+  const int d = ctl->d, B = ctl->blk;
+  long long R = 1;
+  for (int k = 0; k < d - 1; ++k) R *= ctl->r[k];
+  const TW* D = dbufs[ctl->xbuf];
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < R * B;
+       L += (long long)gridDim.x * blockDim.x) {
+    const long long j = L % R, b = L / R;
+    Dt[L] = D[b + B * j];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->eps = ctl->eps / sqrt((double)B);
+}
+
+// Row b of a block update: its projected slice into the D*_{d-1} buffer (the input of the
+// incremental-SVD and core kernels); for b > 0 the per-update record is reset, as the spatial
+// modes' decisions, discards and the block's norm belong to row 0 only.
+template <typename TW>
+__global__ void k_row_begin(Ctl* ctl, int b, TW* const* dbufs, const TW* __restrict__ Dt) {
+  if (ctl->status) return;
+  const int d = ctl->d;
+  long long R = 1;
+  for (int k = 0; k < d - 1; ++k) R *= ctl->r[k];
+  TW* D = dbufs[ctl->xbuf];
+  const TW* src = Dt + (long long)b * R;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < R;
+       L += (long long)gridDim.x * blockDim.x)
+    D[L] = src[L];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->row = b;
+    if (b > 0) {
+      for (int k = 0; k < TK_MAXD; ++k) {
+        ctl->rold[k] = ctl->r[k];
+        ctl->grew[k] = 0;
+        ctl->radd[k] = 0;
+        ctl->e2[k] = 0.0;
+        ctl->disc[k] = 0.0;
+        ctl->tail_prev[k] = 0.0;
+        ctl->eig_m[k] = 0;
+        ctl->eig_it[k] = 0;
+        ctl->eig_fb[k] = 0;
+      }
+      ctl->y2 = 0.0;
+      ctl->aug = 0;
+      ctl->q = 0.0;
+      ctl->q2 = 0.0;
+      ctl->dropped = 0.0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1613,8 +1673,23 @@ cudaError_t launch_cv(Ctl* ctl, void* const* dbufs, void* const* cbufs, void* co
   return cudaGetLastError();
 }
 
-cudaError_t launch_begin(Ctl* ctl, cudaStream_t st) {
-  k_begin_update<<<1, 1, 0, st>>>(ctl);
+template <typename TW>
+cudaError_t launch_block_rows(Ctl* ctl, void* const* dbufs, void* Dt, cudaStream_t st) {
+  k_block_rows<TW><<<152 * 2, 256, 0, st>>>(ctl, (TW* const*)dbufs, (TW*)Dt);
+  return cudaGetLastError();
+}
+template <typename TW>
+cudaError_t launch_row_begin(Ctl* ctl, int b, void* const* dbufs, const void* Dt, cudaStream_t st) {
+  k_row_begin<TW><<<152 * 2, 256, 0, st>>>(ctl, b, (TW* const*)dbufs, (const TW*)Dt);
+  return cudaGetLastError();
+}
+template cudaError_t launch_block_rows<float>(Ctl*, void* const*, void*, cudaStream_t);
+template cudaError_t launch_block_rows<double>(Ctl*, void* const*, void*, cudaStream_t);
+template cudaError_t launch_row_begin<float>(Ctl*, int, void* const*, const void*, cudaStream_t);
+template cudaError_t launch_row_begin<double>(Ctl*, int, void* const*, const void*, cudaStream_t);
+
+cudaError_t launch_begin(Ctl* ctl, cudaStream_t st, int blk) {
+  k_begin_update<<<1, 1, 0, st>>>(ctl, blk);
   return cudaGetLastError();
 }
 

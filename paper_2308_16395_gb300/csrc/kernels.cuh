@@ -79,7 +79,12 @@ template <typename TW>
 cudaError_t launch_cv(Ctl* ctl, void* const* dbufs, void* const* cbufs, void* const* vbufs,
                       SecWork w, const void* Bc, const void* cu, const void* Bv, const void* wv,
                       int ldb, const void* evec, int grid_cv, cudaStream_t st);
-cudaError_t launch_begin(Ctl* ctl, cudaStream_t st);
+cudaError_t launch_begin(Ctl* ctl, cudaStream_t st, int blk = 1);
+// block update (blk > 1): the projected slices as contiguous rows, then each row's turn
+template <typename TW>
+cudaError_t launch_block_rows(Ctl* ctl, void* const* dbufs, void* Dt, cudaStream_t st);
+template <typename TW>
+cudaError_t launch_row_begin(Ctl* ctl, int b, void* const* dbufs, const void* Dt, cudaStream_t st);
 cudaError_t launch_end(Ctl* ctl, const double* Snew, double* S, cudaStream_t st);
 
 // ---- k_tc.cu ----
