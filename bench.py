@@ -11,7 +11,8 @@ Prints one JSON line (rank 0), with the parity of the timed updates against the 
 (run over exactly the same stream in the CPU-baseline leg).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload stream|stream192|batched|adjoint|sine] [--precision mixed|fp64]
+                  [--workload stream|stream192|stream64|batched|adjoint|sine|block]
+                  [--precision mixed|fp64] [--block B]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this build) on the host cores.
 """
@@ -822,10 +823,150 @@ def run_sine(args):
     print(json.dumps(line), flush=True)
 
 
+def _block_case(pkg, torch, Xg, n_init, tau, prec, B, caps):
+    """One stream through blocks of B slices (B = 1: tucker_stream_update), graph form, slices
+    resident: a warm-up block (captures the graph), then as many whole blocks as fit, timed with
+    CUDA events. Returns the state, the timed slice count, the time in ms and the blocks' kernel
+    nodes."""
+    T = Xg.shape[0]
+    ts = pkg.TuckerStream(Xg[:n_init].contiguous(), tau, precision=prec, rank_cap=caps,
+                          steps_cap=T + 8, block_cap=max(B, 1))
+    st = torch.cuda.current_stream()
+
+    def step(t):
+        if B == 1:
+            ts.update(Xg[t])
+        else:
+            ts.update_block(Xg[t:t + B])
+
+    step(n_init)
+    ts.ranks
+    nblk = (T - n_init - B) // B
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for i in range(nblk):
+        step(n_init + B + i * B)
+    e1.record(st)
+    torch.cuda.synchronize()
+    kern = pkg.tucker_graph_kernels(ts.h) if B == 1 else pkg.tucker_block_graph_kernels(ts.h, B)
+    return ts, nblk * B, e0.elapsed_time(e1), kern * nblk
+
+
+def run_block(args):
+    """Block updates (several slices per call, the Conclusions' future work) beside single-slice
+    updates, on the small-slice workloads where an update's chain of dependent launches, not the
+    slice's bytes, sets the time: the exact-rank 24 x 20 x 16 stream of ranks (4, 4, 3, 6)
+    (noise 1e-4, tau = 1e-3, n_init = 10; extended from 40 to 490 steps so that the timed region
+    is long enough; FP64 form, FP64 slices) and the 100 x 100 sine-wave stream of Sec. 5.1
+    (5000 steps, tau = 1e-2, n_init = 200, mixed form, FP32 slices). For each block size B
+    (B = 1 is tucker_stream_update) and each stream: slices/s over the timed blocks (graph form,
+    slices resident in HBM), the final ranks, the true relative error of the reconstruction and
+    the running bound. The exact-rank stream also runs through the oracle's block update at every
+    B (parity: equal ranks after every block, reconstruction against the oracle's). ``value`` is
+    the sine-wave stream's slices/s at B = --block."""
+    import numpy as np
+    import torch
+
+    import paper_2308_16395_gb300 as pkg
+    from workloads import LowRankStream, SineWave
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes = sorted({1, 4, 8, 16, 32, args.block})
+    # exact-rank stream (the FP64 workload's recipe, 490 steps)
+    Te, ne, taue = 490, 10, 1e-3
+    lrs = LowRankStream((24, 20, 16), (4, 4, 3, 6), Te, 1e-4, seed=1, noise_scope="tensor")
+    Xe = lrs.tensor(0, Te)                                            # paper order, FP64
+    Xeg = torch.from_numpy(np.ascontiguousarray(np.moveaxis(Xe, -1, 0).transpose(0, 3, 2, 1))).to(dev)
+    # sine wave (Sec. 5.1)
+    sw = SineWave()
+    Ts, ns, taus = sw.steps, 200, 1e-2
+    hs = np.stack([sw.slice(t) for t in range(Ts)], axis=0)
+    Xsg = torch.from_numpy(np.ascontiguousarray(hs.transpose(0, 2, 1))).to(dev, torch.float32)
+    del hs
+    clocks = ClockSampler(local)
+    clocks.start()
+    cases = {"exact_rank_24x20x16_fp64": [], "sine_100x100_mixed": []}
+    launches = 0
+    import oracle as O
+    oracle_ms = None
+    for B in sizes:
+        ts, n, ms, kern = _block_case(pkg, torch, Xeg, ne, taue, "fp64", B, None)
+        launches += kern
+        used = ne + B + n
+        R = pkg.paper_order(ts.reconstruct(0, used)).cpu().numpy()
+        eb, dn = ts.error_norm()
+        rec = {"B": B, "slices_per_s": n / (ms / 1e3), "ms_per_slice": ms / n, "timed_slices": n,
+               "ranks": list(ts.ranks),
+               "rel_error_true": float(np.linalg.norm(Xe[..., :used] - R) / np.linalg.norm(Xe[..., :used])),
+               "rel_error_bound": eb / dn}
+        if not args.no_cpu:
+            # the oracle over the same slices in the same blocks
+            so = O.init_stream(np.asfortranarray(Xe[..., :ne]), taue)
+            t0 = time.perf_counter()
+            ranks_ok = True
+            log = ts.step_log()
+            t = ne
+            while t < used:
+                b = min(B, used - t)
+                if B == 1:
+                    O.stream_update(so, np.asfortranarray(Xe[..., t]))
+                else:
+                    O.block_update(so, np.asfortranarray(Xe[..., t:t + b]))
+                t += b
+                ranks_ok &= tuple(log[t - ne - 1]["ranks"]) == so.ranks
+            dt = time.perf_counter() - t0
+            if B == args.block:
+                oracle_ms = dt * 1e3 / (used - ne)
+            Ro = O.reconstruct(so.C, so.Us)
+            rec["parity"] = {"ranks_equal_every_block": bool(ranks_ok),
+                             "recon_rel_diff": float(np.linalg.norm(R - Ro) / np.linalg.norm(Ro))}
+        ts.close()
+        cases["exact_rank_24x20x16_fp64"].append(rec)
+    for B in sizes:
+        ts, n, ms, kern = _block_case(pkg, torch, Xsg, ns, taus, "mixed", B, [0, 0, 64])
+        launches += kern
+        used = ns + B + n
+        R = ts.reconstruct(0, used).double()
+        X = Xsg[:used].double()
+        eb, dn = ts.error_norm()
+        cases["sine_100x100_mixed"].append({
+            "B": B, "slices_per_s": n / (ms / 1e3), "ms_per_slice": ms / n, "timed_slices": n,
+            "ranks": list(ts.ranks),
+            "rel_error_true": float(torch.linalg.norm((R - X).flatten()) / torch.linalg.norm(X.flatten())),
+            "rel_error_bound": eb / dn})
+        ts.close()
+    ck = clocks.stop()
+    main = next(r for r in cases["sine_100x100_mixed"] if r["B"] == args.block)
+    line = {
+        "metric": METRIC, "value": main["slices_per_s"], "unit": "slices/s", "n_gpus": 1,
+        "steps": main["timed_slices"] // args.block, "warmup": 1,
+        "ms_per_step": main["ms_per_slice"] * args.block, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"block update (B = {args.block} slices per call) of the 100x100 "
+                               "sine-wave stream (Sec. 5.1), beside the exact-rank 24x20x16 stream; "
+                               "B = 1 is the single-slice update",
+                   "parallelism": "1 gpu", "l2": "small slices: L2-resident, latency-bound"},
+        "cases": cases,
+        "gpu_launches": int(launches),
+        "gpu_launches_note": "kernel nodes of the block graphs (conditional bodies included) x blocks, all cases",
+        "clocks": ck,
+    }
+    if oracle_ms is not None:
+        line["cpu_baseline"] = {"value": 1e3 / oracle_ms, "unit": "slices/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"FP64 oracle block update (B = {args.block}) over the "
+                                          "exact-rank 24x20x16 stream's timed slices"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="stream",
-                    choices=["stream", "stream192", "stream64", "adjoint", "batched", "sine"])
+                    choices=["stream", "stream192", "stream64", "adjoint", "batched", "sine", "block"])
+    ap.add_argument("--block", type=int, default=16, help="slices per block (--workload block)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
@@ -845,6 +986,8 @@ def main():
         run_batched(args)
     elif args.workload == "sine":
         run_sine(args)
+    elif args.workload == "block":
+        run_block(args)
     else:
         run_ours(args)
 

@@ -291,8 +291,11 @@ tucker_status tucker_restore_orthogonality(tucker_state* s, void* stream, double
  * eps / sqrt(nslices) per row: the block adds at most (d - 1) eps^2 + nslices eps^2 / nslices =
  * tau^2 ||Y_block||^2 to the squared error, Alg. 5's guarantee for the block. nslices = 1 is
  * tucker_stream_update. n_d grows by nslices; the step log gets one record per slice (the
- * block's spatial decisions and norm in the first). Runs launch by launch. nslices must not
- * exceed the configuration's block_cap.
+ * block's spatial decisions and norm in the first). nslices must not exceed the configuration's
+ * block_cap. Without phase profiling the first block of each size is captured as a CUDA graph
+ * (the form of tucker_stream_update, with the block's rows unrolled) and later blocks of that
+ * size launch it; with profiling on, blocks run launch by launch. The slices' address must be
+ * 16-byte aligned for the tensor-core pass (EINVAL otherwise).
  * Errors: EINVAL (NULL, nslices < 1 or above block_cap), ESTATE, ECUDA; device errors
  * (ECAPACITY, ENUMERIC, ETIMEOUT) latch and surface at the next synchronizing call. */
 tucker_status tucker_stream_update_block(tucker_state* s, const void* Y_dev, int32_t nslices,
@@ -375,6 +378,10 @@ tucker_status tucker_profile_read(tucker_state* s, tucker_profile* out_host);
  * Returns the kernel nodes of the captured update graph (conditional bodies included: an upper
  * bound of the kernels one update runs), 0 before the first capture, -1 for NULL. */
 int64_t tucker_graph_kernels(const tucker_state* s);
+
+/* Kernel nodes of the captured graph of a block update of nslices slices (conditional bodies
+ * included), 0 before that size's first block, -1 for NULL or nslices outside 2..64. */
+int64_t tucker_block_graph_kernels(const tucker_state* s, int32_t nslices);
 
 /* Launch shape of the update's kernels: CTA counts of its grid-stride passes. The defaults fill
  * the whole GPU (two CTAs per SM for the projection and ISVD passes, one per SM for the

@@ -28,7 +28,7 @@ EXPORTS = ["tucker_init_sthosvd", "tucker_stream_update", "tucker_reconstruct",
            "tucker_reconstruct_noalloc", "tucker_ttm_workspace_bytes", "tucker_ttm_project",
            "tucker_ttm_reconstruct", "tucker_ttm_project_adjoint", "tucker_ttm_reconstruct_adjoint",
            "tucker_batch_create", "tucker_batch_update", "tucker_batch_kernels", "tucker_batch_destroy",
-           "tucker_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
+           "tucker_graph_kernels", "tucker_block_graph_kernels", "tucker_error_norm_async", "tucker_set_launch_plan",
            "tucker_get_launch_plan", "tucker_stream_update_host", "tucker_get_step_log",
            "tucker_replay_next", "tucker_stream_update_batched", "tucker_recompress",
            "tucker_test_stall_next", "tucker_orthogonality_error", "tucker_restore_orthogonality",
@@ -150,6 +150,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tucker_error_norm_async.restype = ctypes.c_int
     lib.tucker_graph_kernels.argtypes = [vp]
     lib.tucker_graph_kernels.restype = i64
+    lib.tucker_block_graph_kernels.argtypes = [vp, i32]
+    lib.tucker_block_graph_kernels.restype = i64
     lib.tucker_batch_kernels.argtypes = [vp]
     lib.tucker_batch_kernels.restype = i64
     lib.tucker_batch_destroy.argtypes = [vp]
@@ -493,6 +495,10 @@ def tucker_get_launch_plan(h: int) -> dict:
 
 def tucker_graph_kernels(h: int) -> int:
     return int(load_library().tucker_graph_kernels(h))
+
+
+def tucker_block_graph_kernels(h: int, nslices: int) -> int:
+    return int(load_library().tucker_block_graph_kernels(h, int(nslices)))
 
 
 def tucker_last_error(h: int) -> str:

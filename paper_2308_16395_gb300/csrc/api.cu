@@ -118,6 +118,10 @@ struct tucker_state {
   cudaGraphExec_t uexec = nullptr;
   bool graph_failed = false;          // capture or instantiation failed once: stay eager
   long long graph_kernels = 0;        // kernel nodes of the update graph (bodies included)
+  // graph form of block updates, one per block size (index = slices per block, 2..64)
+  cudaGraph_t bgraph[65]{};
+  cudaGraphExec_t bexec[65]{};
+  long long bkernels[65]{};
   std::vector<cudaGraph_t> bodies;    // IF bodies created by the last capture
   // host-input updates (tucker_stream_update_host): two staging slices, a copy stream, and per
   // buffer an event after its copy and one after the update that read it
@@ -949,9 +953,11 @@ tucker_status ensure_streams(tucker_state* s) {
   return TUCKER_OK;
 }
 
-// One update of s, slice read from the control block's slot, captured as a CUDA graph whose
-// growth chains are IF nodes on grew[k] (set by k_decide).
-tucker_status capture_update(tucker_state* s) {
+// One update of s (blk slices: 1 for Alg. 5, more for a block update), slice read from the
+// control block's slot, captured as a CUDA graph whose growth chains are IF nodes on grew[k]
+// (set by k_decide).
+tucker_status capture_update(tucker_state* s, int blk, cudaGraph_t* graph, cudaGraphExec_t* exec,
+                             long long* kernels) {
   tucker_status rc = ensure_streams(s);
   if (rc != TUCKER_OK) return rc;
   s->bodies.clear();
@@ -959,7 +965,9 @@ tucker_status capture_update(tucker_state* s) {
   const bool prof = s->prof;
   s->prof = false;
   s->gform = true;
+  s->blk = blk;
   rc = update_dispatch(s, nullptr, s->cap_st);
+  s->blk = 1;
   s->gform = false;
   s->prof = prof;
   if (s->body_open) {
@@ -974,17 +982,29 @@ tucker_status capture_update(tucker_state* s) {
     cudaGetLastError();
     return rc != TUCKER_OK ? rc : TUCKER_ECUDA;
   }
-  if (cudaGraphInstantiate(&s->uexec, g, 0) != cudaSuccess) {
-    s->uexec = nullptr;
+  if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) {
+    *exec = nullptr;
     cudaGraphDestroy(g);
     cudaGetLastError();
     return TUCKER_ECUDA;
   }
-  s->ugraph = g;
-  s->graph_kernels = count_kernel_nodes(g);
-  for (cudaGraph_t b : s->bodies) s->graph_kernels += count_kernel_nodes(b);
+  *graph = g;
+  *kernels = count_kernel_nodes(g);
+  for (cudaGraph_t b : s->bodies) *kernels += count_kernel_nodes(b);
   s->bodies.clear();
   return TUCKER_OK;
+}
+
+// Drop every captured update graph of s (launch shapes changed, or the state is destroyed).
+void drop_graphs(tucker_state* s) {
+  if (s->uexec) { cudaGraphExecDestroy(s->uexec); s->uexec = nullptr; }
+  if (s->ugraph) { cudaGraphDestroy(s->ugraph); s->ugraph = nullptr; }
+  s->graph_kernels = 0;
+  for (int b = 0; b < 65; ++b) {
+    if (s->bexec[b]) { cudaGraphExecDestroy(s->bexec[b]); s->bexec[b] = nullptr; }
+    if (s->bgraph[b]) { cudaGraphDestroy(s->bgraph[b]); s->bgraph[b] = nullptr; }
+    s->bkernels[b] = 0;
+  }
 }
 
 // Capture: origin stream -> fork event -> one branch stream per state (its whole update) ->
@@ -1048,12 +1068,13 @@ tucker_status push_replay(tucker_state* s, cudaStream_t st) {
 }
 
 // Graph-form slice slot: the slice's address (and, for the tensor-core mode-1 pass, its TMA
-// descriptor) written into the control block by a one-block kernel on `st`.
-tucker_status write_slot(tucker_state* s, const void* Y_dev, cudaStream_t st) {
+// descriptor over the blk slices' mode-1 fibers) written into the control block by a one-block
+// kernel on `st`.
+tucker_status write_slot(tucker_state* s, const void* Y_dev, cudaStream_t st, int blk = 1) {
   SlotArgs sa{};
   if ((s->tcmask & 1) && s->tx == 4) {
     CUtensorMap m;
-    if (!make_map_2d_f32(&m, Y_dev, s->N / s->n[0], s->n[0], s->n[0], 32, 128)) {
+    if (!make_map_2d_f32(&m, Y_dev, s->N / s->n[0] * blk, s->n[0], s->n[0], 32, 128)) {
       set_err(s, "slice address unusable for TMA (16-byte alignment)%s%lld", "", 0);
       return TUCKER_EINVAL;
     }
@@ -1087,6 +1108,11 @@ const char* tucker_last_error(const tucker_state* s) { return s ? s->err : "null
 
 int64_t tucker_graph_kernels(const tucker_state* s) { return s ? s->graph_kernels : -1; }
 
+int64_t tucker_block_graph_kernels(const tucker_state* s, int32_t nslices) {
+  if (!s || nslices < 2 || nslices > 64) return -1;
+  return s->bkernels[nslices];
+}
+
 tucker_status tucker_set_launch_plan(tucker_state* s, const tucker_launch_plan* p) {
   if (!s || !p) return TUCKER_EINVAL;
   if (!usable(s)) return TUCKER_ESTATE;
@@ -1104,9 +1130,7 @@ tucker_status tucker_set_launch_plan(tucker_state* s, const tucker_launch_plan* 
   s->grid_cv = gc;
   // the captured update graph holds the old launch shapes: capture again at the next update
   if (s->last_stream) cudaStreamSynchronize(s->last_stream);
-  if (s->uexec) { cudaGraphExecDestroy(s->uexec); s->uexec = nullptr; }
-  if (s->ugraph) { cudaGraphDestroy(s->ugraph); s->ugraph = nullptr; }
-  s->graph_kernels = 0;
+  drop_graphs(s);
   return TUCKER_OK;
 }
 
@@ -1167,7 +1191,8 @@ tucker_status tucker_stream_update(tucker_state* s, const void* Y_dev, void* str
   // the slice's address (and its TMA descriptor) into the control block with a one-block kernel
   // and launches the graph.
   if (!s->prof && !s->graph_failed) {
-    if (!s->uexec && capture_update(s) != TUCKER_OK) s->graph_failed = true;
+    if (!s->uexec && capture_update(s, 1, &s->ugraph, &s->uexec, &s->graph_kernels) != TUCKER_OK)
+      s->graph_failed = true;
     if (s->uexec) {
       tucker_status rs = write_slot(s, Y_dev, st);
       if (rs != TUCKER_OK) return rs;
@@ -1191,8 +1216,19 @@ tucker_status tucker_stream_update_block(tucker_state* s, const void* Y_dev, int
   s->last_stream = st;
   tucker_status rp = push_replay(s, st);
   if (rp != TUCKER_OK) return rp;
-  // launch by launch (the graph form is captured for one slice); the spatial modes see the
-  // block as one tensor with a trailing mode of size nslices
+  // the spatial modes see the block as one tensor with a trailing mode of size nslices; graph
+  // form (one graph per block size, captured at its first use) unless phase profiling is on
+  const int b = nslices;
+  if (!s->prof && !s->graph_failed) {
+    if (!s->bexec[b] && capture_update(s, b, &s->bgraph[b], &s->bexec[b], &s->bkernels[b]) != TUCKER_OK)
+      s->graph_failed = true;
+    if (s->bexec[b]) {
+      tucker_status rs = write_slot(s, Y_dev, st, b);
+      if (rs != TUCKER_OK) return rs;
+      CK(cudaGraphLaunch(s->bexec[b], st));
+      return TUCKER_OK;
+    }
+  }
   s->blk = nslices;
   const tucker_status rc = update_dispatch(s, Y_dev, st);
   s->blk = 1;
@@ -1801,8 +1837,7 @@ void tucker_destroy(tucker_state* s) {
       cudaEventDestroy(s->hconsumed[b]);
     }
   }
-  if (s->uexec) cudaGraphExecDestroy(s->uexec);
-  if (s->ugraph) cudaGraphDestroy(s->ugraph);
+  drop_graphs(s);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
   if (s->body_st) cudaStreamDestroy(s->body_st);
   free_all(s);

@@ -135,3 +135,71 @@ def test_block_of_one_is_the_single_update_and_caps_are_checked(pkg):
         a.update_block(Xg[14:17].contiguous())        # 3 slices above block_cap = 2
     a.update_block(Xg[14:16].contiguous())            # the state is still usable
     assert a.step_log()[-1]["n_d"] == 16
+
+
+def test_block_graph_form_equals_launch_sequence(pkg):
+    """The captured block graph (one per block size, the rows unrolled, conditional growth
+    bodies) and the launch-by-launch block (phase profiling on) give the same state on a stream
+    whose spatial ranks grow; blocks of two sizes alternate."""
+    import torch
+
+    s = LowRankStream((40, 28, 12), (4, 3, 3, 6), 40, 3e-3, seed=23)
+    X = s.tensor(0, 40).astype(np.float32).astype(np.float64)
+    Xg = to_device(X, torch.float32)
+    a = pkg.TuckerStream(Xg[:4].contiguous(), 2e-3, precision="mixed", steps_cap=44, block_cap=4)
+    b = pkg.TuckerStream(Xg[:4].contiguous(), 2e-3, precision="mixed", steps_cap=44, block_cap=4)
+    pkg.tucker_profile_enable(b.h, 1)
+    t = 4
+    sizes = [4, 3]
+    i = 0
+    while t < 40:
+        B = min(sizes[i % 2], 40 - t)
+        a.update_block(Xg[t:t + B].contiguous())
+        b.update_block(Xg[t:t + B].contiguous())
+        assert a.ranks == b.ranks, t
+        t += B
+        i += 1
+    assert pkg.tucker_block_graph_kernels(a.h, 4) > 0 and pkg.tucker_block_graph_kernels(a.h, 3) > 0
+    assert pkg.tucker_block_graph_kernels(b.h, 4) == 0
+    assert any(any(r["grew"]) for r in a.step_log())
+    Ra, Rb = a.reconstruct(0, a.n_d).double(), b.reconstruct(0, b.n_d).double()
+    assert float(torch.linalg.norm(Ra - Rb) / torch.linalg.norm(Rb)) <= 1e-12
+    assert a.error_norm() == b.error_norm()
+    a.close()
+    b.close()
+
+
+def test_block_update_on_the_fp16_pass_at_n1_384(pkg):
+    """Blocks of 4 advected-blob slices of 384 x 96 x 16 x 2 (mode-1 fibers of 384: the FP16
+    tensor-core pass over the block's 4 x 96 x 16 x 2 fibers) against the oracle's block update
+    on the same slices, in lockstep with near-cutoff decisions replayed."""
+    import torch
+    from workloads import BlobField
+
+    bf = BlobField(grid=(384, 96, 16), nvar=2, nblobs=12, noise=1e-5, seed=5)
+    dev = torch.device("cuda")
+    T, n_init, B, tau = 18, 6, 4, 1e-3
+    gs = [bf.slice_torch(t, dev) for t in range(T)]
+    xs = [g.cpu().numpy().T.astype(np.float64) for g in gs]
+    X = np.stack(xs, axis=-1)
+    st = O.init_stream(np.asfortranarray(X[..., :n_init]), tau)
+    ts = pkg.TuckerStream(torch.stack(gs[:n_init]).contiguous(), tau, precision="mixed",
+                          steps_cap=T + 4, block_cap=B)
+    assert ts.ranks == st.ranks
+    for t0 in range(n_init, T, B):
+        t1 = min(t0 + B, T)
+        O.block_update(st, np.asfortranarray(X[..., t0:t1]))
+        lg = st.log[-1]
+        for row in lg["rows"][1:]:
+            assert abs(row.q ** 2 - lg["eps_row"] ** 2) > 0.15 * lg["eps_row"] ** 2, t0
+        rp = _block_replay(lg, 3e-2)
+        if rp is not None:
+            ts.replay_next(*rp)
+        ts.update_block(torch.stack(gs[t0:t1]).contiguous())
+        assert ts.ranks == st.ranks, (t0, ts.ranks, st.ranks)
+    Xh = pkg.paper_order(ts.reconstruct(0, T)).cpu().numpy()
+    ref = O.reconstruct(st.C, st.Us)
+    assert np.linalg.norm(Xh - ref) <= 1e-5 * np.linalg.norm(ref)
+    eb, _ = ts.error_norm()
+    assert np.linalg.norm(X - Xh) <= eb * (1 + 1e-5)
+    assert eb <= tau * np.linalg.norm(X) * (1 + 1e-6)
