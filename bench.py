@@ -823,7 +823,7 @@ def run_sine(args):
     print(json.dumps(line), flush=True)
 
 
-def _block_case(pkg, torch, Xg, n_init, tau, prec, B, caps):
+def _block_case(pkg, torch, Xg, n_init, tau, prec, B, caps, eager=False):
     """One stream through blocks of B slices (B = 1: tucker_stream_update), graph form, slices
     resident: a warm-up block (captures the graph), then as many whole blocks as fit, timed with
     CUDA events. Returns the state, the timed slice count, the time in ms and the blocks' kernel
@@ -831,6 +831,8 @@ def _block_case(pkg, torch, Xg, n_init, tau, prec, B, caps):
     T = Xg.shape[0]
     ts = pkg.TuckerStream(Xg[:n_init].contiguous(), tau, precision=prec, rank_cap=caps,
                           steps_cap=T + 8, block_cap=max(B, 1))
+    if eager:
+        pkg.tucker_profile_enable(ts.h, 1)   # launch by launch, so that a profiler lists kernels
     st = torch.cuda.current_stream()
 
     def step(t):
@@ -849,7 +851,10 @@ def _block_case(pkg, torch, Xg, n_init, tau, prec, B, caps):
         step(n_init + B + i * B)
     e1.record(st)
     torch.cuda.synchronize()
-    kern = pkg.tucker_graph_kernels(ts.h) if B == 1 else pkg.tucker_block_graph_kernels(ts.h, B)
+    if eager:
+        kern = pkg.tucker_profile_read(ts.h)["launches"] // max(nblk + 1, 1)
+    else:
+        kern = pkg.tucker_graph_kernels(ts.h) if B == 1 else pkg.tucker_block_graph_kernels(ts.h, B)
     return ts, nblk * B, e0.elapsed_time(e1), kern * nblk
 
 
@@ -874,7 +879,8 @@ def run_block(args):
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sizes = sorted({1, 4, 8, 16, 32, args.block})
+    sizes = sorted({int(x) for x in args.block_sizes.split(",")} | {args.block})
+    which = set(args.block_cases.split(","))
     # exact-rank stream (the FP64 workload's recipe, 490 steps)
     Te, ne, taue = 490, 10, 1e-3
     lrs = LowRankStream((24, 20, 16), (4, 4, 3, 6), Te, 1e-4, seed=1, noise_scope="tensor")
@@ -889,11 +895,13 @@ def run_block(args):
     clocks = ClockSampler(local)
     clocks.start()
     cases = {"exact_rank_24x20x16_fp64": [], "sine_100x100_mixed": []}
+    sizes_e = sizes if "exact" in which else []
+    sizes_s = sizes if "sine" in which else []
     launches = 0
     import oracle as O
     oracle_ms = None
-    for B in sizes:
-        ts, n, ms, kern = _block_case(pkg, torch, Xeg, ne, taue, "fp64", B, None)
+    for B in sizes_e:
+        ts, n, ms, kern = _block_case(pkg, torch, Xeg, ne, taue, "fp64", B, None, args.eager)
         launches += kern
         used = ne + B + n
         R = pkg.paper_order(ts.reconstruct(0, used)).cpu().numpy()
@@ -925,8 +933,8 @@ def run_block(args):
                              "recon_rel_diff": float(np.linalg.norm(R - Ro) / np.linalg.norm(Ro))}
         ts.close()
         cases["exact_rank_24x20x16_fp64"].append(rec)
-    for B in sizes:
-        ts, n, ms, kern = _block_case(pkg, torch, Xsg, ns, taus, "mixed", B, [0, 0, 64])
+    for B in sizes_s:
+        ts, n, ms, kern = _block_case(pkg, torch, Xsg, ns, taus, "mixed", B, [0, 0, 64], args.eager)
         launches += kern
         used = ns + B + n
         R = ts.reconstruct(0, used).double()
@@ -939,7 +947,8 @@ def run_block(args):
             "rel_error_bound": eb / dn})
         ts.close()
     ck = clocks.stop()
-    main = next(r for r in cases["sine_100x100_mixed"] if r["B"] == args.block)
+    main = next(r for r in (cases["sine_100x100_mixed"] or cases["exact_rank_24x20x16_fp64"])
+                if r["B"] == args.block)
     line = {
         "metric": METRIC, "value": main["slices_per_s"], "unit": "slices/s", "n_gpus": 1,
         "steps": main["timed_slices"] // args.block, "warmup": 1,
@@ -967,6 +976,10 @@ def main():
     ap.add_argument("--workload", default="stream",
                     choices=["stream", "stream192", "stream64", "adjoint", "batched", "sine", "block"])
     ap.add_argument("--block", type=int, default=16, help="slices per block (--workload block)")
+    ap.add_argument("--block-sizes", default="1,4,8,16,32", help="block sizes compared (--workload block)")
+    ap.add_argument("--block-cases", default="exact,sine", help="streams of --workload block: exact, sine")
+    ap.add_argument("--eager", action="store_true",
+                    help="--workload block: launch by launch (phase profiling on), for kernel listings")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)

@@ -289,6 +289,9 @@ __device__ __forceinline__ void tmem_st_wait() {
 // Named barrier over `count` threads that returns the OR of every participant's predicate (a
 // uniform decision for all of them).
 __device__ __forceinline__ bool bar_any(int id, int count, bool pred) {
+  // every caller is a whole warp: reconverge it (its lanes leave their bounded waits at
+  // different iterations) so that it reaches the named barrier as one
+  __syncwarp();
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
