@@ -13,8 +13,9 @@
 //   epi-1 P = 2^-(sigma+14) P_s into a shared staging tile; -2^-19 P_s split into FP16 hi/lo in
 //         tensor memory over the accumulators just read (MMA2's A operand).
 //   MMA2  accumulated onto the stored tile: X_s + (-2^-19 P_s)(2^5 U_k)^T = 2^sigma (X - P U_k^T)
-//         = 2^sigma E, three products per K step, U_k^T's FP16 parts resident in shared memory,
-//         in 128-column blocks.
+//         = 2^sigma E, three products per K step, in 128-column blocks; each block's FP16 parts
+//         of 2^5 U_k (128 rows) come round the input ring after the tile's chunks, so that the
+//         ring has four stages (more input in flight) instead of two beside resident rows.
 //   epi-2 ||E||^2 per CTA (FP32 over a fiber's block, then FP64), E^T for the residual Gram when
 //         the mode grew; then the staged P to global memory, column-major (F x r_k, the next
 //         mode's input).
@@ -44,7 +45,6 @@ constexpr int H_KC = 64;                         // input columns per chunk
 constexpr int H_XB = H_M * H_KC * 4;             // 32 KB: raw FP32 chunk, then FP16 hi | lo
 constexpr int H_UB = TP_RMAX * 128;              // 8 KB: U chunk (hi or lo), <= 64 rows x 128 B
 constexpr int H_STAGE = H_XB + 2 * H_UB;         // 48 KB
-constexpr int H_U2 = TK_H16_NMAX * 128;          // 48 KB: U_k rows (hi or lo), n_k x 64 FP16
 constexpr int H_PST = TP_RMAX * H_M * 4;         // 32 KB: staged P tile, [column][fiber] FP32
 constexpr int H_PF = 6;                          // chunks prefetched into L2 ahead of the loads
 constexpr int H_SPLIT_W = 8;                     // splitter warps 4..11
@@ -61,11 +61,14 @@ __device__ __forceinline__ uint32_t a16_col(int ks, int lo) {
   return (uint32_t)(H_TP + (ks < 2 ? 0 : TP_RMAX) + 16 * lo + 8 * (ks & 1));
 }
 
+// Four stages in both forms; in the residual form MMA2's U_k rows go round the same ring (one
+// item per 128-row block after a tile's input chunks) instead of staying resident.
 template <bool RESID> struct HCfg {
-  static constexpr int S = RESID ? 2 : 4;
-  static constexpr size_t EXTRA = (RESID ? (size_t)2 * H_U2 : 0) + H_PST;
+  static constexpr int S = 4;
+  static constexpr size_t EXTRA = H_PST;
   static constexpr size_t SMEM = (size_t)S * H_STAGE + EXTRA + 1024 + 1024;
 };
+static_assert(H_XB / 2 >= 128 * 128, "a stage holds a 128-row block of U_k's FP16 hi and lo rows");
 static_assert(HCfg<true>::SMEM <= 232448, "shared memory of the residual pass");
 static_assert(HCfg<false>::SMEM <= 232448, "shared memory of the projection pass");
 
@@ -162,9 +165,7 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(hsm_raw) + 1023) & ~uintptr_t(1023));
   constexpr int S = HCfg<RESID>::S;
-  unsigned char* U2hi = base + (size_t)S * H_STAGE;
-  unsigned char* U2lo = U2hi + H_U2;
-  float* Pst = reinterpret_cast<float*>(base + (size_t)S * H_STAGE + (RESID ? (size_t)2 * H_U2 : 0));
+  float* Pst = reinterpret_cast<float*>(base + (size_t)S * H_STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)S * H_STAGE + HCfg<RESID>::EXTRA);
   uint64_t* full = bars;                 // [S] chunk landed
   uint64_t* conv = bars + S;             // [S] chunk's FP16 parts in shared memory
@@ -174,8 +175,7 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
   uint64_t* efull = pready + 1;          // [3] E block b complete
   uint64_t* xfree = efull + 3;           // [3] E block b read out
   uint64_t* xst = xfree + 3;             // the tile's input stored in tensor memory
-  uint64_t* bload = xst + 1;             // resident U rows landed
-  uint64_t* done = bload + 1;            // every MMA complete
+  uint64_t* done = xst + 1;              // every MMA complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* red = reinterpret_cast<double*>(tmem_slot + 4);        // [16] per-warp sums
@@ -195,7 +195,6 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
       mbar_init(&xfree[b], 128);
     }
     mbar_init(xst, 32 * H_SPLIT_W);
-    mbar_init(bload, 1);
     mbar_init(done, 1);
     *abort = 0;
     fence_barrier_init();
@@ -228,11 +227,6 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
       if (RESID) {
         tma_prefetch(&mU2hi);
         tma_prefetch(&mU2lo);
-        mbar_arrive_expect_tx(bload, (uint32_t)u2rows * 128u * 2u);
-        for (int r0 = 0; r0 < u2rows; r0 += 64) {
-          tma_load_2d(&mU2hi, bload, U2hi + (size_t)r0 * 128, 0, r0);
-          tma_load_2d(&mU2lo, bload, U2lo + (size_t)r0 * 128, 0, r0);
-        }
       }
       const long long nq = myt * Kc;
       auto prefetch_chunk = [&](long long qq) {
@@ -243,12 +237,12 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
         if (x0 + 32 < n1) tma_prefetch_l2_2d(mX, x0 + 32, (int)(tt * H_M));
       };
       for (long long qq = 0; qq < H_PF; ++qq) prefetch_chunk(qq);
-      long long q = 0;
+      long long q = 0, qx = 0;   // ring items; input chunks among them
       bool ok = true;
       for (long long t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
-        for (int c = 0; c < Kc; ++c, ++q) {
+        for (int c = 0; c < Kc; ++c, ++q, ++qx) {
           const int s = (int)(q % S);
-          prefetch_chunk(q + H_PF);
+          prefetch_chunk(qx + H_PF);
           if (!h_wait(&empty[s], (uint32_t)(((q / S) & 1) ^ 1), abort)) { ok = false; break; }
           unsigned char* st = base + (size_t)s * H_STAGE;
           mbar_arrive_expect_tx(&full[s], (uint32_t)(H_XB + Rp * 128 * 2));
@@ -260,10 +254,23 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
             tma_load_2d(&mU1lo, &full[s], st + H_XB + H_UB + n0 * 128, c * H_KC, n0);
           }
         }
+        if (!RESID || !ok) continue;
+        // MMA2's U_k rows, one 128-row block per item (FP16 hi, then lo 16 KB further); rows past
+        // n_k arrive as zeros
+        for (int b = 0; b < nblk; ++b, ++q) {
+          const int s = (int)(q % S);
+          if (!h_wait(&empty[s], (uint32_t)(((q / S) & 1) ^ 1), abort)) { ok = false; break; }
+          unsigned char* st = base + (size_t)s * H_STAGE;
+          const int r1 = min(128 * b + 128, u2rows);
+          mbar_arrive_expect_tx(&full[s], (uint32_t)(r1 - 128 * b) * 128u * 2u);
+          for (int r0 = 128 * b; r0 < r1; r0 += 64) {
+            tma_load_2d(&mU2hi, &full[s], st + (size_t)(r0 - 128 * b) * 128, 0, r0);
+            tma_load_2d(&mU2lo, &full[s], st + H_XB / 2 + (size_t)(r0 - 128 * b) * 128, 0, r0);
+          }
+        }
       }
       // every load issued has landed before the CTA's shared memory goes away
       for (long long j = (q > S ? q - S : 0); j < q; ++j) h_drain(&full[j % S], (uint32_t)((j / S) & 1));
-      if (RESID) h_drain(bload, 0);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -271,8 +278,9 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
     if (lane == 0) {
       const uint32_t id1 = idesc_f16(H_M, Rp);
       const uint32_t tP = tmem + H_TP, tC = tmem + H_TP + TP_RMAX;
-      bool ok = RESID ? h_wait(bload, 0, abort) : true;
+      bool ok = true;
       long long q = 0;
+      uint32_t cpar = 0u;   // bit s: parity of stage s's next input-chunk conversion
       int it = 0;
       for (long long t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++it) {
         // projection form: the P accumulators are free once the epilogue has read the previous
@@ -281,7 +289,8 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
         tc_fence_after();
         for (int c = 0; c < Kc; ++c, ++q) {
           const int s = (int)(q % S);
-          if (!h_wait(&conv[s], (uint32_t)((q / S) & 1), abort)) { ok = false; break; }
+          if (!h_wait(&conv[s], (cpar >> s) & 1u, abort)) { ok = false; break; }
+          cpar ^= 1u << s;
           tc_fence_after();
           unsigned char* st = base + (size_t)s * H_STAGE;
           const uint64_t ahi = desc_sw128(st), alo = desc_sw128(st + H_XB / 2);
@@ -304,11 +313,16 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
           if (!h_wait(pready, (uint32_t)(it & 1), abort)) { ok = false; break; }
           if (!h_wait(xst, (uint32_t)(it & 1), abort)) { ok = false; break; }
           tc_fence_after();
-          for (int b = 0; b < nblk; ++b) {
+          for (int b = 0; b < nblk; ++b, ++q) {
+            // block b of U_k's rows landed in its ring stage
+            const int s = (int)(q % S);
+            if (!h_wait(&full[s], (uint32_t)((q / S) & 1), abort)) { ok = false; break; }
+            tc_fence_after();
+            unsigned char* st = base + (size_t)s * H_STAGE;
             const int c0 = 128 * b;
             const int nc = min(128, n1p - c0);
             const uint32_t idb = idesc_f16(H_M, nc);
-            const uint64_t uhi = desc_sw128(U2hi + (size_t)c0 * 128), ulo = desc_sw128(U2lo + (size_t)c0 * 128);
+            const uint64_t uhi = desc_sw128(st), ulo = desc_sw128(st + H_XB / 2);
             for (int ks = 0; ks < Rp / 16; ++ks) {
               const uint64_t o = (uint64_t)(ks * 32) >> 4;
               mma_f16_ts(tmem + c0, tmem + a16_col(ks, 0), uhi + o, idb, 1u);
@@ -316,7 +330,9 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
               mma_f16_ts(tmem + c0, tmem + a16_col(ks, 1), uhi + o, idb, 1u);
             }
             tc_commit(&efull[b]);
+            tc_commit(&empty[s]);
           }
+          if (!ok) break;
         }
       }
       tc_commit(done);
@@ -389,6 +405,7 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
         }
       }
       yacc += (double)yt;
+      if (RESID) q += nblk;   // the tile's U_k-row items, which the MMA issuer takes
     }
     const double sy = warp_sum(yacc);
     float m = xm;

@@ -1,8 +1,10 @@
 """Model check of the barrier protocol of the FP16 tensor-core pass (k_tc_pass16, residual form):
 TMA producer, splitters (FP16 parts to shared memory, then the FP32 tile to tensor memory),
-MMA issuer, epilogue (P, then E block by block, then the staged P out), over a ring of input
-stages, one tile of the input in tensor memory released block by block, and one pair of P
-accumulators over which the epilogue writes MMA2's A operand.
+MMA issuer, epilogue (P, then E block by block, then the staged P out), over a ring of stages
+that carries a tile's input chunks and then (residual form) the blocks of U_k's rows that MMA2
+reads, one tile of the input in tensor memory released block by block, and one pair of P
+accumulators over which the epilogue writes MMA2's A operand. The splitters' conversion barrier
+of a stage completes for input chunks only, so the issuer tracks its parity per stage.
 
 Each role is a coroutine issuing the waits and arrivals the kernel issues, in the same order;
 tensor-core work runs in issue order on one pipe; durations are random. Two kinds of check:
@@ -36,6 +38,7 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
         seq[0] += 1
         heapq.heappush(events, (clock[0] + delay, seq[0], fn))
 
+    per_tile = nchunks + (nblk if resid else 0)    # ring items per tile
     full = [_Bar("full%d" % s) for s in range(stages)]
     conv = [_Bar("conv%d" % s) for s in range(stages)]
     empty = [_Bar("empty%d" % s) for s in range(stages)]
@@ -44,7 +47,7 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
     xfree = [_Bar("xfree%d" % b) for b in range(nblk)]
     pipe_free = [0.0]
     # data state
-    stage_chunk = [None] * stages        # chunk index q whose data the stage holds
+    stage_chunk = [None] * stages        # ring item q whose data the stage holds
     stage_used = [True] * stages         # its MMAs have run
     blk_stored = [[-1] * 2 for _ in range(nblk)]   # tile whose chunk (2 b + j) is in TMEM
     blk_read = [-1] * nblk              # last tile whose E block the epilogue read
@@ -67,7 +70,7 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
     def producer():
         q = 0
         for _ in range(ntiles):
-            for _ in range(nchunks):
+            for _ in range(per_tile):
                 s = q % stages
                 if q >= stages:
                     yield wait(empty[s], q // stages - 1)
@@ -100,15 +103,21 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
                     if c == nchunks - 1:
                         xst.done += 1
                 q += 1
+            q += per_tile - nchunks             # the U_k-row items go to the issuer
 
     def issuer():
         q = 0
+        xuse = [0] * stages                 # input chunks converted in each stage so far
         for it in range(ntiles):
             if not resid and it > 0 and bug != "no_pacc_wait":
                 yield wait(pready, it - 1)
             for c in range(nchunks):
                 s = q % stages
-                yield wait(conv[s], q // stages)
+                if bug == "conv_by_item":
+                    yield wait(conv[s], q // stages)
+                else:
+                    yield wait(conv[s], xuse[s])
+                xuse[s] += 1
 
                 def start(s=s, q=q, it=it, c=c):
                     if stage_chunk[s] != q:
@@ -131,17 +140,26 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
                 if bug != "no_xst_wait":
                     yield wait(xst, it)
                 for b in range(nblk):
-                    def start2(b=b, it=it):
+                    s = q % stages
+                    if bug != "no_u_wait":
+                        yield wait(full[s], q // stages)
+
+                    def start2(b=b, it=it, s=s, q=q):
                         if blk_stored[b][0] != it or (2 * b + 1 < nchunks and blk_stored[b][1] != it):
                             errors.append("MMA2 of tile %d read TMEM block %d before it was stored" % (it, b))
                         if p16_tile[0] != it:
                             errors.append("MMA2 of tile %d read the A operand of tile %s" % (it, p16_tile[0]))
+                        if stage_chunk[s] != q:
+                            errors.append("MMA2 read stage %d without U rows item %d" % (s, q))
 
-                    def fin2(b=b, it=it):
+                    def fin2(b=b, it=it, s=s):
                         efull[b].done += 1
+                        stage_used[s] = True
+                        empty[s].done += 1
                         if b == nblk - 1:
                             mma2_done_tile[0] = it
                     tensor(rng.uniform(0.1, 0.5), start2, fin2)
+                    q += 1
 
     def epilogue():
         for it in range(ntiles):
@@ -204,7 +222,7 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
     return errors, len(finished) == len(roles)
 
 
-@pytest.mark.parametrize("resid,stages", [(True, 2), (False, 4)])
+@pytest.mark.parametrize("resid,stages", [(True, 4), (True, 2), (True, 3), (False, 4)])
 def test_fp16_pass_protocol_has_no_deadlock_aliasing_or_hazard(resid, stages):
     rng = random.Random(11)
     for _ in range(500):
@@ -218,12 +236,13 @@ def test_fp16_pass_protocol_has_no_deadlock_aliasing_or_hazard(resid, stages):
 # residual form that MMA1 follows, on the same in-order pipe, the previous tile's MMA2, which
 # waited for the read-out)
 @pytest.mark.parametrize("bug,resid", [("no_xfree_wait", True), ("no_pacc_wait", False),
-                                       ("no_xst_wait", True), ("no_efull_wait", True)])
+                                       ("no_xst_wait", True), ("no_efull_wait", True),
+                                       ("no_u_wait", True), ("conv_by_item", True)])
 def test_the_check_catches_a_missing_wait(bug, resid):
     rng = random.Random(5)
     caught = 0
     for _ in range(300):
-        errors, done = _simulate(rng.randint(2, 12), rng.randint(1, 6), 2 if resid else 4, rng,
+        errors, done = _simulate(rng.randint(2, 12), rng.randint(1, 6), 4, rng,
                                  resid=resid, bug=bug)
         caught += bool(errors) or not done
     assert caught > 0
