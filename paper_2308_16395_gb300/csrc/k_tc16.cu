@@ -17,8 +17,9 @@
 //         of 2^5 U_k (128 rows) come round the input ring after the tile's chunks, so that the
 //         ring has four stages (more input in flight) instead of two beside resident rows.
 //   epi-2 ||E||^2 per CTA (FP32 over a fiber's block, then FP64), E^T for the residual Gram when
-//         the mode grew; then the staged P to global memory, column-major (F x r_k, the next
-//         mode's input).
+//         the mode grew.
+//   out   two otherwise idle warps write the staged P to global memory, column-major (F x r_k,
+//         the next mode's input), while the epilogue goes on to E.
 // Block b of the tensor-memory tile is released to the next tile's chunks as soon as epi-2 has
 // read it; the splitters hand each chunk's FP16 parts to MMA1 before they wait for that release,
 // so the next tile's MMA1 follows MMA2 on the tensor pipe without waiting for the epilogue. The
@@ -176,7 +177,9 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
   uint64_t* xfree = efull + 3;           // [3] E block b read out
   uint64_t* xst = xfree + 3;             // the tile's input stored in tensor memory
   uint64_t* done = xst + 1;              // every MMA complete
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* pstaged = done + 1;          // the tile's P in the staging tile
+  uint64_t* pfree = pstaged + 1;         // the staging tile written out
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pfree + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* red = reinterpret_cast<double*>(tmem_slot + 4);        // [16] per-warp sums
   unsigned* redm = reinterpret_cast<unsigned*>(red + 16);        // [16] per-warp max |x|
@@ -196,6 +199,8 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
     }
     mbar_init(xst, 32 * H_SPLIT_W);
     mbar_init(done, 1);
+    mbar_init(pstaged, 128);
+    mbar_init(pfree, 64);
     *abort = 0;
     fence_barrier_init();
   }
@@ -339,6 +344,26 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
       h_drain(done, 0);
     }
     __syncwarp();
+  } else if (warp == 2 || warp == 3) {
+    // ---------------- P writers: the staged P out (passes that write P) ----------------
+    if (!WRITE_ET) {
+      int it = 0;
+      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const bool okw = h_wait(pstaged, (uint32_t)(it & 1), abort);
+        if (bar_any(3, 64, !okw)) break;
+        // column-major (F x r): a warp writes 32 consecutive fibers of a column at a time
+        const long long f0 = t * H_M;
+        for (int c = warp - 2; c < r; c += 2) {
+          const float* src = Pst + c * H_M;
+          float* dst = P + F * c + f0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (f0 + 32 * j + lane < F) dst[32 * j + lane] = src[32 * j + lane];
+        }
+        // the staging tile is free again for the next tile's epi-1
+        mbar_arrive(pfree);
+      }
+    }
   } else if (warp >= 4 && warp < 4 + H_SPLIT_W) {
     // ---------------- splitters ----------------
     const int q4 = warp & 3, h = (warp - 4) >> 2;
@@ -416,7 +441,7 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
       redm[warp] = __float_as_uint(m);
     }
   } else if (warp >= H_EPI_W0) {
-    // ---------------- epilogue: P (epi-1), E (epi-2), then the staged P out ----------------
+    // ---------------- epilogue: P (epi-1) into the staging tile, then E (epi-2) ----------------
     const int q4 = warp & 3;
     const int row = q4 * 32 + lane;
     const uint32_t lq = (uint32_t)(q4 * 32) << 16;
@@ -424,16 +449,17 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
     constexpr bool OUT = !WRITE_ET;   // this pass writes P
     double eacc = 0.0;
     int it = 0;
-    // every give-up below is decided for the four warps together (named barrier 2 also orders
-    // the staging tile between them, so none of them may leave the loop alone)
+    // every give-up below is decided for the four warps together (none of them may leave the
+    // loop alone)
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       bool okw = h_wait(d1full, (uint32_t)(it & 1), abort);
+      // the P writers have written the previous tile's P out of the staging tile
+      if (OUT && it > 0 && okw) okw = h_wait(pfree, (uint32_t)((it - 1) & 1), abort);
       if (bar_any(2, 128, !okw)) break;
       tc_fence_after();
       const long long f = t * H_M + row;
       const bool live = f < F;
-      // P = sum of the two accumulators, 32 columns at a time; the staging tile was emptied by
-      // these threads at the end of the previous tile
+      // P = sum of the two accumulators, 32 columns at a time
       for (int c0 = 0; c0 < Rp; c0 += 32) {
         float v[32];
         {
@@ -460,6 +486,7 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
       if (RESID) tmem_st_wait();
       tc_fence_before();
       mbar_arrive(pready);
+      if (OUT) mbar_arrive(pstaged);
       if (RESID) {
         for (int b = 0; okw && b < nblk; ++b) {
           okw = h_wait(&efull[b], (uint32_t)(it & 1), abort);
@@ -496,20 +523,6 @@ __global__ void __launch_bounds__(H_NT, 1) k_tc_pass16(Ctl* __restrict__ ctl, in
           if (live) eacc += (double)eb;
         }
         if (!okw) break;
-      }
-      if (OUT) {
-        // staged P out, column-major (F x r): a warp writes 32 consecutive fibers of a column
-        asm volatile("bar.sync 2, 128;" ::: "memory");
-        const long long f0 = t * H_M;
-        for (int c = q4; c < r; c += 4) {
-          const float* src = Pst + c * H_M;
-          float* dst = P + F * c + f0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (f0 + 32 * j + lane < F) dst[32 * j + lane] = src[32 * j + lane];
-        }
-        // the staging tile is free again for the next tile's epi-1
-        asm volatile("bar.sync 2, 128;" ::: "memory");
       }
     }
     const double se = warp_sum(eacc);

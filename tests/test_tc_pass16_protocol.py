@@ -1,6 +1,7 @@
 """Model check of the barrier protocol of the FP16 tensor-core pass (k_tc_pass16, residual form):
 TMA producer, splitters (FP16 parts to shared memory, then the FP32 tile to tensor memory),
-MMA issuer, epilogue (P, then E block by block, then the staged P out), over a ring of stages
+MMA issuer, epilogue (P into the staging tile, then E block by block), P writers (the staged P
+out, handed over and back through two barriers), over a ring of stages
 that carries a tile's input chunks and then (residual form) the blocks of U_k's rows that MMA2
 reads, one tile of the input in tensor memory released block by block, and one pair of P
 accumulators over which the epilogue writes MMA2's A operand. The splitters' conversion barrier
@@ -44,6 +45,8 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
     empty = [_Bar("empty%d" % s) for s in range(stages)]
     d1full, pready, xst = _Bar("d1full"), _Bar("pready"), _Bar("xst")
     efull = [_Bar("efull%d" % b) for b in range(nblk)]
+    pstaged, pfree = _Bar("pstaged"), _Bar("pfree")
+    pst_tile, pst_out = [-1], [-1]      # tile in the staging tile; last tile written out
     xfree = [_Bar("xfree%d" % b) for b in range(nblk)]
     pipe_free = [0.0]
     # data state
@@ -164,15 +167,21 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
     def epilogue():
         for it in range(ntiles):
             yield wait(d1full, it)
+            if it > 0 and bug != "no_pfree_wait":
+                yield wait(pfree, it - 1)
             yield ("delay", rng.uniform(0.2, 0.8))
             if pacc_tile[0] != it:
                 errors.append("epilogue read P of tile %s for tile %d" % (pacc_tile[0], it))
+            if pst_out[0] < it - 1:
+                errors.append("P of tile %d staged before tile %d was written out" % (it, it - 1))
+            pst_tile[0] = it
             pacc_read[0] = it
             if resid:
                 if mma2_done_tile[0] < it - 1:
                     errors.append("A operand of tile %d written while MMA2 of tile %d reads it" % (it, it - 1))
                 p16_tile[0] = it
             pready.done += 1
+            pstaged.done += 1
             if resid:
                 for b in range(nblk):
                     if bug != "no_efull_wait":
@@ -183,9 +192,19 @@ def _simulate(ntiles, nchunks, stages, rng, resid=True, bug=None):
                         errors.append("E block %d of tile %d read before MMA2 wrote it" % (b, it))
                     blk_read[b] = it
                     xfree[b].done += 1
-            yield ("delay", rng.uniform(0.3, 2.0))    # the staged P out
 
-    roles = [producer(), splitters(), issuer(), epilogue()]
+    def writers():
+        for it in range(ntiles):
+            if bug != "no_pstaged_wait":
+                yield wait(pstaged, it)
+            # the staged P out, now and then slowly
+            yield ("delay", rng.uniform(3.0, 8.0) if rng.random() < 0.1 else rng.uniform(0.3, 2.0))
+            if pst_tile[0] != it:
+                errors.append("tile %d's P written out from a staging tile holding tile %s" % (it, pst_tile[0]))
+            pst_out[0] = it
+            pfree.done += 1
+
+    roles = [producer(), splitters(), issuer(), epilogue(), writers()]
     pending, finished = {}, set()
 
     def run(i):
@@ -237,7 +256,9 @@ def test_fp16_pass_protocol_has_no_deadlock_aliasing_or_hazard(resid, stages):
 # waited for the read-out)
 @pytest.mark.parametrize("bug,resid", [("no_xfree_wait", True), ("no_pacc_wait", False),
                                        ("no_xst_wait", True), ("no_efull_wait", True),
-                                       ("no_u_wait", True), ("conv_by_item", True)])
+                                       ("no_u_wait", True), ("conv_by_item", True),
+                                       ("no_pfree_wait", True), ("no_pstaged_wait", True),
+                                       ("no_pfree_wait", False), ("no_pstaged_wait", False)])
 def test_the_check_catches_a_missing_wait(bug, resid):
     rng = random.Random(5)
     caught = 0
