@@ -610,6 +610,38 @@ def run_adjoint(args):
                 "d2h_bytes_per_step": 4},
         "clocks": ck,
     }
+    peak, src = _peaks()
+    gbs = alg_bytes / (ms_graph / 1e3) / 1e9
+    line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                        "frac": gbs / peak, "traffic": None, "peak_source": src,
+                        "kernel": "one gradient evaluation (the k_ttm_mode / k_ttm_gram chain)",
+                        "algorithmic_bytes_per_eval": alg_bytes,
+                        "note": "the 8 MB working set stays in L2, so the HBM copy bandwidth is a "
+                                "nominal denominator; ~20 dependent launches set the time"}
+    if not args.no_cpu:
+        import numpy as np
+
+        import oracle.tucker_adjoint as OA
+
+        Yn = Y.detach().double().cpu().numpy()
+        Tn = T.detach().double().cpu().numpy()
+        Un = [U.detach().double().cpu().numpy() for U in Us]
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            gY, gU = OA.composite_grad(Yn, Un, Tn)
+        dt = (time.perf_counter() - t0) / reps
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "slices/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"FP64 oracle gradient (oracle/tucker_adjoint.py), {reps} "
+                                          "evaluations on the same Y, T, U_n"}
+        # parity of the graph's last evaluation (same inputs) against the FP64 oracle
+        rY = float(np.linalg.norm(Y.grad.double().cpu().numpy() - gY) / np.linalg.norm(gY))
+        rU = max(float(np.linalg.norm(U.grad.double().cpu().numpy() - g) / np.linalg.norm(g))
+                 for U, g in zip(Us, gU))
+        line["parity"] = {"grad_Y_rel": rY, "grad_U_rel_max": rU,
+                          "loss_rel": abs(float(Ls.item()) - OA.composite_loss(Yn, Un, Tn))
+                          / OA.composite_loss(Yn, Un, Tn)}
     print(json.dumps(line), flush=True)
 
 
@@ -723,9 +755,77 @@ def run_batched(args):
                        min(r[3] for r in ranks), max(r[3] for r in ranks)],
         "clocks": ck,
     }
+    peak, src = _peaks()
+    gbs = slice_bytes * K / (ms / 1e3) / 1e9
+    line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                        "frac": gbs / peak, "traffic": None, "peak_source": src,
+                        "kernel": "one batched time step (all states' update chains in one graph)",
+                        "note": "slice bytes ingested per step / step time; the step is a chain of "
+                                "short dependent launches per stream (latency-bound), so this is "
+                                "far from the bandwidth bound"}
     batch.close()
     for st in states:
         st.close()
+    if not args.no_fp64 and ws == 1:
+        # the plain FP64 GPU form on the same 64 streams (fresh noise draws, same structure and
+        # tolerances), one graph launch per time step, launch shapes tuned the same way
+        K64 = min(K, 10)
+        T64 = N_INIT + W_TUNE + W + K64
+        st64 = []
+        for gi, (s, tau, _, _, _) in enumerate(gens):
+            X0 = torch.stack([make_slice(gi, t) for t in range(N_INIT)]).contiguous()
+            st64.append(pkg.TuckerStream(X0, tau, precision="fp64", steps_cap=T64 + 4,
+                                         rank_cap=[0, 0, 0, (T64 + 4 + 7) // 8 * 8]))
+            del X0
+        tstep[0] = N_INIT
+        best64, tune64 = tune_batch(st64, feed)
+        b64 = pkg.TuckerBatch(st64)
+        for t in range(N_INIT + W_TUNE, N_INIT + W_TUNE + W):
+            for gi, slot in enumerate(b64.slots):
+                make_slice(gi, t, slot)
+            b64.update()
+        torch.cuda.synchronize()
+        ms64 = 0.0
+        for t in range(N_INIT + W_TUNE + W, T64):
+            for gi, slot in enumerate(b64.slots):
+                make_slice(gi, t, slot)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b64.update()
+            e1.record(stream)
+            e1.synchronize()
+            ms64 += e0.elapsed_time(e1)
+        line["fp64_form"] = {"value": len(all_specs) * K64 / (ms64 / 1e3), "unit": "slices/s",
+                             "ms_per_step": ms64 / K64, "steps": K64,
+                             "share_multiplier": best64,
+                             "tuning_ms_per_step": {str(c): round(v, 3) for c, v in tune64.items()},
+                             "note": "plain FP64 GPU form, same streams and tolerances, time steps "
+                                     f"{N_INIT + W_TUNE + W}..{T64 - 1}, launch shapes tuned as for "
+                                     "the mixed form"}
+        b64.close()
+        for st in st64:
+            st.close()
+    if not args.no_cpu and rank == 0:
+        # the FP64 oracle on the host over a bounded sample: the first three streams, initial
+        # ST-HOSVD untimed, then five updates each
+        import numpy as np
+
+        import oracle as O
+
+        n_up, t_cpu, n_sl = 5, 0.0, 0
+        for gi in range(3):
+            s, tau = gens[gi][0], gens[gi][1]
+            xs = [make_slice(gi, t).permute(2, 1, 0).double().cpu().numpy() for t in range(N_INIT + n_up)]
+            so = O.init_stream(np.asfortranarray(np.stack(xs[:N_INIT], axis=-1)), tau)
+            t0 = time.perf_counter()
+            for t in range(N_INIT, N_INIT + n_up):
+                O.stream_update(so, np.asfortranarray(xs[t]))
+            t_cpu += time.perf_counter() - t0
+            n_sl += n_up
+        line["cpu_baseline"] = {"value": n_sl / t_cpu, "unit": "slices/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": "FP64 oracle, streams 0-2 of the 64 (their own sizes), "
+                                          "5 updates each after an untimed initial ST-HOSVD"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
