@@ -71,8 +71,9 @@ typedef struct {
   int32_t ndim;                         /* d, 2..8 (spatial modes + the streaming mode) */
   int32_t dtype;                        /* TUCKER_F32 or TUCKER_F64: element type of slices */
   int32_t precision;                    /* TUCKER_PREC_FP64 or TUCKER_PREC_MIXED */
-  int32_t block_cap;                    /* most slices one tucker_stream_update_block call takes
-                                           (0 = 1); the slice buffers scale with it */
+  int32_t block_cap;                    /* most slices one tucker_stream_update_block call takes,
+                                           0..64 (0 = 1); the D* work buffers are allocated at
+                                           creation for this many slices */
   int64_t n[TUCKER_MAX_MODES];          /* n_1..n_{d-1}; entries >= d-1 ignored */
   int64_t rank_cap[TUCKER_MAX_MODES];   /* capacity of r_1..r_d (0 = default: n_k for spatial
                                            modes, 256 for the streaming mode); r_d cap <= 512,
