@@ -27,7 +27,16 @@ Readings of the paper where it is silent, garbled or ambiguous:
   R7 the core update uses the explicit product U~_d(1:n_d,:)^T U_d (Alg. 5, last step);
   R8 the "<=" tests of Alg. 3 and Alg. 4 are taken literally;
   R9 index typos of Sec. 3.3 (P_{k-1}, L_{k-1} in the concatenation) read as P_k, L_k;
-  R10 all-zero initial data is rejected (Assumption 1(c) needs S > 0).
+  R10 all-zero initial data is rejected (Assumption 1(c) needs S > 0);
+  R11 re-compression (Sec. 5 observes over-estimated streamed ranks, Tables 1-2): Alg. 2 on the
+      current representation, budget eps' = (tau_total ||X|| - b) / sqrt(d), new bound
+      b + ||X^ - X^'|| (``recompress``);
+  R12 orthogonality of U_d (Sec. 3.1 names the loss of orthogonality in U' U''): restored by the
+      polar factor, C, S and V kept, the reconstruction's change added to the bound
+      (``restore_orthogonality``);
+  R13 block update (the Conclusions name several slices at once as future work): Alg. 4 on the
+      block as one tensor with eps = tau ||Y_b|| / sqrt(d), then one Alg. 3 step per slice with
+      eps / sqrt(B), so a block adds at most tau^2 ||Y_b||^2 (``block_update``).
 """
 
 from __future__ import annotations
