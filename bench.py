@@ -262,9 +262,106 @@ def gpu_snapshot(pkg, ts, slices, t_end: int, samples):
     return snap
 
 
+def _reference_line(args, rate, unit, workload, sample, extra=None, dtype="f64", hib=True):
+    line = {
+        "metric": METRIC, "value": rate, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 / rate, "higher_is_better": hib,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "impl": "reference", "config": {"workload": workload, "parallelism": "host cores (numpy)"},
+        "cpu_baseline": {"value": rate, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": rate, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    line.update(extra or {})
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_other(args):
+    """The FP64 oracle on the host cores for the sine, block, adjoint and batched workloads: a
+    bounded sample of each, on the workload, metric and unit of this build's line for it."""
+    import numpy as np
+
+    import oracle as O
+
+    K = max(1, min(args.steps, 40))
+    wl = args.workload
+    if wl == "sine":
+        from workloads import SineWave
+
+        sw = SineWave()
+        n_init, tau = 200, 1e-2
+        xs = [sw.slice(t) for t in range(n_init + K)]
+        st = O.init_stream(np.asfortranarray(np.stack(xs[:n_init], axis=-1)), tau)
+        t0 = time.perf_counter()
+        for t in range(n_init, n_init + K):
+            O.stream_update(st, xs[t])
+        rate = K / (time.perf_counter() - t0)
+        _reference_line(args, rate, "slices/s",
+                        "sine-wave stream (Sec. 5.1): 100x100 spatial, 5000 steps, rank bump at "
+                        "2500, eta=1e-3, tau=1e-2, n_init=200",
+                        f"FP64 oracle: initial ST-HOSVD of 200 slices (untimed), {K} timed updates",
+                        {"final_ranks": list(st.ranks)})
+    elif wl == "block":
+        from workloads import LowRankStream
+
+        B = args.block
+        ne, tau = 10, 1e-3
+        nb = max(1, min(K, 30))
+        lrs = LowRankStream((24, 20, 16), (4, 4, 3, 6), ne + B * nb, 1e-4, seed=1, noise_scope="tensor")
+        X = lrs.tensor(0, ne + B * nb)
+        st = O.init_stream(np.asfortranarray(X[..., :ne]), tau)
+        t0 = time.perf_counter()
+        for i in range(nb):
+            O.block_update(st, np.asfortranarray(X[..., ne + i * B:ne + (i + 1) * B]))
+        rate = nb * B / (time.perf_counter() - t0)
+        _reference_line(args, rate, "slices/s",
+                        f"block update (B = {B} slices per call); the oracle's block update on the "
+                        "exact-rank 24x20x16 stream",
+                        f"FP64 oracle block update, {nb} blocks of {B} after an untimed initial "
+                        "ST-HOSVD of 10 slices", {"final_ranks": list(st.ranks)})
+    elif wl == "adjoint":
+        import oracle.tucker_adjoint as OA
+
+        rng = np.random.default_rng(230816395 + 3)
+        n, r = (128, 128, 64), (20, 20, 12)
+        Y = rng.standard_normal(n)
+        T = rng.standard_normal(n)
+        Us = [np.linalg.qr(rng.standard_normal((nk, rk)))[0] for nk, rk in zip(n, r)]
+        reps = max(1, min(K, 3))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            OA.composite_grad(Y, Us, T)
+        rate = reps / (time.perf_counter() - t0)
+        _reference_line(args, rate, "slices/s",
+                        "adjoint: gradient of ||(Y x U^T) x U - T||^2 w.r.t. Y and U_n, "
+                        "128x128x64, ranks (20,20,12)",
+                        f"FP64 oracle gradient (oracle/tucker_adjoint.py), {reps} evaluations")
+    else:   # batched
+        from workloads import batched_streams
+
+        specs = batched_streams(nstreams=64, steps=100)
+        n_up, dt, n_sl = max(1, min(K, 5)), 0.0, 0
+        for s, tau in specs[:3]:
+            xs = [s.slice(t).astype(np.float64) for t in range(N_INIT + n_up)]
+            st = O.init_stream(np.asfortranarray(np.stack(xs[:N_INIT], axis=-1)), tau)
+            t0 = time.perf_counter()
+            for t in range(N_INIT, N_INIT + n_up):
+                O.stream_update(st, np.asfortranarray(xs[t]))
+            dt += time.perf_counter() - t0
+            n_sl += n_up
+        _reference_line(args, n_sl / dt, "slices/s",
+                        "batched: 64 independent streams, sizes U{32..160}^3, ranks 4..24, "
+                        "noise 1e-4, tau in {1e-2,1e-3,1e-4}",
+                        f"FP64 oracle, streams 0-2 of the 64 (their own sizes), {n_up} updates each "
+                        "after an untimed initial ST-HOSVD")
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
+        return
+    if args.workload in ("sine", "block", "adjoint", "batched"):
+        run_reference_other(args)
         return
     import torch
 
